@@ -1,0 +1,290 @@
+"""HERS oracle: Python wrapper around oracle/hers_oracle.c.
+
+TEST INFRASTRUCTURE ONLY.  A plain, slow, exact CPU implementation of the HERS
+encrypted search (FV scheme of App. A, encoding of Sec. 3.2, Alg 7), used to
+check the CUDA library bit for bit.  Only tests/, __graft_entry__.smoke() and
+bench.py's cpu_baseline / reference legs may import it; the CUDA library never
+does, and this package imports nothing from the library.
+
+Exchange format (the same as the library's canonical form): a ciphertext is a
+uint64 array [2 polys][2 limbs][n] of residues in [0, q1) and [0, q2).
+
+Parity status: every function below is pinned by tests/test_oracle_pins.py
+against closed forms, brute force or an independent library (see the pin
+list in that file); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hers_oracle.c")
+_HDR = os.path.join(_HERE, "cdt_table.h")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libhers_oracle.so")
+
+N = 4096
+Q1 = 18014398509309953
+Q2 = 18014398509293569
+Q = Q1 * Q2
+T = 4169729
+PURPOSE_GALLERY = 0x11  # u, e1, e2 streams at 0x11, 0x12, 0x13; obj = block * d + dim
+PURPOSE_PROBE = 0x21    # u, e1, e2 streams at 0x21, 0x22, 0x23; obj = dim
+
+_lock = threading.Lock()
+_lib = None
+
+
+class OracleStats(ctypes.Structure):
+    _fields_ = [
+        ("tensor_products", ctypes.c_uint64),
+        ("tensor_adds", ctypes.c_uint64),
+        ("scale_rounds", ctypes.c_uint64),
+        ("key_switches", ctypes.c_uint64),
+        ("rotations", ctypes.c_uint64),
+        ("ties", ctypes.c_uint64),
+        ("bound_violations", ctypes.c_uint64),
+        ("max_x_bits", ctypes.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP) into oracle/_build/. Returns the path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    stale = force or not os.path.exists(_LIB) or any(
+        os.path.getmtime(p) > os.path.getmtime(_LIB) for p in (_SRC, _HDR))
+    if stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC]
+        subprocess.run(cmd, check=True, cwd=_HERE)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            u64p = ctypes.POINTER(ctypes.c_uint64)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            i8p = ctypes.POINTER(ctypes.c_int8)
+            c_int, c_u64, c_u32 = ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32
+            sp = ctypes.POINTER(OracleStats)
+            L.orc_chacha20_block.argtypes = [u32p, c_u32, u32p, u32p]
+            L.orc_sample.argtypes = [c_u64, c_u32, c_u64, c_int, c_int, c_u64, i64p]
+            L.orc_negacyclic_z.argtypes = [c_int, i64p, i64p, u64p]
+            L.orc_psi_t.argtypes = [c_int]
+            L.orc_psi_t.restype = c_u64
+            L.orc_encode.argtypes = [c_int, i64p, u32p]
+            L.orc_decode.argtypes = [c_int, u32p, i64p]
+            L.orc_keygen.argtypes = [c_int, c_u64, i8p, u64p, u64p]
+            L.orc_encrypt.argtypes = [c_int, u64p, u32p, c_u64, c_u32, c_u64, u64p]
+            L.orc_search_block.argtypes = [c_int, c_int, u64p, u64p, u64p, u64p, u64p, sp]
+            L.orc_search_block_per_product.argtypes = [c_int, c_int, u64p, u64p, u64p, u64p,
+                                                       u64p, sp]
+            L.orc_decrypt.argtypes = [c_int, i8p, u64p, c_int, i64p, u32p, u64p]
+            L.orc_params.argtypes = [u64p]
+            _lib = L
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with status {rc}")
+
+
+# --------------------------------------------------------------------------
+# primitives exposed for pins
+# --------------------------------------------------------------------------
+
+def chacha20_block(key_words, counter, nonce_words):
+    """The 16 output words of one ChaCha20 block (RFC 8439, Sec. 2.3)."""
+    k = np.ascontiguousarray(key_words, dtype=np.uint32)
+    nn = np.ascontiguousarray(nonce_words, dtype=np.uint32)
+    out = np.zeros(16, dtype=np.uint32)
+    lib().orc_chacha20_block(_p(k, ctypes.c_uint32), counter, _p(nn, ctypes.c_uint32),
+                             _p(out, ctypes.c_uint32))
+    return out
+
+
+def sample(seed, purpose, obj, n, kind, qj=0):
+    """kind 0: ternary, 1: chi (Gaussian), 2: uniform mod qj."""
+    out = np.zeros(n, dtype=np.int64)
+    _check(lib().orc_sample(seed, purpose, obj, n, kind, qj, _p(out, ctypes.c_int64)), "sample")
+    return out
+
+
+def negacyclic_z(a, b):
+    """(a * b) mod (x^n + 1) over Z for integer lists |a_j|, |b_j| < 2^107."""
+    n = len(a)
+    aw = np.zeros(2 * n, dtype=np.int64)
+    bw = np.zeros(2 * n, dtype=np.int64)
+    mask = (1 << 64) - 1
+    for j in range(n):
+        for arr, v in ((aw, a[j]), (bw, b[j])):
+            u = v & ((1 << 128) - 1)
+            arr[2 * j] = np.uint64(u & mask).astype(np.int64)
+            arr[2 * j + 1] = np.uint64(u >> 64).astype(np.int64)
+    out = np.zeros(5 * n, dtype=np.uint64)
+    _check(lib().orc_negacyclic_z(n, _p(aw, ctypes.c_int64), _p(bw, ctypes.c_int64),
+                                  _p(out, ctypes.c_uint64)), "negacyclic_z")
+    res = []
+    for k in range(n):
+        v = 0
+        for w in range(5):
+            v |= int(out[5 * k + w]) << (64 * w)
+        if v >> 319:
+            v -= 1 << 320
+        res.append(v)
+    return res
+
+
+def psi_t(n=N):
+    return int(lib().orc_psi_t(n))
+
+
+# --------------------------------------------------------------------------
+# scheme
+# --------------------------------------------------------------------------
+
+def encode(slots, n=N):
+    s = np.ascontiguousarray(slots, dtype=np.int64)
+    assert s.shape == (n,)
+    m = np.zeros(n, dtype=np.uint32)
+    _check(lib().orc_encode(n, _p(s, ctypes.c_int64), _p(m, ctypes.c_uint32)), "encode")
+    return m
+
+
+def decode(m, n=N):
+    mm = np.ascontiguousarray(m, dtype=np.uint32)
+    out = np.zeros(n, dtype=np.int64)
+    _check(lib().orc_decode(n, _p(mm, ctypes.c_uint32), _p(out, ctypes.c_int64)), "decode")
+    return out
+
+
+def keygen(seed, n=N):
+    """Alg 1. Returns (sk int8[n], pk uint64[2,2,n], evk uint64[2,2,2,n])."""
+    sk = np.zeros(n, dtype=np.int8)
+    pk = np.zeros((2, 2, n), dtype=np.uint64)
+    evk = np.zeros((2, 2, 2, n), dtype=np.uint64)
+    _check(lib().orc_keygen(n, seed, _p(sk, ctypes.c_int8), _p(pk, ctypes.c_uint64),
+                            _p(evk, ctypes.c_uint64)), "keygen")
+    return sk, pk, evk
+
+
+def encrypt(pk, m, seed, purpose_base, obj, n=N):
+    """Alg 2 on a plaintext m (uint32[n] in [0, t))."""
+    pkc = np.ascontiguousarray(pk, dtype=np.uint64)
+    mm = np.ascontiguousarray(m, dtype=np.uint32)
+    ct = np.zeros((2, 2, n), dtype=np.uint64)
+    _check(lib().orc_encrypt(n, _p(pkc, ctypes.c_uint64), _p(mm, ctypes.c_uint32), seed,
+                             purpose_base, obj, _p(ct, ctypes.c_uint64)), "encrypt")
+    return ct
+
+
+def gallery_block_slots(feats, b, n=N):
+    """Slots of the d gallery plaintexts of block b (Eq. 3): [d][n], slot j <- p_{bn+j}[i]."""
+    m, d = feats.shape
+    lo, hi = b * n, min((b + 1) * n, m)
+    slots = np.zeros((d, n), dtype=np.int64)
+    slots[:, : hi - lo] = feats[lo:hi, :].T.astype(np.int64)
+    return slots
+
+
+def encrypt_gallery_block(pk, feats, b, seed, n=N):
+    """Ciphertexts [d][2][2][n] of gallery block b (Eq. 3 + Alg 2; obj = b*d + i)."""
+    d = feats.shape[1]
+    slots = gallery_block_slots(feats, b, n)
+    out = np.zeros((d, 2, 2, n), dtype=np.uint64)
+    for i in range(d):
+        out[i] = encrypt(pk, encode(slots[i], n), seed, PURPOSE_GALLERY, b * d + i, n)
+    return out
+
+
+def encrypt_probe(pk, qfeat, seed, n=N):
+    """Ciphertexts [d][2][2][n] of a probe (Eq. 2: dimension i in every slot; obj = i)."""
+    d = len(qfeat)
+    out = np.zeros((d, 2, 2, n), dtype=np.uint64)
+    for i in range(d):
+        m = encode(np.full(n, int(qfeat[i]), dtype=np.int64), n)
+        out[i] = encrypt(pk, m, seed, PURPOSE_PROBE, i, n)
+    return out
+
+
+def search_block(probe_cts, gal_cts, evk, n=N, want_pre=False):
+    """Score ciphertext of one block: accumulate over d, scale once, relinearise once."""
+    d = probe_cts.shape[0]
+    pc = np.ascontiguousarray(probe_cts, dtype=np.uint64)
+    gc = np.ascontiguousarray(gal_cts, dtype=np.uint64)
+    ev = np.ascontiguousarray(evk, dtype=np.uint64)
+    out = np.zeros((2, 2, n), dtype=np.uint64)
+    pre = np.zeros((3, 2, n), dtype=np.uint64)
+    st = OracleStats()
+    rc = lib().orc_search_block(n, d, _p(pc, ctypes.c_uint64), _p(gc, ctypes.c_uint64),
+                                _p(ev, ctypes.c_uint64), _p(out, ctypes.c_uint64),
+                                _p(pre, ctypes.c_uint64) if want_pre else None,
+                                ctypes.byref(st))
+    _check(rc, "search_block")
+    return (out, pre, st.as_dict()) if want_pre else (out, st.as_dict())
+
+
+def search_block_per_product(probe_cts, gal_cts, evk, init_ct=None, n=N):
+    """Paper-literal Alg 7 inner loop with Alg 5 (scale + relinearise) per product."""
+    d = probe_cts.shape[0]
+    pc = np.ascontiguousarray(probe_cts, dtype=np.uint64)
+    gc = np.ascontiguousarray(gal_cts, dtype=np.uint64)
+    ev = np.ascontiguousarray(evk, dtype=np.uint64)
+    out = np.zeros((2, 2, n), dtype=np.uint64)
+    st = OracleStats()
+    ini = None if init_ct is None else np.ascontiguousarray(init_ct, dtype=np.uint64)
+    rc = lib().orc_search_block_per_product(n, d, _p(pc, ctypes.c_uint64),
+                                            _p(gc, ctypes.c_uint64), _p(ev, ctypes.c_uint64),
+                                            None if ini is None else _p(ini, ctypes.c_uint64),
+                                            _p(out, ctypes.c_uint64), ctypes.byref(st))
+    _check(rc, "search_block_per_product")
+    return out, st.as_dict()
+
+
+def decrypt(sk, ct, n=N):
+    """Alg 3 + decode. ct: [2 or 3][2][n]. Returns (slots int64[n], pt uint32[n], max |noise|)."""
+    c = np.ascontiguousarray(ct, dtype=np.uint64)
+    ncomp = c.shape[0]
+    s = np.ascontiguousarray(sk, dtype=np.int8)
+    slots = np.zeros(n, dtype=np.int64)
+    pt = np.zeros(n, dtype=np.uint32)
+    noise = np.zeros(2, dtype=np.uint64)
+    _check(lib().orc_decrypt(n, _p(s, ctypes.c_int8), _p(c, ctypes.c_uint64), ncomp,
+                             _p(slots, ctypes.c_int64), _p(pt, ctypes.c_uint32),
+                             _p(noise, ctypes.c_uint64)), "decrypt")
+    return slots, pt, int(noise[0]) | (int(noise[1]) << 64)
+
+
+def res_to_int(ct_poly_res):
+    """[2 limbs][n] residues -> list of Python ints in [0, q) (CRT, for tests)."""
+    r1, r2 = ct_poly_res
+    inv = pow(Q1, -1, Q2)
+    return [int(a) + Q1 * (((int(b) - int(a)) * inv) % Q2) for a, b in zip(r1, r2)]
+
+
+def search_gallery(probe_cts, gal_blocks_cts, evk, n=N):
+    """Score ciphertexts for a list of gallery blocks (Alg 7's outer loop)."""
+    outs, tot = [], None
+    for g in gal_blocks_cts:
+        o, st = search_block(probe_cts, g, evk, n)
+        outs.append(o)
+        tot = st if tot is None else {k: tot[k] + st[k] for k in st}
+    return np.stack(outs), tot
