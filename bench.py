@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark: HERS encrypted search throughput on GB300.
+
+Workload (one GPU): 1,048,576 encrypted gallery entries (256 slot-packed
+blocks of N = 4096), d = 64, int8 features (i.i.d. N(0,1), L2-normalised,
+scale 127), one probe with a planted mate.  A step is one pass of the search
+path over the whole gallery for one probe: preparing the probe's d received
+ciphertexts (extension + NTT) and the search itself (tensor accumulate over
+d, inverse NTTs, exact scale-and-round, one key switch per block).  Entries
+scored per second = 1,048,576 per step / step time.
+
+  value  device time (CUDA events on the launching stream), inputs resident;
+  e2e    the same through hers_search_host: the probe's ciphertexts copied
+         from pinned host memory and the score ciphertexts copied back, every
+         step, inside the timed region.
+
+The gallery (5 GiB resident) is larger than L2 (129 MB), so no flush is needed
+between steps.  Multi-GPU: each rank searches its own 256-block gallery (the
+blocks are independent, Sec. 3.2 footnote), no data-path collective: weak
+scaling.  `--impl reference` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 4096
+FEAT_SEED, MATE_SEED, NOISE_SEED, KEY_SEED, GAL_SEED, PRB_SEED = 1001, 1002, 1003, 1004, 1005, 1006
+METRIC = "encrypted gallery entries scored/sec at N=4096, d=64 (bit-exact)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--m", type=int, default=1 << 20, help="gallery entries per GPU")
+    ap.add_argument("--d", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Dist:
+    """Barrier and max-over-ranks only; no data-path collective."""
+
+    def __init__(self, world, backend):
+        self.world = world
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x, device):
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 11:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        busy = [float(r[2]) for r in rows if r[5].isdigit() and int(r[5]) > 50]
+        smax = max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[7 + i] == "Active"})
+        use = busy or sm
+        return {"sm_mhz": statistics.median(use) if use else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows), "samples_busy": len(busy)}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+
+def cpu_oracle_rate(d, blocks, budget_s=12.0):
+    """Oracle search timed on a bounded sample of gallery blocks on the host cores."""
+    import numpy as np
+
+    import oracle as O
+    import workloads as W
+    _, opk, oevk = O.keygen(KEY_SEED)
+    mate = int(W.mate_indices(blocks * N, 1, MATE_SEED)[0])
+    q = W.probe_for_mate(mate, d, FEAT_SEED, NOISE_SEED)
+    oprb = O.encrypt_probe(opk, q, PRB_SEED)
+    feats = W.gallery_features(min(blocks, 16) * N, d, FEAT_SEED)
+    done, t_search = 0, 0.0
+    for b in range(min(blocks, 16)):
+        ogal = O.encrypt_gallery_block(opk, feats, b, GAL_SEED)
+        t0 = time.perf_counter()
+        O.search_block(oprb, ogal, oevk)
+        t_search += time.perf_counter() - t0
+        done += 1
+        if t_search >= budget_s:
+            break
+    del np
+    return done * N / t_search, done, t_search
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    import workloads as W
+    d = args.d
+    _, opk, oevk = O.keygen(KEY_SEED)
+    feats = W.gallery_features(N, d, FEAT_SEED)
+    mate = int(W.mate_indices(args.m, 1, MATE_SEED)[0])
+    q = W.probe_for_mate(mate, d, FEAT_SEED, NOISE_SEED)
+    oprb = O.encrypt_probe(opk, q, PRB_SEED)
+    ogal = O.encrypt_gallery_block(opk, feats, 0, GAL_SEED)
+    for _ in range(args.warmup):
+        O.search_block(oprb, ogal, oevk)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.search_block(oprb, ogal, oevk)
+    dt = time.perf_counter() - t0
+    value = args.steps * N / dt
+    sample = (f"each step: one {N}-entry gallery block (of the {args.m}-entry workload) "
+              f"searched by the oracle, d = {d}")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "entries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"plain single-probe search, m={args.m}, d={d}, N={N}",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "entries/s", "cores": omp_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_2003_12197_gb300 as H
+    import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = Dist(world, "nccl")
+    if rank == 0:
+        H.build_library()
+    dist.barrier()
+
+    m, d = args.m, args.d
+    nb = H.hers_blocks_for(m)
+    feat_seed = FEAT_SEED + 7919 * rank
+    feats_np = W.gallery_features(m, d, feat_seed)
+    mate = int(W.mate_indices(m, 1, MATE_SEED + rank)[0])
+    q_np = W.probe_for_mate(mate, d, feat_seed, NOISE_SEED)
+
+    ctx = H.Context(local)
+    keys = H.hers_keygen(ctx, KEY_SEED)
+    stream = torch.cuda.current_stream(dev)
+    gal, _ = H.hers_encrypt_gallery(ctx, keys, torch.from_numpy(feats_np).to(dev), GAL_SEED)
+    pct = H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q_np).to(dev), PRB_SEED)
+    pr = H.hers_probe_prepare(ctx, pct)
+    ws = torch.empty(H.hers_search_workspace_bytes(nb) // 8, dtype=torch.int64, device=dev)
+    sc = torch.empty((nb, 2, 2, N), dtype=torch.int64, device=dev)
+    H.hers_check(ctx)
+
+    # correctness of the benchmarked path: exact scores and the planted mate
+    H.hers_search(ctx, keys, gal, nb, d, pr, out=sc, workspace=ws)
+    scores = H.hers_decrypt_scores(ctx, keys, sc, m).cpu().numpy().astype(np.int64)
+    exact = bool(np.array_equal(scores, W.plain_inner_products(feats_np, q_np)))
+    top1 = int(np.argmax(scores)) == mate
+    if not (exact and top1):
+        raise SystemExit(f"benchmark path is not exact (exact={exact}, top1={top1})")
+
+    def step():
+        H.hers_probe_prepare(ctx, pct, out=pr)
+        H.hers_search(ctx, keys, gal, nb, d, pr, out=sc, workspace=ws)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    H.hers_trace_enable(ctx, args.steps)
+    launches0 = H.hers_kernel_launches()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    launches = H.hers_kernel_launches() - launches0
+    ms_total = dist.max(e0.elapsed_time(e1), dev)
+    ncalls, phases = H.hers_trace_read(ctx)
+    H.hers_trace_enable(ctx, 0)
+    clk = clocks.stop()
+
+    # e2e through the C ABI with host buffers
+    wsh = torch.empty(H.hers_search_host_workspace_bytes(nb, d) // 8, dtype=torch.int64, device=dev)
+    pct_host = pct.cpu().pin_memory()
+    sc_host = torch.empty((nb, 2, 2, N), dtype=torch.int64).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        H.hers_search_host(ctx, keys, gal, nb, d, pct_host, sc_host, wsh)
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        H.hers_search_host(ctx, keys, gal, nb, d, pct_host, sc_host, wsh)
+    torch.cuda.synchronize()
+    e2e_s = dist.max(time.perf_counter() - t0, dev)
+    dist.barrier()
+    e2e_ok = bool(np.array_equal(sc_host.numpy(), sc.cpu().numpy()))
+
+    entries_total = m * world * args.steps
+    value = entries_total / (ms_total / 1e3)
+    e2e_value = entries_total / e2e_s
+
+    # roofline of the dominant kernel (tensor accumulate): algorithmic bytes per launch
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    gal_bytes = nb * d * 2 * 5 * N * 8
+    probe_bytes = d * 2 * 5 * N * 8
+    acc_bytes = nb * 3 * 5 * N * 8
+    alg_bytes = gal_bytes + probe_bytes + acc_bytes
+    t_tensor = phases["tensor"] / 1e3
+    achieved = alg_bytes / t_tensor / 1e9 if t_tensor > 0 else 0.0
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic_k_tensor.json")
+    if os.path.exists(prof):
+        try:
+            tj = json.load(open(prof))
+            if tj.get("nblocks") and tj.get("d") == d:
+                traffic = tj["bytes_per_block"] * nb + tj.get("bytes_fixed", 0)
+        except (OSError, ValueError, KeyError):
+            traffic = None
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, blocks, secs = cpu_oracle_rate(d, nb)
+        cpu = {"value": rate, "unit": "entries/s", "cores": omp_threads(), "kind": "oracle",
+               "sample": f"{blocks} block(s) of {N} entries (d = {d}) of this workload searched by "
+                         f"the oracle, {secs:.1f} s of search time"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded int8 features, planted mate; keys and encryption seeded)",
+            "config": {"workload": f"plain single-probe search, m={m} entries per GPU "
+                                   f"({nb} blocks), d={d}, N={N}, q=2x54-bit, t=4169729",
+                       "global_batch": m * world, "parallelism": f"dp{world}",
+                       "l2": "inputs larger than L2 (5 GiB resident gallery per GPU), no flush"},
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "entries/s",
+                    "h2d_bytes_per_step": d * 4 * N * 8, "d2h_bytes_per_step": nb * 4 * N * 8,
+                    "bit_exact_vs_device": e2e_ok},
+            "roofline": {"kernel": "k_tensor (tensor-product accumulate over d)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
+                         "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes},
+            "phases_ms": {k: round(v, 4) for k, v in phases.items()},
+            "traced_calls": ncalls,
+            "correct": {"scores_exact": exact, "top1_planted_mate": top1},
+            "clocks": clk,
+        }
+        if cpu:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out))
+    keys.close()
+    ctx.close()
+    dist.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

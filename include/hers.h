@@ -1,0 +1,202 @@
+/*
+ * hers.h -- C ABI of the GB300 HERS encrypted-search library (libhers.so).
+ *
+ * HERS (Engelsma, Jain, Boddeti) scores an encrypted probe q against an
+ * encrypted gallery P = [p_1 .. p_m] of d-dimensional int8 features: the
+ * server computes Enc(P^T q) (Sec. 3.1, Eq. 1) without decrypting either
+ * side, and the client decrypts the m scores and takes the argmax (Alg 7).
+ *
+ * Scheme: FV (App. A, Algs 1-5) over R_q = Z_q[x]/(x^N + 1), N = 4096,
+ * q = q1 q2 (two 54-bit NTT primes, 108 bits), plaintext modulus t = 4169729
+ * (prime, t = 1 mod 2N, so plaintexts have N SIMD slots).  Gallery dimension
+ * i of entries bN .. bN+N-1 is one plaintext (Eq. 3, one "block" b); probe
+ * dimension i fills every slot (Eq. 2).  A block's score ciphertext is
+ * sum_i ct_i (x) D_i^b (Eq. 4, Alg 7), with the degree-2 tensor accumulated
+ * over i, scaled by t/q once and relinearised once (Alg 5's steps, moved
+ * after the sum).
+ *
+ * Conventions common to every call:
+ *  - Return value: HERS_OK (0) or a negative HERS_E_* status; on error the
+ *    context's message is available from hers_last_error(ctx).
+ *  - Pointers documented "device" are CUDA device pointers on the context's
+ *    device, owned by the caller, who allocates them with the byte counts the
+ *    hers_*_bytes() helpers give; pointers documented "host" are ordinary
+ *    host memory, owned by the caller.  The library never frees caller memory.
+ *  - stream: a cudaStream_t cast to void*, or NULL for the context's own
+ *    stream.  Calls that only read/write device memory are asynchronous on
+ *    that stream; calls that write host memory return after the data is there.
+ *  - Canonical ciphertext ("ct"): uint64 [2 polys][2 limbs][N], coefficient
+ *    domain, limb 0 holds residues mod q1 in [0, q1), limb 1 mod q2 in [0, q2).
+ *    This is the form ciphertexts are exchanged and compared in.
+ *  - Handles (hers_ctx, hers_keys) are not safe for concurrent mutation from
+ *    several host threads.
+ *  - Every random draw (keys, encryption randomness) is a ChaCha20 (RFC 8439)
+ *    stream keyed by the 64-bit seed argument, so identical seeds give
+ *    identical bytes.
+ */
+#ifndef HERS_H
+#define HERS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HERS_OK 0
+#define HERS_E_INVAL (-1)   /* bad argument (null pointer, size, d mismatch) */
+#define HERS_E_NOMEM (-2)   /* device allocation failed or workspace too small */
+#define HERS_E_CUDA (-3)    /* a CUDA call or kernel failed */
+#define HERS_E_TIMEOUT (-4) /* a bounded device-side wait gave up */
+#define HERS_E_PARAM (-5)   /* unsupported scheme parameters */
+#define HERS_E_SAMPLER (-7) /* a rejection sampler exhausted its attempts */
+
+#define HERS_N 4096u        /* ring degree n (Sec. 4.1) */
+#define HERS_MAX_D 512u     /* largest feature dimension d accepted */
+
+typedef struct hers_ctx hers_ctx;
+typedef struct hers_keys hers_keys;
+
+/* Scheme parameters (App. A; Sec. 4.1 fixes n, the rest is this library's
+ * reading).  Only the default set is supported; hers_create() checks. */
+typedef struct hers_params {
+    uint32_t n;       /* ring degree, 4096 */
+    uint64_t q[2];    /* ciphertext modulus primes q1, q2 */
+    uint64_t t;       /* plaintext modulus */
+    uint32_t flags;   /* reserved, 0 */
+} hers_params;
+
+/* Fills *out with the supported parameter set. */
+int hers_default_params(hers_params* out);
+
+/* Creates a context on CUDA device `device`: uploads NTT twiddle tables and
+ * creates the context stream.  *out is owned by the caller, freed by
+ * hers_destroy. */
+int hers_create(const hers_params* p, int device, hers_ctx** out);
+int hers_destroy(hers_ctx* ctx);
+
+/* Message of the last failed call on ctx (never NULL; "" when none). */
+const char* hers_last_error(const hers_ctx* ctx);
+/* Static name of a status code. */
+const char* hers_status_string(int status);
+
+/* Buffer sizes, in bytes. */
+uint64_t hers_ct_bytes(void);                                    /* one canonical ct: 2*2*N*8 */
+uint64_t hers_gallery_bytes(uint64_t nblocks, uint32_t d);       /* resident gallery */
+uint64_t hers_probe_bytes(uint32_t d);                           /* prepared probe */
+uint64_t hers_search_workspace_bytes(uint64_t nblocks);          /* hers_search scratch */
+uint64_t hers_blocks_for(uint64_t m);                            /* ceil(m / N) (Sec. 3.2 footnote) */
+
+/*
+ * Key generation (App. A, Alg 1).  Samples the ternary secret s, the public
+ * key pk = ([-(a s + e)]_q, a) and two relinearisation keys
+ * evk_j = ([-(a_j s + e_j) + g_j s^2]_q, a_j), g_j = (q/q_j) [(q/q_j)^-1]_{q_j}
+ * (an RNS gadget: the base-w decomposition of Alg 1 with one digit per prime).
+ * All key material stays in device memory inside *out (freed by
+ * hers_keys_free).  Synchronous.  HERS_E_SAMPLER if a sampler ran out of
+ * attempts (probability below 2^-400).
+ */
+int hers_keygen(hers_ctx* ctx, uint64_t seed, hers_keys** out);
+int hers_keys_free(hers_keys* keys);
+
+/* Copies the keys to host memory in canonical form (for checking and
+ * storage): sk int8[N] in {-1,0,1}; pk uint64[2][2][N]; evk uint64[2][2][2][N]
+ * ([digit j][poly][limb][N]).  Any pointer may be NULL to skip it. */
+int hers_keys_export(hers_ctx* ctx, const hers_keys* keys, int8_t* sk, uint64_t* pk,
+                     uint64_t* evk);
+
+/*
+ * Enrollment, batch form (Alg 6; Eq. 3 encoding; Alg 2 encryption).
+ * feats: device int8 [m][d] row-major (entry-major).  Block b, dimension i
+ * becomes the plaintext whose slot j holds feats[b N + j][i] (0 past m),
+ * encrypted with randomness stream obj = b d + i.
+ * gallery: device, hers_gallery_bytes(ceil(m/N), d) bytes: the resident form
+ *   the search streams (NTT domain, extended to the 5-prime basis q1 q2 p1 p2 p3).
+ * gallery_ct: device uint64 [ceil(m/N)][d][2][2][N] canonical cts, or NULL.
+ * Asynchronous on stream; sampler failures are reported by the next
+ * synchronous call on ctx (hers_check).
+ */
+int hers_encrypt_gallery(hers_ctx* ctx, const hers_keys* keys, const int8_t* feats, uint64_t m,
+                         uint32_t d, uint64_t seed, uint64_t* gallery, uint64_t* gallery_ct,
+                         void* stream);
+
+/*
+ * Probe encryption (Alg 7 client side; Eq. 2 encoding; Alg 2).
+ * q: device int8 [d].  Dimension i is the constant plaintext q[i] (every slot
+ * = q[i]), encrypted under pk with randomness stream obj = i.
+ * probe_ct: device uint64 [d][2][2][N] canonical cts (what the client sends).
+ */
+int hers_encrypt_probe(hers_ctx* ctx, const hers_keys* keys, const int8_t* q, uint32_t d,
+                       uint64_t seed, uint64_t* probe_ct, void* stream);
+
+/* Server side: turns d received canonical probe cts (device) into the form
+ * the search reads (device, hers_probe_bytes(d) bytes). */
+int hers_probe_prepare(hers_ctx* ctx, const uint64_t* probe_ct, uint32_t d, uint64_t* probe,
+                       void* stream);
+
+/*
+ * Encrypted search (Alg 7 server loop; Eq. 4; Alg 5), one probe against
+ * blocks [0, nblocks) of a resident gallery of dimension d.
+ * For every block b: X_k = sum_i tensor_k(ct_i, D_i^b) exactly (k = 0, 1, 2),
+ * c_k = [round(t X_k / q)]_q, then one relinearisation with evk.
+ * scores_ct: device uint64 [nblocks][2][2][N] canonical score cts.
+ * workspace: device scratch of at least hers_search_workspace_bytes(nblocks).
+ * Reads only the evaluation key of `keys`.  Asynchronous on stream.
+ */
+int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
+                uint32_t d, const uint64_t* probe, uint64_t* scores_ct, void* workspace,
+                uint64_t workspace_bytes, void* stream);
+
+/*
+ * End-to-end server step with host buffers: copies the probe's d canonical
+ * cts from host memory (probe_ct_host, [d][2][2][N]) to the device, prepares
+ * them, searches blocks [0, nblocks) and copies the score cts back to host
+ * memory (scores_ct_host, [nblocks][2][2][N]).  workspace: device scratch of
+ * at least hers_search_host_workspace_bytes(nblocks, d) bytes (search scratch,
+ * the probe's cts and prepared form, and the staged score cts); the call
+ * allocates nothing.  Host buffers may be pageable; pinned ones copy faster.
+ * Returns after the scores are in host memory.
+ */
+int hers_search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
+                     uint64_t nblocks, uint32_t d, const uint64_t* probe_ct_host,
+                     uint64_t* scores_ct_host, void* workspace, uint64_t workspace_bytes,
+                     void* stream);
+uint64_t hers_search_host_workspace_bytes(uint64_t nblocks, uint32_t d);
+
+/*
+ * Client-side decryption (App. A, Alg 3) and decoding of block score cts
+ * (Alg 7 client side): pt = [round(t/q [c0 + c1 s]_q)]_t, slot j of block b
+ * is entry bN + j, centred in [-(t-1)/2, (t-1)/2].
+ * scores_ct: device [nblocks][2][2][N]; scores: device int32 [m] with
+ * m <= nblocks N.  Asynchronous on stream.
+ */
+int hers_decrypt_scores(hers_ctx* ctx, const hers_keys* keys, const uint64_t* scores_ct,
+                        uint64_t nblocks, int32_t* scores, uint64_t m, void* stream);
+
+/* Synchronises ctx's stream (or `stream`) and reports deferred device-side
+ * errors (sampler exhaustion) as a status. */
+int hers_check(hers_ctx* ctx, void* stream);
+
+/*
+ * Tracing (no counterpart in the paper, which reports wall-clock times only).
+ * hers_trace_enable(ctx, n) makes the next n hers_search / hers_search_host
+ * calls on ctx record CUDA events at their phase boundaries on the stream they
+ * run on (n = 0 turns tracing off).  hers_trace_read() waits for those events
+ * and writes, into avg_ms[HERS_TRACE_PHASES], the average milliseconds per
+ * call of: the tensor-accumulate kernel, the inverse NTTs, the exact
+ * scale-and-round, the key switch (forward NTT, multiply, inverse NTT, add),
+ * and the whole search; *ncalls is the number of calls averaged.  Reading
+ * re-arms the n slots.
+ */
+#define HERS_TRACE_PHASES 5
+int hers_trace_enable(hers_ctx* ctx, uint32_t max_calls);
+int hers_trace_read(hers_ctx* ctx, uint32_t* ncalls, double* avg_ms);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t hers_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HERS_H */

@@ -1,0 +1,283 @@
+"""GB300 HERS encrypted search: Python binding of libhers.so (include/hers.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  PyTorch provides device memory (uint64 data is held in int64
+tensors, bit for bit) and streams.  There is no CPU fallback: if the library
+is missing this module raises on import of the library (`lib()`), and the
+functions raise HersError on any non-zero status.
+
+The functions keep the C names:
+  hers_keygen, hers_encrypt_gallery, hers_encrypt_probe, hers_probe_prepare,
+  hers_search, hers_search_host, hers_decrypt_scores, hers_keys_export, ...
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+N = 4096
+MAX_D = 512
+HERS_OK = 0
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhers.so")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class HersError(RuntimeError):
+    pass
+
+
+def build_library(force: bool = False) -> str:
+    """Compile libhers.so in-tree with nvcc (sm_103a)."""
+    from .build import build as _build
+    return _build(force=force)
+
+
+def lib():
+    """The loaded libhers.so.  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise HersError(f"{LIB_PATH} is missing: build it with "
+                                "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+            sigs = {
+                "hers_default_params": ([vp], i32),
+                "hers_create": ([vp, i32, vp], i32),
+                "hers_destroy": ([vp], i32),
+                "hers_last_error": ([vp], ctypes.c_char_p),
+                "hers_status_string": ([i32], ctypes.c_char_p),
+                "hers_ct_bytes": ([], u64),
+                "hers_gallery_bytes": ([u64, u32], u64),
+                "hers_probe_bytes": ([u32], u64),
+                "hers_search_workspace_bytes": ([u64], u64),
+                "hers_search_host_workspace_bytes": ([u64, u32], u64),
+                "hers_blocks_for": ([u64], u64),
+                "hers_keygen": ([vp, u64, vp], i32),
+                "hers_keys_free": ([vp], i32),
+                "hers_keys_export": ([vp, vp, vp, vp, vp], i32),
+                "hers_encrypt_gallery": ([vp, vp, vp, u64, u32, u64, vp, vp, vp], i32),
+                "hers_encrypt_probe": ([vp, vp, vp, u32, u64, vp, vp], i32),
+                "hers_probe_prepare": ([vp, vp, u32, vp, vp], i32),
+                "hers_search": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
+                "hers_search_host": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
+                "hers_decrypt_scores": ([vp, vp, vp, u64, vp, u64, vp], i32),
+                "hers_check": ([vp, vp], i32),
+                "hers_trace_enable": ([vp, u32], i32),
+                "hers_trace_read": ([vp, vp, vp], i32),
+                "hers_kernel_launches": ([], u64),
+            }
+            for name, (args, res) in sigs.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A library context on one CUDA device (hers_create / hers_destroy)."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = lib().hers_create(None, device, ctypes.byref(h))
+        if rc != HERS_OK:
+            raise HersError(f"hers_create: {lib().hers_status_string(rc).decode()}")
+        self.h = h
+
+    def check(self, rc, what):
+        if rc != HERS_OK:
+            msg = lib().hers_last_error(self.h).decode()
+            raise HersError(f"{what}: {lib().hers_status_string(rc).decode()}: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hers_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Keys:
+    def __init__(self, ctx: Context, h):
+        self.ctx, self.h = ctx, h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hers_keys_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ sizes
+
+def hers_ct_bytes():
+    return int(lib().hers_ct_bytes())
+
+
+def hers_blocks_for(m):
+    return int(lib().hers_blocks_for(m))
+
+
+def hers_gallery_bytes(nblocks, d):
+    return int(lib().hers_gallery_bytes(nblocks, d))
+
+
+def hers_probe_bytes(d):
+    return int(lib().hers_probe_bytes(d))
+
+
+def hers_search_workspace_bytes(nblocks):
+    return int(lib().hers_search_workspace_bytes(nblocks))
+
+
+def hers_search_host_workspace_bytes(nblocks, d):
+    return int(lib().hers_search_host_workspace_bytes(nblocks, d))
+
+
+def _words(nbytes, device):
+    import torch
+    return torch.empty(nbytes // 8, dtype=torch.int64, device=device)
+
+
+# ------------------------------------------------------------------ scheme
+
+def hers_keygen(ctx: Context, seed: int) -> Keys:
+    h = ctypes.c_void_p()
+    ctx.check(lib().hers_keygen(ctx.h, seed, ctypes.byref(h)), "hers_keygen")
+    return Keys(ctx, h)
+
+
+def hers_keys_export(ctx: Context, keys: Keys):
+    """(sk int8[N], pk uint64[2,2,N], evk uint64[2,2,2,N]) as numpy arrays."""
+    import numpy as np
+    sk = np.zeros(N, dtype=np.int8)
+    pk = np.zeros((2, 2, N), dtype=np.uint64)
+    evk = np.zeros((2, 2, 2, N), dtype=np.uint64)
+    ctx.check(lib().hers_keys_export(ctx.h, keys.h, sk.ctypes.data, pk.ctypes.data,
+                                     evk.ctypes.data), "hers_keys_export")
+    return sk, pk, evk
+
+
+def hers_encrypt_gallery(ctx: Context, keys: Keys, feats, seed: int, want_ct: bool = False,
+                         out=None, out_ct=None, stream=None):
+    """feats: cuda int8 [m, d].  Returns (gallery words, canonical cts [nb,d,2,2,N] or None)."""
+    import torch
+    assert feats.is_cuda and feats.dtype == torch.int8 and feats.dim() == 2
+    feats = feats.contiguous()
+    m, d = feats.shape
+    nb = hers_blocks_for(m)
+    gal = out if out is not None else _words(hers_gallery_bytes(nb, d), feats.device)
+    cts = out_ct
+    if want_ct and cts is None:
+        cts = torch.empty((nb, d, 2, 2, N), dtype=torch.int64, device=feats.device)
+    ctx.check(lib().hers_encrypt_gallery(ctx.h, keys.h, _ptr(feats), m, d, seed, _ptr(gal),
+                                         _ptr(cts), _stream(stream)), "hers_encrypt_gallery")
+    return gal, cts
+
+
+def hers_encrypt_probe(ctx: Context, keys: Keys, q, seed: int, out=None, stream=None):
+    """q: cuda int8 [d].  Returns canonical probe cts [d, 2, 2, N] (int64 view of uint64)."""
+    import torch
+    assert q.is_cuda and q.dtype == torch.int8 and q.dim() == 1
+    q = q.contiguous()
+    d = q.shape[0]
+    cts = out if out is not None else torch.empty((d, 2, 2, N), dtype=torch.int64, device=q.device)
+    ctx.check(lib().hers_encrypt_probe(ctx.h, keys.h, _ptr(q), d, seed, _ptr(cts), _stream(stream)),
+              "hers_encrypt_probe")
+    return cts
+
+
+def hers_probe_prepare(ctx: Context, probe_ct, out=None, stream=None):
+    d = probe_ct.shape[0]
+    pr = out if out is not None else _words(hers_probe_bytes(d), probe_ct.device)
+    ctx.check(lib().hers_probe_prepare(ctx.h, _ptr(probe_ct), d, _ptr(pr), _stream(stream)),
+              "hers_probe_prepare")
+    return pr
+
+
+def hers_search(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, probe, out=None,
+                workspace=None, stream=None):
+    """Score cts [nblocks, 2, 2, N] (int64 view) of one prepared probe."""
+    import torch
+    dev = gallery.device
+    sc = out if out is not None else torch.empty((nblocks, 2, 2, N), dtype=torch.int64, device=dev)
+    wsb = hers_search_workspace_bytes(nblocks)
+    ws = workspace if workspace is not None else _words(wsb, dev)
+    ctx.check(lib().hers_search(ctx.h, keys.h, _ptr(gallery), nblocks, d, _ptr(probe), _ptr(sc),
+                                _ptr(ws), ws.numel() * 8, _stream(stream)), "hers_search")
+    return sc
+
+
+def hers_search_host(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, probe_ct_host,
+                     scores_host, workspace, stream=None):
+    """probe_ct_host / scores_host: CPU tensors (ideally pinned) of int64 words."""
+    ctx.check(lib().hers_search_host(ctx.h, keys.h, _ptr(gallery), nblocks, d, _ptr(probe_ct_host),
+                                     _ptr(scores_host), _ptr(workspace), workspace.numel() * 8,
+                                     _stream(stream)), "hers_search_host")
+    return scores_host
+
+
+def hers_decrypt_scores(ctx: Context, keys: Keys, scores_ct, m: int, out=None, stream=None):
+    """int32 [m] decrypted, decoded scores (cuda)."""
+    import torch
+    nb = scores_ct.shape[0]
+    out = out if out is not None else torch.empty(m, dtype=torch.int32, device=scores_ct.device)
+    ctx.check(lib().hers_decrypt_scores(ctx.h, keys.h, _ptr(scores_ct), nb, _ptr(out), m,
+                                        _stream(stream)), "hers_decrypt_scores")
+    return out
+
+
+def hers_check(ctx: Context, stream=None):
+    ctx.check(lib().hers_check(ctx.h, _stream(stream) if stream is not None else None),
+              "hers_check")
+
+
+TRACE_PHASES = ("tensor", "intt", "scale_round", "key_switch", "search")
+
+
+def hers_trace_enable(ctx: Context, max_calls: int):
+    ctx.check(lib().hers_trace_enable(ctx.h, max_calls), "hers_trace_enable")
+
+
+def hers_trace_read(ctx: Context):
+    """(ncalls, {phase: average ms}) of the traced search calls since enabling."""
+    n = ctypes.c_uint32()
+    avg = (ctypes.c_double * len(TRACE_PHASES))()
+    ctx.check(lib().hers_trace_read(ctx.h, ctypes.byref(n), avg), "hers_trace_read")
+    return int(n.value), dict(zip(TRACE_PHASES, list(avg)))
+
+
+def hers_kernel_launches():
+    return int(lib().hers_kernel_launches())
+
+
+def to_u64(t):
+    """A device/host int64 tensor of ciphertext words as a numpy uint64 array."""
+    return t.detach().cpu().numpy().view("uint64")

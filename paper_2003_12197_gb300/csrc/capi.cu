@@ -1,0 +1,428 @@
+// C ABI of the HERS library (declared in include/hers.h): contexts, keys,
+// argument checking and the orchestration of the kernels in scheme.cu and
+// search.cu.  No computation of the method runs on the host; the host only
+// builds the NTT twiddle tables once per context.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+#include <vector>
+
+#include "hers.h"
+#include "hers_consts.h"
+#include "internal.h"
+
+using namespace hers;
+
+struct hers_ctx {
+    int device;
+    cudaStream_t stream;
+    uint64_t* tw;   // device twiddle tables [6][4][N]
+    int* err;       // device flag: a sampler ran out of attempts
+    char msg[512];
+    // tracing: SEARCH_EVENTS events per traced hers_search call
+    std::vector<cudaEvent_t> tev;
+    uint32_t tcap = 0, tn = 0;
+};
+
+namespace hers {
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace hers
+
+struct hers_keys {
+    hers_ctx* ctx;
+    DevKeys k;
+    void* base;     // single device allocation holding every key array
+};
+
+namespace {
+
+const uint64_t H_MOD[NUM_MODS] = HERS_MOD_INIT;
+const uint64_t H_PSI[NUM_MODS] = HERS_PSI_INIT;
+
+typedef unsigned __int128 u128;
+
+uint64_t h_mulmod(uint64_t a, uint64_t b, uint64_t p) { return (uint64_t)((u128)a * b % p); }
+
+uint64_t h_pow(uint64_t b, uint64_t e, uint64_t p) {
+    uint64_t r = 1;
+    b %= p;
+    while (e) {
+        if (e & 1) r = h_mulmod(r, b, p);
+        b = h_mulmod(b, b, p);
+        e >>= 1;
+    }
+    return r;
+}
+
+int h_brev(int x, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; i++) {
+        r = (r << 1) | (x & 1);
+        x >>= 1;
+    }
+    return r;
+}
+
+int fail(hers_ctx* ctx, int code, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->msg, sizeof ctx->msg, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(hers_ctx* ctx, cudaError_t e, const char* where) {
+    return fail(ctx, HERS_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Makes ctx's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+cudaStream_t pick(hers_ctx* ctx, void* stream) {
+    return stream ? (cudaStream_t)stream : ctx->stream;
+}
+
+// Events of the next traced search call, or null when tracing is off / full.
+cudaEvent_t* next_trace(hers_ctx* ctx) {
+    if (ctx->tn >= ctx->tcap) return nullptr;
+    return &ctx->tev[(size_t)(ctx->tn++) * SEARCH_EVENTS];
+}
+
+void trace_free(hers_ctx* ctx) {
+    for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
+    ctx->tev.clear();
+    ctx->tcap = ctx->tn = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hers_default_params(hers_params* out) {
+    if (!out) return HERS_E_INVAL;
+    out->n = N;
+    out->q[0] = H_MOD[0];
+    out->q[1] = H_MOD[1];
+    out->t = H_MOD[MOD_T];
+    out->flags = 0;
+    return HERS_OK;
+}
+
+const char* hers_status_string(int s) {
+    switch (s) {
+        case HERS_OK: return "HERS_OK";
+        case HERS_E_INVAL: return "HERS_E_INVAL";
+        case HERS_E_NOMEM: return "HERS_E_NOMEM";
+        case HERS_E_CUDA: return "HERS_E_CUDA";
+        case HERS_E_TIMEOUT: return "HERS_E_TIMEOUT";
+        case HERS_E_PARAM: return "HERS_E_PARAM";
+        case HERS_E_SAMPLER: return "HERS_E_SAMPLER";
+        default: return "HERS_E_UNKNOWN";
+    }
+}
+
+const char* hers_last_error(const hers_ctx* ctx) { return ctx ? ctx->msg : "null context"; }
+
+uint64_t hers_ct_bytes(void) { return 4ull * N * 8; }
+uint64_t hers_gallery_bytes(uint64_t nblocks, uint32_t d) { return nblocks * d * 10ull * N * 8; }
+uint64_t hers_probe_bytes(uint32_t d) { return (uint64_t)d * 10ull * N * 8; }
+uint64_t hers_search_workspace_bytes(uint64_t nblocks) { return nblocks * SEARCH_WS_WORDS_PER_BLOCK * 8; }
+uint64_t hers_blocks_for(uint64_t m) { return (m + N - 1) / N; }
+uint64_t hers_search_host_workspace_bytes(uint64_t nblocks, uint32_t d) {
+    return hers_search_workspace_bytes(nblocks) + hers_probe_bytes(d) +
+           (uint64_t)d * hers_ct_bytes() + nblocks * hers_ct_bytes();
+}
+
+int hers_create(const hers_params* p, int device, hers_ctx** out) {
+    if (!out) return HERS_E_INVAL;
+    *out = nullptr;
+    hers_params def;
+    hers_default_params(&def);
+    if (p && (p->n != def.n || p->q[0] != def.q[0] || p->q[1] != def.q[1] || p->t != def.t ||
+              p->flags != 0))
+        return HERS_E_PARAM;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return HERS_E_CUDA;
+    hers_ctx* ctx = new (std::nothrow) hers_ctx();
+    if (!ctx) return HERS_E_NOMEM;
+    ctx->device = device;
+    ctx->msg[0] = 0;
+    DeviceGuard g(device);
+    if (!g.ok) { delete ctx; return HERS_E_CUDA; }
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete ctx;
+        return HERS_E_CUDA;
+    }
+    // twiddles: [mod][fwd, fwd', inv, inv'][N]
+    const size_t words = (size_t)NUM_MODS * 4 * N;
+    uint64_t* h = new (std::nothrow) uint64_t[words];
+    if (!h) { cudaStreamDestroy(ctx->stream); delete ctx; return HERS_E_NOMEM; }
+    for (int i = 0; i < NUM_MODS; i++) {
+        const uint64_t pm = H_MOD[i], psi = H_PSI[i], psi_inv = h_pow(psi, pm - 2, pm);
+        uint64_t* f = h + (size_t)(4 * i) * N;
+        for (int k = 0; k < N; k++) {
+            const int r = h_brev(k, LOGN);
+            const uint64_t w = h_pow(psi, (uint64_t)r, pm), wi = h_pow(psi_inv, (uint64_t)r, pm);
+            f[k] = w;
+            f[N + k] = (uint64_t)(((u128)w << 64) / pm);
+            f[2 * N + k] = wi;
+            f[3 * N + k] = (uint64_t)(((u128)wi << 64) / pm);
+        }
+    }
+    cudaError_t e = cudaMalloc(&ctx->tw, words * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->tw, h, words * 8, cudaMemcpyHostToDevice);
+    delete[] h;
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(ctx->tw);
+        cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return HERS_E_CUDA;
+    }
+    *out = ctx;
+    return HERS_OK;
+}
+
+int hers_destroy(hers_ctx* ctx) {
+    if (!ctx) return HERS_E_INVAL;
+    {
+        DeviceGuard g(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->tw);
+        cudaFree(ctx->err);
+        trace_free(ctx);
+        cudaStreamDestroy(ctx->stream);
+    }
+    delete ctx;
+    return HERS_OK;
+}
+
+int hers_check(hers_ctx* ctx, void* stream) {
+    if (!ctx) return HERS_E_INVAL;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(pick(ctx, stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    int flag = 0;
+    e = cudaMemcpy(&flag, ctx->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "error flag read");
+    if (flag) {
+        cudaMemset(ctx->err, 0, sizeof(int));
+        return fail(ctx, HERS_E_SAMPLER, "a rejection sampler exhausted its attempts");
+    }
+    return HERS_OK;
+}
+
+int hers_keygen(hers_ctx* ctx, uint64_t seed, hers_keys** out) {
+    if (!ctx || !out) return fail(ctx, HERS_E_INVAL, "hers_keygen: null argument");
+    *out = nullptr;
+    DeviceGuard g(ctx->device);
+    hers_keys* K = new (std::nothrow) hers_keys();
+    if (!K) return fail(ctx, HERS_E_NOMEM, "hers_keygen: host allocation");
+    K->ctx = ctx;
+    // sizes in words
+    const size_t w_sk = N / 8, w_pk = 4 * N, w_evk = 8 * N, w_pkn = 8 * N, w_evkn = 16 * N, w_sn = 4 * N;
+    const size_t total = w_sk + w_pk + w_evk + w_pkn + w_evkn + w_sn;
+    cudaError_t e = cudaMalloc(&K->base, total * 8);
+    if (e != cudaSuccess) { delete K; return fail(ctx, HERS_E_NOMEM, "hers_keygen: %s", cudaGetErrorString(e)); }
+    uint64_t* b = (uint64_t*)K->base;
+    K->k.pk = b;
+    K->k.evk = b + w_pk;
+    K->k.pk_ntt = K->k.evk + w_evk;
+    K->k.evk_ntt = K->k.pk_ntt + w_pkn;
+    K->k.s_ntt = K->k.evk_ntt + w_evkn;
+    K->k.sk = (int8_t*)(K->k.s_ntt + w_sn);
+    e = launch_keygen(ctx->tw, seed, K->k, ctx->err, ctx->stream);
+    if (e != cudaSuccess) { cudaFree(K->base); delete K; return cuda_fail(ctx, e, "hers_keygen"); }
+    int rc = hers_check(ctx, nullptr);
+    if (rc != HERS_OK) { cudaFree(K->base); delete K; return rc; }
+    *out = K;
+    return HERS_OK;
+}
+
+int hers_keys_free(hers_keys* keys) {
+    if (!keys) return HERS_E_INVAL;
+    {
+        DeviceGuard g(keys->ctx->device);
+        cudaStreamSynchronize(keys->ctx->stream);
+        cudaFree(keys->base);
+    }
+    delete keys;
+    return HERS_OK;
+}
+
+int hers_keys_export(hers_ctx* ctx, const hers_keys* keys, int8_t* sk, uint64_t* pk, uint64_t* evk) {
+    if (!ctx || !keys) return fail(ctx, HERS_E_INVAL, "hers_keys_export: null argument");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaSuccess;
+    if (sk) e = cudaMemcpy(sk, keys->k.sk, N, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && pk) e = cudaMemcpy(pk, keys->k.pk, 4 * N * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && evk) e = cudaMemcpy(evk, keys->k.evk, 8 * N * 8, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_keys_export");
+}
+
+int hers_encrypt_gallery(hers_ctx* ctx, const hers_keys* keys, const int8_t* feats, uint64_t m,
+                         uint32_t d, uint64_t seed, uint64_t* gallery, uint64_t* gallery_ct,
+                         void* stream) {
+    if (!ctx || !keys || !feats || !gallery)
+        return fail(ctx, HERS_E_INVAL, "hers_encrypt_gallery: null argument");
+    if (m == 0 || d == 0 || d > HERS_MAX_D)
+        return fail(ctx, HERS_E_INVAL, "hers_encrypt_gallery: m = %llu, d = %u", (unsigned long long)m, d);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick(ctx, stream);
+    const uint64_t nb = hers_blocks_for(m), nct = nb * d;
+    // Encrypt in chunks of canonical cts (into gallery_ct, or a temporary
+    // buffer), then extend each chunk to the resident form.
+    const uint64_t chunk = 4096;  // cts per pass: 512 MiB of canonical cts at most
+    uint64_t* tmp = nullptr;
+    if (!gallery_ct) {
+        cudaError_t e = cudaMallocAsync(&tmp, (nct < chunk ? nct : chunk) * 4 * N * 8, st);
+        if (e != cudaSuccess) return fail(ctx, HERS_E_NOMEM, "hers_encrypt_gallery: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = cudaSuccess;
+    for (uint64_t c0 = 0; c0 < nct && e == cudaSuccess; c0 += chunk) {
+        const uint64_t n = nct - c0 < chunk ? nct - c0 : chunk;
+        uint64_t* ct = gallery_ct ? gallery_ct + c0 * 4 * N : tmp;
+        e = launch_encrypt(ctx->tw, keys->k, feats, m, d, c0, n, false, seed, ct, ctx->err, st);
+        if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, ct, n, gallery + c0 * 10 * N, st);
+    }
+    if (tmp) cudaFreeAsync(tmp, st);
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_encrypt_gallery");
+}
+
+int hers_encrypt_probe(hers_ctx* ctx, const hers_keys* keys, const int8_t* q, uint32_t d,
+                       uint64_t seed, uint64_t* probe_ct, void* stream) {
+    if (!ctx || !keys || !q || !probe_ct) return fail(ctx, HERS_E_INVAL, "hers_encrypt_probe: null argument");
+    if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_encrypt_probe: d = %u", d);
+    DeviceGuard g(ctx->device);
+    cudaError_t e = launch_encrypt(ctx->tw, keys->k, q, 0, d, 0, d, true, seed, probe_ct, ctx->err,
+                                   pick(ctx, stream));
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_encrypt_probe");
+}
+
+int hers_probe_prepare(hers_ctx* ctx, const uint64_t* probe_ct, uint32_t d, uint64_t* probe,
+                       void* stream) {
+    if (!ctx || !probe_ct || !probe) return fail(ctx, HERS_E_INVAL, "hers_probe_prepare: null argument");
+    if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_probe_prepare: d = %u", d);
+    DeviceGuard g(ctx->device);
+    cudaError_t e = launch_extend_ntt(ctx->tw, probe_ct, d, probe, pick(ctx, stream));
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_probe_prepare");
+}
+
+int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
+                uint32_t d, const uint64_t* probe, uint64_t* scores_ct, void* workspace,
+                uint64_t workspace_bytes, void* stream) {
+    if (!ctx || !keys || !gallery || !probe || !scores_ct || !workspace)
+        return fail(ctx, HERS_E_INVAL, "hers_search: null argument");
+    if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_search: d = %u", d);
+    if (workspace_bytes < hers_search_workspace_bytes(nblocks))
+        return fail(ctx, HERS_E_NOMEM, "hers_search: workspace %llu < %llu bytes",
+                    (unsigned long long)workspace_bytes,
+                    (unsigned long long)hers_search_workspace_bytes(nblocks));
+    DeviceGuard g(ctx->device);
+    cudaError_t e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, scores_ct,
+                                  (uint64_t*)workspace, pick(ctx, stream), next_trace(ctx));
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search");
+}
+
+int hers_search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
+                     uint64_t nblocks, uint32_t d, const uint64_t* probe_ct_host,
+                     uint64_t* scores_ct_host, void* workspace, uint64_t workspace_bytes,
+                     void* stream) {
+    if (!ctx || !keys || !gallery || !probe_ct_host || !scores_ct_host || !workspace)
+        return fail(ctx, HERS_E_INVAL, "hers_search_host: null argument");
+    if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_search_host: d = %u", d);
+    if (workspace_bytes < hers_search_host_workspace_bytes(nblocks, d))
+        return fail(ctx, HERS_E_NOMEM, "hers_search_host: workspace too small");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick(ctx, stream);
+    // workspace: [search scratch][probe cts d*4N][probe form d*10N][score cts nblocks*4N]
+    uint64_t* ws = (uint64_t*)workspace;
+    uint64_t* probe_ct = ws + nblocks * SEARCH_WS_WORDS_PER_BLOCK;
+    uint64_t* probe = probe_ct + (uint64_t)d * 4 * N;
+    uint64_t* out_dev = probe + (uint64_t)d * 10 * N;
+    cudaError_t e = cudaMemcpyAsync(probe_ct, probe_ct_host, (uint64_t)d * 4 * N * 8,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, probe_ct, d, probe, st);
+    if (e == cudaSuccess)
+        e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, out_dev, ws, st, next_trace(ctx));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(scores_ct_host, out_dev, nblocks * 4 * N * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search_host");
+}
+
+int hers_decrypt_scores(hers_ctx* ctx, const hers_keys* keys, const uint64_t* scores_ct,
+                        uint64_t nblocks, int32_t* scores, uint64_t m, void* stream) {
+    if (!ctx || !keys || !scores_ct || !scores) return fail(ctx, HERS_E_INVAL, "hers_decrypt_scores: null argument");
+    if (m > nblocks * N) return fail(ctx, HERS_E_INVAL, "hers_decrypt_scores: m > nblocks N");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = launch_decrypt(ctx->tw, keys->k, scores_ct, nblocks, scores, m, pick(ctx, stream));
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_decrypt_scores");
+}
+
+int hers_trace_enable(hers_ctx* ctx, uint32_t max_calls) {
+    if (!ctx) return HERS_E_INVAL;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    trace_free(ctx);
+    if (max_calls == 0) return HERS_OK;
+    ctx->tev.resize((size_t)max_calls * SEARCH_EVENTS);
+    for (size_t i = 0; i < ctx->tev.size(); i++) {
+        cudaError_t e = cudaEventCreate(&ctx->tev[i]);
+        if (e != cudaSuccess) {
+            ctx->tev.resize(i);
+            trace_free(ctx);
+            return cuda_fail(ctx, e, "hers_trace_enable");
+        }
+    }
+    ctx->tcap = max_calls;
+    ctx->tn = 0;
+    return HERS_OK;
+}
+
+int hers_trace_read(hers_ctx* ctx, uint32_t* ncalls, double* avg_ms) {
+    if (!ctx || !ncalls || !avg_ms) return fail(ctx, HERS_E_INVAL, "hers_trace_read: null argument");
+    DeviceGuard g(ctx->device);
+    double sum[HERS_TRACE_PHASES] = {0, 0, 0, 0, 0};
+    for (uint32_t c = 0; c < ctx->tn; c++) {
+        cudaEvent_t* ev = &ctx->tev[(size_t)c * SEARCH_EVENTS];
+        cudaError_t e = cudaEventSynchronize(ev[SEARCH_EVENTS - 1]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_trace_read");
+        for (int ph = 0; ph < SEARCH_EVENTS - 1; ph++) {
+            float ms = 0;
+            e = cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_trace_read");
+            sum[ph] += ms;
+        }
+        float tot = 0;
+        cudaEventElapsedTime(&tot, ev[0], ev[SEARCH_EVENTS - 1]);
+        sum[HERS_TRACE_PHASES - 1] += tot;
+    }
+    *ncalls = ctx->tn;
+    for (int ph = 0; ph < HERS_TRACE_PHASES; ph++) avg_ms[ph] = ctx->tn ? sum[ph] / ctx->tn : 0.0;
+    ctx->tn = 0;
+    return HERS_OK;
+}
+
+uint64_t hers_kernel_launches(void) { return launches_total(); }
+
+}  // extern "C"

@@ -1,0 +1,331 @@
+// Device-side building blocks of the HERS library: compile-time moduli and
+// constants, 64-bit modular arithmetic on the integer pipes, the ChaCha20
+// stream and samplers every random draw comes from, and the negacyclic NTT
+// over one polynomial held in shared memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hers_consts.h"
+
+namespace hers {
+
+// ---------------------------------------------------------------- constants
+// Modulus index i: 0 = q1, 1 = q2, 2 = p1, 3 = p2, 4 = p3, 5 = t.
+static __constant__ uint64_t c_mod[NUM_MODS] = HERS_MOD_INIT;
+static __constant__ uint64_t c_ninv[NUM_MODS] = HERS_NINV_INIT;
+static __constant__ uint64_t c_ninv_s[NUM_MODS] = HERS_NINV_S_INIT;
+static __constant__ uint64_t c_one_s[NUM_MODS] = HERS_ONE_S_INIT;
+static __constant__ uint64_t c_barrett[NUM_RNS] = HERS_BARRETT_INIT;
+static __constant__ uint64_t c_r27[NUM_MODS] = HERS_R27_INIT;
+static __constant__ uint64_t c_r27_s[NUM_MODS] = HERS_R27_S_INIT;
+static __constant__ uint64_t c_r54[NUM_MODS] = HERS_R54_INIT;
+static __constant__ uint64_t c_r54_s[NUM_MODS] = HERS_R54_S_INIT;
+static __constant__ uint64_t c_t_s[NUM_MODS] = HERS_T_S_INIT;
+static __constant__ uint64_t c_q1_mod[NUM_RNS] = HERS_Q1_MOD_INIT;
+static __constant__ uint64_t c_q1_mod_s[NUM_RNS] = HERS_Q1_MOD_S_INIT;
+static __constant__ uint64_t c_q_mod[NUM_RNS] = HERS_Q_MOD_INIT;
+static __constant__ uint64_t c_qinv_p[3] = HERS_QINV_P_INIT;
+static __constant__ uint64_t c_qinv_p_s[3] = HERS_QINV_P_S_INIT;
+static __constant__ uint64_t c_p1_mod_q[2] = HERS_P1_MOD_Q_INIT;
+static __constant__ uint64_t c_p1_mod_q_s[2] = HERS_P1_MOD_Q_S_INIT;
+static __constant__ uint64_t c_p1p2_mod_q[2] = HERS_P1P2_MOD_Q_INIT;
+static __constant__ uint64_t c_p1p2_mod_q_s[2] = HERS_P1P2_MOD_Q_S_INIT;
+static __constant__ uint64_t c_p_mod_q[2] = HERS_P_MOD_Q_INIT;
+static __constant__ uint64_t c_delta[2] = HERS_DELTA_MOD_Q_INIT;
+static __constant__ uint64_t c_delta_s[2] = HERS_DELTA_MOD_Q_S_INIT;
+static __constant__ uint64_t c_chi_cdt[CHI_LEN] = HERS_CHI_CDT_INIT;
+
+constexpr uint64_t T_PLAIN = 4169729ULL;
+constexpr int NTT_THREADS = 512;          // threads of every one-polynomial-per-CTA kernel
+constexpr uint32_t MASK27 = (1u << 27) - 1;
+
+// Twiddle table of modulus i inside the table buffer the context owns:
+// [i][fwd w, fwd w', inv w, inv w'][N], w' = floor(w 2^64 / p) (Shoup).
+__device__ __forceinline__ const uint64_t* tw_fwd(const uint64_t* tw, int i) { return tw + (size_t)(4 * i + 0) * N; }
+__device__ __forceinline__ const uint64_t* tw_fwd_s(const uint64_t* tw, int i) { return tw + (size_t)(4 * i + 1) * N; }
+__device__ __forceinline__ const uint64_t* tw_inv(const uint64_t* tw, int i) { return tw + (size_t)(4 * i + 2) * N; }
+__device__ __forceinline__ const uint64_t* tw_inv_s(const uint64_t* tw, int i) { return tw + (size_t)(4 * i + 3) * N; }
+
+// ---------------------------------------------------------------- arithmetic
+
+__device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t p) { return x >= p ? x - p : x; }
+
+__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t p) { return csub(a + b, p); }
+
+__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t p) {
+    return a >= b ? a - b : a + p - b;
+}
+
+// Shoup multiplication by a fixed w < p with ws = floor(w 2^64 / p):
+// x w mod p, lazily in [0, 2p), for any x < 2^64 and p < 2^63.
+__device__ __forceinline__ uint64_t shoup_lazy(uint64_t x, uint64_t w, uint64_t ws, uint64_t p) {
+    return x * w - __umul64hi(x, ws) * p;
+}
+
+__device__ __forceinline__ uint64_t shoup(uint64_t x, uint64_t w, uint64_t ws, uint64_t p) {
+    return csub(shoup_lazy(x, w, ws, p), p);
+}
+
+// x mod p_i for any 64-bit x (Shoup with w = 1).
+__device__ __forceinline__ uint64_t reduce64(uint64_t x, int i) {
+    return csub(shoup_lazy(x, 1, c_one_s[i], c_mod[i]), c_mod[i]);
+}
+
+// a b mod p_i for a, b < p_i, i an RNS prime (2^53 < p_i < 2^54): Barrett on
+// the 108-bit product with mu = floor(2^108 / p), quotient estimate
+// floor(floor(x / 2^53) mu / 2^55), which is at most 2 below the true one.
+__device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, int i) {
+    const uint64_t p = c_mod[i];
+    uint64_t lo = a * b, hi = __umul64hi(a, b);
+    uint64_t z = (hi << 11) | (lo >> 53);
+    uint64_t mu = c_barrett[i];
+    uint64_t qh = (__umul64hi(z, mu) << 9) | ((z * mu) >> 55);
+    uint64_t r = lo - qh * p;
+    r = csub(r, p);
+    return csub(r, p);
+}
+
+// mod-t arithmetic (t < 2^23): products fit in 64 bits
+__device__ __forceinline__ uint64_t mul_mod_t(uint64_t a, uint64_t b) { return (a * b) % T_PLAIN; }
+
+// value of a split-stored residue (hi27 << 32 | lo27)
+__device__ __forceinline__ uint64_t split_store(uint64_t v) {
+    return ((v >> 27) << 32) | (v & MASK27);
+}
+__device__ __forceinline__ uint64_t split_load(uint64_t s) {
+    return ((s >> 32) << 27) | (s & 0xFFFFFFFFull);
+}
+
+__device__ __forceinline__ int brev12(int x) { return (int)(__brev((unsigned)x) >> (32 - LOGN)); }
+
+// ---------------------------------------------------------------- ChaCha20 (RFC 8439, Sec. 2.3)
+
+__device__ __forceinline__ uint32_t rotl32(uint32_t x, int r) { return __funnelshift_l(x, x, r); }
+
+#define HERS_QR(a, b, c, d)                                  \
+    a += b; d ^= a; d = rotl32(d, 16);                      \
+    c += d; b ^= c; b = rotl32(b, 12);                      \
+    a += b; d ^= a; d = rotl32(d, 8);                       \
+    c += d; b ^= c; b = rotl32(b, 7);
+
+// Block `counter` of the stream keyed by (seed_lo, seed_hi, 0 x 6) with nonce
+// (purpose, obj_lo, obj_hi): 16 little-endian words.
+__device__ __forceinline__ void chacha20(uint64_t seed, uint32_t purpose, uint64_t obj,
+                                         uint32_t counter, uint32_t out[16]) {
+    uint32_t s[16];
+    s[0] = 0x61707865u; s[1] = 0x3320646eu; s[2] = 0x79622d32u; s[3] = 0x6b206574u;
+    s[4] = (uint32_t)seed; s[5] = (uint32_t)(seed >> 32);
+    s[6] = s[7] = s[8] = s[9] = s[10] = s[11] = 0u;
+    s[12] = counter;
+    s[13] = purpose; s[14] = (uint32_t)obj; s[15] = (uint32_t)(obj >> 32);
+    uint32_t x0 = s[0], x1 = s[1], x2 = s[2], x3 = s[3], x4 = s[4], x5 = s[5], x6 = s[6], x7 = s[7];
+    uint32_t x8 = s[8], x9 = s[9], x10 = s[10], x11 = s[11], x12 = s[12], x13 = s[13], x14 = s[14], x15 = s[15];
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        HERS_QR(x0, x4, x8, x12) HERS_QR(x1, x5, x9, x13) HERS_QR(x2, x6, x10, x14) HERS_QR(x3, x7, x11, x15)
+        HERS_QR(x0, x5, x10, x15) HERS_QR(x1, x6, x11, x12) HERS_QR(x2, x7, x8, x13) HERS_QR(x3, x4, x9, x14)
+    }
+    out[0] = x0 + s[0]; out[1] = x1 + s[1]; out[2] = x2 + s[2]; out[3] = x3 + s[3];
+    out[4] = x4 + s[4]; out[5] = x5 + s[5]; out[6] = x6 + s[6]; out[7] = x7 + s[7];
+    out[8] = x8 + s[8]; out[9] = x9 + s[9]; out[10] = x10 + s[10]; out[11] = x11 + s[11];
+    out[12] = x12 + s[12]; out[13] = x13 + s[13]; out[14] = x14 + s[14]; out[15] = x15 + s[15];
+}
+#undef HERS_QR
+
+// Stream purposes (nonce word 0).  Encryption streams: base + 0 = u, + 1 = e1, + 2 = e2.
+constexpr uint32_t PRF_KG_SK = 0x01u;
+constexpr uint32_t PRF_KG_PK_A = 0x02u;   // obj = limb
+constexpr uint32_t PRF_KG_PK_E = 0x03u;
+constexpr uint32_t PRF_KG_EVK_A = 0x04u;  // obj = 2 j + limb
+constexpr uint32_t PRF_KG_EVK_E = 0x05u;  // obj = j
+constexpr uint32_t PRF_GALLERY = 0x11u;   // obj = block * d + dim
+constexpr uint32_t PRF_PROBE = 0x21u;     // obj = dim
+constexpr int MAX_ATTEMPTS = 16;
+
+// One coefficient k of a ternary stream, walking attempts a = 0, 1, ...
+// (32-bit word a N + k; accept w < 3 floor(2^32 / 3)).  Returns -2 when all
+// attempts were rejected.
+static __device__ __noinline__ int ternary_slow(uint64_t seed, uint32_t purpose, uint64_t obj, int k) {
+    for (int a = 0; a < MAX_ATTEMPTS; a++) {
+        uint32_t W = (uint32_t)(a * N + k);
+        uint32_t blk[16];
+        chacha20(seed, purpose, obj, W >> 4, blk);
+        uint32_t w = blk[W & 15];
+        if (w < 0xFFFFFFFFu) return (int)(w % 3u) - 1;
+    }
+    return -2;
+}
+
+// One coefficient k of a uniform stream mod p (64-bit word a N + k masked to
+// 54 bits, accept below p).  Returns ~0 when all attempts were rejected.
+static __device__ __noinline__ uint64_t uniform_slow(uint64_t seed, uint32_t purpose, uint64_t obj, int k,
+                                              uint64_t p) {
+    for (int a = 0; a < MAX_ATTEMPTS; a++) {
+        uint32_t w = (uint32_t)(a * N + k);
+        uint32_t blk[16];
+        chacha20(seed, purpose, obj, w >> 3, blk);
+        uint64_t v = ((uint64_t)blk[(2 * w + 1) & 15] << 32 | blk[(2 * w) & 15]) & ((1ull << 54) - 1);
+        if (v < p) return v;
+    }
+    return ~0ull;
+}
+
+__device__ __forceinline__ int chi_from_word(uint64_t U) {
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < CHI_LEN; j++) c += (c_chi_cdt[j] <= U) ? 1 : 0;
+    return CHI_MIN + c;
+}
+
+// Fill out[0..N) with a ternary polynomial as residues mod p (-1 -> p - 1).
+// All threads of the CTA call this; the block stream is split over threads.
+__device__ __forceinline__ void sample_ternary_mod(uint64_t seed, uint32_t purpose, uint64_t obj,
+                                                   uint64_t p, uint64_t* out, int* err) {
+    for (int c = threadIdx.x; c < N / 16; c += blockDim.x) {
+        uint32_t blk[16];
+        chacha20(seed, purpose, obj, (uint32_t)c, blk);
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            int k = 16 * c + j;
+            int v;
+            if (blk[j] < 0xFFFFFFFFu) v = (int)(blk[j] % 3u) - 1;
+            else v = ternary_slow(seed, purpose, obj, k);
+            if (v == -2) { atomicOr(err, 1); v = 0; }
+            out[k] = v < 0 ? p - 1 : (uint64_t)v;
+        }
+    }
+}
+
+// Fill out[0..N) with a chi sample (signed small values).
+__device__ __forceinline__ void sample_chi(uint64_t seed, uint32_t purpose, uint64_t obj, int* out) {
+    for (int c = threadIdx.x; c < N / 8; c += blockDim.x) {
+        uint32_t blk[16];
+        chacha20(seed, purpose, obj, (uint32_t)c, blk);
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            uint64_t U = ((uint64_t)blk[2 * j + 1] << 32) | blk[2 * j];
+            out[8 * c + j] = chi_from_word(U);
+        }
+    }
+}
+
+// Fill out[0..N) with a uniform polynomial mod p.
+__device__ __forceinline__ void sample_uniform(uint64_t seed, uint32_t purpose, uint64_t obj,
+                                               uint64_t p, uint64_t* out, int* err) {
+    for (int c = threadIdx.x; c < N / 8; c += blockDim.x) {
+        uint32_t blk[16];
+        chacha20(seed, purpose, obj, (uint32_t)c, blk);
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            int k = 8 * c + j;
+            uint64_t v = (((uint64_t)blk[2 * j + 1] << 32) | blk[2 * j]) & ((1ull << 54) - 1);
+            if (v >= p) {
+                v = uniform_slow(seed, purpose, obj, k, p);
+                if (v == ~0ull) { atomicOr(err, 1); v = 0; }
+            }
+            out[k] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- NTT (one polynomial in smem)
+//
+// Forward: Cooley-Tukey over the negacyclic ring with psi-powers in
+// bit-reversed order; input a[0..N) with residues < p (any value < 2p is
+// fine), output in bit-reversed order, fully reduced.  Output index j is the
+// evaluation at psi^(2 brev(j) + 1).  Values are kept lazily in [0, 4p)
+// between stages (p < 2^54 leaves ample headroom).  All threads of the CTA
+// must call it; it starts and ends with __syncthreads().
+
+__device__ __forceinline__ void ntt_fwd_smem(uint64_t* a, const uint64_t* __restrict__ w,
+                                             const uint64_t* __restrict__ ws, uint64_t p) {
+    const uint64_t two_p = 2 * p;
+    __syncthreads();
+#pragma unroll 1
+    for (int lg = LOGN - 1, m = 1; lg >= 0; lg--, m <<= 1) {
+        const int tt = 1 << lg;
+        for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
+            const int i = b >> lg;
+            const int j = (i << (lg + 1)) + (b & (tt - 1));
+            const uint64_t W = __ldg(w + m + i), Ws = __ldg(ws + m + i);
+            uint64_t U = a[j];
+            U = U >= two_p ? U - two_p : U;
+            const uint64_t V = shoup_lazy(a[j + tt], W, Ws, p);
+            a[j] = U + V;
+            a[j + tt] = U - V + two_p;
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        uint64_t x = a[k];
+        x = x >= two_p ? x - two_p : x;
+        a[k] = csub(x, p);
+    }
+    __syncthreads();
+}
+
+// Inverse: Gentleman-Sande with inverse psi-powers in bit-reversed order,
+// bit-reversed input (< 2p), natural-order output multiplied by N^-1, fully
+// reduced.
+__device__ __forceinline__ void ntt_inv_smem(uint64_t* a, const uint64_t* __restrict__ w,
+                                             const uint64_t* __restrict__ ws, uint64_t p,
+                                             uint64_t ninv, uint64_t ninv_s) {
+    const uint64_t two_p = 2 * p;
+    __syncthreads();
+#pragma unroll 1
+    for (int lg = 0, m = N / 2; lg < LOGN; lg++, m >>= 1) {
+        const int tt = 1 << lg;
+        for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
+            const int i = b >> lg;
+            const int j = (i << (lg + 1)) + (b & (tt - 1));
+            const uint64_t W = __ldg(w + m + i), Ws = __ldg(ws + m + i);
+            const uint64_t U = a[j], V = a[j + tt];
+            uint64_t S = U + V;
+            a[j] = S >= two_p ? S - two_p : S;
+            a[j + tt] = shoup_lazy(U - V + two_p, W, Ws, p);
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < N; k += blockDim.x) a[k] = shoup(a[k], ninv, ninv_s, p);
+    __syncthreads();
+}
+
+__device__ __forceinline__ void ntt_fwd_mod(uint64_t* a, const uint64_t* tw, int i) {
+    ntt_fwd_smem(a, tw_fwd(tw, i), tw_fwd_s(tw, i), c_mod[i]);
+}
+__device__ __forceinline__ void ntt_inv_mod(uint64_t* a, const uint64_t* tw, int i) {
+    ntt_inv_smem(a, tw_inv(tw, i), tw_inv_s(tw, i), c_mod[i], c_ninv[i], c_ninv_s[i]);
+}
+
+// ---------------------------------------------------------------- base extension Q -> p_i
+// x given by its residues (x1 mod q1, x2 mod q2), read as the centred integer
+// in (-q/2, q/2] (App. A's symmetric representative); returns x mod p_i,
+// exactly, for i in 0..4.
+struct Lifted {
+    uint64_t x1;   // x1 in [0, q1)
+    uint64_t h;    // Garner digit in [0, q2): x = x1 + q1 h in [0, q)
+    bool neg;      // x > (q-1)/2, i.e. the centred value is x - q
+};
+
+__device__ __forceinline__ Lifted lift_q(uint64_t x1, uint64_t x2) {
+    const uint64_t q2 = c_mod[1];
+    uint64_t x1r = csub(x1, q2);  // q1 < 2 q2
+    uint64_t h = shoup(sub_mod(x2, x1r, q2), Q1INV_Q2, Q1INV_Q2_S, q2);
+    Lifted L;
+    L.x1 = x1;
+    L.h = h;
+    L.neg = (h > HALFQ_HI) || (h == HALFQ_HI && x1 > HALFQ_LO);
+    return L;
+}
+
+__device__ __forceinline__ uint64_t lifted_mod(const Lifted& L, int i, uint64_t x2) {
+    if (i == 0) return L.x1;
+    if (i == 1) return x2;
+    const uint64_t p = c_mod[i];
+    uint64_t v = add_mod(csub(L.x1, p), shoup(L.h, c_q1_mod[i], c_q1_mod_s[i], p), p);
+    return L.neg ? sub_mod(v, c_q_mod[i], p) : v;
+}
+
+}  // namespace hers

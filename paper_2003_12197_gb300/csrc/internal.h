@@ -1,0 +1,50 @@
+// Declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hers {
+
+// Key material in device memory (all uint64 unless noted):
+//   sk        int8 [N]                  ternary secret
+//   pk        [2 polys][2 limbs][N]     canonical public key
+//   evk       [2 j][2 polys][2 limbs][N] canonical relinearisation keys
+//   pk_ntt    [2 polys][2 limbs][2][N]  NTT form and Shoup companion (encryption)
+//   evk_ntt   [2 j][2 polys][2 limbs][2][N] NTT form + Shoup (key switch)
+//   s_ntt     [2 limbs][2][N]           NTT form of s + Shoup (decryption)
+struct DevKeys {
+    int8_t* sk;
+    uint64_t* pk;
+    uint64_t* evk;
+    uint64_t* pk_ntt;
+    uint64_t* evk_ntt;
+    uint64_t* s_ntt;
+};
+
+// scheme.cu
+cudaError_t launch_keygen(const uint64_t* tw, uint64_t seed, DevKeys k, int* err, cudaStream_t st);
+cudaError_t launch_encrypt(const uint64_t* tw, const DevKeys& k, const int8_t* feats, uint64_t m,
+                           uint32_t d, uint64_t ct_begin, uint64_t nct, bool probe, uint64_t seed,
+                           uint64_t* out_ct, int* err, cudaStream_t st);
+cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t* out,
+                              cudaStream_t st);
+cudaError_t launch_decrypt(const uint64_t* tw, const DevKeys& k, const uint64_t* scores_ct,
+                           uint64_t nblocks, int32_t* scores, uint64_t m, cudaStream_t st);
+
+// search.cu
+// Workspace words per gallery block used by the search pipeline.
+constexpr uint64_t SEARCH_WS_WORDS_PER_BLOCK = (15 + 6 + 4) * 4096ull;
+// Phase boundaries recorded by launch_search when `ev` is non-null:
+// ev[0] before the tensor kernel, ev[1] after it, ev[2] after the inverse
+// NTTs, ev[3] after scale-and-round, ev[4] after the key switch.
+constexpr int SEARCH_EVENTS = 5;
+cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
+                          uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
+                          uint64_t* ws, cudaStream_t st, cudaEvent_t* ev = nullptr);
+
+// Kernel launches issued by this library in this process (all contexts).
+void count_launches(uint64_t n);
+uint64_t launches_total();
+
+}  // namespace hers

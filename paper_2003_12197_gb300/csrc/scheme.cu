@@ -1,0 +1,292 @@
+// FV scheme kernels of the HERS library: key generation (App. A, Alg 1),
+// SIMD encoding + encryption of gallery rows and probe dimensions (Sec. 3.2
+// Eqs 2-3; Alg 2), extension of canonical ciphertexts to the resident
+// 5-prime NTT form, and decryption + decoding of score ciphertexts (Alg 3).
+#include "common.cuh"
+#include "internal.h"
+
+namespace hers {
+
+__device__ __forceinline__ uint64_t shoup_companion(uint64_t w, uint64_t p) {
+    return (uint64_t)(((unsigned __int128)w << 64) / p);
+}
+
+// ---------------------------------------------------------------- key generation
+//
+// Grid (2 limbs, 3 components): component 0 is pk, 1 and 2 are evk_1, evk_2.
+// Each CTA works on one limb q_l of one component:
+//   c0 = [-(a s + e) + g_j s^2]_{q_l},  c1 = a,
+// with g_j = 1 mod q_j and 0 mod the other prime, so the s^2 term appears only
+// in the limb l = j.  Products use the NTT mod q_l (exact ring arithmetic mod q_l).
+__global__ void __launch_bounds__(NTT_THREADS) k_keygen(const uint64_t* __restrict__ tw,
+                                                        uint64_t seed, DevKeys K, int* err) {
+    extern __shared__ uint64_t sm[];
+    uint64_t* S = sm;
+    uint64_t* A = sm + N;
+    uint64_t* X = sm + 2 * N;
+    const int limb = blockIdx.x, comp = blockIdx.y;
+    const uint64_t p = c_mod[limb];
+
+    sample_ternary_mod(seed, PRF_KG_SK, 0, p, S, err);
+    __syncthreads();
+    if (limb == 0 && comp == 0)
+        for (int k = threadIdx.x; k < N; k += blockDim.x)
+            K.sk[k] = S[k] == 0 ? 0 : (S[k] == 1 ? 1 : -1);
+    ntt_fwd_mod(S, tw, limb);
+    if (comp == 0)
+        for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            K.s_ntt[(limb * 2 + 0) * N + k] = S[k];
+            K.s_ntt[(limb * 2 + 1) * N + k] = shoup_companion(S[k], p);
+        }
+
+    const uint32_t pa = comp == 0 ? PRF_KG_PK_A : PRF_KG_EVK_A;
+    const uint64_t oa = comp == 0 ? (uint64_t)limb : (uint64_t)(2 * (comp - 1) + limb);
+    sample_uniform(seed, pa, oa, p, A, err);
+    __syncthreads();
+    // canonical output: [2 polys][2 limbs][N] for pk, [j][2][2][N] for evk_j
+    uint64_t* outc = comp == 0 ? K.pk : K.evk + (size_t)(comp - 1) * 4 * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) outc[(2 + limb) * N + k] = A[k];
+    ntt_fwd_mod(A, tw, limb);
+    const bool gadget = comp >= 1 && (comp - 1) == limb;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        A[k] = mul_mod(A[k], S[k], limb);
+        if (gadget) X[k] = mul_mod(S[k], S[k], limb);
+    }
+    ntt_inv_mod(A, tw, limb);
+    if (gadget) ntt_inv_mod(X, tw, limb);  // uniform per CTA
+
+    // e from its stream; 8 coefficients per ChaCha block
+    const uint32_t pe = comp == 0 ? PRF_KG_PK_E : PRF_KG_EVK_E;
+    const uint64_t oe = comp == 0 ? 0 : (uint64_t)(comp - 1);
+    for (int c = threadIdx.x; c < N / 8; c += blockDim.x) {
+        uint32_t blk[16];
+        chacha20(seed, pe, oe, (uint32_t)c, blk);
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int k = 8 * c + j;
+            const int e = chi_from_word(((uint64_t)blk[2 * j + 1] << 32) | blk[2 * j]);
+            uint64_t v = add_mod(A[k], e < 0 ? p - (uint64_t)(-e) : (uint64_t)e, p);
+            v = v == 0 ? 0 : p - v;  // -(a s + e)
+            if (gadget) v = add_mod(v, X[k], p);
+            outc[limb * N + k] = v;
+        }
+    }
+}
+
+// Forward NTT of canonical key polynomials, stored with Shoup companions.
+// Poly index P of a [..][2 limbs][N] array has limb P % 2; out is [..][2][N].
+__global__ void __launch_bounds__(NTT_THREADS) k_key_ntt(const uint64_t* __restrict__ tw,
+                                                         const uint64_t* __restrict__ in,
+                                                         uint64_t* __restrict__ out) {
+    extern __shared__ uint64_t sm[];
+    const int P = blockIdx.x, limb = P & 1;
+    const uint64_t p = c_mod[limb];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) sm[k] = in[(size_t)P * N + k];
+    ntt_fwd_mod(sm, tw, limb);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        out[((size_t)P * 2 + 0) * N + k] = sm[k];
+        out[((size_t)P * 2 + 1) * N + k] = shoup_companion(sm[k], p);
+    }
+}
+
+cudaError_t launch_keygen(const uint64_t* tw, uint64_t seed, DevKeys k, int* err, cudaStream_t st) {
+    const int smem = 3 * N * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_keygen, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_keygen<<<dim3(2, 3), NTT_THREADS, smem, st>>>(tw, seed, k, err);
+    k_key_ntt<<<4, NTT_THREADS, N * 8, st>>>(tw, k.pk, k.pk_ntt);
+    k_key_ntt<<<8, NTT_THREADS, N * 8, st>>>(tw, k.evk, k.evk_ntt);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- encryption
+//
+// Grid (nct, 2 limbs).  CTA (c, l) writes limb l of ciphertext ct_begin + c:
+//   ct0 = [Delta m + pk0 u + e1]_q,  ct1 = [pk1 u + e2]_q   (Alg 2)
+// The plaintext m is computed in the CTA:
+//   probe (Eq. 2): dimension i in every slot, i.e. the constant polynomial q[i];
+//   gallery (Eq. 3): ct c = b d + i has slot j = feats[b N + j][i] (0 past m);
+//     slot j is the evaluation at psi_t^(2j+1), which the forward NTT mod t
+//     puts at index brev(j), so m = INTT_t of the slots placed at brev(j).
+// Randomness: u, e1, e2 are the streams (seed, base + 0/1/2, obj) with
+// obj = b d + i (gallery) or i (probe).
+__global__ void __launch_bounds__(NTT_THREADS) k_encrypt(const uint64_t* __restrict__ tw,
+                                                         const uint64_t* __restrict__ pk_ntt,
+                                                         const int8_t* __restrict__ feats,
+                                                         uint64_t m, uint32_t d, uint64_t ct_begin,
+                                                         int probe, uint64_t seed,
+                                                         uint64_t* __restrict__ out, int* err) {
+    extern __shared__ uint64_t sm[];
+    uint64_t* U = sm;
+    uint64_t* B = sm + N;
+    uint64_t* M = sm + 2 * N;
+    const uint64_t c = ct_begin + blockIdx.x;
+    const int limb = blockIdx.y;
+    const uint64_t p = c_mod[limb];
+    const uint32_t base = probe ? PRF_PROBE : PRF_GALLERY;
+    const uint64_t obj = c;  // gallery: b d + i; probe: i
+
+    // plaintext
+    if (probe) {
+        const int v = feats[c];
+        const uint64_t mv = v < 0 ? T_PLAIN - (uint64_t)(-v) : (uint64_t)v;
+        for (int k = threadIdx.x; k < N; k += blockDim.x) M[k] = k == 0 ? mv : 0;
+    } else {
+        const uint64_t b = c / d, i = c % d;
+        for (int s = threadIdx.x; s < N; s += blockDim.x) {
+            const uint64_t e = b * N + (uint64_t)s;
+            const int v = e < m ? feats[e * d + i] : 0;
+            M[brev12(s)] = v < 0 ? T_PLAIN - (uint64_t)(-v) : (uint64_t)v;
+        }
+        ntt_inv_mod(M, tw, MOD_T);
+    }
+
+    // u, NTT, products with the public key
+    sample_ternary_mod(seed, base + 0, obj, p, U, err);
+    ntt_fwd_mod(U, tw, limb);
+    const uint64_t* pk0 = pk_ntt + (size_t)((0 * 2 + limb) * 2) * N;
+    const uint64_t* pk1 = pk_ntt + (size_t)((1 * 2 + limb) * 2) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const uint64_t u = U[k];
+        B[k] = shoup(u, pk1[k], pk1[N + k], p);
+        U[k] = shoup(u, pk0[k], pk0[N + k], p);
+    }
+    ntt_inv_mod(U, tw, limb);
+    ntt_inv_mod(B, tw, limb);
+
+    // add Delta m + e1 and e2, write the canonical ciphertext limb
+    uint64_t* o0 = out + ((size_t)blockIdx.x * 4 + 0 * 2 + limb) * N;
+    uint64_t* o1 = out + ((size_t)blockIdx.x * 4 + 1 * 2 + limb) * N;
+    for (int cb = threadIdx.x; cb < N / 8; cb += blockDim.x) {
+        uint32_t b1[16], b2[16];
+        chacha20(seed, base + 1, obj, (uint32_t)cb, b1);
+        chacha20(seed, base + 2, obj, (uint32_t)cb, b2);
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int k = 8 * cb + j;
+            const int e1 = chi_from_word(((uint64_t)b1[2 * j + 1] << 32) | b1[2 * j]);
+            const int e2 = chi_from_word(((uint64_t)b2[2 * j + 1] << 32) | b2[2 * j]);
+            uint64_t v0 = add_mod(U[k], shoup(M[k], c_delta[limb], c_delta_s[limb], p), p);
+            v0 = e1 < 0 ? sub_mod(v0, (uint64_t)(-e1), p) : add_mod(v0, (uint64_t)e1, p);
+            uint64_t v1 = e2 < 0 ? sub_mod(B[k], (uint64_t)(-e2), p) : add_mod(B[k], (uint64_t)e2, p);
+            o0[k] = v0;
+            o1[k] = v1;
+        }
+    }
+}
+
+cudaError_t launch_encrypt(const uint64_t* tw, const DevKeys& k, const int8_t* feats, uint64_t m,
+                           uint32_t d, uint64_t ct_begin, uint64_t nct, bool probe, uint64_t seed,
+                           uint64_t* out_ct, int* err, cudaStream_t st) {
+    const int smem = 3 * N * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_encrypt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t chunk = 1u << 30;  // grid.x limit is 2^31 - 1
+    for (uint64_t off = 0; off < nct; off += chunk) {
+        const uint64_t n = nct - off < chunk ? nct - off : chunk;
+        k_encrypt<<<dim3((unsigned)n, 2), NTT_THREADS, smem, st>>>(
+            tw, k.pk_ntt, feats, m, d, ct_begin + off, probe ? 1 : 0, seed, out_ct + off * 4 * N, err);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- extension to the search form
+//
+// Grid (2 nct polys, 5 limbs).  Reads a canonical ciphertext polynomial
+// (residues mod q1, q2), takes its centred representative x in (-q/2, q/2]
+// (App. A) and writes NTT_{p_l}(x mod p_l) for l = 0..4 in split storage
+// (high 27 bits << 32 | low 27 bits), layout [nct][2 polys][5 limbs][N].
+// Exactness of the later tensor product needs the centred lift: the product
+// of two such polynomials over Z is then below q P / 2 (|X| < 2^235).
+__global__ void __launch_bounds__(NTT_THREADS) k_extend_ntt(const uint64_t* __restrict__ tw,
+                                                            const uint64_t* __restrict__ ct,
+                                                            uint64_t* __restrict__ out) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t P = blockIdx.x;
+    const int limb = blockIdx.y;
+    const uint64_t* x1 = ct + (P * 2 + 0) * N;
+    const uint64_t* x2 = ct + (P * 2 + 1) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const uint64_t a = x1[k], b = x2[k];
+        sm[k] = lifted_mod(lift_q(a, b), limb, b);
+    }
+    ntt_fwd_mod(sm, tw, limb);
+    uint64_t* o = out + (P * 5 + limb) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) o[k] = split_store(sm[k]);
+}
+
+cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t* out,
+                              cudaStream_t st) {
+    const uint64_t chunk = 1u << 30;
+    for (uint64_t off = 0; off < 2 * nct; off += chunk) {
+        const uint64_t n = 2 * nct - off < chunk ? 2 * nct - off : chunk;
+        k_extend_ntt<<<dim3((unsigned)n, 5), NTT_THREADS, N * 8, st>>>(tw, ct + off * 2 * N,
+                                                                      out + off * 5 * N);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- decryption + decoding
+//
+// One CTA per block b.  v = [c0 + c1 s]_q per limb (NTT product with s);
+// pt = round(t v / q) mod t computed exactly as pt = [-r q^-1]_t with
+// r = [t v]_q centred (t v = q pt' + r, |r| < q/2, so pt' = (t v - r)/q);
+// slots = NTT_t(pt), slot j at index brev(j), centred mod t.
+__global__ void __launch_bounds__(NTT_THREADS) k_decrypt(const uint64_t* __restrict__ tw,
+                                                         const uint64_t* __restrict__ s_ntt,
+                                                         const uint64_t* __restrict__ cts,
+                                                         int32_t* __restrict__ scores, uint64_t m) {
+    extern __shared__ uint64_t sm[];
+    uint64_t* V0 = sm;
+    uint64_t* V1 = sm + N;
+    uint64_t* PT = sm + 2 * N;
+    const uint64_t b = blockIdx.x;
+    const uint64_t* ct = cts + b * 4 * N;
+    for (int l = 0; l < 2; l++) {
+        uint64_t* V = l ? V1 : V0;
+        const uint64_t p = c_mod[l];
+        for (int k = threadIdx.x; k < N; k += blockDim.x) V[k] = ct[(2 + l) * N + k];
+        ntt_fwd_mod(V, tw, l);
+        const uint64_t* s = s_ntt + (size_t)l * 2 * N;
+        for (int k = threadIdx.x; k < N; k += blockDim.x) V[k] = shoup(V[k], s[k], s[N + k], p);
+        ntt_inv_mod(V, tw, l);
+        for (int k = threadIdx.x; k < N; k += blockDim.x) V[k] = add_mod(V[k], ct[l * N + k], p);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const uint64_t a1 = shoup(V0[k], T_PLAIN, c_t_s[0], c_mod[0]);
+        const uint64_t a2 = shoup(V1[k], T_PLAIN, c_t_s[1], c_mod[1]);
+        const Lifted L = lift_q(a1, a2);
+        uint64_t r = (a1 % T_PLAIN + mul_mod_t(Q1_MOD_T, L.h % T_PLAIN)) % T_PLAIN;
+        if (L.neg) r = (r + T_PLAIN - Q_MOD_T) % T_PLAIN;
+        PT[k] = mul_mod_t((T_PLAIN - r) % T_PLAIN, QINV_T);
+    }
+    ntt_fwd_mod(PT, tw, MOD_T);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const uint64_t e = b * N + (uint64_t)brev12(j);
+        if (e < m) {
+            const uint64_t v = PT[j];
+            scores[e] = v > (T_PLAIN - 1) / 2 ? (int32_t)((int64_t)v - (int64_t)T_PLAIN) : (int32_t)v;
+        }
+    }
+}
+
+cudaError_t launch_decrypt(const uint64_t* tw, const DevKeys& k, const uint64_t* scores_ct,
+                           uint64_t nblocks, int32_t* scores, uint64_t m, cudaStream_t st) {
+    const int smem = 3 * N * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_decrypt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t chunk = 1u << 30;
+    for (uint64_t off = 0; off < nblocks; off += chunk) {
+        const uint64_t n = nblocks - off < chunk ? nblocks - off : chunk;
+        k_decrypt<<<(unsigned)n, NTT_THREADS, smem, st>>>(tw, k.s_ntt, scores_ct + off * 4 * N,
+                                                          scores + off * N, m > off * N ? m - off * N : 0);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace hers

@@ -1,0 +1,180 @@
+"""GPU parity: the CUDA library against the CPU oracle, bit for bit.
+
+Every input is seeded and synthetic (workloads/).  Keys, probe and gallery
+ciphertexts, score ciphertexts and decrypted scores are compared element by
+element with the oracle run on the same seeds; decrypted scores are also
+compared with the plaintext inner products (Eq. 1), which holds at any size.
+Integer work: the tolerance is zero.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2003_12197_gb300 as H  # noqa: E402
+
+KEY_SEED, GAL_SEED, PRB_SEED, FEAT_SEED, MATE_SEED, NOISE_SEED = 1004, 1005, 1006, 1001, 1002, 1003
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    H.build_library()
+    c = H.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def keys(ctx):
+    k = H.hers_keygen(ctx, KEY_SEED)
+    yield k
+    k.close()
+
+
+@pytest.fixture(scope="module")
+def oracle_keys():
+    return O.keygen(KEY_SEED)
+
+
+def u64(t):
+    return H.to_u64(t)
+
+
+def run_search(ctx, keys, feats_np, q_np, gal_seed=GAL_SEED, prb_seed=PRB_SEED):
+    m, d = feats_np.shape
+    feats = torch.from_numpy(feats_np).cuda()
+    q = torch.from_numpy(q_np).cuda()
+    gal, gct = H.hers_encrypt_gallery(ctx, keys, feats, gal_seed, want_ct=True)
+    pct = H.hers_encrypt_probe(ctx, keys, q, prb_seed)
+    pr = H.hers_probe_prepare(ctx, pct)
+    nb = H.hers_blocks_for(m)
+    sc = H.hers_search(ctx, keys, gal, nb, d, pr)
+    scores = H.hers_decrypt_scores(ctx, keys, sc, m)
+    H.hers_check(ctx)
+    torch.cuda.synchronize()
+    return dict(gct=gct, pct=pct, sc=sc, scores=scores.cpu().numpy(), gal=gal, pr=pr, nb=nb)
+
+
+def test_keygen_bit_exact(ctx, keys, oracle_keys):
+    sk, pk, evk = H.hers_keys_export(ctx, keys)
+    osk, opk, oevk = oracle_keys
+    assert np.array_equal(sk, osk)
+    assert np.array_equal(pk, opk)
+    assert np.array_equal(evk, oevk)
+
+
+def test_keygen_other_seed_differs(ctx):
+    k2 = H.hers_keygen(ctx, KEY_SEED + 1)
+    sk, pk, _ = H.hers_keys_export(ctx, k2)
+    osk, opk, _ = O.keygen(KEY_SEED + 1)
+    assert np.array_equal(sk, osk) and np.array_equal(pk, opk)
+    k2.close()
+
+
+def test_probe_encryption_bit_exact(ctx, keys, oracle_keys):
+    d = 64
+    q = W.probe_for_mate(5, d, FEAT_SEED, NOISE_SEED)
+    pct = H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).cuda(), PRB_SEED)
+    want = O.encrypt_probe(oracle_keys[1], q, PRB_SEED)
+    assert np.array_equal(u64(pct), want)
+
+
+@pytest.fixture(scope="module")
+def config1(ctx, keys, oracle_keys):
+    """4,096 entries (one block), d = 64, one probe with a planted mate."""
+    n, d = 4096, 64
+    feats = W.gallery_features(n, d, FEAT_SEED)
+    mate = int(W.mate_indices(n, 1, MATE_SEED)[0])
+    q = W.probe_for_mate(mate, d, FEAT_SEED, NOISE_SEED)
+    res = run_search(ctx, keys, feats, q)
+    ogal = O.encrypt_gallery_block(oracle_keys[1], feats, 0, GAL_SEED)
+    oprb = O.encrypt_probe(oracle_keys[1], q, PRB_SEED)
+    osc, st = O.search_block(oprb, ogal, oracle_keys[2])
+    return dict(res=res, ogal=ogal, oprb=oprb, osc=osc, st=st, feats=feats, q=q, mate=mate)
+
+
+def test_config1_gallery_cts_bit_exact(config1):
+    assert np.array_equal(u64(config1["res"]["gct"])[0], config1["ogal"])
+
+
+def test_config1_score_ct_bit_exact(config1):
+    assert np.array_equal(u64(config1["res"]["sc"])[0], config1["osc"])
+
+
+def test_config1_scores_exact_and_top1(config1, oracle_keys):
+    scores = config1["res"]["scores"]
+    want = W.plain_inner_products(config1["feats"], config1["q"])
+    assert np.array_equal(scores.astype(np.int64), want)
+    oscores, _, _ = O.decrypt(oracle_keys[0], config1["osc"])
+    assert np.array_equal(scores.astype(np.int64), oscores)
+    assert int(np.argmax(scores)) == config1["mate"]
+
+
+@pytest.mark.parametrize("m,d", [(2 * 4096 + 1000, 16), (300, 200), (4096, 1), (1, 3)])
+def test_ragged_and_edge_sizes_bit_exact(ctx, keys, oracle_keys, m, d):
+    """Several blocks with a ragged tail, d > 128 (chunked accumulation), d = 1, m = 1."""
+    feats = W.gallery_features(m, d, FEAT_SEED + m + d)
+    q = W.probe_for_mate(m // 2, d, FEAT_SEED + m + d, NOISE_SEED)
+    res = run_search(ctx, keys, feats, q)
+    oprb = O.encrypt_probe(oracle_keys[1], q, PRB_SEED)
+    assert np.array_equal(u64(res["pct"]), oprb)
+    gct, sc = u64(res["gct"]), u64(res["sc"])
+    for b in range(res["nb"]):
+        ogal = O.encrypt_gallery_block(oracle_keys[1], feats, b, GAL_SEED)
+        assert np.array_equal(gct[b], ogal), f"gallery block {b}"
+        osc, st = O.search_block(oprb, ogal, oracle_keys[2])
+        assert np.array_equal(sc[b], osc), f"score block {b}"
+    assert np.array_equal(res["scores"].astype(np.int64), W.plain_inner_products(feats, q))
+
+
+def test_search_host_path_matches_device_path(ctx, keys, config1):
+    res = config1["res"]
+    nb, d = res["nb"], 64
+    ws = torch.empty(H.hers_search_host_workspace_bytes(nb, d) // 8, dtype=torch.int64,
+                     device="cuda")
+    pct_host = res["pct"].cpu().pin_memory()
+    out = torch.empty((nb, 2, 2, 4096), dtype=torch.int64).pin_memory()
+    H.hers_search_host(ctx, keys, res["gal"], nb, d, pct_host, out, ws)
+    assert np.array_equal(out.numpy().view(np.uint64), u64(res["sc"]))
+
+
+def test_repeat_search_is_deterministic(ctx, keys, config1):
+    res = config1["res"]
+    a = H.hers_search(ctx, keys, res["gal"], res["nb"], 64, res["pr"])
+    b = H.hers_search(ctx, keys, res["gal"], res["nb"], 64, res["pr"])
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(a, res["sc"])
+
+
+def test_invalid_arguments_are_rejected(ctx, keys):
+    with pytest.raises(H.HersError):
+        H.hers_encrypt_probe(ctx, keys, torch.zeros(0, dtype=torch.int8, device="cuda"), 1)
+    gal = torch.zeros(16, dtype=torch.int64, device="cuda")
+    with pytest.raises(H.HersError):
+        H.hers_search(ctx, keys, gal, 1, 64, gal, workspace=torch.zeros(8, dtype=torch.int64,
+                                                                         device="cuda"))
+
+
+@pytest.mark.slow
+def test_config2_full_size(ctx, keys, oracle_keys):
+    """1,048,576 entries (256 blocks), d = 64, one planted mate: every decrypted
+    score exact; sampled blocks' score ciphertexts bit-exact against the oracle."""
+    m, d = 1 << 20, 64
+    feats = W.gallery_features(m, d, FEAT_SEED)
+    mate = int(W.mate_indices(m, 1, MATE_SEED)[0])
+    q = W.probe_for_mate(mate, d, FEAT_SEED, NOISE_SEED)
+    res = run_search(ctx, keys, feats, q)
+    assert np.array_equal(res["scores"].astype(np.int64), W.plain_inner_products(feats, q))
+    assert int(np.argmax(res["scores"])) == mate
+    oprb = O.encrypt_probe(oracle_keys[1], q, PRB_SEED)
+    sc = u64(res["sc"])
+    for b in sorted({mate // 4096, res["nb"] - 1}):
+        ogal = O.encrypt_gallery_block(oracle_keys[1], feats, b, GAL_SEED)
+        osc, _ = O.search_block(oprb, ogal, oracle_keys[2])
+        assert np.array_equal(sc[b], osc), f"block {b}"
