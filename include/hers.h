@@ -22,9 +22,11 @@
  *    device, owned by the caller, who allocates them with the byte counts the
  *    hers_*_bytes() helpers give; pointers documented "host" are ordinary
  *    host memory, owned by the caller.  The library never frees caller memory.
- *  - stream: a cudaStream_t cast to void*, or NULL for the context's own
+ *  - stream: a cudaStream_t cast to void*; NULL is CUDA's default (legacy)
  *    stream.  Calls that only read/write device memory are asynchronous on
- *    that stream; calls that write host memory return after the data is there.
+ *    that stream, so the caller keeps their buffers alive until the stream
+ *    has run them; calls that write host memory return after the data is
+ *    there.  Synchronous calls (hers_keygen) use the context's own stream.
  *  - Canonical ciphertext ("ct"): uint64 [2 polys][2 limbs][N], coefficient
  *    domain, limb 0 holds residues mod q1 in [0, q1), limb 1 mod q2 in [0, q2).
  *    This is the form ciphertexts are exchanged and compared in.
@@ -173,8 +175,8 @@ uint64_t hers_search_host_workspace_bytes(uint64_t nblocks, uint32_t d);
 int hers_decrypt_scores(hers_ctx* ctx, const hers_keys* keys, const uint64_t* scores_ct,
                         uint64_t nblocks, int32_t* scores, uint64_t m, void* stream);
 
-/* Synchronises ctx's stream (or `stream`) and reports deferred device-side
- * errors (sampler exhaustion) as a status. */
+/* Synchronises `stream` and the context's own stream, then reports deferred
+ * device-side errors (sampler exhaustion) as a status. */
 int hers_check(hers_ctx* ctx, void* stream);
 
 /*
@@ -194,6 +196,16 @@ int hers_trace_read(hers_ctx* ctx, uint32_t* ncalls, double* avg_ms);
 
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t hers_kernel_launches(void);
+
+/*
+ * Diagnostic with no counterpart in the paper: sustained integer-pipe rate on
+ * `device`, in operations per second over all SMs, for op 0 = 32x32 -> 64-bit
+ * multiply-add (IMAD.WIDE.U32, the tensor kernel's inner operation), 1 =
+ * 32-bit multiply-add, 2 = high half of a 64x64-bit product (__umul64hi, the
+ * Shoup/Barrett step).  Runs one kernel of `iters` iterations per thread;
+ * allocates an 8-byte buffer for the duration of the call.
+ */
+int hers_probe_int_pipe(int device, uint32_t op, uint64_t iters, double* ops_per_s);
 
 #ifdef __cplusplus
 }

@@ -71,6 +71,7 @@ def lib():
                 "hers_trace_enable": ([vp, u32], i32),
                 "hers_trace_read": ([vp, vp, vp], i32),
                 "hers_kernel_launches": ([], u64),
+                "hers_probe_int_pipe": ([i32, u32, u64, vp], i32),
             }
             for name, (args, res) in sigs.items():
                 f = getattr(L, name)
@@ -255,8 +256,7 @@ def hers_decrypt_scores(ctx: Context, keys: Keys, scores_ct, m: int, out=None, s
 
 
 def hers_check(ctx: Context, stream=None):
-    ctx.check(lib().hers_check(ctx.h, _stream(stream) if stream is not None else None),
-              "hers_check")
+    ctx.check(lib().hers_check(ctx.h, _stream(stream)), "hers_check")
 
 
 TRACE_PHASES = ("tensor", "intt", "scale_round", "key_switch", "search")
@@ -276,6 +276,21 @@ def hers_trace_read(ctx: Context):
 
 def hers_kernel_launches():
     return int(lib().hers_kernel_launches())
+
+
+INT_PIPE_OPS = ("imad_wide_u32", "imad_u32", "umul64hi")
+
+
+def hers_probe_int_pipe(device: int = 0, iters: int = 1 << 16):
+    """{op name: operations per second} of the integer pipes on `device`."""
+    out = {}
+    for i, name in enumerate(INT_PIPE_OPS):
+        v = ctypes.c_double()
+        rc = lib().hers_probe_int_pipe(device, i, iters, ctypes.byref(v))
+        if rc != HERS_OK:
+            raise HersError(f"hers_probe_int_pipe({name}): {lib().hers_status_string(rc).decode()}")
+        out[name] = v.value
+    return out
 
 
 def to_u64(t):

@@ -96,9 +96,9 @@ struct DeviceGuard {
     }
 };
 
-cudaStream_t pick(hers_ctx* ctx, void* stream) {
-    return stream ? (cudaStream_t)stream : ctx->stream;
-}
+// The stream a call runs on: the caller's, where NULL is CUDA's default
+// (legacy) stream -- the stream PyTorch's default stream maps to.
+cudaStream_t pick(hers_ctx*, void* stream) { return (cudaStream_t)stream; }
 
 // Events of the next traced search call, or null when tracing is off / full.
 cudaEvent_t* next_trace(hers_ctx* ctx) {
@@ -220,12 +220,14 @@ int hers_check(hers_ctx* ctx, void* stream) {
     if (!ctx) return HERS_E_INVAL;
     DeviceGuard g(ctx->device);
     cudaError_t e = cudaStreamSynchronize(pick(ctx, stream));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
     int flag = 0;
     e = cudaMemcpy(&flag, ctx->err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "error flag read");
     if (flag) {
         cudaMemset(ctx->err, 0, sizeof(int));
+        if (flag & 2) return fail(ctx, HERS_E_TIMEOUT, "a bounded device-side wait gave up");
         return fail(ctx, HERS_E_SAMPLER, "a rejection sampler exhausted its attempts");
     }
     return HERS_OK;
@@ -339,7 +341,7 @@ int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
                     (unsigned long long)hers_search_workspace_bytes(nblocks));
     DeviceGuard g(ctx->device);
     cudaError_t e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, scores_ct,
-                                  (uint64_t*)workspace, pick(ctx, stream), next_trace(ctx));
+                                  (uint64_t*)workspace, ctx->err, pick(ctx, stream), next_trace(ctx));
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search");
 }
 
@@ -363,7 +365,8 @@ int hers_search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* galle
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, probe_ct, d, probe, st);
     if (e == cudaSuccess)
-        e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, out_dev, ws, st, next_trace(ctx));
+        e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, out_dev, ws, ctx->err, st,
+                          next_trace(ctx));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(scores_ct_host, out_dev, nblocks * 4 * N * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -39,9 +39,10 @@ constexpr uint64_t SEARCH_WS_WORDS_PER_BLOCK = (15 + 6 + 4) * 4096ull;
 // ev[0] before the tensor kernel, ev[1] after it, ev[2] after the inverse
 // NTTs, ev[3] after scale-and-round, ev[4] after the key switch.
 constexpr int SEARCH_EVENTS = 5;
+// `err` receives bit 2 if a bounded wait inside a streaming kernel gave up.
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
-                          uint64_t* ws, cudaStream_t st, cudaEvent_t* ev = nullptr);
+                          uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev = nullptr);
 
 // Kernel launches issued by this library in this process (all contexts).
 void count_launches(uint64_t n);

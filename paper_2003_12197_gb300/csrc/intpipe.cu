@@ -1,0 +1,71 @@
+// Integer-pipe throughput probe: the rates that bound the library's
+// ALU-limited kernels (NTT butterflies, the tensor accumulate once gallery
+// bytes are shared by many probes).  Each thread runs 8 independent
+// dependent chains of one operation; ops/s = threads * iters * 8 / time.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hers.h"
+#include "internal.h"
+
+namespace hers {
+
+template <int OP>
+__global__ void __launch_bounds__(256) k_intpipe(uint64_t iters, uint32_t c, uint64_t* sink) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t a[8];
+    uint32_t b[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        a[j] = (uint64_t)t * 0x9E3779B97F4A7C15ull + j;
+        b[j] = t * 2654435761u + j;
+    }
+    for (uint64_t i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            if (OP == 0) a[j] += (uint64_t)(uint32_t)a[j] * c;          // IMAD.WIDE.U32
+            else if (OP == 1) b[j] = b[j] * c + (uint32_t)j;            // IMAD (32-bit)
+            else a[j] = __umul64hi(a[j], a[j] | 1) + (uint64_t)c;       // 64x64 high half
+        }
+    }
+    uint64_t r = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) r ^= a[j] ^ b[j];
+    if (r == 0x123456789ull) sink[0] = r;  // keeps the chains live
+}
+
+}  // namespace hers
+
+extern "C" int hers_probe_int_pipe(int device, uint32_t op, uint64_t iters, double* ops_per_s) {
+    using namespace hers;
+    if (!ops_per_s || op > 2 || iters == 0) return HERS_E_INVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return HERS_E_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return HERS_E_CUDA;
+    const int blocks = sms * 8, threads = 256;
+    uint64_t* sink = nullptr;
+    cudaEvent_t e0, e1;
+    if (cudaMalloc(&sink, 8) != cudaSuccess) return HERS_E_NOMEM;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto launch = [&](uint64_t it) {
+        if (op == 0) k_intpipe<0><<<blocks, threads>>>(it, 0x9E3779B1u, sink);
+        else if (op == 1) k_intpipe<1><<<blocks, threads>>>(it, 0x9E3779B1u, sink);
+        else k_intpipe<2><<<blocks, threads>>>(it, 0x9E3779B1u, sink);
+    };
+    launch(iters / 8 + 1);  // warm-up
+    cudaEventRecord(e0);
+    launch(iters);
+    cudaEventRecord(e1);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    count_launches(2);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess || ms <= 0) return HERS_E_CUDA;
+    *ops_per_s = (double)blocks * threads * (double)iters * 8.0 / (ms * 1e-3);
+    return HERS_OK;
+}

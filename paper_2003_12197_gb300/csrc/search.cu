@@ -97,6 +97,156 @@ __global__ void __launch_bounds__(TENSOR_THREADS) k_tensor(const uint64_t* __res
             for (int c = 0; c < 3; c++) acc[(((b0 + j) * 3 + c) * 5 + l) * N + k] = fold[j][c];
 }
 
+// ---------------------------------------------------------------- tensor accumulate, TMA pipeline
+//
+// Same result as k_tensor, organised for HBM streaming on sm_103a:
+//  - CTA (tile, l, group): TT = 256 consumer threads, one coefficient each,
+//    for NB gallery blocks, plus one producer warp;
+//  - the producer's elected lane streams, per dimension i, the probe rows
+//    (2 polys x TT words) and the NB gallery rows (NB x 2 polys x TT words) into
+//    a STAGES-deep shared-memory ring with cp.async.bulk (2 KiB per row),
+//    completion tracked by one "full" mbarrier per stage; consumers release a
+//    stage through its "empty" mbarrier (one arrival per consumer warp);
+//  - consumers use two-level Karatsuba on the 27-bit digits: with
+//    x = xh 2^27 + xl,  x y = xh yh 2^54 + ((xh+xl)(yh+yl) - xh yh - xl yl) 2^27 + xl yl,
+//    and T1 = (A0+A1)(B0+B1) - T0 - T2, so each (dimension, coefficient, limb,
+//    block) costs 9 IMAD.WIDE.U32 instead of 16.  The largest partial product
+//    is (2^29)^2 = 2^58, so sums are folded mod p every KCHUNK = 32 dimensions.
+//  - a wait that exceeds WAIT_LIMIT polls sets *err and ends the thread's work.
+constexpr int TT = 256;
+constexpr int KCHUNK = 32;
+
+template <int NB, int STAGES>
+__global__ void __launch_bounds__(TT + 32) k_tensor_tma(const uint64_t* __restrict__ gal,
+                                                        const uint64_t* __restrict__ probe,
+                                                        uint64_t* __restrict__ acc,
+                                                        uint64_t nblocks, uint32_t d, int* err) {
+    extern __shared__ __align__(128) uint64_t sm[];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+    constexpr int ROWS = 2 + 2 * NB;  // rows of TT words per stage
+    const int tile = blockIdx.x, l = blockIdx.y;
+    const uint64_t b0 = (uint64_t)blockIdx.z * NB;
+    const int nb = (int)((nblocks - b0) < (uint64_t)NB ? (nblocks - b0) : NB);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t poly = (size_t)5 * N, ct = 2 * poly;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], TT / 32);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == TT / 32) {  // producer warp
+        if (lane == 0) {
+            const uint64_t pol_g = policy_evict_first(), pol_p = policy_evict_last();
+            const uint32_t bytes = (uint32_t)((2 + 2 * nb) * TT * 8);
+            const uint64_t* pb = probe + (size_t)l * N + (size_t)tile * TT;
+            const uint64_t* gb = gal + b0 * d * ct + (size_t)l * N + (size_t)tile * TT;
+            uint32_t issued = 0;
+            for (uint32_t i = 0; i < d; i++) {
+                const int st = (int)(i % STAGES);
+                if (i >= STAGES && !mbar_wait(&empty[st], ((i / STAGES) + 1) & 1)) {
+                    atomicOr(err, 2);
+                    break;
+                }
+                issued = i + 1;
+                uint64_t* dst = sm + (size_t)st * ROWS * TT;
+                mbar_expect_tx(&full[st], bytes);
+                bulk_g2s(dst, pb + (size_t)i * ct, TT * 8, &full[st], pol_p);
+                bulk_g2s(dst + TT, pb + (size_t)i * ct + poly, TT * 8, &full[st], pol_p);
+                for (int j = 0; j < nb; j++) {
+                    const uint64_t* g = gb + (size_t)j * d * ct + (size_t)i * ct;
+                    bulk_g2s(dst + (2 + 2 * j) * TT, g, TT * 8, &full[st], pol_g);
+                    bulk_g2s(dst + (3 + 2 * j) * TT, g + poly, TT * 8, &full[st], pol_g);
+                }
+            }
+            // drain: the copies of the last stages issued have landed before this
+            // thread leaves (bounded; consumers wait on the same phases)
+            for (uint32_t i = issued > STAGES ? issued - STAGES : 0; i < issued; i++)
+                if (!mbar_wait(&full[i % STAGES], (i / STAGES) & 1)) atomicOr(err, 2);
+        }
+        return;
+    }
+
+    // consumers
+    const int t = threadIdx.x;
+    const uint64_t p = c_mod[l];
+    uint64_t fold[NB][3];
+#pragma unroll
+    for (int j = 0; j < NB; j++) fold[j][0] = fold[j][1] = fold[j][2] = 0;
+    bool ok = true;
+    for (uint32_t i0 = 0; i0 < d && ok; i0 += KCHUNK) {
+        const uint32_t i1 = min(d, i0 + KCHUNK);
+        uint64_t s[NB][9];  // per block: LL0 HH0 MM0 | LL2 HH2 MM2 | LLk HHk MMk
+#pragma unroll
+        for (int j = 0; j < NB; j++)
+#pragma unroll
+            for (int r = 0; r < 9; r++) s[j][r] = 0;
+        for (uint32_t i = i0; i < i1; i++) {
+            const int st = (int)(i % STAGES);
+            if (!mbar_wait(&full[st], (i / STAGES) & 1)) {
+                atomicOr(err, 2);
+                ok = false;
+                break;
+            }
+            const uint64_t* row = sm + (size_t)st * ROWS * TT + t;
+            const uint64_t A0 = row[0], A1 = row[TT];
+            const uint32_t a0l = (uint32_t)A0, a0h = (uint32_t)(A0 >> 32);
+            const uint32_t a1l = (uint32_t)A1, a1h = (uint32_t)(A1 >> 32);
+            const uint32_t a0s = a0l + a0h, a1s = a1l + a1h;
+            const uint32_t sal = a0l + a1l, sah = a0h + a1h, sas = sal + sah;
+#pragma unroll
+            for (int j = 0; j < NB; j++) {
+                if (j < nb) {
+                    const uint64_t B0 = row[(2 + 2 * j) * TT], B1 = row[(3 + 2 * j) * TT];
+                    const uint32_t b0l = (uint32_t)B0, b0h = (uint32_t)(B0 >> 32);
+                    const uint32_t b1l = (uint32_t)B1, b1h = (uint32_t)(B1 >> 32);
+                    const uint32_t b0s = b0l + b0h, b1s = b1l + b1h;
+                    const uint32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
+                    s[j][0] += (uint64_t)a0l * b0l;
+                    s[j][1] += (uint64_t)a0h * b0h;
+                    s[j][2] += (uint64_t)a0s * b0s;
+                    s[j][3] += (uint64_t)a1l * b1l;
+                    s[j][4] += (uint64_t)a1h * b1h;
+                    s[j][5] += (uint64_t)a1s * b1s;
+                    s[j][6] += (uint64_t)sal * sbl;
+                    s[j][7] += (uint64_t)sah * sbh;
+                    s[j][8] += (uint64_t)sas * sbs;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+        }
+        // fold the chunk: value = LL + (MM - HH - LL) 2^27 + HH 2^54 (mod p)
+#pragma unroll
+        for (int j = 0; j < NB; j++) {
+            uint64_t v[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const uint64_t LL = s[j][3 * c], HH = s[j][3 * c + 1], MM = s[j][3 * c + 2];
+                v[c] = reduce64(shoup_lazy(LL, 1, c_one_s[l], p) +
+                                    shoup_lazy(MM - HH - LL, c_r27[l], c_r27_s[l], p) +
+                                    shoup_lazy(HH, c_r54[l], c_r54_s[l], p),
+                                l);
+            }
+            // T0 = v0, T2 = v1, T1 = K - T0 - T2 with K = v2
+            fold[j][0] = add_mod(fold[j][0], v[0], p);
+            fold[j][2] = add_mod(fold[j][2], v[1], p);
+            fold[j][1] = add_mod(fold[j][1], sub_mod(sub_mod(v[2], v[0], p), v[1], p), p);
+        }
+    }
+    if (!ok) return;
+    const int k = tile * TT + t;
+#pragma unroll
+    for (int j = 0; j < NB; j++)
+        if (j < nb)
+#pragma unroll
+            for (int c = 0; c < 3; c++) acc[(((b0 + j) * 3 + c) * 5 + l) * N + k] = fold[j][c];
+}
+
 // ---------------------------------------------------------------- batched NTTs
 // CTA per polynomial of a contiguous [npolys][N] array; modulus index
 // mod_off + (P % mod_period).
@@ -210,7 +360,7 @@ __global__ void __launch_bounds__(256) k_ks_finish(const uint64_t* __restrict__ 
 // Workspace per block: X [3][5][N] (reused for O [2][2][N]), C [3][2][N], KS [4][N].
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
-                          uint64_t* ws, cudaStream_t st, cudaEvent_t* ev) {
+                          uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev) {
     if (nblocks == 0) return cudaSuccess;
     uint64_t nl = 0;
     constexpr int NB = 2;
@@ -221,11 +371,16 @@ cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* 
     // grid.z is limited to 65535: process at most 65535 groups / blocks per pass
     const uint64_t max_z = 65535;
     if (ev) cudaEventRecord(ev[0], st);
+    constexpr int STAGES = 6;
+    const int smem = STAGES * (2 + 2 * NB) * TT * 8;
+    cudaError_t ea = cudaFuncSetAttribute(k_tensor_tma<NB, STAGES>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (ea != cudaSuccess) return ea;
     for (uint64_t g0 = 0; g0 < nblocks; g0 += max_z * NB) {
         const uint64_t nb = nblocks - g0 < max_z * NB ? nblocks - g0 : max_z * NB;
-        dim3 grid(N / TENSOR_THREADS, 5, (unsigned)((nb + NB - 1) / NB));
-        k_tensor<NB><<<grid, TENSOR_THREADS, 0, st>>>(gallery + g0 * d * 10 * N, probe,
-                                                       X + g0 * 15 * N, nb, d);
+        dim3 grid(N / TT, 5, (unsigned)((nb + NB - 1) / NB));
+        k_tensor_tma<NB, STAGES><<<grid, TT + 32, smem, st>>>(gallery + g0 * d * 10 * N, probe,
+                                                               X + g0 * 15 * N, nb, d, err);
         nl++;
     }
     if (ev) cudaEventRecord(ev[1], st);

@@ -178,3 +178,19 @@ def test_config2_full_size(ctx, keys, oracle_keys):
         ogal = O.encrypt_gallery_block(oracle_keys[1], feats, b, GAL_SEED)
         osc, _ = O.search_block(oprb, ogal, oracle_keys[2])
         assert np.array_equal(sc[b], osc), f"block {b}"
+
+
+def test_inline_temporaries_on_default_stream(ctx, keys):
+    """Inputs passed as temporaries: the library must run on the caller's stream
+    (here the default stream), so a freed input is not overwritten while it is read."""
+    m, d = 3 * 4096, 32
+    feats = W.gallery_features(m, d, 77)
+    q = W.probe_for_mate(5000, d, 77, 78)
+    gal, _ = H.hers_encrypt_gallery(ctx, keys, torch.from_numpy(feats).cuda(), GAL_SEED)
+    junk = [torch.full((m * d,), 7, dtype=torch.int8, device="cuda") for _ in range(4)]
+    pct = H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).cuda(), PRB_SEED)
+    junk += [torch.full((d,), -9, dtype=torch.int8, device="cuda") for _ in range(4)]
+    sc = H.hers_search(ctx, keys, gal, 3, d, H.hers_probe_prepare(ctx, pct))
+    scores = H.hers_decrypt_scores(ctx, keys, sc, m).cpu().numpy().astype(np.int64)
+    del junk
+    assert np.array_equal(scores, W.plain_inner_products(feats, q))
