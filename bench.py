@@ -25,9 +25,7 @@ import argparse
 import json
 import os
 import statistics
-import subprocess
 import sys
-import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -41,7 +39,7 @@ METRIC = "encrypted gallery entries scored/sec at N=4096, d=64 (bit-exact)"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--m", type=int, default=1 << 20, help="gallery entries per GPU")
@@ -90,50 +88,85 @@ class Dist:
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
-              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+    """SM clock, power and clock-event reasons of one GPU, polled through NVML
+    (read-only queries, ctypes) every 10 ms in a thread; summarised over the
+    samples taken inside the timed window [mark_start, mark_stop]."""
 
-    def __init__(self, index):
-        self.index = index
-        self.proc = None
-        self.path = None
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index):
+        import ctypes
+        import threading
+        self.samples, self.window = [], [None, None]
+        self.stop_ev = threading.Event()
+        self.thread = None
+        self.max_mhz = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            ok = False
+            try:
+                import torch
+                uuid = "GPU-" + str(torch.cuda.get_device_properties(cuda_index).uuid)
+                ok = nv.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) == 0
+            except Exception:
+                ok = False
+            if not ok:
+                cnt = ctypes.c_uint()
+                nv.nvmlDeviceGetCount_v2(ctypes.byref(cnt))
+                idx = 0 if cnt.value == 1 else cuda_index
+                if nv.nvmlDeviceGetHandleByIndex_v2(idx, ctypes.byref(h)) != 0:
+                    raise OSError("no NVML handle")
+            self.nv, self.h = nv, h
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = float(mx.value)
+            self.reason_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        except OSError:
+            self.nv = None
+
+    def _poll(self):
+        import ctypes
+        clk, pw, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop_ev.is_set():
+            t = time.perf_counter()
+            if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk)) == 0:
+                self.nv.nvmlDeviceGetPowerUsage(self.h, ctypes.byref(pw))
+                self.reason_fn(self.h, ctypes.byref(rs))
+                self.samples.append((t, float(clk.value), pw.value / 1e3, int(rs.value)))
+            time.sleep(0.01)
 
     def start(self):
-        fd, self.path = tempfile.mkstemp(suffix=".csv")
-        os.close(fd)
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-i", str(self.index), "-lms", "50"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
-        except (OSError, FileNotFoundError):
-            self.proc = None
+        import threading
+        if self.nv is None:
+            return
+        self.thread = threading.Thread(target=self._poll, daemon=True)
+        self.thread.start()
+
+    def mark_start(self):
+        self.window[0] = time.perf_counter()
+
+    def mark_stop(self):
+        self.window[1] = time.perf_counter()
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 11:
-                continue
-            rows.append(parts)
-        os.unlink(self.path)
-        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        busy = [float(r[2]) for r in rows if r[5].isdigit() and int(r[5]) > 50]
-        smax = max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[7 + i] == "Active"})
-        use = busy or sm
-        return {"sm_mhz": statistics.median(use) if use else None, "sm_max_mhz": smax,
-                "reasons": reasons, "samples": len(rows), "samples_busy": len(busy)}
+        if self.nv is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["NVML unavailable"]}
+        self.stop_ev.set()
+        self.thread.join(timeout=5)
+        t0, t1 = self.window
+        inside = [x for x in self.samples if t0 is not None and t0 <= x[0] <= (t1 or 1e30)]
+        use = inside or self.samples
+        reasons = sorted({name for x in use for bit, name in self.REASONS.items() if x[3] & bit})
+        return {"sm_mhz": statistics.median(x[1] for x in use) if use else None,
+                "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "power_w_max": max((x[2] for x in use), default=None),
+                "samples_in_timed_region": len(inside), "samples": len(self.samples),
+                "source": "NVML, 10 ms polling"}
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
@@ -148,9 +181,10 @@ def cpu_oracle_rate(d, blocks, budget_s=12.0):
     mate = int(W.mate_indices(blocks * N, 1, MATE_SEED)[0])
     q = W.probe_for_mate(mate, d, FEAT_SEED, NOISE_SEED)
     oprb = O.encrypt_probe(opk, q, PRB_SEED)
-    feats = W.gallery_features(min(blocks, 16) * N, d, FEAT_SEED)
+    nsample = min(blocks, 6)
+    feats = W.gallery_features(nsample * N, d, FEAT_SEED)
     done, t_search = 0, 0.0
-    for b in range(min(blocks, 16)):
+    for b in range(nsample):
         ogal = O.encrypt_gallery_block(opk, feats, b, GAL_SEED)
         t0 = time.perf_counter()
         O.search_block(oprb, ogal, oevk)
@@ -261,11 +295,13 @@ def run_gpu(args):
     dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark_start()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark_stop()
     dist.barrier()
     launches = H.hers_kernel_launches() - launches0
     ms_total = dist.max(e0.elapsed_time(e1), dev)
