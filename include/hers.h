@@ -150,6 +150,35 @@ int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
                 uint64_t workspace_bytes, void* stream);
 
 /*
+ * hers_search without caller-supplied scratch, for callers that cannot
+ * allocate device memory when they search: processes whose device memory is
+ * owned by another framework, plugins handed buffers but no allocator, and
+ * fixed-budget services that forbid allocation after start-up.  The paper
+ * has no counterpart; the result is the same as hers_search's.
+ *
+ * The scratch is one array of HERS_NOALLOC_MAX_BLOCKS * 800 KiB (6.25 MiB)
+ * compiled into the library.  Every GPU that loads the library holds it
+ * until the process exits.  The call itself allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).  The caller still
+ * passes the gallery, the probe and scores_ct (device, [nblocks][2][2][N]).
+ *  - nblocks above HERS_NOALLOC_MAX_BLOCKS is rejected with HERS_E_INVAL.
+ *    Larger galleries are searched by calling once per range of at most
+ *    that many blocks: gallery + b*d*10*N words, scores_ct + b*4*N words.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current.  Make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and leaves its contents behind.
+ *    Nothing in it needs to start at zero.  Calls that overlap on the GPU
+ *    (other streams, other contexts on the same device, other host threads)
+ *    race on it: serialise them.
+ * Asynchronous on stream (NULL = CUDA's default stream).
+ */
+#define HERS_NOALLOC_MAX_BLOCKS 8u
+int hers_search_noalloc(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
+                        uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
+                        void* stream);
+
+/*
  * End-to-end server step with host buffers: copies the probe's d canonical
  * cts from host memory (probe_ct_host, [d][2][2][N]) to the device, prepares
  * them, searches blocks [0, nblocks) and copies the score cts back to host

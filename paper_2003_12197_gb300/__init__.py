@@ -66,6 +66,7 @@ def lib():
                 "hers_probe_prepare": ([vp, vp, u32, vp, vp], i32),
                 "hers_search": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
                 "hers_search_host": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
+                "hers_search_noalloc": ([vp, vp, vp, u64, u32, vp, vp, vp], i32),
                 "hers_decrypt_scores": ([vp, vp, vp, u64, vp, u64, vp], i32),
                 "hers_check": ([vp, vp], i32),
                 "hers_trace_enable": ([vp, u32], i32),

@@ -16,28 +16,36 @@
 
 using namespace hers;
 
-struct hers_ctx {
-    int device;
-    cudaStream_t stream;
-    uint64_t* tw;   // device twiddle tables [6][4][N]
-    int* err;       // device flag: a sampler ran out of attempts
-    char msg[512];
-    // tracing: SEARCH_EVENTS events per traced hers_search call
-    std::vector<cudaEvent_t> tev;
-    uint32_t tcap = 0, tn = 0;
-};
 
 namespace hers {
 static std::atomic<uint64_t> g_launches{0};
 void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+int fail(hers_ctx* ctx, int code, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->msg, sizeof ctx->msg, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(hers_ctx* ctx, cudaError_t e, const char* where) {
+    return fail(ctx, HERS_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+DeviceGuard::DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+}
+DeviceGuard::~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+}
 }  // namespace hers
 
-struct hers_keys {
-    hers_ctx* ctx;
-    DevKeys k;
-    void* base;     // single device allocation holding every key array
-};
 
 namespace {
 
@@ -68,36 +76,6 @@ int h_brev(int x, int bits) {
     return r;
 }
 
-int fail(hers_ctx* ctx, int code, const char* fmt, ...) {
-    if (ctx) {
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(ctx->msg, sizeof ctx->msg, fmt, ap);
-        va_end(ap);
-    }
-    return code;
-}
-
-int cuda_fail(hers_ctx* ctx, cudaError_t e, const char* where) {
-    return fail(ctx, HERS_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
-}
-
-// Makes ctx's device current for the duration of a call.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
-// The stream a call runs on: the caller's, where NULL is CUDA's default
-// (legacy) stream -- the stream PyTorch's default stream maps to.
 cudaStream_t pick(hers_ctx*, void* stream) { return (cudaStream_t)stream; }
 
 // Events of the next traced search call, or null when tracing is off / full.

@@ -4,6 +4,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
+// The opaque context handle of include/hers.h.
+struct hers_ctx {
+    int device;
+    cudaStream_t stream;  // the context's own stream (synchronous calls)
+    uint64_t* tw;         // device twiddle tables [6][4][N]
+    int* err;             // device flag: 1 = a sampler ran out of attempts, 2 = a wait gave up
+    char msg[512];
+    // tracing: SEARCH_EVENTS events per traced hers_search call
+    std::vector<cudaEvent_t> tev;
+    uint32_t tcap = 0, tn = 0;
+};
+
 namespace hers {
 
 // Key material in device memory (all uint64 unless noted):
@@ -20,6 +34,26 @@ struct DevKeys {
     uint64_t* pk_ntt;
     uint64_t* evk_ntt;
     uint64_t* s_ntt;
+};
+}  // namespace hers
+
+// The opaque key handle of include/hers.h.
+struct hers_keys {
+    hers_ctx* ctx;
+    hers::DevKeys k;
+    void* base;  // single device allocation holding every key array
+};
+
+namespace hers {
+// Host helpers shared by the entry-point files.
+int fail(hers_ctx* ctx, int code, const char* fmt, ...);
+int cuda_fail(hers_ctx* ctx, cudaError_t e, const char* where);
+// Makes a device current for the duration of a call, restoring the previous one.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
 };
 
 // scheme.cu
