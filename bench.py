@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--m", type=int, default=1 << 20, help="gallery entries per GPU")
     ap.add_argument("--d", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", default=None,
+                    help="tensor-kernel shape by name (skips the autotuner), e.g. nb2_s2_d4_m2")
     return ap.parse_args()
 
 
@@ -273,6 +275,15 @@ def run_gpu(args):
     sc = torch.empty((nb, 2, 2, N), dtype=torch.int64, device=dev)
     H.hers_check(ctx)
 
+    # the autotuner picks the tensor-kernel shape for this workload (setup, untimed)
+    if args.variant:
+        variant = H.hers_tensor_variants().index(args.variant)
+        H.hers_set_tensor_variant(ctx, variant)
+        tune_ms = {}
+    else:
+        variant, tune_ms = H.hers_autotune(ctx, keys, gal, nb, d, pr, workspace=ws)
+    variant_name = H.hers_tensor_variants()[variant]
+
     # correctness of the benchmarked path: exact scores and the planted mate
     H.hers_search(ctx, keys, gal, nb, d, pr, out=sc, workspace=ws)
     scores = H.hers_decrypt_scores(ctx, keys, sc, m).cpu().numpy().astype(np.int64)
@@ -343,12 +354,14 @@ def run_gpu(args):
     alg_bytes = gal_bytes + probe_bytes + acc_bytes
     t_tensor = phases["tensor"] / 1e3
     achieved = alg_bytes / t_tensor / 1e9 if t_tensor > 0 else 0.0
+    # DRAM traffic of the same kernel shape from a committed ncu capture, scaled
+    # to this launch by blocks (null when no capture matches the current shape)
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic_k_tensor.json")
     if os.path.exists(prof):
         try:
             tj = json.load(open(prof))
-            if tj.get("nblocks") and tj.get("d") == d:
+            if tj.get("variant") == variant_name and tj.get("d") == d:
                 traffic = tj["bytes_per_block"] * nb + tj.get("bytes_fixed", 0)
         except (OSError, ValueError, KeyError):
             traffic = None
@@ -374,7 +387,10 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": "entries/s",
                     "h2d_bytes_per_step": d * 4 * N * 8, "d2h_bytes_per_step": nb * 4 * N * 8,
                     "bit_exact_vs_device": e2e_ok},
-            "roofline": {"kernel": "k_tensor (tensor-product accumulate over d)", "bound": "hbm",
+            "autotune": {"chosen": variant_name,
+                         "ms_per_variant": {k: round(v, 4) for k, v in tune_ms.items()}},
+            "roofline": {"kernel": f"k_tensor<{variant_name}> (tensor-product accumulate over d)",
+                         "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
                          "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes},

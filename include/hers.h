@@ -227,6 +227,24 @@ int hers_trace_read(hers_ctx* ctx, uint32_t* ncalls, double* avg_ms);
 uint64_t hers_kernel_launches(void);
 
 /*
+ * Autotuner (no counterpart in the paper).  The tensor-accumulate kernel comes
+ * in several shapes: gallery blocks per CTA, pipeline stages, dimensions per
+ * stage, CTAs per SM.  Every shape computes the same exact result.
+ * hers_autotune times each shape's kernel on the given search: 1 warm-up and
+ * 3 timed launches each on `stream`, minimum kept.  It keeps the fastest shape
+ * for later searches on ctx.  If ms_per_variant is non-null it receives
+ * hers_tensor_variants() timings in ms.  workspace: as for hers_search.
+ * Synchronous.  hers_set_tensor_variant selects a shape by index.
+ */
+int hers_tensor_variants(void);
+const char* hers_tensor_variant_name(int v);
+int hers_get_tensor_variant(const hers_ctx* ctx);
+int hers_set_tensor_variant(hers_ctx* ctx, int v);
+int hers_autotune(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
+                  uint32_t d, const uint64_t* probe, void* workspace, uint64_t workspace_bytes,
+                  void* stream, int* chosen, double* ms_per_variant);
+
+/*
  * Diagnostic with no counterpart in the paper: sustained integer-pipe rate on
  * `device`, in operations per second over all SMs, for op 0 = 32x32 -> 64-bit
  * multiply-add (IMAD.WIDE.U32, the tensor kernel's inner operation), 1 =

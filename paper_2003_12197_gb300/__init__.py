@@ -73,6 +73,11 @@ def lib():
                 "hers_trace_read": ([vp, vp, vp], i32),
                 "hers_kernel_launches": ([], u64),
                 "hers_probe_int_pipe": ([i32, u32, u64, vp], i32),
+                "hers_tensor_variants": ([], i32),
+                "hers_tensor_variant_name": ([i32], ctypes.c_char_p),
+                "hers_get_tensor_variant": ([vp], i32),
+                "hers_set_tensor_variant": ([vp, i32], i32),
+                "hers_autotune": ([vp, vp, vp, u64, u32, vp, vp, u64, vp, vp, vp], i32),
             }
             for name, (args, res) in sigs.items():
                 f = getattr(L, name)
@@ -277,6 +282,35 @@ def hers_trace_read(ctx: Context):
 
 def hers_kernel_launches():
     return int(lib().hers_kernel_launches())
+
+
+def hers_tensor_variants():
+    """Names of the tensor-kernel shapes, by index."""
+    L = lib()
+    return [L.hers_tensor_variant_name(i).decode() for i in range(L.hers_tensor_variants())]
+
+
+def hers_get_tensor_variant(ctx: Context) -> int:
+    return int(lib().hers_get_tensor_variant(ctx.h))
+
+
+def hers_set_tensor_variant(ctx: Context, v: int):
+    ctx.check(lib().hers_set_tensor_variant(ctx.h, v), "hers_set_tensor_variant")
+
+
+def hers_autotune(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, probe, workspace=None,
+                  stream=None):
+    """Times every tensor-kernel shape on this search, keeps the fastest on ctx.
+    Returns (chosen index, {name: ms})."""
+    names = hers_tensor_variants()
+    ws = workspace if workspace is not None else _words(hers_search_workspace_bytes(nblocks),
+                                                        gallery.device)
+    chosen = ctypes.c_int()
+    ms = (ctypes.c_double * len(names))()
+    ctx.check(lib().hers_autotune(ctx.h, keys.h, _ptr(gallery), nblocks, d, _ptr(probe), _ptr(ws),
+                                  ws.numel() * 8, _stream(stream), ctypes.byref(chosen), ms),
+              "hers_autotune")
+    return int(chosen.value), dict(zip(names, list(ms)))
 
 
 INT_PIPE_OPS = ("imad_wide_u32", "imad_u32", "umul64hi")

@@ -282,7 +282,7 @@ int hers_encrypt_gallery(hers_ctx* ctx, const hers_keys* keys, const int8_t* fea
         const uint64_t n = nct - c0 < chunk ? nct - c0 : chunk;
         uint64_t* ct = gallery_ct ? gallery_ct + c0 * 4 * N : tmp;
         e = launch_encrypt(ctx->tw, keys->k, feats, m, d, c0, n, false, seed, ct, ctx->err, st);
-        if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, ct, n, gallery + c0 * 10 * N, st);
+        if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, ct, n, c0, d, gallery, st);
     }
     if (tmp) cudaFreeAsync(tmp, st);
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_encrypt_gallery");
@@ -303,7 +303,7 @@ int hers_probe_prepare(hers_ctx* ctx, const uint64_t* probe_ct, uint32_t d, uint
     if (!ctx || !probe_ct || !probe) return fail(ctx, HERS_E_INVAL, "hers_probe_prepare: null argument");
     if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_probe_prepare: d = %u", d);
     DeviceGuard g(ctx->device);
-    cudaError_t e = launch_extend_ntt(ctx->tw, probe_ct, d, probe, pick(ctx, stream));
+    cudaError_t e = launch_extend_ntt(ctx->tw, probe_ct, d, 0, d, probe, pick(ctx, stream));
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_probe_prepare");
 }
 
@@ -319,7 +319,8 @@ int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
                     (unsigned long long)hers_search_workspace_bytes(nblocks));
     DeviceGuard g(ctx->device);
     cudaError_t e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, scores_ct,
-                                  (uint64_t*)workspace, ctx->err, pick(ctx, stream), next_trace(ctx));
+                                  (uint64_t*)workspace, ctx->err, pick(ctx, stream), next_trace(ctx),
+                                  ctx->tensor_variant);
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search");
 }
 
@@ -341,10 +342,10 @@ int hers_search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* galle
     uint64_t* out_dev = probe + (uint64_t)d * 10 * N;
     cudaError_t e = cudaMemcpyAsync(probe_ct, probe_ct_host, (uint64_t)d * 4 * N * 8,
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, probe_ct, d, probe, st);
+    if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, probe_ct, d, 0, d, probe, st);
     if (e == cudaSuccess)
         e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, out_dev, ws, ctx->err, st,
-                          next_trace(ctx));
+                          next_trace(ctx), ctx->tensor_variant);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(scores_ct_host, out_dev, nblocks * 4 * N * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -405,5 +406,65 @@ int hers_trace_read(hers_ctx* ctx, uint32_t* ncalls, double* avg_ms) {
 }
 
 uint64_t hers_kernel_launches(void) { return launches_total(); }
+
+int hers_tensor_variants(void) { return tensor_variant_count(); }
+
+const char* hers_tensor_variant_name(int v) {
+    const char* n = tensor_variant_name(v);
+    return n ? n : "";
+}
+
+int hers_get_tensor_variant(const hers_ctx* ctx) { return ctx ? ctx->tensor_variant : -1; }
+
+int hers_set_tensor_variant(hers_ctx* ctx, int v) {
+    if (!ctx) return HERS_E_INVAL;
+    if (v < 0 || v >= tensor_variant_count())
+        return fail(ctx, HERS_E_INVAL, "hers_set_tensor_variant: %d not in [0, %d)", v,
+                    tensor_variant_count());
+    ctx->tensor_variant = v;
+    return HERS_OK;
+}
+
+int hers_autotune(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
+                  uint32_t d, const uint64_t* probe, void* workspace, uint64_t workspace_bytes,
+                  void* stream, int* chosen, double* ms_per_variant) {
+    if (!ctx || !keys || !gallery || !probe || !workspace || nblocks == 0)
+        return fail(ctx, HERS_E_INVAL, "hers_autotune: null argument or no blocks");
+    if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_autotune: d = %u", d);
+    if (workspace_bytes < hers_search_workspace_bytes(nblocks))
+        return fail(ctx, HERS_E_NOMEM, "hers_autotune: workspace too small");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick(ctx, stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(ctx, HERS_E_CUDA, "hers_autotune: event creation");
+    int best = -1;
+    float best_ms = 0;
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < tensor_variant_count() && e == cudaSuccess; v++) {
+        e = launch_tensor(v, gallery, nblocks, d, probe, (uint64_t*)workspace, ctx->err, st);  // warm
+        float vbest = 0;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; rep++) {
+            cudaEventRecord(e0, st);
+            e = launch_tensor(v, gallery, nblocks, d, probe, (uint64_t*)workspace, ctx->err, st);
+            cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 0 || ms < vbest) vbest = ms;
+        }
+        if (ms_per_variant) ms_per_variant[v] = vbest;
+        if (e == cudaSuccess && (best < 0 || vbest < best_ms)) {
+            best = v;
+            best_ms = vbest;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_autotune");
+    ctx->tensor_variant = best;
+    if (chosen) *chosen = best;
+    return HERS_OK;
+}
 
 }  // extern "C"

@@ -38,7 +38,19 @@ static __constant__ uint64_t c_delta_s[2] = HERS_DELTA_MOD_Q_S_INIT;
 static __constant__ uint64_t c_chi_cdt[CHI_LEN] = HERS_CHI_CDT_INIT;
 
 constexpr uint64_t T_PLAIN = 4169729ULL;
-constexpr int NTT_THREADS = 512;          // threads of every one-polynomial-per-CTA kernel
+
+// Resident (search) form of ciphertexts: NTT domain over the five primes, split
+// storage, tiled so that everything one search CTA streams is contiguous:
+//   [block][limb][tile][dim][poly][TILE]   (TILE coefficients per tile)
+// A gallery block occupies 10 d N words; a prepared probe is block 0 of it.
+constexpr int TILE = 256;
+constexpr int NTILES = N / TILE;
+__host__ __device__ __forceinline__ uint64_t resident_offset(uint64_t b, int limb, int k, uint32_t d,
+                                                             uint32_t i, int poly) {
+    return ((((b * 5 + (uint64_t)limb) * NTILES + (uint64_t)(k / TILE)) * d + i) * 2 + (uint64_t)poly) *
+               TILE +
+           (uint64_t)(k % TILE);
+}
 constexpr uint32_t MASK27 = (1u << 27) - 1;
 
 // Twiddle table of modulus i inside the table buffer the context owns:
@@ -99,6 +111,10 @@ __device__ __forceinline__ uint64_t split_load(uint64_t s) {
 }
 
 __device__ __forceinline__ int brev12(int x) { return (int)(__brev((unsigned)x) >> (32 - LOGN)); }
+
+// Word of coefficient x of a polynomial held in shared memory (swizzled order,
+// see the NTT section below).
+__device__ __forceinline__ int swz(int x) { return x ^ ((x >> 4) & 15); }
 
 // ---------------------------------------------------------------- ChaCha20 (RFC 8439, Sec. 2.3)
 
@@ -179,7 +195,8 @@ __device__ __forceinline__ int chi_from_word(uint64_t U) {
     return CHI_MIN + c;
 }
 
-// Fill out[0..N) with a ternary polynomial as residues mod p (-1 -> p - 1).
+// Fill the shared-memory polynomial out (swizzled order) with a ternary
+// polynomial as residues mod p (-1 -> p - 1).
 // All threads of the CTA call this; the block stream is split over threads.
 __device__ __forceinline__ void sample_ternary_mod(uint64_t seed, uint32_t purpose, uint64_t obj,
                                                    uint64_t p, uint64_t* out, int* err) {
@@ -193,25 +210,13 @@ __device__ __forceinline__ void sample_ternary_mod(uint64_t seed, uint32_t purpo
             if (blk[j] < 0xFFFFFFFFu) v = (int)(blk[j] % 3u) - 1;
             else v = ternary_slow(seed, purpose, obj, k);
             if (v == -2) { atomicOr(err, 1); v = 0; }
-            out[k] = v < 0 ? p - 1 : (uint64_t)v;
+            out[swz(k)] = v < 0 ? p - 1 : (uint64_t)v;
         }
     }
 }
 
-// Fill out[0..N) with a chi sample (signed small values).
-__device__ __forceinline__ void sample_chi(uint64_t seed, uint32_t purpose, uint64_t obj, int* out) {
-    for (int c = threadIdx.x; c < N / 8; c += blockDim.x) {
-        uint32_t blk[16];
-        chacha20(seed, purpose, obj, (uint32_t)c, blk);
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            uint64_t U = ((uint64_t)blk[2 * j + 1] << 32) | blk[2 * j];
-            out[8 * c + j] = chi_from_word(U);
-        }
-    }
-}
-
-// Fill out[0..N) with a uniform polynomial mod p.
+// Fill the shared-memory polynomial out (swizzled order) with a uniform
+// polynomial mod p.
 __device__ __forceinline__ void sample_uniform(uint64_t seed, uint32_t purpose, uint64_t obj,
                                                uint64_t p, uint64_t* out, int* err) {
     for (int c = threadIdx.x; c < N / 8; c += blockDim.x) {
@@ -225,70 +230,149 @@ __device__ __forceinline__ void sample_uniform(uint64_t seed, uint32_t purpose, 
                 v = uniform_slow(seed, purpose, obj, k, p);
                 if (v == ~0ull) { atomicOr(err, 1); v = 0; }
             }
-            out[k] = v;
+            out[swz(k)] = v;
         }
     }
 }
 
 // ---------------------------------------------------------------- NTT (one polynomial in smem)
 //
-// Forward: Cooley-Tukey over the negacyclic ring with psi-powers in
-// bit-reversed order; input a[0..N) with residues < p (any value < 2p is
-// fine), output in bit-reversed order, fully reduced.  Output index j is the
-// evaluation at psi^(2 brev(j) + 1).  Values are kept lazily in [0, 4p)
-// between stages (p < 2^54 leaves ample headroom).  All threads of the CTA
-// must call it; it starts and ends with __syncthreads().
+// Negacyclic NTT of one N = 4096 polynomial held in shared memory by a CTA of
+// NTT_THREADS = 256 threads, 16 coefficients per thread.  The twelve radix-2
+// stages run as three phases of four stages on registers:
+//   phase A: thread t holds x = t + 256 a        (stages with distance 2048 .. 256)
+//   phase B: thread t holds x = 256 (t/16) + (t%16) + 16 a   (distance 128 .. 16)
+//   phase C: thread t holds x = 16 t + a         (distance 8 .. 1),   a = 0..15.
+// Between A and B the CTA synchronises; B and C exchange data only inside
+// groups of 16 threads (half a warp), so a __syncwarp suffices.
+//
+// Polynomials live in shared memory in swizzled order: coefficient x is at
+// word swz(x) = x ^ ((x >> 4) & 15).  Every access pattern used here and in
+// the kernels (t + 256 a, t + 512 a, the three phases) then touches each bank
+// at most twice per warp, the minimum for 32 8-byte words.
+//
+// Forward: Cooley-Tukey with psi-powers in bit-reversed order; input residues
+// < 2p, output fully reduced in bit-reversed order: index j holds the
+// evaluation at psi^(2 brev(j) + 1).  Values stay below 4p between stages.
+// Inverse: Gentleman-Sande with inverse psi-powers; bit-reversed input < 2p,
+// natural-order output times N^-1, fully reduced.
+// All NTT_THREADS threads must call these; they begin and end with a barrier.
+constexpr int NTT_THREADS = 256;
 
-__device__ __forceinline__ void ntt_fwd_smem(uint64_t* a, const uint64_t* __restrict__ w,
-                                             const uint64_t* __restrict__ ws, uint64_t p) {
+template <int STRIDE>
+__device__ __forceinline__ void ct_phase(uint64_t v[16], int base, const uint64_t* __restrict__ w,
+                                         const uint64_t* __restrict__ ws, uint64_t p) {
     const uint64_t two_p = 2 * p;
-    __syncthreads();
-#pragma unroll 1
-    for (int lg = LOGN - 1, m = 1; lg >= 0; lg--, m <<= 1) {
-        const int tt = 1 << lg;
-        for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
-            const int i = b >> lg;
-            const int j = (i << (lg + 1)) + (b & (tt - 1));
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {
+        const int t = STRIDE * h;       // butterfly distance
+        const int m = N / (2 * t);      // groups in this stage
+#pragma unroll
+        for (int a = 0; a < 16; a++) {
+            if (a & h) continue;
+            const int i = (base + STRIDE * a) / (2 * t);
             const uint64_t W = __ldg(w + m + i), Ws = __ldg(ws + m + i);
-            uint64_t U = a[j];
+            uint64_t U = v[a];
             U = U >= two_p ? U - two_p : U;
-            const uint64_t V = shoup_lazy(a[j + tt], W, Ws, p);
-            a[j] = U + V;
-            a[j + tt] = U - V + two_p;
+            const uint64_t V = shoup_lazy(v[a + h], W, Ws, p);
+            v[a] = U + V;
+            v[a + h] = U - V + two_p;
         }
-        __syncthreads();
     }
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        uint64_t x = a[k];
-        x = x >= two_p ? x - two_p : x;
-        a[k] = csub(x, p);
+}
+
+template <int STRIDE>
+__device__ __forceinline__ void gs_phase(uint64_t v[16], int base, const uint64_t* __restrict__ w,
+                                         const uint64_t* __restrict__ ws, uint64_t p) {
+    const uint64_t two_p = 2 * p;
+#pragma unroll
+    for (int h = 1; h <= 8; h <<= 1) {
+        const int t = STRIDE * h;
+        const int m = N / (2 * t);
+#pragma unroll
+        for (int a = 0; a < 16; a++) {
+            if (a & h) continue;
+            const int i = (base + STRIDE * a) / (2 * t);
+            const uint64_t W = __ldg(w + m + i), Ws = __ldg(ws + m + i);
+            const uint64_t U = v[a], V = v[a + h];
+            const uint64_t S = U + V;
+            v[a] = S >= two_p ? S - two_p : S;
+            v[a + h] = shoup_lazy(U - V + two_p, W, Ws, p);
+        }
+    }
+}
+
+__device__ __forceinline__ void ntt_fwd_smem(uint64_t* sm, const uint64_t* __restrict__ w,
+                                             const uint64_t* __restrict__ ws, uint64_t p) {
+    const int t = threadIdx.x;
+    uint64_t v[16];
+    __syncthreads();
+    {   // phase A
+        const int base = t;
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz(base + 256 * a)];
+        ct_phase<256>(v, base, w, ws, p);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz(base + 256 * a)] = v[a];
+    }
+    __syncthreads();
+    {   // phase B
+        const int base = 256 * (t >> 4) + (t & 15);
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz(base + 16 * a)];
+        ct_phase<16>(v, base, w, ws, p);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz(base + 16 * a)] = v[a];
+    }
+    __syncwarp();
+    {   // phase C, then full reduction
+        const int base = 16 * t;
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz(base + a)];
+        ct_phase<1>(v, base, w, ws, p);
+        const uint64_t two_p = 2 * p;
+#pragma unroll
+        for (int a = 0; a < 16; a++) {
+            uint64_t x = v[a];
+            x = x >= two_p ? x - two_p : x;
+            sm[swz(base + a)] = csub(x, p);
+        }
     }
     __syncthreads();
 }
 
-// Inverse: Gentleman-Sande with inverse psi-powers in bit-reversed order,
-// bit-reversed input (< 2p), natural-order output multiplied by N^-1, fully
-// reduced.
-__device__ __forceinline__ void ntt_inv_smem(uint64_t* a, const uint64_t* __restrict__ w,
+__device__ __forceinline__ void ntt_inv_smem(uint64_t* sm, const uint64_t* __restrict__ w,
                                              const uint64_t* __restrict__ ws, uint64_t p,
                                              uint64_t ninv, uint64_t ninv_s) {
-    const uint64_t two_p = 2 * p;
+    const int t = threadIdx.x;
+    uint64_t v[16];
     __syncthreads();
-#pragma unroll 1
-    for (int lg = 0, m = N / 2; lg < LOGN; lg++, m >>= 1) {
-        const int tt = 1 << lg;
-        for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
-            const int i = b >> lg;
-            const int j = (i << (lg + 1)) + (b & (tt - 1));
-            const uint64_t W = __ldg(w + m + i), Ws = __ldg(ws + m + i);
-            const uint64_t U = a[j], V = a[j + tt];
-            uint64_t S = U + V;
-            a[j] = S >= two_p ? S - two_p : S;
-            a[j + tt] = shoup_lazy(U - V + two_p, W, Ws, p);
-        }
-        __syncthreads();
+    {   // phase C pattern first (distances 1 .. 8)
+        const int base = 16 * t;
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz(base + a)];
+        gs_phase<1>(v, base, w, ws, p);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz(base + a)] = v[a];
     }
-    for (int k = threadIdx.x; k < N; k += blockDim.x) a[k] = shoup(a[k], ninv, ninv_s, p);
+    __syncwarp();
+    {   // distances 16 .. 128
+        const int base = 256 * (t >> 4) + (t & 15);
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz(base + 16 * a)];
+        gs_phase<16>(v, base, w, ws, p);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz(base + 16 * a)] = v[a];
+    }
+    __syncthreads();
+    {   // distances 256 .. 2048, then N^-1
+        const int base = t;
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz(base + 256 * a)];
+        gs_phase<256>(v, base, w, ws, p);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz(base + 256 * a)] = shoup(v[a], ninv, ninv_s, p);
+    }
     __syncthreads();
 }
 
@@ -297,6 +381,14 @@ __device__ __forceinline__ void ntt_fwd_mod(uint64_t* a, const uint64_t* tw, int
 }
 __device__ __forceinline__ void ntt_inv_mod(uint64_t* a, const uint64_t* tw, int i) {
     ntt_inv_smem(a, tw_inv(tw, i), tw_inv_s(tw, i), c_mod[i], c_ninv[i], c_ninv_s[i]);
+}
+// Out-of-line versions for kernels that run several NTTs among other work:
+// each call then gets its own register allocation.
+static __device__ __noinline__ void ntt_fwd_call(uint64_t* a, const uint64_t* tw, int i) {
+    ntt_fwd_mod(a, tw, i);
+}
+static __device__ __noinline__ void ntt_inv_call(uint64_t* a, const uint64_t* tw, int i) {
+    ntt_inv_mod(a, tw, i);
 }
 
 // ---------------------------------------------------------------- mbarrier + bulk async copy (TMA engine)

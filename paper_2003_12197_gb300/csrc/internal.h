@@ -16,6 +16,7 @@ struct hers_ctx {
     // tracing: SEARCH_EVENTS events per traced hers_search call
     std::vector<cudaEvent_t> tev;
     uint32_t tcap = 0, tn = 0;
+    int tensor_variant = 1;  // tensor-kernel shape used by searches on this context
 };
 
 namespace hers {
@@ -61,8 +62,10 @@ cudaError_t launch_keygen(const uint64_t* tw, uint64_t seed, DevKeys k, int* err
 cudaError_t launch_encrypt(const uint64_t* tw, const DevKeys& k, const int8_t* feats, uint64_t m,
                            uint32_t d, uint64_t ct_begin, uint64_t nct, bool probe, uint64_t seed,
                            uint64_t* out_ct, int* err, cudaStream_t st);
-cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t* out,
-                              cudaStream_t st);
+// Canonical cts ct[0 .. nct) (global indices ct_begin ..) of dimension d into
+// the resident form at `out` (the base of block 0).
+cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t ct_begin,
+                              uint32_t d, uint64_t* out, cudaStream_t st);
 cudaError_t launch_decrypt(const uint64_t* tw, const DevKeys& k, const uint64_t* scores_ct,
                            uint64_t nblocks, int32_t* scores, uint64_t m, cudaStream_t st);
 
@@ -74,9 +77,17 @@ constexpr uint64_t SEARCH_WS_WORDS_PER_BLOCK = (15 + 6 + 4) * 4096ull;
 // NTTs, ev[3] after scale-and-round, ev[4] after the key switch.
 constexpr int SEARCH_EVENTS = 5;
 // `err` receives bit 2 if a bounded wait inside a streaming kernel gave up.
+// `variant` selects the tensor-kernel shape (see tensor_variant_name).
+constexpr int DEFAULT_TENSOR_VARIANT = 1;
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
-                          uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev = nullptr);
+                          uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev = nullptr,
+                          int variant = DEFAULT_TENSOR_VARIANT);
+// The tensor kernel alone, into X [nblocks][3][5][N].
+cudaError_t launch_tensor(int variant, const uint64_t* gallery, uint64_t nblocks, uint32_t d,
+                          const uint64_t* probe, uint64_t* X, int* err, cudaStream_t st);
+int tensor_variant_count();
+const char* tensor_variant_name(int v);
 
 // Kernel launches issued by this library in this process (all contexts).
 void count_launches(uint64_t n);

@@ -60,6 +60,6 @@ extern "C" int hers_search_noalloc(hers_ctx* ctx, const hers_keys* keys, const u
     // launch_search writes every scratch word it later reads, so the contents
     // left by the previous call need no clearing.
     e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, scores_ct, ws, ctx->err,
-                      (cudaStream_t)stream);
+                      (cudaStream_t)stream, nullptr, ctx->tensor_variant);
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search_noalloc");
 }

@@ -18,7 +18,7 @@ __device__ __forceinline__ uint64_t shoup_companion(uint64_t w, uint64_t p) {
 //   c0 = [-(a s + e) + g_j s^2]_{q_l},  c1 = a,
 // with g_j = 1 mod q_j and 0 mod the other prime, so the s^2 term appears only
 // in the limb l = j.  Products use the NTT mod q_l (exact ring arithmetic mod q_l).
-__global__ void __launch_bounds__(NTT_THREADS) k_keygen(const uint64_t* __restrict__ tw,
+__global__ void __launch_bounds__(NTT_THREADS, 2) k_keygen(const uint64_t* __restrict__ tw,
                                                         uint64_t seed, DevKeys K, int* err) {
     extern __shared__ uint64_t sm[];
     uint64_t* S = sm;
@@ -31,12 +31,12 @@ __global__ void __launch_bounds__(NTT_THREADS) k_keygen(const uint64_t* __restri
     __syncthreads();
     if (limb == 0 && comp == 0)
         for (int k = threadIdx.x; k < N; k += blockDim.x)
-            K.sk[k] = S[k] == 0 ? 0 : (S[k] == 1 ? 1 : -1);
-    ntt_fwd_mod(S, tw, limb);
+            K.sk[k] = S[swz(k)] == 0 ? 0 : (S[swz(k)] == 1 ? 1 : -1);
+    ntt_fwd_call(S, tw, limb);
     if (comp == 0)
         for (int k = threadIdx.x; k < N; k += blockDim.x) {
-            K.s_ntt[(limb * 2 + 0) * N + k] = S[k];
-            K.s_ntt[(limb * 2 + 1) * N + k] = shoup_companion(S[k], p);
+            K.s_ntt[(limb * 2 + 0) * N + k] = S[swz(k)];
+            K.s_ntt[(limb * 2 + 1) * N + k] = shoup_companion(S[swz(k)], p);
         }
 
     const uint32_t pa = comp == 0 ? PRF_KG_PK_A : PRF_KG_EVK_A;
@@ -45,15 +45,16 @@ __global__ void __launch_bounds__(NTT_THREADS) k_keygen(const uint64_t* __restri
     __syncthreads();
     // canonical output: [2 polys][2 limbs][N] for pk, [j][2][2][N] for evk_j
     uint64_t* outc = comp == 0 ? K.pk : K.evk + (size_t)(comp - 1) * 4 * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) outc[(2 + limb) * N + k] = A[k];
-    ntt_fwd_mod(A, tw, limb);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) outc[(2 + limb) * N + k] = A[swz(k)];
+    ntt_fwd_call(A, tw, limb);
     const bool gadget = comp >= 1 && (comp - 1) == limb;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        A[k] = mul_mod(A[k], S[k], limb);
-        if (gadget) X[k] = mul_mod(S[k], S[k], limb);
+        const int x = swz(k);
+        A[x] = mul_mod(A[x], S[x], limb);
+        if (gadget) X[x] = mul_mod(S[x], S[x], limb);
     }
-    ntt_inv_mod(A, tw, limb);
-    if (gadget) ntt_inv_mod(X, tw, limb);  // uniform per CTA
+    ntt_inv_call(A, tw, limb);
+    if (gadget) ntt_inv_call(X, tw, limb);  // uniform per CTA
 
     // e from its stream; 8 coefficients per ChaCha block
     const uint32_t pe = comp == 0 ? PRF_KG_PK_E : PRF_KG_EVK_E;
@@ -65,9 +66,9 @@ __global__ void __launch_bounds__(NTT_THREADS) k_keygen(const uint64_t* __restri
         for (int j = 0; j < 8; j++) {
             const int k = 8 * c + j;
             const int e = chi_from_word(((uint64_t)blk[2 * j + 1] << 32) | blk[2 * j]);
-            uint64_t v = add_mod(A[k], e < 0 ? p - (uint64_t)(-e) : (uint64_t)e, p);
+            uint64_t v = add_mod(A[swz(k)], e < 0 ? p - (uint64_t)(-e) : (uint64_t)e, p);
             v = v == 0 ? 0 : p - v;  // -(a s + e)
-            if (gadget) v = add_mod(v, X[k], p);
+            if (gadget) v = add_mod(v, X[swz(k)], p);
             outc[limb * N + k] = v;
         }
     }
@@ -81,11 +82,11 @@ __global__ void __launch_bounds__(NTT_THREADS) k_key_ntt(const uint64_t* __restr
     extern __shared__ uint64_t sm[];
     const int P = blockIdx.x, limb = P & 1;
     const uint64_t p = c_mod[limb];
-    for (int k = threadIdx.x; k < N; k += blockDim.x) sm[k] = in[(size_t)P * N + k];
-    ntt_fwd_mod(sm, tw, limb);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) sm[swz(k)] = in[(size_t)P * N + k];
+    ntt_fwd_call(sm, tw, limb);
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        out[((size_t)P * 2 + 0) * N + k] = sm[k];
-        out[((size_t)P * 2 + 1) * N + k] = shoup_companion(sm[k], p);
+        out[((size_t)P * 2 + 0) * N + k] = sm[swz(k)];
+        out[((size_t)P * 2 + 1) * N + k] = shoup_companion(sm[swz(k)], p);
     }
 }
 
@@ -111,7 +112,7 @@ cudaError_t launch_keygen(const uint64_t* tw, uint64_t seed, DevKeys k, int* err
 //     puts at index brev(j), so m = INTT_t of the slots placed at brev(j).
 // Randomness: u, e1, e2 are the streams (seed, base + 0/1/2, obj) with
 // obj = b d + i (gallery) or i (probe).
-__global__ void __launch_bounds__(NTT_THREADS) k_encrypt(const uint64_t* __restrict__ tw,
+__global__ void __launch_bounds__(NTT_THREADS, 2) k_encrypt(const uint64_t* __restrict__ tw,
                                                          const uint64_t* __restrict__ pk_ntt,
                                                          const int8_t* __restrict__ feats,
                                                          uint64_t m, uint32_t d, uint64_t ct_begin,
@@ -131,47 +132,52 @@ __global__ void __launch_bounds__(NTT_THREADS) k_encrypt(const uint64_t* __restr
     if (probe) {
         const int v = feats[c];
         const uint64_t mv = v < 0 ? T_PLAIN - (uint64_t)(-v) : (uint64_t)v;
-        for (int k = threadIdx.x; k < N; k += blockDim.x) M[k] = k == 0 ? mv : 0;
+        for (int k = threadIdx.x; k < N; k += blockDim.x) M[swz(k)] = k == 0 ? mv : 0;
     } else {
         const uint64_t b = c / d, i = c % d;
         for (int s = threadIdx.x; s < N; s += blockDim.x) {
             const uint64_t e = b * N + (uint64_t)s;
             const int v = e < m ? feats[e * d + i] : 0;
-            M[brev12(s)] = v < 0 ? T_PLAIN - (uint64_t)(-v) : (uint64_t)v;
+            M[swz(brev12(s))] = v < 0 ? T_PLAIN - (uint64_t)(-v) : (uint64_t)v;
         }
-        ntt_inv_mod(M, tw, MOD_T);
+        ntt_inv_call(M, tw, MOD_T);
     }
 
     // u, NTT, products with the public key
     sample_ternary_mod(seed, base + 0, obj, p, U, err);
-    ntt_fwd_mod(U, tw, limb);
+    ntt_fwd_call(U, tw, limb);
     const uint64_t* pk0 = pk_ntt + (size_t)((0 * 2 + limb) * 2) * N;
     const uint64_t* pk1 = pk_ntt + (size_t)((1 * 2 + limb) * 2) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const uint64_t u = U[k];
-        B[k] = shoup(u, pk1[k], pk1[N + k], p);
-        U[k] = shoup(u, pk0[k], pk0[N + k], p);
+        const int x = swz(k);
+        const uint64_t u = U[x];
+        B[x] = shoup(u, pk1[k], pk1[N + k], p);
+        U[x] = shoup(u, pk0[k], pk0[N + k], p);
     }
-    ntt_inv_mod(U, tw, limb);
-    ntt_inv_mod(B, tw, limb);
+    ntt_inv_call(U, tw, limb);
+    ntt_inv_call(B, tw, limb);
 
     // add Delta m + e1 and e2, write the canonical ciphertext limb
     uint64_t* o0 = out + ((size_t)blockIdx.x * 4 + 0 * 2 + limb) * N;
     uint64_t* o1 = out + ((size_t)blockIdx.x * 4 + 1 * 2 + limb) * N;
     for (int cb = threadIdx.x; cb < N / 8; cb += blockDim.x) {
-        uint32_t b1[16], b2[16];
-        chacha20(seed, base + 1, obj, (uint32_t)cb, b1);
-        chacha20(seed, base + 2, obj, (uint32_t)cb, b2);
+        uint32_t blk[16];
+        chacha20(seed, base + 1, obj, (uint32_t)cb, blk);
 #pragma unroll
         for (int j = 0; j < 8; j++) {
             const int k = 8 * cb + j;
-            const int e1 = chi_from_word(((uint64_t)b1[2 * j + 1] << 32) | b1[2 * j]);
-            const int e2 = chi_from_word(((uint64_t)b2[2 * j + 1] << 32) | b2[2 * j]);
-            uint64_t v0 = add_mod(U[k], shoup(M[k], c_delta[limb], c_delta_s[limb], p), p);
-            v0 = e1 < 0 ? sub_mod(v0, (uint64_t)(-e1), p) : add_mod(v0, (uint64_t)e1, p);
-            uint64_t v1 = e2 < 0 ? sub_mod(B[k], (uint64_t)(-e2), p) : add_mod(B[k], (uint64_t)e2, p);
-            o0[k] = v0;
-            o1[k] = v1;
+            const int e1 = chi_from_word(((uint64_t)blk[2 * j + 1] << 32) | blk[2 * j]);
+            const int x = swz(k);
+            uint64_t v0 = add_mod(U[x], shoup(M[x], c_delta[limb], c_delta_s[limb], p), p);
+            o0[k] = e1 < 0 ? sub_mod(v0, (uint64_t)(-e1), p) : add_mod(v0, (uint64_t)e1, p);
+        }
+        chacha20(seed, base + 2, obj, (uint32_t)cb, blk);
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int k = 8 * cb + j;
+            const int e2 = chi_from_word(((uint64_t)blk[2 * j + 1] << 32) | blk[2 * j]);
+            const uint64_t x1 = B[swz(k)];
+            o1[k] = e2 < 0 ? sub_mod(x1, (uint64_t)(-e2), p) : add_mod(x1, (uint64_t)e2, p);
         }
     }
 }
@@ -194,14 +200,16 @@ cudaError_t launch_encrypt(const uint64_t* tw, const DevKeys& k, const int8_t* f
 
 // ---------------------------------------------------------------- extension to the search form
 //
-// Grid (2 nct polys, 5 limbs).  Reads a canonical ciphertext polynomial
+// Grid (2 n polys, 5 limbs).  Reads a canonical ciphertext polynomial
 // (residues mod q1, q2), takes its centred representative x in (-q/2, q/2]
 // (App. A) and writes NTT_{p_l}(x mod p_l) for l = 0..4 in split storage
-// (high 27 bits << 32 | low 27 bits), layout [nct][2 polys][5 limbs][N].
-// Exactness of the later tensor product needs the centred lift: the product
-// of two such polynomials over Z is then below q P / 2 (|X| < 2^235).
-__global__ void __launch_bounds__(NTT_THREADS) k_extend_ntt(const uint64_t* __restrict__ tw,
+// (high 27 bits << 32 | low 27 bits) at the resident (tiled) position of
+// ciphertext ct_begin + P/2 = b d + i.  Exactness of the later tensor product
+// needs the centred lift: the product of two such polynomials over Z, summed
+// over d <= 512 dimensions, stays below q P / 2 (|X| < 2^237).
+__global__ void __launch_bounds__(NTT_THREADS, 2) k_extend_ntt(const uint64_t* __restrict__ tw,
                                                             const uint64_t* __restrict__ ct,
+                                                            uint64_t ct_begin, uint32_t d,
                                                             uint64_t* __restrict__ out) {
     extern __shared__ uint64_t sm[];
     const uint64_t P = blockIdx.x;
@@ -210,20 +218,24 @@ __global__ void __launch_bounds__(NTT_THREADS) k_extend_ntt(const uint64_t* __re
     const uint64_t* x2 = ct + (P * 2 + 1) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const uint64_t a = x1[k], b = x2[k];
-        sm[k] = lifted_mod(lift_q(a, b), limb, b);
+        sm[swz(k)] = lifted_mod(lift_q(a, b), limb, b);
     }
-    ntt_fwd_mod(sm, tw, limb);
-    uint64_t* o = out + (P * 5 + limb) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) o[k] = split_store(sm[k]);
+    ntt_fwd_call(sm, tw, limb);
+    const uint64_t c = ct_begin + P / 2;
+    const uint64_t blk = c / d;
+    const uint32_t i = (uint32_t)(c % d);
+    const int poly = (int)(P & 1);
+    for (int k = threadIdx.x; k < N; k += blockDim.x)
+        out[resident_offset(blk, limb, k, d, i, poly)] = split_store(sm[swz(k)]);
 }
 
-cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t* out,
-                              cudaStream_t st) {
+cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t ct_begin,
+                              uint32_t d, uint64_t* out, cudaStream_t st) {
     const uint64_t chunk = 1u << 30;
     for (uint64_t off = 0; off < 2 * nct; off += chunk) {
         const uint64_t n = 2 * nct - off < chunk ? 2 * nct - off : chunk;
         k_extend_ntt<<<dim3((unsigned)n, 5), NTT_THREADS, N * 8, st>>>(tw, ct + off * 2 * N,
-                                                                      out + off * 5 * N);
+                                                                      ct_begin + off / 2, d, out);
         count_launches(1);
     }
     return cudaGetLastError();
@@ -235,7 +247,7 @@ cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t n
 // pt = round(t v / q) mod t computed exactly as pt = [-r q^-1]_t with
 // r = [t v]_q centred (t v = q pt' + r, |r| < q/2, so pt' = (t v - r)/q);
 // slots = NTT_t(pt), slot j at index brev(j), centred mod t.
-__global__ void __launch_bounds__(NTT_THREADS) k_decrypt(const uint64_t* __restrict__ tw,
+__global__ void __launch_bounds__(NTT_THREADS, 2) k_decrypt(const uint64_t* __restrict__ tw,
                                                          const uint64_t* __restrict__ s_ntt,
                                                          const uint64_t* __restrict__ cts,
                                                          int32_t* __restrict__ scores, uint64_t m) {
@@ -248,27 +260,27 @@ __global__ void __launch_bounds__(NTT_THREADS) k_decrypt(const uint64_t* __restr
     for (int l = 0; l < 2; l++) {
         uint64_t* V = l ? V1 : V0;
         const uint64_t p = c_mod[l];
-        for (int k = threadIdx.x; k < N; k += blockDim.x) V[k] = ct[(2 + l) * N + k];
-        ntt_fwd_mod(V, tw, l);
+        for (int k = threadIdx.x; k < N; k += blockDim.x) V[swz(k)] = ct[(2 + l) * N + k];
+        ntt_fwd_call(V, tw, l);
         const uint64_t* s = s_ntt + (size_t)l * 2 * N;
-        for (int k = threadIdx.x; k < N; k += blockDim.x) V[k] = shoup(V[k], s[k], s[N + k], p);
-        ntt_inv_mod(V, tw, l);
-        for (int k = threadIdx.x; k < N; k += blockDim.x) V[k] = add_mod(V[k], ct[l * N + k], p);
+        for (int k = threadIdx.x; k < N; k += blockDim.x) V[swz(k)] = shoup(V[swz(k)], s[k], s[N + k], p);
+        ntt_inv_call(V, tw, l);
+        for (int k = threadIdx.x; k < N; k += blockDim.x) V[swz(k)] = add_mod(V[swz(k)], ct[l * N + k], p);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const uint64_t a1 = shoup(V0[k], T_PLAIN, c_t_s[0], c_mod[0]);
-        const uint64_t a2 = shoup(V1[k], T_PLAIN, c_t_s[1], c_mod[1]);
+        const uint64_t a1 = shoup(V0[swz(k)], T_PLAIN, c_t_s[0], c_mod[0]);
+        const uint64_t a2 = shoup(V1[swz(k)], T_PLAIN, c_t_s[1], c_mod[1]);
         const Lifted L = lift_q(a1, a2);
         uint64_t r = (a1 % T_PLAIN + mul_mod_t(Q1_MOD_T, L.h % T_PLAIN)) % T_PLAIN;
         if (L.neg) r = (r + T_PLAIN - Q_MOD_T) % T_PLAIN;
-        PT[k] = mul_mod_t((T_PLAIN - r) % T_PLAIN, QINV_T);
+        PT[swz(k)] = mul_mod_t((T_PLAIN - r) % T_PLAIN, QINV_T);
     }
-    ntt_fwd_mod(PT, tw, MOD_T);
+    ntt_fwd_call(PT, tw, MOD_T);
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         const uint64_t e = b * N + (uint64_t)brev12(j);
         if (e < m) {
-            const uint64_t v = PT[j];
+            const uint64_t v = PT[swz(j)];
             scores[e] = v > (T_PLAIN - 1) / 2 ? (int32_t)((int64_t)v - (int64_t)T_PLAIN) : (int32_t)v;
         }
     }

@@ -15,158 +15,81 @@ namespace hers {
 
 // ---------------------------------------------------------------- tensor accumulate
 //
-// Thread (k, l) of CTA (tile, l, group) owns coefficient k of limb l for NB
-// consecutive gallery blocks.  Operands are split-stored (a = ah 2^27 + al,
-// 27-bit halves), so every partial product is one 32x32 -> 64-bit
-// multiply-add on the integer pipe, accumulated without reduction:
-//   T0 = sum a0 b0,  T1 = sum (a0 b1 + a1 b0),  T2 = sum a1 b1
-// each kept as (lo, mid, hi) with value lo + mid 2^27 + hi 2^54.  A
-// partial product is < 2^54 and mid of T1 takes 4 per dimension, so 128
-// dimensions fit in 64 bits; longer sums are folded mod p every 128.
-constexpr int TENSOR_THREADS = 256;
-constexpr int TENSOR_CHUNK = 128;
-
-template <int NB>
-__global__ void __launch_bounds__(TENSOR_THREADS) k_tensor(const uint64_t* __restrict__ gal,
-                                                           const uint64_t* __restrict__ probe,
-                                                           uint64_t* __restrict__ acc,
-                                                           uint64_t nblocks, uint32_t d) {
-    const int k = blockIdx.x * TENSOR_THREADS + threadIdx.x;
-    const int l = blockIdx.y;
-    const uint64_t b0 = (uint64_t)blockIdx.z * NB;
-    const uint64_t p = c_mod[l];
-    const size_t poly = (size_t)5 * N;  // stride between the two polys of a ct
-    const size_t ct = 2 * poly;         // stride between cts
-
-    int nb = (int)((nblocks - b0) < (uint64_t)NB ? (nblocks - b0) : NB);
-    uint64_t fold[NB][3];
-#pragma unroll
-    for (int j = 0; j < NB; j++) fold[j][0] = fold[j][1] = fold[j][2] = 0;
-
-    const uint64_t* pa = probe + (size_t)l * N + k;
-    const uint64_t* ga = gal + (b0 * d) * ct + (size_t)l * N + k;
-    const size_t gstride = (size_t)d * ct;  // between consecutive gallery blocks
-
-    for (uint32_t i0 = 0; i0 < d; i0 += TENSOR_CHUNK) {
-        const uint32_t i1 = min(d, i0 + TENSOR_CHUNK);
-        uint64_t s[NB][9];
-#pragma unroll
-        for (int j = 0; j < NB; j++)
-#pragma unroll
-            for (int r = 0; r < 9; r++) s[j][r] = 0;
-#pragma unroll 2
-        for (uint32_t i = i0; i < i1; i++) {
-            const uint64_t A0 = __ldg(pa + (size_t)i * ct), A1 = __ldg(pa + (size_t)i * ct + poly);
-            const uint32_t a0l = (uint32_t)A0, a0h = (uint32_t)(A0 >> 32);
-            const uint32_t a1l = (uint32_t)A1, a1h = (uint32_t)(A1 >> 32);
-#pragma unroll
-            for (int j = 0; j < NB; j++) {
-                if (j < nb) {
-                    const uint64_t* g = ga + j * gstride + (size_t)i * ct;
-                    const uint64_t B0 = __ldcs(g), B1 = __ldcs(g + poly);
-                    const uint32_t b0l = (uint32_t)B0, b0h = (uint32_t)(B0 >> 32);
-                    const uint32_t b1l = (uint32_t)B1, b1h = (uint32_t)(B1 >> 32);
-                    s[j][0] += (uint64_t)a0l * b0l;
-                    s[j][1] += (uint64_t)a0l * b0h + (uint64_t)a0h * b0l;
-                    s[j][2] += (uint64_t)a0h * b0h;
-                    s[j][3] += (uint64_t)a0l * b1l + (uint64_t)a1l * b0l;
-                    s[j][4] += (uint64_t)a0l * b1h + (uint64_t)a0h * b1l + (uint64_t)a1l * b0h +
-                               (uint64_t)a1h * b0l;
-                    s[j][5] += (uint64_t)a0h * b1h + (uint64_t)a1h * b0h;
-                    s[j][6] += (uint64_t)a1l * b1l;
-                    s[j][7] += (uint64_t)a1l * b1h + (uint64_t)a1h * b1l;
-                    s[j][8] += (uint64_t)a1h * b1h;
-                }
-            }
-        }
-        // fold: value = lo + mid 2^27 + hi 2^54 mod p
-#pragma unroll
-        for (int j = 0; j < NB; j++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                uint64_t v = shoup_lazy(s[j][3 * c + 0], 1, c_one_s[l], p) +
-                             shoup_lazy(s[j][3 * c + 1], c_r27[l], c_r27_s[l], p) +
-                             shoup_lazy(s[j][3 * c + 2], c_r54[l], c_r54_s[l], p) + fold[j][c];
-                fold[j][c] = reduce64(v, l);  // v < 7p
-            }
-    }
-#pragma unroll
-    for (int j = 0; j < NB; j++)
-        if (j < nb)
-#pragma unroll
-            for (int c = 0; c < 3; c++) acc[(((b0 + j) * 3 + c) * 5 + l) * N + k] = fold[j][c];
-}
-
-// ---------------------------------------------------------------- tensor accumulate, TMA pipeline
+// X_k = sum_i tensor_k(probe_i, gallery_i^b) for k = 0, 1, 2, per (block,
+// limb, coefficient), in the NTT domain (pointwise), exactly mod p_l:
+//   T0 = sum a0 b0,  T1 = sum (a0 b1 + a1 b0),  T2 = sum a1 b1.
 //
-// Same result as k_tensor, organised for HBM streaming on sm_103a:
-//  - CTA (tile, l, group): TT = 256 consumer threads, one coefficient each,
-//    for NB gallery blocks, plus one producer warp;
-//  - the producer's elected lane streams, per dimension i, the probe rows
-//    (2 polys x TT words) and the NB gallery rows (NB x 2 polys x TT words) into
-//    a STAGES-deep shared-memory ring with cp.async.bulk (2 KiB per row),
-//    completion tracked by one "full" mbarrier per stage; consumers release a
-//    stage through its "empty" mbarrier (one arrival per consumer warp);
-//  - consumers use two-level Karatsuba on the 27-bit digits: with
-//    x = xh 2^27 + xl,  x y = xh yh 2^54 + ((xh+xl)(yh+yl) - xh yh - xl yl) 2^27 + xl yl,
-//    and T1 = (A0+A1)(B0+B1) - T0 - T2, so each (dimension, coefficient, limb,
-//    block) costs 9 IMAD.WIDE.U32 instead of 16.  The largest partial product
-//    is (2^29)^2 = 2^58, so sums are folded mod p every KCHUNK = 32 dimensions.
-//  - a wait that exceeds WAIT_LIMIT polls sets *err and ends the thread's work.
-constexpr int TT = 256;
+// Organisation (sm_103a): CTA (tile, l, group) has TILE consumer threads, one
+// coefficient each, for NB gallery blocks, plus one producer warp.  In the
+// resident layout everything a CTA reads is contiguous: the probe's
+// [dim][poly][TILE] run and one such run per block.  The producer's elected
+// lane streams DPS dimensions per stage with one cp.async.bulk per run into a
+// STAGES-deep shared-memory ring; "full" mbarriers track the copies and
+// "empty" mbarriers (one arrival per consumer warp) hand stages back.
+//
+// Arithmetic: operands are split-stored 27-bit digits, x = xh 2^27 + xl, and
+//   x y = xh yh 2^54 + ((xh+xl)(yh+yl) - xh yh - xl yl) 2^27 + xl yl,
+//   T1 = (a0+a1)(b0+b1) - T0 - T2,
+// so each (dimension, coefficient, limb, block) costs 9 32x32->64 multiply-adds
+// (mad.wide.u32) into 64-bit sums without reduction.  The largest partial
+// product is (2^29)^2 = 2^58, so the sums are folded mod p every KCHUNK = 32
+// dimensions.  A wait that exceeds WAIT_LIMIT polls sets bit 2 of *err.
 constexpr int KCHUNK = 32;
 
-template <int NB, int STAGES>
-__global__ void __launch_bounds__(TT + 32) k_tensor_tma(const uint64_t* __restrict__ gal,
-                                                        const uint64_t* __restrict__ probe,
-                                                        uint64_t* __restrict__ acc,
-                                                        uint64_t nblocks, uint32_t d, int* err) {
+__device__ __forceinline__ void madw(uint64_t& acc, uint32_t a, uint32_t b) {
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+template <int NB, int STAGES, int DPS, int MINB>
+__global__ void __launch_bounds__(TILE + 32, MINB)
+    k_tensor(const uint64_t* __restrict__ gal, const uint64_t* __restrict__ probe,
+             uint64_t* __restrict__ acc, uint64_t nblocks, uint32_t d, int* err) {
+    static_assert(KCHUNK % DPS == 0, "stages must not straddle a fold");
     extern __shared__ __align__(128) uint64_t sm[];
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
-    constexpr int ROWS = 2 + 2 * NB;  // rows of TT words per stage
+    constexpr int RUN = DPS * 2 * TILE;         // words of one run per stage
+    constexpr int STAGE_WORDS = (1 + NB) * RUN;
     const int tile = blockIdx.x, l = blockIdx.y;
     const uint64_t b0 = (uint64_t)blockIdx.z * NB;
     const int nb = (int)((nblocks - b0) < (uint64_t)NB ? (nblocks - b0) : NB);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const size_t poly = (size_t)5 * N, ct = 2 * poly;
+    const uint32_t nst = (d + DPS - 1) / DPS;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], TT / 32);
+            mbar_init(&empty[s], TILE / 32);
         }
         mbar_fence_init();
     }
     __syncthreads();
 
-    if (warp == TT / 32) {  // producer warp
+    if (warp == TILE / 32) {  // producer warp
         if (lane == 0) {
             const uint64_t pol_g = policy_evict_first(), pol_p = policy_evict_last();
-            const uint32_t bytes = (uint32_t)((2 + 2 * nb) * TT * 8);
-            const uint64_t* pb = probe + (size_t)l * N + (size_t)tile * TT;
-            const uint64_t* gb = gal + b0 * d * ct + (size_t)l * N + (size_t)tile * TT;
+            const uint64_t* pr = probe + resident_offset(0, l, tile * TILE, d, 0, 0);
+            const uint64_t* gr = gal + resident_offset(b0, l, tile * TILE, d, 0, 0);
+            const size_t gstride = (size_t)10 * d * N;  // words per gallery block
             uint32_t issued = 0;
-            for (uint32_t i = 0; i < d; i++) {
-                const int st = (int)(i % STAGES);
-                if (i >= STAGES && !mbar_wait(&empty[st], ((i / STAGES) + 1) & 1)) {
+            for (uint32_t si = 0; si < nst; si++) {
+                const int st = (int)(si % STAGES);
+                if (si >= STAGES && !mbar_wait(&empty[st], ((si / STAGES) + 1) & 1)) {
                     atomicOr(err, 2);
                     break;
                 }
-                issued = i + 1;
-                uint64_t* dst = sm + (size_t)st * ROWS * TT;
-                mbar_expect_tx(&full[st], bytes);
-                bulk_g2s(dst, pb + (size_t)i * ct, TT * 8, &full[st], pol_p);
-                bulk_g2s(dst + TT, pb + (size_t)i * ct + poly, TT * 8, &full[st], pol_p);
-                for (int j = 0; j < nb; j++) {
-                    const uint64_t* g = gb + (size_t)j * d * ct + (size_t)i * ct;
-                    bulk_g2s(dst + (2 + 2 * j) * TT, g, TT * 8, &full[st], pol_g);
-                    bulk_g2s(dst + (3 + 2 * j) * TT, g + poly, TT * 8, &full[st], pol_g);
-                }
+                issued = si + 1;
+                const uint32_t nd = min((uint32_t)DPS, d - si * DPS);
+                const uint32_t bytes = nd * 2 * TILE * 8;
+                uint64_t* dst = sm + (size_t)st * STAGE_WORDS;
+                mbar_expect_tx(&full[st], bytes * (uint32_t)(1 + nb));
+                bulk_g2s(dst, pr + (size_t)si * RUN, bytes, &full[st], pol_p);
+                for (int j = 0; j < nb; j++)
+                    bulk_g2s(dst + (1 + j) * RUN, gr + j * gstride + (size_t)si * RUN, bytes, &full[st],
+                             pol_g);
             }
-            // drain: the copies of the last stages issued have landed before this
-            // thread leaves (bounded; consumers wait on the same phases)
-            for (uint32_t i = issued > STAGES ? issued - STAGES : 0; i < issued; i++)
-                if (!mbar_wait(&full[i % STAGES], (i / STAGES) & 1)) atomicOr(err, 2);
+            // drain: the last stages' copies land before this thread leaves
+            for (uint32_t si = issued > STAGES ? issued - STAGES : 0; si < issued; si++)
+                if (!mbar_wait(&full[si % STAGES], (si / STAGES) & 1)) atomicOr(err, 2);
         }
         return;
     }
@@ -177,74 +100,119 @@ __global__ void __launch_bounds__(TT + 32) k_tensor_tma(const uint64_t* __restri
     uint64_t fold[NB][3];
 #pragma unroll
     for (int j = 0; j < NB; j++) fold[j][0] = fold[j][1] = fold[j][2] = 0;
-    bool ok = true;
-    for (uint32_t i0 = 0; i0 < d && ok; i0 += KCHUNK) {
-        const uint32_t i1 = min(d, i0 + KCHUNK);
-        uint64_t s[NB][9];  // per block: LL0 HH0 MM0 | LL2 HH2 MM2 | LLk HHk MMk
+    uint64_t s[NB][9];  // per block: LL0 HH0 MM0 | LL2 HH2 MM2 | LLk HHk MMk
 #pragma unroll
-        for (int j = 0; j < NB; j++)
+    for (int j = 0; j < NB; j++)
 #pragma unroll
-            for (int r = 0; r < 9; r++) s[j][r] = 0;
-        for (uint32_t i = i0; i < i1; i++) {
-            const int st = (int)(i % STAGES);
-            if (!mbar_wait(&full[st], (i / STAGES) & 1)) {
-                atomicOr(err, 2);
-                ok = false;
-                break;
-            }
-            const uint64_t* row = sm + (size_t)st * ROWS * TT + t;
-            const uint64_t A0 = row[0], A1 = row[TT];
-            const uint32_t a0l = (uint32_t)A0, a0h = (uint32_t)(A0 >> 32);
-            const uint32_t a1l = (uint32_t)A1, a1h = (uint32_t)(A1 >> 32);
-            const uint32_t a0s = a0l + a0h, a1s = a1l + a1h;
-            const uint32_t sal = a0l + a1l, sah = a0h + a1h, sas = sal + sah;
+        for (int r = 0; r < 9; r++) s[j][r] = 0;
+    for (uint32_t si = 0; si < nst; si++) {
+        const int st = (int)(si % STAGES);
+        if (!mbar_wait(&full[st], (si / STAGES) & 1)) {
+            atomicOr(err, 2);
+            return;
+        }
+        const uint32_t nd = min((uint32_t)DPS, d - si * DPS);
+        const uint64_t* base = sm + (size_t)st * STAGE_WORDS + t;
 #pragma unroll
-            for (int j = 0; j < NB; j++) {
-                if (j < nb) {
-                    const uint64_t B0 = row[(2 + 2 * j) * TT], B1 = row[(3 + 2 * j) * TT];
-                    const uint32_t b0l = (uint32_t)B0, b0h = (uint32_t)(B0 >> 32);
-                    const uint32_t b1l = (uint32_t)B1, b1h = (uint32_t)(B1 >> 32);
-                    const uint32_t b0s = b0l + b0h, b1s = b1l + b1h;
-                    const uint32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
-                    s[j][0] += (uint64_t)a0l * b0l;
-                    s[j][1] += (uint64_t)a0h * b0h;
-                    s[j][2] += (uint64_t)a0s * b0s;
-                    s[j][3] += (uint64_t)a1l * b1l;
-                    s[j][4] += (uint64_t)a1h * b1h;
-                    s[j][5] += (uint64_t)a1s * b1s;
-                    s[j][6] += (uint64_t)sal * sbl;
-                    s[j][7] += (uint64_t)sah * sbh;
-                    s[j][8] += (uint64_t)sas * sbs;
+        for (int dd = 0; dd < DPS; dd++) {
+            if ((uint32_t)dd < nd) {
+                const uint64_t A0 = base[dd * 2 * TILE], A1 = base[dd * 2 * TILE + TILE];
+                const uint32_t a0l = (uint32_t)A0, a0h = (uint32_t)(A0 >> 32);
+                const uint32_t a1l = (uint32_t)A1, a1h = (uint32_t)(A1 >> 32);
+                const uint32_t a0s = a0l + a0h, a1s = a1l + a1h;
+                const uint32_t sal = a0l + a1l, sah = a0h + a1h, sas = sal + sah;
+#pragma unroll
+                for (int j = 0; j < NB; j++) {
+                    if (j < nb) {
+                        const uint64_t* g = base + (1 + j) * RUN + dd * 2 * TILE;
+                        const uint64_t B0 = g[0], B1 = g[TILE];
+                        const uint32_t b0l = (uint32_t)B0, b0h = (uint32_t)(B0 >> 32);
+                        const uint32_t b1l = (uint32_t)B1, b1h = (uint32_t)(B1 >> 32);
+                        const uint32_t b0s = b0l + b0h, b1s = b1l + b1h;
+                        const uint32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
+                        madw(s[j][0], a0l, b0l);
+                        madw(s[j][1], a0h, b0h);
+                        madw(s[j][2], a0s, b0s);
+                        madw(s[j][3], a1l, b1l);
+                        madw(s[j][4], a1h, b1h);
+                        madw(s[j][5], a1s, b1s);
+                        madw(s[j][6], sal, sbl);
+                        madw(s[j][7], sah, sbh);
+                        madw(s[j][8], sas, sbs);
+                    }
                 }
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[st]);
         }
-        // fold the chunk: value = LL + (MM - HH - LL) 2^27 + HH 2^54 (mod p)
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+        const uint32_t done = si * DPS + nd;
+        if (done % KCHUNK == 0 || done == d) {
+            // fold: value = LL + (MM - HH - LL) 2^27 + HH 2^54 (mod p)
 #pragma unroll
-        for (int j = 0; j < NB; j++) {
-            uint64_t v[3];
+            for (int j = 0; j < NB; j++) {
+                uint64_t v[3];
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const uint64_t LL = s[j][3 * c], HH = s[j][3 * c + 1], MM = s[j][3 * c + 2];
-                v[c] = reduce64(shoup_lazy(LL, 1, c_one_s[l], p) +
-                                    shoup_lazy(MM - HH - LL, c_r27[l], c_r27_s[l], p) +
-                                    shoup_lazy(HH, c_r54[l], c_r54_s[l], p),
-                                l);
+                for (int c = 0; c < 3; c++) {
+                    const uint64_t LL = s[j][3 * c], HH = s[j][3 * c + 1], MM = s[j][3 * c + 2];
+                    v[c] = reduce64(shoup_lazy(LL, 1, c_one_s[l], p) +
+                                        shoup_lazy(MM - HH - LL, c_r27[l], c_r27_s[l], p) +
+                                        shoup_lazy(HH, c_r54[l], c_r54_s[l], p),
+                                    l);
+                    s[j][3 * c] = s[j][3 * c + 1] = s[j][3 * c + 2] = 0;
+                }
+                // T0 = v0, T2 = v1, T1 = K - T0 - T2 with K = v2
+                fold[j][0] = add_mod(fold[j][0], v[0], p);
+                fold[j][2] = add_mod(fold[j][2], v[1], p);
+                fold[j][1] = add_mod(fold[j][1], sub_mod(sub_mod(v[2], v[0], p), v[1], p), p);
             }
-            // T0 = v0, T2 = v1, T1 = K - T0 - T2 with K = v2
-            fold[j][0] = add_mod(fold[j][0], v[0], p);
-            fold[j][2] = add_mod(fold[j][2], v[1], p);
-            fold[j][1] = add_mod(fold[j][1], sub_mod(sub_mod(v[2], v[0], p), v[1], p), p);
         }
     }
-    if (!ok) return;
-    const int k = tile * TT + t;
+    const int k = tile * TILE + t;
 #pragma unroll
     for (int j = 0; j < NB; j++)
         if (j < nb)
 #pragma unroll
             for (int c = 0; c < 3; c++) acc[(((b0 + j) * 3 + c) * 5 + l) * N + k] = fold[j][c];
+}
+
+// The variants the autotuner chooses from: (blocks per CTA, pipeline stages,
+// dimensions per stage, minimum CTAs per SM for the register budget).
+using TensorFn = void (*)(const uint64_t*, const uint64_t*, uint64_t*, uint64_t, uint32_t, int*);
+struct TensorVariant {
+    const char* name;
+    TensorFn fn;
+    int nb, stages, dps;
+};
+#define HERS_TV(NB, S, D, M) \
+    {"nb" #NB "_s" #S "_d" #D "_m" #M, k_tensor<NB, S, D, M>, NB, S, D}
+static const TensorVariant kTensorVariants[] = {
+    HERS_TV(2, 6, 1, 1), HERS_TV(2, 4, 2, 2), HERS_TV(2, 3, 2, 3), HERS_TV(1, 4, 2, 3),
+    HERS_TV(1, 6, 2, 2), HERS_TV(2, 2, 4, 2), HERS_TV(4, 3, 2, 1), HERS_TV(1, 3, 4, 3),
+};
+#undef HERS_TV
+constexpr int NUM_TENSOR_VARIANTS = sizeof(kTensorVariants) / sizeof(kTensorVariants[0]);
+
+int tensor_variant_count() { return NUM_TENSOR_VARIANTS; }
+const char* tensor_variant_name(int v) {
+    return (v >= 0 && v < NUM_TENSOR_VARIANTS) ? kTensorVariants[v].name : nullptr;
+}
+
+cudaError_t launch_tensor(int variant, const uint64_t* gallery, uint64_t nblocks, uint32_t d,
+                          const uint64_t* probe, uint64_t* X, int* err, cudaStream_t st) {
+    if (variant < 0 || variant >= NUM_TENSOR_VARIANTS) return cudaErrorInvalidValue;
+    const TensorVariant& v = kTensorVariants[variant];
+    const int smem = v.stages * (1 + v.nb) * v.dps * 2 * TILE * 8;
+    cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t max_z = 65535ull * v.nb;
+    for (uint64_t g0 = 0; g0 < nblocks; g0 += max_z) {
+        const uint64_t nb = nblocks - g0 < max_z ? nblocks - g0 : max_z;
+        dim3 grid(NTILES, 5, (unsigned)((nb + v.nb - 1) / v.nb));
+        v.fn<<<grid, TILE + 32, smem, st>>>(gallery + g0 * 10ull * d * N, probe, X + g0 * 15 * N, nb,
+                                            d, err);
+        count_launches(1);
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- batched NTTs
@@ -258,10 +226,10 @@ __global__ void __launch_bounds__(NTT_THREADS) k_ntt_batch(const uint64_t* __res
     const uint64_t P = blockIdx.x;
     const int mi = mod_off + (int)(P % (uint64_t)mod_period);
     uint64_t* g = data + P * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) sm[k] = g[k];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) sm[swz(k)] = g[k];
     if (INV) ntt_inv_mod(sm, tw, mi);
     else ntt_fwd_mod(sm, tw, mi);
-    for (int k = threadIdx.x; k < N; k += blockDim.x) g[k] = sm[k];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) g[k] = sm[swz(k)];
 }
 
 // ---------------------------------------------------------------- exact scale-and-round
@@ -360,10 +328,10 @@ __global__ void __launch_bounds__(256) k_ks_finish(const uint64_t* __restrict__ 
 // Workspace per block: X [3][5][N] (reused for O [2][2][N]), C [3][2][N], KS [4][N].
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
-                          uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev) {
+                          uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev,
+                          int variant) {
     if (nblocks == 0) return cudaSuccess;
     uint64_t nl = 0;
-    constexpr int NB = 2;
     uint64_t* X = ws;
     uint64_t* C = X + nblocks * 15 * N;
     uint64_t* KS = C + nblocks * 6 * N;
@@ -371,17 +339,9 @@ cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* 
     // grid.z is limited to 65535: process at most 65535 groups / blocks per pass
     const uint64_t max_z = 65535;
     if (ev) cudaEventRecord(ev[0], st);
-    constexpr int STAGES = 6;
-    const int smem = STAGES * (2 + 2 * NB) * TT * 8;
-    cudaError_t ea = cudaFuncSetAttribute(k_tensor_tma<NB, STAGES>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (ea != cudaSuccess) return ea;
-    for (uint64_t g0 = 0; g0 < nblocks; g0 += max_z * NB) {
-        const uint64_t nb = nblocks - g0 < max_z * NB ? nblocks - g0 : max_z * NB;
-        dim3 grid(N / TT, 5, (unsigned)((nb + NB - 1) / NB));
-        k_tensor_tma<NB, STAGES><<<grid, TT + 32, smem, st>>>(gallery + g0 * d * 10 * N, probe,
-                                                               X + g0 * 15 * N, nb, d, err);
-        nl++;
+    {
+        cudaError_t et = launch_tensor(variant, gallery, nblocks, d, probe, X, err, st);
+        if (et != cudaSuccess) return et;
     }
     if (ev) cudaEventRecord(ev[1], st);
     const uint64_t chunk = 1u << 30;

@@ -194,3 +194,30 @@ def test_inline_temporaries_on_default_stream(ctx, keys):
     scores = H.hers_decrypt_scores(ctx, keys, sc, m).cpu().numpy().astype(np.int64)
     del junk
     assert np.array_equal(scores, W.plain_inner_products(feats, q))
+
+
+def test_every_tensor_shape_gives_the_same_ciphertexts(ctx, keys, oracle_keys):
+    """Exact integer arithmetic makes the result independent of the kernel's
+    tiling: every autotuner candidate must give the oracle's score ciphertexts."""
+    m, d = 3 * 4096 + 17, 40   # d not a multiple of the stage depth: ragged last stage
+    feats = W.gallery_features(m, d, 99)
+    q = W.probe_for_mate(4100, d, 99, 98)
+    gal, _ = H.hers_encrypt_gallery(ctx, keys, torch.from_numpy(feats).cuda(), GAL_SEED)
+    pr = H.hers_probe_prepare(ctx, H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).cuda(), PRB_SEED))
+    names = H.hers_tensor_variants()
+    assert len(names) >= 4
+    keep = H.hers_get_tensor_variant(ctx)
+    outs = []
+    for v in range(len(names)):
+        H.hers_set_tensor_variant(ctx, v)
+        outs.append(u64(H.hers_search(ctx, keys, gal, 4, d, pr)))
+    H.hers_set_tensor_variant(ctx, keep)
+    oprb = O.encrypt_probe(oracle_keys[1], q, PRB_SEED)
+    ogal = O.encrypt_gallery_block(oracle_keys[1], feats, 3, GAL_SEED)
+    osc, _ = O.search_block(oprb, ogal, oracle_keys[2])
+    for v, o in enumerate(outs):
+        assert np.array_equal(o, outs[0]), names[v]
+        assert np.array_equal(o[3], osc), names[v]
+    chosen, ms = H.hers_autotune(ctx, keys, gal, 4, d, pr)
+    assert 0 <= chosen < len(names) and len(ms) == len(names)
+    H.hers_set_tensor_variant(ctx, keep)
