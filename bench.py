@@ -45,6 +45,14 @@ def parse():
     ap.add_argument("--m", type=int, default=1 << 20, help="gallery entries per GPU")
     ap.add_argument("--d", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving"],
+                    help="plain: 1,048,576 entries, d = 64, one probe (the headline line); "
+                         "batched: 64 probes x uneven subsets of 256 blocks, mixed d; "
+                         "serving: Poisson requests against 10M-entry galleries at d 32/64/128")
+    ap.add_argument("--rates", default="50,200,500,1000,2000",
+                    help="serving: arrival rates (requests/s) to sweep")
+    ap.add_argument("--window", type=float, default=2.0, help="serving: seconds of arrivals per rate")
+    ap.add_argument("--max-requests", type=int, default=240, help="serving: cap per rate")
     ap.add_argument("--variant", default=None,
                     help="tensor-kernel shape by name (skips the autotuner), e.g. nb2_s2_d4_m2")
     return ap.parse_args()
@@ -408,10 +416,253 @@ def run_gpu(args):
     return 0
 
 
+def run_batched(args):
+    """Config 3: 64 probes against uneven subsets (1..64 blocks, 256 blocks in
+    all) of mixed dimensionality d in {32, 64, 128}, each probe with a planted
+    mate in its subset.  The batched plan (one CUDA graph, autotuned) is timed
+    against 64 sequential plain searches of the same (probe, subset) pairs."""
+    import numpy as np
+    import torch
+
+    import paper_2003_12197_gb300 as H
+    import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    H.build_library()
+    ctx = H.Context(local)
+    keys = H.hers_keygen(ctx, KEY_SEED)
+    subsets, probe_subset = W.batched_workload(256, 64, seed=FEAT_SEED + rank)
+    gals = []
+    for si, (_, nb, d) in enumerate(subsets):
+        feats = W.gallery_features(nb * N, d, FEAT_SEED + 31 * si)
+        gal, _ = H.hers_encrypt_gallery(ctx, keys, torch.from_numpy(feats).to(dev), GAL_SEED + si)
+        gals.append((feats, gal, nb, d))
+    items, truth = [], []
+    for i, si in enumerate(probe_subset):
+        feats, gal, nb, d = gals[int(si)]
+        mate = int(W.mate_indices(nb * N, 1, MATE_SEED + i)[0])
+        q = W.probe_for_mate(mate, d, FEAT_SEED + 31 * int(si), NOISE_SEED + i)
+        pr = H.hers_probe_prepare(ctx, H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).to(dev),
+                                                            PRB_SEED + i))
+        items.append((gal, nb, d, pr))
+        truth.append((int(si), q, mate))
+    H.hers_check(ctx)
+    entries = sum(nb for _, nb, _, _ in items) * N
+    stream = torch.cuda.current_stream(dev)
+
+    # 64 sequential plain searches (the autotuned plain kernel shape)
+    maxnb = max(nb for _, nb, _, _ in items)
+    ws = torch.empty(H.hers_search_workspace_bytes(maxnb) // 8, dtype=torch.int64, device=dev)
+    g0, _, nb0, d0 = gals[0][1], None, gals[0][2], gals[0][3]
+    H.hers_autotune(ctx, keys, gals[0][1], gals[0][2], gals[0][3], items[0][3], workspace=ws)
+    plain_out = [torch.empty((nb, 2, 2, N), dtype=torch.int64, device=dev) for _, nb, _, _ in items]
+
+    def plain_pass():
+        for (gal, nb, d, pr), out in zip(items, plain_out):
+            H.hers_search(ctx, keys, gal, nb, d, pr, out=out, workspace=ws)
+
+    for _ in range(max(1, args.warmup)):
+        plain_pass()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        plain_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / args.steps
+
+    # the batched plan: one graph launch per step
+    b = H.Batch(ctx, keys, items, flags=H.BATCH_AUTOTUNE)
+    for _ in range(max(1, args.warmup)):
+        b.run()
+    torch.cuda.synchronize()
+    tensor_ms = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    clocks.mark_start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark_stop()
+    clk = clocks.stop()
+    batch_ms = e0.elapsed_time(e1) / args.steps
+    for _ in range(3):
+        tensor_ms.append(b.trace()[0])
+    info = b.info()
+
+    # bit-exact against the plain path, exact scores, planted mates
+    exact = all(torch.equal(b.item_scores(i, nb), plain_out[i]) for i, (_, nb, _, _) in enumerate(items))
+    top1 = 0
+    for i, (gal, nb, d, pr) in enumerate(items):
+        si, q, mate = truth[i]
+        feats = gals[si][0]
+        sc = H.hers_decrypt_scores(ctx, keys, b.item_scores(i, nb), feats.shape[0])
+        sc = sc.cpu().numpy().astype(np.int64)
+        if not np.array_equal(sc, W.plain_inner_products(feats, q)):
+            exact = False
+        top1 += int(np.argmax(sc)) == mate
+    if not exact:
+        raise SystemExit("batched search is not bit-exact against the plain path")
+
+    imad = sum(nb * d for _, nb, d, _ in items) * N * 5 * 9
+    pipe = H.hers_probe_int_pipe(local)["imad_wide_u32"]
+    t_tensor = min(tensor_ms) / 1e3
+    gal_bytes = sum(nb * d * 10 * N * 8 for _, _, nb, d in gals)
+    out = {
+        "metric": METRIC.replace("d=64", "d in {32,64,128}"), "workload": "batched",
+        "value": entries / (batch_ms / 1e3), "unit": "entries/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_ms,
+        "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"batched: 64 probes over {len(subsets)} uneven subsets of 256 blocks "
+                               f"(1..64 blocks each), d per subset from {{32, 64, 128}}",
+                   "subsets": [[nb, d] for _, nb, d in subsets], "entries_per_step": entries},
+        "plain_sequential": {"value": entries / (plain_ms / 1e3), "ms_per_step": plain_ms},
+        "speedup_vs_plain": plain_ms / batch_ms,
+        "batch": info, "tensor_ms": min(tensor_ms),
+        "roofline": {"kernel": f"k_tensor_batched<{info['variant']}>", "bound": "alu",
+                     "achieved": imad / t_tensor / 1e12, "peak": pipe / 1e12, "unit": "T IMAD.WIDE/s",
+                     "frac": imad / t_tensor / pipe,
+                     "peak_source": "measured in this run (hers_probe_int_pipe)",
+                     "gallery_bytes": gal_bytes,
+                     "hbm_gbs_if_gallery_read_once": gal_bytes / t_tensor / 1e9},
+        "correct": {"bit_exact_vs_plain": exact, "scores_exact": exact, "top1": f"{top1}/64"},
+        "clocks": clk,
+    }
+    print(json.dumps(out))
+    b.close()
+    keys.close()
+    ctx.close()
+    del g0, nb0, d0
+    return 0
+
+
+def run_serving(args):
+    """Config 4: continuous-batching server over three resident 10M-entry
+    galleries (2,442 blocks each) at d = 32, 64 and 128.  For each arrival rate,
+    Poisson requests (size uniform in [10k, 10M] entries, start block uniform,
+    d uniform) are submitted at their arrival times; latency runs from the
+    arrival time to the request's score ciphertexts being in host memory."""
+    import numpy as np
+    import torch
+
+    import paper_2003_12197_gb300 as H
+    import workloads as W
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    H.build_library()
+    ctx = H.Context(local)
+    keys = H.hers_keygen(ctx, KEY_SEED)
+    nblocks = H.hers_blocks_for(10_000_000)
+    dims = (32, 64, 128)
+    t0 = time.perf_counter()
+    gals = []
+    for gi, d in enumerate(dims):
+        feats = W.gallery_features_device(10_000_000, d, FEAT_SEED + 100 + gi, dev)
+        g, _ = H.hers_encrypt_gallery(ctx, keys, feats, GAL_SEED + 100 + gi)
+        del feats
+        gals.append((g, nblocks, d))
+    H.hers_check(ctx)
+    setup_s = time.perf_counter() - t0
+    resident = sum(g.numel() * 8 for g, _, _ in gals)
+    # a pool of 8 probes per d (canonical cts in pinned host memory)
+    rng = np.random.default_rng(FEAT_SEED)
+    probes = {}
+    for gi, d in enumerate(dims):
+        probes[gi] = []
+        for j in range(8):
+            q = W.quantise(rng.standard_normal((1, d)))[0]
+            pct = H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).to(dev), PRB_SEED + 8 * gi + j)
+            probes[gi].append(pct.cpu().pin_memory())
+    free_b, _ = torch.cuda.mem_get_info(dev)
+    pool = max(1 << 30, free_b - (8 << 30))
+    srv = H.Server(ctx, keys, gals, workspace_bytes=pool, max_batch=16, variant=1)
+    # pinned host arena for score ciphertexts, handed out as a ring
+    ct_bytes = 4 * N * 8
+    arena_blocks = 4 * nblocks * 16
+    arena = torch.empty((arena_blocks, 4 * N), dtype=torch.int64).pin_memory()
+    results = []
+    for rate in [float(r) for r in args.rates.split(",")]:
+        reqs = W.serving_requests(rate, args.window, args.max_requests, nblocks, dims,
+                                  seed=int(rate))
+        outstanding, lat, pos = [], [], 0
+        entries = 0
+        t_start = time.perf_counter()
+
+        def reap_oldest(timeout_ms):
+            """Collect the oldest outstanding request if it is done within timeout_ms.
+            The server stamps completion itself, so collecting late does not
+            change the recorded latency."""
+            rid, arrive, submit_t, _, _ = outstanding[0]
+            rc, ms = srv.wait(rid, timeout_ms)
+            if rc == -4:
+                return False
+            outstanding.pop(0)
+            if rc != 0:
+                raise SystemExit(f"serving request failed with status {rc}")
+            lat.append(ms + max(0.0, (submit_t - arrive) * 1e3))
+            return True
+
+        for t_arr, gi, b0, b1 in reqs:
+            now = time.perf_counter() - t_start
+            if now < t_arr:
+                time.sleep(t_arr - now)
+            nb = b1 - b0
+            if pos + nb > arena_blocks:
+                pos = 0
+            # the ring slot must be free of outstanding requests' buffers
+            while outstanding and any(not (pos + nb <= o[3] or o[3] + o[4] <= pos)
+                                      for o in outstanding):
+                reap_oldest(600000)
+            out = arena[pos: pos + nb]
+            submit_t = time.perf_counter() - t_start
+            rid = srv.submit(gi, b0, b1, probes[gi][int(rng.integers(0, 8))], out)
+            outstanding.append((rid, t_arr, submit_t, pos, nb))
+            pos += nb
+            entries += nb * N
+            while outstanding and reap_oldest(0):
+                pass
+        while outstanding:
+            reap_oldest(600000)
+        wall = time.perf_counter() - t_start
+        lat = np.array(lat)
+        results.append({"rate_req_s": rate, "requests": len(reqs), "window_s": args.window,
+                        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                        "mean_ms": float(lat.mean()), "entries_per_s": entries / wall,
+                        "offered_entries_per_s": entries / max(args.window, reqs[-1][0]),
+                        "achieved_req_s": len(reqs) / wall, "wall_s": wall})
+    st = srv.stats()
+    srv.close()
+    out = {"metric": "encrypted gallery entries scored/sec and p50/p99 latency (serving)",
+           "workload": "serving", "unit": "entries/s", "n_gpus": 1, "dtype": "u64",
+           "data": "synthetic (seeded int8 features drawn on the device; Poisson arrivals)",
+           "config": {"galleries": "3 x 10,000,000 entries (2,442 blocks) at d = 32, 64, 128",
+                      "resident_gallery_bytes": resident, "pool_bytes": st["pool_bytes"],
+                      "request_size_entries": "uniform [10k, 10M]", "max_batch": 16,
+                      "setup_s": setup_s},
+           "value": max(r["entries_per_s"] for r in results), "higher_is_better": True,
+           "rates": results, "server": st}
+    print(json.dumps(out))
+    keys.close()
+    ctx.close()
+    del ct_bytes
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gpu(args)
 
 

@@ -179,6 +179,110 @@ int hers_search_noalloc(hers_ctx* ctx, const hers_keys* keys, const uint64_t* ga
                         void* stream);
 
 /*
+ * Batched search: many probes, each against its own subset of gallery
+ * blocks, subsets uneven and of mixed dimensionality, in one persistent launch
+ * captured with the rest of the pipeline as one CUDA graph.  This is Alg 7's
+ * server loop run for many queries at once; every (probe, block) result equals
+ * hers_search's.
+ *
+ * Item i = (gallery, nblocks, d, probe): blocks [0, nblocks) of a resident
+ * gallery of dimension d against one prepared probe of dimension d.  Items
+ * with the same (gallery, nblocks, d) form a group.  Each gallery byte a group
+ * streams from HBM is used for up to NP of its probes at once (NP = 1, 2 or 4,
+ * per variant).
+ *
+ * scores_ct: device [sum_i nblocks_i][2][2][N].  Item i's blocks start at
+ * sum_{j<i} nblocks_j.  workspace: device, hers_batch_workspace_bytes().  The
+ * plan keeps both pointers, and they must stay valid until hers_batch_free.
+ *
+ * flags:
+ *  - HERS_BATCH_AUTOTUNE builds and times every variant and keeps the fastest
+ *    (hers_batch_info reports the timings);
+ *  - HERS_BATCH_VARIANT(v) forces variant v;
+ *  - with neither, variant 1.
+ *
+ * hers_batch_create allocates the plan's work tables and instantiates the
+ * graph (synchronous).  hers_batch_run launches the graph on `stream`
+ * (asynchronous; NULL = CUDA's default stream).  Runs of one plan must not
+ * overlap.
+ */
+typedef struct hers_batch_item {
+    const uint64_t* gallery;  /* device: resident gallery of the subset */
+    uint64_t nblocks;         /* blocks searched: [0, nblocks) */
+    uint32_t d;               /* feature dimension of gallery and probe */
+    const uint64_t* probe;    /* device: prepared probe (hers_probe_prepare) */
+} hers_batch_item;
+typedef struct hers_batch hers_batch;
+#define HERS_BATCH_AUTOTUNE 1u
+#define HERS_BATCH_VARIANT(v) ((uint32_t)((v) + 1) << 8)
+uint64_t hers_batch_workspace_bytes(const hers_batch_item* items, uint32_t nitems);
+int hers_batch_create(hers_ctx* ctx, const hers_keys* keys, const hers_batch_item* items,
+                      uint32_t nitems, uint64_t* scores_ct, void* workspace,
+                      uint64_t workspace_bytes, uint32_t flags, hers_batch** out);
+int hers_batch_run(hers_batch* batch, void* stream);
+/* variant, groups, work units, pairs (sum of nblocks) and, if tune_ms is
+ * non-null, hers_batch_variants() autotune timings in ms (-1: not timed). */
+int hers_batch_info(const hers_batch* batch, int* variant, uint32_t* ngroups, uint32_t* nunits,
+                    uint64_t* npairs, double* tune_ms);
+/* One traced run: the batch's launches issued directly on `stream` (outside
+ * the graph, the same work) with CUDA events between them; returns after it
+ * completes with the tensor kernel's and the whole run's device time in ms. */
+int hers_batch_trace(hers_batch* batch, void* stream, double* tensor_ms, double* total_ms);
+int hers_batch_free(hers_batch* batch);
+int hers_batch_variants(void);
+const char* hers_batch_variant_name(int v);
+
+/*
+ * Serving loop with continuous batching.  A server keeps the given resident
+ * galleries and the evaluation key on the device.  It takes requests at any
+ * time: (gallery, block range, probe ciphertexts in host memory).
+ *
+ * A scheduler thread admits queued requests in arrival order while their
+ * device memory fits a pool carved out of free HBM at creation.  The pool is
+ * workspace_bytes, or all free HBM minus 1 GiB when that is 0.  Each admitted
+ * set of up to max_batch requests runs as one batch on one of two streams:
+ *  - probe copy-in and preparation;
+ *  - the persistent batched tensor kernel, where overlapping block ranges of
+ *    one gallery share each gallery read;
+ *  - the epilogue;
+ *  - copy-out of each request's score ciphertexts.
+ * Batches on the two streams overlap on the device.  Requests arriving
+ * meanwhile form the next batch as soon as a stream and memory free up.  Every
+ * result equals hers_search's on the same range.
+ *
+ * hers_server_submit: probe_ct_host is host [d][2][2][N] (pinned copies
+ * faster).  scores_ct_host is host [end - begin][2][2][N], written when the
+ * request completes.  Both must stay valid until hers_server_wait returns
+ * for the id.
+ * hers_server_wait: waits up to timeout_ms.  It returns the request's
+ * status: HERS_OK, HERS_E_NOMEM if the request alone cannot fit the pool, or
+ * HERS_E_TIMEOUT if the wait expired (the request then stays pending).
+ * latency_ms receives the time from submission until its scores were in host
+ * memory.  Each id is waited for once.
+ * variant: the batched tensor-kernel shape (hers_batch_variant_name).
+ * A request of dimension d over n blocks holds 8 (14 d N + 29 N n) bytes of
+ * the pool while it runs, plus its share of the batch's work tables
+ * (16 bytes per (block, limb, tile) and probe chunk).
+ */
+typedef struct hers_server_gallery {
+    const uint64_t* gallery;  /* device: resident gallery (block 0) */
+    uint64_t nblocks;
+    uint32_t d;
+} hers_server_gallery;
+typedef struct hers_server hers_server;
+int hers_server_create(hers_ctx* ctx, const hers_keys* keys, const hers_server_gallery* galleries,
+                       uint32_t ngalleries, uint64_t workspace_bytes, uint32_t max_batch, int variant,
+                       hers_server** out);
+int hers_server_submit(hers_server* srv, uint32_t gallery, uint64_t block_begin, uint64_t block_end,
+                       const uint64_t* probe_ct_host, uint64_t* scores_ct_host, uint64_t* id);
+int hers_server_wait(hers_server* srv, uint64_t id, uint32_t timeout_ms, double* latency_ms);
+/* Counters since creation; returns a sticky error status (HERS_OK if none). */
+int hers_server_stats(hers_server* srv, uint64_t* submitted, uint64_t* completed, uint64_t* batches,
+                      uint64_t* entries, uint64_t* max_batch_seen, uint64_t* pool_bytes);
+/* Finishes in-flight batches, drops queued requests and frees the server. */
+int hers_server_free(hers_server* srv);
+
+/*
  * End-to-end server step with host buffers: copies the probe's d canonical
  * cts from host memory (probe_ct_host, [d][2][2][N]) to the device, prepares
  * them, searches blocks [0, nblocks) and copies the score cts back to host

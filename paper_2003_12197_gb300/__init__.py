@@ -78,6 +78,19 @@ def lib():
                 "hers_get_tensor_variant": ([vp], i32),
                 "hers_set_tensor_variant": ([vp, i32], i32),
                 "hers_autotune": ([vp, vp, vp, u64, u32, vp, vp, u64, vp, vp, vp], i32),
+                "hers_batch_workspace_bytes": ([vp, u32], u64),
+                "hers_batch_create": ([vp, vp, vp, u32, vp, vp, u64, u32, vp], i32),
+                "hers_batch_run": ([vp, vp], i32),
+                "hers_batch_info": ([vp, vp, vp, vp, vp, vp], i32),
+                "hers_batch_free": ([vp], i32),
+                "hers_batch_trace": ([vp, vp, vp, vp], i32),
+                "hers_server_create": ([vp, vp, vp, u32, u64, u32, i32, vp], i32),
+                "hers_server_submit": ([vp, u32, u64, u64, vp, vp, vp], i32),
+                "hers_server_wait": ([vp, u64, u32, vp], i32),
+                "hers_server_stats": ([vp, vp, vp, vp, vp, vp, vp], i32),
+                "hers_server_free": ([vp], i32),
+                "hers_batch_variants": ([], i32),
+                "hers_batch_variant_name": ([i32], ctypes.c_char_p),
             }
             for name, (args, res) in sigs.items():
                 f = getattr(L, name)
@@ -311,6 +324,153 @@ def hers_autotune(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, probe
                                   ws.numel() * 8, _stream(stream), ctypes.byref(chosen), ms),
               "hers_autotune")
     return int(chosen.value), dict(zip(names, list(ms)))
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("gallery", ctypes.c_void_p), ("nblocks", ctypes.c_uint64), ("d", ctypes.c_uint32),
+                ("probe", ctypes.c_void_p)]
+
+
+BATCH_AUTOTUNE = 1
+
+
+def batch_variant_flag(v: int) -> int:
+    return (v + 1) << 8
+
+
+def hers_batch_variants():
+    L = lib()
+    return [L.hers_batch_variant_name(i).decode() for i in range(L.hers_batch_variants())]
+
+
+class Batch:
+    """A planned, graph-captured batched search (hers_batch_create / run / free).
+
+    items: list of (gallery tensor, nblocks, d, prepared probe tensor).
+    Score ciphertexts of item i are rows [off_i, off_i + nblocks_i) of .scores,
+    off_i = sum of the previous items' nblocks.
+    """
+
+    def __init__(self, ctx: Context, keys: Keys, items, flags: int = BATCH_AUTOTUNE):
+        import torch
+        self.ctx, self.keys = ctx, keys
+        self._keep = [(g, p) for g, _, _, p in items]  # the plan points into these
+        arr = (BatchItem * len(items))()
+        for i, (g, nb, d, p) in enumerate(items):
+            arr[i] = BatchItem(g.data_ptr(), nb, d, p.data_ptr())
+        self._items = arr
+        self.offsets = []
+        off = 0
+        for _, nb, _, _ in items:
+            self.offsets.append(off)
+            off += nb
+        self.npairs = off
+        dev = items[0][0].device
+        self.scores = torch.empty((off, 2, 2, N), dtype=torch.int64, device=dev)
+        wsb = int(lib().hers_batch_workspace_bytes(arr, len(items)))
+        self.workspace = _words(wsb, dev)
+        h = ctypes.c_void_p()
+        torch.cuda.synchronize(dev)
+        ctx.check(lib().hers_batch_create(ctx.h, keys.h, arr, len(items), _ptr(self.scores),
+                                          _ptr(self.workspace), wsb, flags, ctypes.byref(h)),
+                  "hers_batch_create")
+        self.h = h
+
+    def run(self, stream=None):
+        self.ctx.check(lib().hers_batch_run(self.h, _stream(stream)), "hers_batch_run")
+        return self.scores
+
+    def info(self):
+        v, ng, nu, npairs = ctypes.c_int(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+        names = hers_batch_variants()
+        tm = (ctypes.c_double * len(names))()
+        lib().hers_batch_info(self.h, ctypes.byref(v), ctypes.byref(ng), ctypes.byref(nu),
+                              ctypes.byref(npairs), tm)
+        return {"variant": names[v.value], "groups": ng.value, "units": nu.value,
+                "pairs": npairs.value, "tune_ms": {n: t for n, t in zip(names, list(tm)) if t >= 0}}
+
+    def trace(self, stream=None):
+        """One traced run (same launches, outside the graph): (tensor ms, whole run ms)."""
+        t, a = ctypes.c_double(), ctypes.c_double()
+        self.ctx.check(lib().hers_batch_trace(self.h, _stream(stream), ctypes.byref(t),
+                                              ctypes.byref(a)), "hers_batch_trace")
+        return t.value, a.value
+
+    def item_scores(self, i, nblocks):
+        return self.scores[self.offsets[i]: self.offsets[i] + nblocks]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hers_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ServerGallery(ctypes.Structure):
+    _fields_ = [("gallery", ctypes.c_void_p), ("nblocks", ctypes.c_uint64), ("d", ctypes.c_uint32)]
+
+
+class Server:
+    """Continuous-batching server (hers_server_*).
+
+    galleries: list of (resident gallery tensor, nblocks, d).  submit() takes
+    the probe's canonical cts and an output buffer as CPU tensors (pinned for
+    speed) which must stay alive until wait() returns for that id.
+    """
+
+    def __init__(self, ctx: Context, keys: Keys, galleries, workspace_bytes=0, max_batch=16,
+                 variant=1):
+        self.ctx = ctx
+        self._keep = [g for g, _, _ in galleries]
+        arr = (ServerGallery * len(galleries))()
+        for i, (g, nb, d) in enumerate(galleries):
+            arr[i] = ServerGallery(g.data_ptr(), nb, d)
+        h = ctypes.c_void_p()
+        ctx.check(lib().hers_server_create(ctx.h, keys.h, arr, len(galleries), workspace_bytes,
+                                           max_batch, variant, ctypes.byref(h)), "hers_server_create")
+        self.h = h
+        self._bufs = {}
+
+    def submit(self, gallery: int, begin: int, end: int, probe_ct_host, scores_host) -> int:
+        rid = ctypes.c_uint64()
+        self.ctx.check(lib().hers_server_submit(self.h, gallery, begin, end, _ptr(probe_ct_host),
+                                                _ptr(scores_host), ctypes.byref(rid)),
+                       "hers_server_submit")
+        self._bufs[rid.value] = (probe_ct_host, scores_host)
+        return rid.value
+
+    def wait(self, rid: int, timeout_ms: int = 600000):
+        """(status, latency ms)."""
+        lat = ctypes.c_double()
+        rc = lib().hers_server_wait(self.h, rid, timeout_ms, ctypes.byref(lat))
+        if rc != -4:
+            self._bufs.pop(rid, None)
+        return rc, lat.value
+
+    def stats(self):
+        v = [ctypes.c_uint64() for _ in range(6)]
+        rc = lib().hers_server_stats(self.h, *[ctypes.byref(x) for x in v])
+        keys = ("submitted", "completed", "batches", "entries", "max_batch_seen", "pool_bytes")
+        out = dict(zip(keys, [x.value for x in v]))
+        out["status"] = rc
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hers_server_free(self.h)
+            self.h = None
+            self._bufs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 INT_PIPE_OPS = ("imad_wide_u32", "imad_u32", "umul64hi")

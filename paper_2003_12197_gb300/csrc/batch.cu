@@ -1,0 +1,559 @@
+// Batched encrypted search: many probes against uneven gallery subsets of
+// mixed dimensionality in one persistent launch, captured with the rest of
+// the pipeline as a single CUDA graph (Alg 7's server loop for many probes at
+// once; the result for every (probe, block) pair is the one hers_search gives).
+//
+// Items (probe, subset) that share a resident gallery form a group.  A group's
+// probes are cut into chunks of NP; a work unit is (chunk, block, limb, tile).
+// The persistent tensor kernel's producer warp claims units from an atomic
+// counter and streams, per stage, the NP probes' rows and the block's gallery
+// rows into a shared-memory ring (cp.async.bulk + mbarriers, as in k_tensor);
+// the consumers accumulate all NP products from the one copy of the gallery
+// rows, so each gallery byte read from HBM serves NP probes.  The epilogue
+// (inverse NTTs, exact scale-and-round, key switch) then runs over all pairs.
+#include <stdio.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "hers.h"
+#include "internal.h"
+
+namespace hers {
+
+constexpr uint32_t UNIT_STOP = 0xFFFFFFFFu;
+constexpr int BKCHUNK = 32;  // fold period in dimensions (see k_tensor)
+
+__device__ __forceinline__ void madw_b(uint64_t& acc, uint32_t a, uint32_t b) {
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+template <int NP, int STAGES, int DPS, int MINB>
+__global__ void __launch_bounds__(TILE + 32, MINB)
+    k_tensor_batched(const BatchChunk* __restrict__ chunks, const BatchUnit* __restrict__ units,
+                     uint32_t nunits, uint32_t* counter, uint64_t* __restrict__ X, int* err) {
+    static_assert(BKCHUNK % DPS == 0, "stages must not straddle a fold");
+    extern __shared__ __align__(128) uint64_t sm[];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+    __shared__ uint32_t hdr_unit[STAGES], hdr_si[STAGES];
+    constexpr int RUN = DPS * 2 * TILE;
+    constexpr int STAGE_WORDS = (NP + 1) * RUN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], TILE / 32);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == TILE / 32) {  // producer warp: claims units, streams their stages
+        if (lane == 0) {
+            const uint64_t pol_g = policy_evict_first(), pol_p = policy_evict_last();
+            uint32_t g = 0;  // stages issued by this CTA
+            bool failed = false;
+            for (;;) {
+                const uint32_t u = atomicAdd(counter, 1u);
+                const bool stop = u >= nunits;
+                BatchUnit U = {};
+                BatchChunk Ch = {};
+                uint32_t nst = 1;
+                if (!stop) {
+                    U = units[u];
+                    Ch = chunks[U.chunk];
+                    nst = (Ch.d + DPS - 1) / DPS;
+                }
+                for (uint32_t si = 0; si < nst; si++, g++) {
+                    const int st = (int)(g % STAGES);
+                    if (g >= STAGES && !mbar_wait(&empty[st], ((g / STAGES) + 1) & 1)) {
+                        atomicOr(err, 2);
+                        failed = true;
+                        break;
+                    }
+                    hdr_unit[st] = stop ? UNIT_STOP : u;
+                    hdr_si[st] = si;
+                    if (stop) {
+                        mbar_arrive(&full[st]);
+                        continue;
+                    }
+                    const uint32_t nd = min((uint32_t)DPS, Ch.d - si * DPS);
+                    const uint32_t bytes = nd * 2 * TILE * 8;
+                    uint64_t* dst = sm + (size_t)st * STAGE_WORDS;
+                    mbar_expect_tx(&full[st], bytes * (Ch.np + 1));
+                    const uint64_t off = resident_offset(0, U.limb, U.tile * TILE, Ch.d, 0, 0) +
+                                         (uint64_t)si * RUN;
+                    for (uint32_t p = 0; p < Ch.np; p++)
+                        bulk_g2s(dst + p * RUN, Ch.probe[p] + off, bytes, &full[st], pol_p);
+                    bulk_g2s(dst + NP * RUN,
+                             Ch.gallery + resident_offset(U.block, U.limb, U.tile * TILE, Ch.d, 0, 0) +
+                                 (uint64_t)si * RUN,
+                             bytes, &full[st], pol_g);
+                }
+                if (stop || failed) break;
+            }
+            // drain: the copies of the last stages issued land before this thread leaves
+            for (uint32_t i = g > STAGES ? g - STAGES : 0; i < g; i++)
+                if (!mbar_wait(&full[i % STAGES], (i / STAGES) & 1)) atomicOr(err, 2);
+        }
+        return;
+    }
+
+    // consumers
+    const int t = threadIdx.x;
+    uint64_t s[NP][9], fold[NP][3];
+    for (uint32_t g = 0;; g++) {
+        const int st = (int)(g % STAGES);
+        if (!mbar_wait(&full[st], (g / STAGES) & 1)) {
+            atomicOr(err, 2);
+            return;
+        }
+        const uint32_t u = hdr_unit[st], si = hdr_si[st];
+        if (u == UNIT_STOP) break;
+        const BatchUnit U = units[u];
+        const uint32_t d = chunks[U.chunk].d, np = chunks[U.chunk].np;
+        const int l = U.limb;
+        const uint64_t p = c_mod[l];
+        if (si == 0) {
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                fold[q][0] = fold[q][1] = fold[q][2] = 0;
+#pragma unroll
+                for (int r = 0; r < 9; r++) s[q][r] = 0;
+            }
+        }
+        const uint32_t nd = min((uint32_t)DPS, d - si * DPS);
+        const uint64_t* base = sm + (size_t)st * STAGE_WORDS + t;
+#pragma unroll
+        for (int dd = 0; dd < DPS; dd++) {
+            if ((uint32_t)dd < nd) {
+                const uint64_t B0 = base[NP * RUN + dd * 2 * TILE], B1 = base[NP * RUN + dd * 2 * TILE + TILE];
+                const uint32_t b0l = (uint32_t)B0, b0h = (uint32_t)(B0 >> 32);
+                const uint32_t b1l = (uint32_t)B1, b1h = (uint32_t)(B1 >> 32);
+                const uint32_t b0s = b0l + b0h, b1s = b1l + b1h;
+                const uint32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
+#pragma unroll
+                for (int q = 0; q < NP; q++) {
+                    if ((uint32_t)q < np) {
+                        const uint64_t A0 = base[q * RUN + dd * 2 * TILE], A1 = base[q * RUN + dd * 2 * TILE + TILE];
+                        const uint32_t a0l = (uint32_t)A0, a0h = (uint32_t)(A0 >> 32);
+                        const uint32_t a1l = (uint32_t)A1, a1h = (uint32_t)(A1 >> 32);
+                        const uint32_t sal = a0l + a1l, sah = a0h + a1h;
+                        madw_b(s[q][0], a0l, b0l);
+                        madw_b(s[q][1], a0h, b0h);
+                        madw_b(s[q][2], a0l + a0h, b0s);
+                        madw_b(s[q][3], a1l, b1l);
+                        madw_b(s[q][4], a1h, b1h);
+                        madw_b(s[q][5], a1l + a1h, b1s);
+                        madw_b(s[q][6], sal, sbl);
+                        madw_b(s[q][7], sah, sbh);
+                        madw_b(s[q][8], sal + sah, sbs);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+        const uint32_t done = si * DPS + nd;
+        if (done % BKCHUNK == 0 || done == d) {
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                uint64_t v[3];
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const uint64_t LL = s[q][3 * c], HH = s[q][3 * c + 1], MM = s[q][3 * c + 2];
+                    v[c] = reduce64(shoup_lazy(LL, 1, c_one_s[l], p) +
+                                        shoup_lazy(MM - HH - LL, c_r27[l], c_r27_s[l], p) +
+                                        shoup_lazy(HH, c_r54[l], c_r54_s[l], p),
+                                    l);
+                    s[q][3 * c] = s[q][3 * c + 1] = s[q][3 * c + 2] = 0;
+                }
+                fold[q][0] = add_mod(fold[q][0], v[0], p);
+                fold[q][2] = add_mod(fold[q][2], v[1], p);
+                fold[q][1] = add_mod(fold[q][1], sub_mod(sub_mod(v[2], v[0], p), v[1], p), p);
+            }
+        }
+        if (done == d) {
+            const int k = U.tile * TILE + t;
+#pragma unroll
+            for (int q = 0; q < NP; q++)
+                if ((uint32_t)q < np) {
+                    const uint64_t pair = chunks[U.chunk].pair[q] + U.block;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) X[((pair * 3 + c) * 5 + l) * N + k] = fold[q][c];
+                }
+        }
+    }
+}
+
+using BatchFn = void (*)(const BatchChunk*, const BatchUnit*, uint32_t, uint32_t*, uint64_t*, int*);
+struct BatchVariant {
+    const char* name;
+    BatchFn fn;
+    int np, stages, dps, minb;
+};
+#define HERS_BV(NP, S, D, M) \
+    {"np" #NP "_s" #S "_d" #D "_m" #M, k_tensor_batched<NP, S, D, M>, NP, S, D, M}
+static const BatchVariant kBatchVariants[] = {
+    HERS_BV(1, 4, 2, 3), HERS_BV(2, 3, 2, 2), HERS_BV(2, 2, 4, 2),
+    HERS_BV(4, 2, 2, 1), HERS_BV(4, 3, 1, 1),
+};
+#undef HERS_BV
+constexpr int NUM_BATCH_VARIANTS = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
+
+static int batch_smem(const BatchVariant& v) { return v.stages * (v.np + 1) * v.dps * 2 * TILE * 8; }
+
+int batch_variant_count() { return NUM_BATCH_VARIANTS; }
+int batch_variant_np(int v) { return kBatchVariants[v].np; }
+
+// Direct launch of the persistent kernel of variant v over device tables.
+cudaError_t launch_batched(int v, const BatchChunk* d_chunks, const BatchUnit* d_units, uint32_t nunits,
+                           uint32_t* d_counter, uint64_t* X, int* err, int device, cudaStream_t st) {
+    if (v < 0 || v >= NUM_BATCH_VARIANTS) return cudaErrorInvalidValue;
+    const BatchVariant& V = kBatchVariants[v];
+    const int smem = batch_smem(V);
+    cudaError_t e = cudaFuncSetAttribute(V.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int per_sm = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, V.fn, TILE + 32, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)per_sm * sms, nunits ? nunits : 1);
+    e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    V.fn<<<grid, TILE + 32, smem, st>>>(d_chunks, d_units, nunits, d_counter, X, err);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace hers
+
+using namespace hers;
+
+struct hers_batch {
+    hers_ctx* ctx;
+    const hers_keys* keys;
+    int variant;
+    uint32_t ngroups, nunits;
+    uint64_t npairs;
+    uint64_t* scores;
+    uint64_t* ws;
+    void* dev;  // chunks, units and the counter, one allocation
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaEvent_t ev[3];  // traced runs: start, after the tensor kernel, end
+    // launch parameters of the built variant (what the graph holds)
+    BatchFn fn;
+    unsigned grid;
+    int smem;
+    BatchChunk* d_chunks;
+    BatchUnit* d_units;
+    uint32_t* d_counter;
+    double tune_ms[NUM_BATCH_VARIANTS];
+};
+
+namespace {
+
+struct Plan {
+    std::vector<BatchChunk> chunks;
+    std::vector<BatchUnit> units;
+    uint32_t ngroups = 0;
+    uint64_t npairs = 0;
+};
+
+}  // namespace
+
+namespace hers {
+
+// Plans work over range items: item i searches blocks [begin_i, end_i) of the
+// resident gallery at `gallery` (block 0) with dimension d; its pair of
+// block b is pair_base_i + (b - begin_i).  For every gallery, the items' range
+// end points cut the blocks into segments over which the set of covering items
+// is constant; each segment with covering items is a group, so every block of
+// a gallery is streamed once per chunk of NP covering items.  Units are
+// block-major, then limb, tile and chunk, so the chunks of one tile are
+// adjacent and the later ones find the gallery rows in L2.
+void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, std::vector<BatchChunk>& chunks,
+                 std::vector<BatchUnit>& units, uint32_t* ngroups) {
+    std::map<std::pair<const uint64_t*, uint32_t>, std::vector<uint32_t>> by_gallery;
+    std::vector<std::pair<const uint64_t*, uint32_t>> order;
+    for (uint32_t i = 0; i < nitems; i++) {
+        auto key = std::make_pair(items[i].gallery, items[i].d);
+        if (!by_gallery.count(key)) order.push_back(key);
+        by_gallery[key].push_back(i);
+    }
+    uint32_t groups = 0;
+    for (const auto& key : order) {
+        const std::vector<uint32_t>& its = by_gallery[key];
+        std::vector<uint64_t> cuts;
+        for (uint32_t i : its) {
+            cuts.push_back(items[i].begin);
+            cuts.push_back(items[i].end);
+        }
+        std::sort(cuts.begin(), cuts.end());
+        cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
+        for (size_t c = 0; c + 1 < cuts.size(); c++) {
+            const uint64_t s0 = cuts[c], s1 = cuts[c + 1];
+            std::vector<uint32_t> cover;
+            for (uint32_t i : its)
+                if (items[i].begin <= s0 && items[i].end >= s1) cover.push_back(i);
+            if (cover.empty()) continue;
+            groups++;
+            const uint32_t first = (uint32_t)chunks.size();
+            for (size_t c0 = 0; c0 < cover.size(); c0 += np_max) {
+                BatchChunk ch = {};
+                ch.gallery = key.first;
+                ch.d = key.second;
+                ch.np = (uint32_t)std::min<size_t>(np_max, cover.size() - c0);
+                for (uint32_t q = 0; q < ch.np; q++) {
+                    const RangeItem& it = items[cover[c0 + q]];
+                    ch.probe[q] = it.probe;
+                    ch.pair[q] = it.pair_base - it.begin;  // + absolute block (mod 2^64)
+                }
+                chunks.push_back(ch);
+            }
+            const uint32_t nch = (uint32_t)chunks.size() - first;
+            for (uint64_t blk = s0; blk < s1; blk++)
+                for (uint16_t l = 0; l < 5; l++)
+                    for (uint16_t tl = 0; tl < NTILES; tl++)
+                        for (uint32_t c2 = 0; c2 < nch; c2++)
+                            units.push_back({first + c2, (uint32_t)blk, l, tl, 0});
+        }
+    }
+    if (ngroups) *ngroups = groups;
+}
+
+}  // namespace hers
+
+namespace {
+
+Plan make_plan(const hers_batch_item* items, uint32_t nitems, int np_max) {
+    Plan P;
+    std::vector<RangeItem> r(nitems);
+    for (uint32_t i = 0; i < nitems; i++) {
+        r[i] = {items[i].gallery, 0, items[i].nblocks, items[i].d, items[i].probe, P.npairs};
+        P.npairs += items[i].nblocks;
+    }
+    plan_ranges(r.data(), nitems, np_max, P.chunks, P.units, &P.ngroups);
+    return P;
+}
+
+void batch_release(hers_batch* B) {
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->dev) cudaFree(B->dev);
+    B->exec = nullptr;
+    B->graph = nullptr;
+    B->dev = nullptr;
+}
+
+// The batch's launches: counter reset, persistent tensor kernel, epilogue.
+// With `traced`, events go between them (used outside a graph only).
+cudaError_t batch_launch(hers_batch* B, cudaStream_t st, bool traced) {
+    uint64_t* X = B->ws;
+    uint64_t* C = X + B->npairs * 15 * N;
+    uint64_t* KS = C + B->npairs * 6 * N;
+    cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(uint32_t), st);
+    if (traced) cudaEventRecord(B->ev[0], st);
+    B->fn<<<B->grid, TILE + 32, B->smem, st>>>(B->d_chunks, B->d_units, B->nunits, B->d_counter, X,
+                                                B->ctx->err);
+    if (traced) cudaEventRecord(B->ev[1], st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaError_t el = launch_epilogue(B->ctx->tw, B->keys->k, B->npairs, X, C, KS, B->scores, st);
+    if (traced) cudaEventRecord(B->ev[2], st);
+    return e != cudaSuccess ? e : el;
+}
+
+// Builds the device tables and the graph of one variant.
+int batch_build(hers_batch* B, const hers_batch_item* items, uint32_t nitems, int v) {
+    hers_ctx* ctx = B->ctx;
+    const BatchVariant& V = kBatchVariants[v];
+    Plan P = make_plan(items, nitems, V.np);
+    if (P.units.size() >= UNIT_STOP) return fail(ctx, HERS_E_INVAL, "hers_batch_create: too many units");
+    const size_t cbytes = P.chunks.size() * sizeof(BatchChunk);
+    const size_t ubytes = P.units.size() * sizeof(BatchUnit);
+    const size_t total = ((cbytes + 255) / 256) * 256 + ((ubytes + 255) / 256) * 256 + 256;
+    cudaError_t e = cudaMalloc(&B->dev, total);
+    if (e != cudaSuccess) return fail(ctx, HERS_E_NOMEM, "hers_batch_create: %s", cudaGetErrorString(e));
+    BatchChunk* d_chunks = (BatchChunk*)B->dev;
+    BatchUnit* d_units = (BatchUnit*)((char*)B->dev + ((cbytes + 255) / 256) * 256);
+    uint32_t* d_counter = (uint32_t*)((char*)d_units + ((ubytes + 255) / 256) * 256);
+    e = cudaMemcpy(d_chunks, P.chunks.data(), cbytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_units, P.units.data(), ubytes, cudaMemcpyHostToDevice);
+    const int smem = batch_smem(V);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(V.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int per_sm = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, V.fn, TILE + 32, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_batch_create: setup");
+    if (per_sm < 1) return fail(ctx, HERS_E_CUDA, "hers_batch_create: variant %s does not fit an SM", V.name);
+    const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)per_sm * sms, P.units.size());
+
+    B->fn = V.fn;
+    B->grid = grid;
+    B->smem = smem;
+    B->d_chunks = d_chunks;
+    B->d_units = d_units;
+    B->d_counter = d_counter;
+    B->variant = v;
+    B->ngroups = P.ngroups;
+    B->nunits = (uint32_t)P.units.size();
+    B->npairs = P.npairs;
+    cudaStream_t cs = ctx->stream;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_batch_create: begin capture");
+    cudaError_t el = batch_launch(B, cs, false);
+    e = cudaStreamEndCapture(cs, &B->graph);
+    if (el != cudaSuccess) e = el;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, B->graph, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_batch_create: graph");
+    return HERS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hers_batch_variants(void) { return NUM_BATCH_VARIANTS; }
+
+const char* hers_batch_variant_name(int v) {
+    return (v >= 0 && v < NUM_BATCH_VARIANTS) ? kBatchVariants[v].name : "";
+}
+
+uint64_t hers_batch_workspace_bytes(const hers_batch_item* items, uint32_t nitems) {
+    uint64_t np = 0;
+    for (uint32_t i = 0; items && i < nitems; i++) np += items[i].nblocks;
+    return hers_search_workspace_bytes(np);
+}
+
+int hers_batch_create(hers_ctx* ctx, const hers_keys* keys, const hers_batch_item* items,
+                      uint32_t nitems, uint64_t* scores_ct, void* workspace, uint64_t workspace_bytes,
+                      uint32_t flags, hers_batch** out) {
+    if (!ctx || !keys || !items || !scores_ct || !workspace || !out || nitems == 0)
+        return fail(ctx, HERS_E_INVAL, "hers_batch_create: null argument or no items");
+    *out = nullptr;
+    for (uint32_t i = 0; i < nitems; i++) {
+        const hers_batch_item& it = items[i];
+        if (!it.gallery || !it.probe || it.nblocks == 0 || it.d == 0 || it.d > HERS_MAX_D)
+            return fail(ctx, HERS_E_INVAL, "hers_batch_create: item %u is invalid", i);
+    }
+    if (workspace_bytes < hers_batch_workspace_bytes(items, nitems))
+        return fail(ctx, HERS_E_NOMEM, "hers_batch_create: workspace too small");
+    const int forced = (int)((flags >> 8) & 0xFF) - 1;
+    if (forced >= NUM_BATCH_VARIANTS)
+        return fail(ctx, HERS_E_INVAL, "hers_batch_create: variant %d not in [0, %d)", forced,
+                    NUM_BATCH_VARIANTS);
+    DeviceGuard g(ctx->device);
+    hers_batch* B = new (std::nothrow) hers_batch();
+    if (!B) return fail(ctx, HERS_E_NOMEM, "hers_batch_create: host allocation");
+    B->ctx = ctx;
+    B->keys = keys;
+    B->scores = scores_ct;
+    B->ws = (uint64_t*)workspace;
+    for (int i = 0; i < 3; i++)
+        if (cudaEventCreate(&B->ev[i]) != cudaSuccess) {
+            for (int j = 0; j < i; j++) cudaEventDestroy(B->ev[j]);
+            delete B;
+            return fail(ctx, HERS_E_CUDA, "hers_batch_create: event creation");
+        }
+    for (int v = 0; v < NUM_BATCH_VARIANTS; v++) B->tune_ms[v] = -1;
+    int rc = HERS_OK;
+    if (forced >= 0 || !(flags & HERS_BATCH_AUTOTUNE)) {
+        rc = batch_build(B, items, nitems, forced >= 0 ? forced : 1);
+    } else {
+        // autotune: build every variant, time 3 graph launches each, keep the fastest
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        int best = -1;
+        double best_ms = 0;
+        for (int v = 0; v < NUM_BATCH_VARIANTS && rc == HERS_OK; v++) {
+            rc = batch_build(B, items, nitems, v);
+            if (rc != HERS_OK) break;
+            cudaError_t e = cudaGraphLaunch(B->exec, ctx->stream);  // warm
+            double vb = 0;
+            for (int rep = 0; rep < 3 && e == cudaSuccess; rep++) {
+                cudaEventRecord(e0, ctx->stream);
+                e = cudaGraphLaunch(B->exec, ctx->stream);
+                cudaEventRecord(e1, ctx->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 0 || ms < vb) vb = ms;
+            }
+            if (e != cudaSuccess) rc = cuda_fail(ctx, e, "hers_batch_create: autotune");
+            B->tune_ms[v] = vb;
+            if (rc == HERS_OK && (best < 0 || vb < best_ms)) {
+                best = v;
+                best_ms = vb;
+            }
+            batch_release(B);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc == HERS_OK) rc = batch_build(B, items, nitems, best);
+    }
+    if (rc == HERS_OK) rc = hers_check(ctx, nullptr);
+    if (rc != HERS_OK) {
+        batch_release(B);
+        for (int i = 0; i < 3; i++) cudaEventDestroy(B->ev[i]);
+        delete B;
+        return rc;
+    }
+    *out = B;
+    return HERS_OK;
+}
+
+int hers_batch_trace(hers_batch* B, void* stream, double* tensor_ms, double* total_ms) {
+    if (!B) return HERS_E_INVAL;
+    DeviceGuard g(B->ctx->device);
+    cudaError_t e = batch_launch(B, (cudaStream_t)stream, true);
+    if (e == cudaSuccess) count_launches(8);
+    if (e == cudaSuccess) e = cudaEventSynchronize(B->ev[2]);
+    float t = 0, a = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, B->ev[0], B->ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&a, B->ev[0], B->ev[2]);
+    if (e != cudaSuccess) return cuda_fail(B->ctx, e, "hers_batch_trace");
+    if (tensor_ms) *tensor_ms = t;
+    if (total_ms) *total_ms = a;
+    return HERS_OK;
+}
+
+int hers_batch_run(hers_batch* B, void* stream) {
+    if (!B) return HERS_E_INVAL;
+    DeviceGuard g(B->ctx->device);
+    cudaError_t e = cudaGraphLaunch(B->exec, (cudaStream_t)stream);
+    if (e == cudaSuccess) count_launches(8);
+    return e == cudaSuccess ? HERS_OK : cuda_fail(B->ctx, e, "hers_batch_run");
+}
+
+int hers_batch_info(const hers_batch* B, int* variant, uint32_t* ngroups, uint32_t* nunits,
+                    uint64_t* npairs, double* tune_ms) {
+    if (!B) return HERS_E_INVAL;
+    if (variant) *variant = B->variant;
+    if (ngroups) *ngroups = B->ngroups;
+    if (nunits) *nunits = B->nunits;
+    if (npairs) *npairs = B->npairs;
+    if (tune_ms)
+        for (int v = 0; v < NUM_BATCH_VARIANTS; v++) tune_ms[v] = B->tune_ms[v];
+    return HERS_OK;
+}
+
+int hers_batch_free(hers_batch* B) {
+    if (!B) return HERS_E_INVAL;
+    {
+        DeviceGuard g(B->ctx->device);
+        cudaStreamSynchronize(B->ctx->stream);
+        batch_release(B);
+        for (int i = 0; i < 3; i++) cudaEventDestroy(B->ev[i]);
+    }
+    delete B;
+    return HERS_OK;
+}
+
+}  // extern "C"

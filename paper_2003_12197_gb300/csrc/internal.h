@@ -83,11 +83,47 @@ cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* 
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
                           uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev = nullptr,
                           int variant = DEFAULT_TENSOR_VARIANT);
+// Epilogue over npairs accumulators X [npairs][3][5][N]; workspace C, KS as in
+// launch_search; `ev` (optional) receives the boundaries after the inverse
+// NTTs (ev[0]) and after scale-and-round (ev[1]).
+cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npairs, uint64_t* X,
+                            uint64_t* C, uint64_t* KS, uint64_t* out, cudaStream_t st,
+                            cudaEvent_t* ev = nullptr);
 // The tensor kernel alone, into X [nblocks][3][5][N].
 cudaError_t launch_tensor(int variant, const uint64_t* gallery, uint64_t nblocks, uint32_t d,
                           const uint64_t* probe, uint64_t* X, int* err, cudaStream_t st);
 int tensor_variant_count();
 const char* tensor_variant_name(int v);
+
+// A block range of one resident gallery against one prepared probe; the
+// result of block b goes to pair pair_base + (b - begin).
+struct RangeItem {
+    const uint64_t* gallery;  // block 0 of the resident gallery
+    uint64_t begin, end;
+    uint32_t d;
+    const uint64_t* probe;
+    uint64_t pair_base;
+};
+
+// batch.cu: work tables of the persistent batched tensor kernel.
+constexpr int BATCH_NPMAX = 4;
+struct BatchChunk {  // up to BATCH_NPMAX probes sharing one gallery segment
+    const uint64_t* gallery;
+    const uint64_t* probe[BATCH_NPMAX];
+    uint64_t pair[BATCH_NPMAX];  // pair of probe q at absolute block b: pair[q] + b (mod 2^64)
+    uint32_t d, np;
+};
+struct BatchUnit {  // (chunk, absolute block, limb, tile)
+    uint32_t chunk, block;
+    uint16_t limb, tile;
+    uint32_t pad;
+};
+void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, std::vector<BatchChunk>& chunks,
+                 std::vector<BatchUnit>& units, uint32_t* ngroups);
+int batch_variant_count();
+int batch_variant_np(int v);
+cudaError_t launch_batched(int v, const BatchChunk* d_chunks, const BatchUnit* d_units, uint32_t nunits,
+                           uint32_t* d_counter, uint64_t* X, int* err, int device, cudaStream_t st);
 
 // Kernel launches issued by this library in this process (all contexts).
 void count_launches(uint64_t n);

@@ -325,64 +325,71 @@ __global__ void __launch_bounds__(256) k_ks_finish(const uint64_t* __restrict__ 
 }
 
 // ---------------------------------------------------------------- pipeline
-// Workspace per block: X [3][5][N] (reused for O [2][2][N]), C [3][2][N], KS [4][N].
-cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
-                          uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
-                          uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev,
-                          int variant) {
-    if (nblocks == 0) return cudaSuccess;
+// Epilogue over npairs (probe, block) pairs whose accumulators are in
+// X [npairs][3][5][N] (NTT domain): inverse NTTs, exact scale-and-round into
+// C [npairs][3][2][N] and KS [npairs][4][N], key switch (the output O reuses X),
+// canonical score ciphertexts into out [npairs][2][2][N].
+cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npairs, uint64_t* X,
+                            uint64_t* C, uint64_t* KS, uint64_t* out, cudaStream_t st,
+                            cudaEvent_t* ev) {
     uint64_t nl = 0;
-    uint64_t* X = ws;
-    uint64_t* C = X + nblocks * 15 * N;
-    uint64_t* KS = C + nblocks * 6 * N;
     uint64_t* O = X;
-    // grid.z is limited to 65535: process at most 65535 groups / blocks per pass
     const uint64_t max_z = 65535;
-    if (ev) cudaEventRecord(ev[0], st);
-    {
-        cudaError_t et = launch_tensor(variant, gallery, nblocks, d, probe, X, err, st);
-        if (et != cudaSuccess) return et;
-    }
-    if (ev) cudaEventRecord(ev[1], st);
     const uint64_t chunk = 1u << 30;
-    for (uint64_t off = 0; off < nblocks * 15; off += chunk) {
-        const uint64_t n = nblocks * 15 - off < chunk ? nblocks * 15 - off : chunk;
+    for (uint64_t off = 0; off < npairs * 15; off += chunk) {
+        const uint64_t n = npairs * 15 - off < chunk ? npairs * 15 - off : chunk;
         k_ntt_batch<true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, X + off * N, 5, 0);
         nl++;
     }
-    if (ev) cudaEventRecord(ev[2], st);
-    for (uint64_t b0 = 0; b0 < nblocks; b0 += max_z) {
-        const uint64_t nb = nblocks - b0 < max_z ? nblocks - b0 : max_z;
+    if (ev) cudaEventRecord(ev[0], st);
+    for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
+        const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
         k_scale_round<<<dim3(N / 256, 3, (unsigned)nb), 256, 0, st>>>(X + b0 * 15 * N, C + b0 * 6 * N,
                                                                      KS + b0 * 4 * N);
         nl++;
     }
-    if (ev) cudaEventRecord(ev[3], st);
-    for (uint64_t off = 0; off < nblocks * 4; off += chunk) {
-        const uint64_t n = nblocks * 4 - off < chunk ? nblocks * 4 - off : chunk;
+    if (ev) cudaEventRecord(ev[1], st);
+    for (uint64_t off = 0; off < npairs * 4; off += chunk) {
+        const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
         k_ntt_batch<false><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, KS + off * N, 2, 0);
         nl++;
     }
-    for (uint64_t b0 = 0; b0 < nblocks; b0 += max_z) {
-        const uint64_t nb = nblocks - b0 < max_z ? nblocks - b0 : max_z;
+    for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
+        const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
         k_ks_mul<<<dim3(N / 256, 2, (unsigned)nb), 256, 0, st>>>(KS + b0 * 4 * N, k.evk_ntt,
                                                                  O + b0 * 4 * N);
         nl++;
     }
-    for (uint64_t off = 0; off < nblocks * 4; off += chunk) {
-        const uint64_t n = nblocks * 4 - off < chunk ? nblocks * 4 - off : chunk;
+    for (uint64_t off = 0; off < npairs * 4; off += chunk) {
+        const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
         k_ntt_batch<true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, O + off * N, 2, 0);
         nl++;
     }
-    for (uint64_t b0 = 0; b0 < nblocks; b0 += max_z) {
-        const uint64_t nb = nblocks - b0 < max_z ? nblocks - b0 : max_z;
+    for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
+        const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
         k_ks_finish<<<dim3(N / 256, 4, (unsigned)nb), 256, 0, st>>>(C + b0 * 6 * N, O + b0 * 4 * N,
-                                                                    scores_ct + b0 * 4 * N);
+                                                                    out + b0 * 4 * N);
         nl++;
     }
-    if (ev) cudaEventRecord(ev[4], st);
     count_launches(nl);
     return cudaGetLastError();
+}
+
+// Workspace per block: X [3][5][N] (reused for O [2][2][N]), C [3][2][N], KS [4][N].
+cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
+                          uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
+                          uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev, int variant) {
+    if (nblocks == 0) return cudaSuccess;
+    uint64_t* X = ws;
+    uint64_t* C = X + nblocks * 15 * N;
+    uint64_t* KS = C + nblocks * 6 * N;
+    if (ev) cudaEventRecord(ev[0], st);
+    cudaError_t e = launch_tensor(variant, gallery, nblocks, d, probe, X, err, st);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], st);
+    e = launch_epilogue(tw, k, nblocks, X, C, KS, scores_ct, st, ev ? ev + 2 : nullptr);
+    if (ev) cudaEventRecord(ev[4], st);
+    return e;
 }
 
 }  // namespace hers

@@ -71,6 +71,45 @@ def plain_inner_products(feats: np.ndarray, probe: np.ndarray) -> np.ndarray:
     return feats.astype(np.int64) @ probe.astype(np.int64)
 
 
+def gallery_features_device(m: int, d: int, seed: int, device, chunk: int = 1 << 22):
+    """int8 [m, d] gallery features drawn on a CUDA device (torch's seeded
+    generator): the same recipe as gallery_features, for galleries too large to
+    draw on the host in reasonable time.  Deterministic for a given seed,
+    device type and torch version; not bit-equal to gallery_features."""
+    import torch
+    out = torch.empty((m, d), dtype=torch.int8, device=device)
+    for c in range((m + chunk - 1) // chunk):
+        lo, hi = c * chunk, min((c + 1) * chunk, m)
+        g = torch.Generator(device=device)
+        g.manual_seed((seed * 1_000_003 + c) % (1 << 63))
+        x = torch.randn((hi - lo, d), generator=g, device=device, dtype=torch.float32)
+        x = x / x.norm(dim=1, keepdim=True).clamp_min(1e-12)
+        out[lo:hi] = torch.round(SCALE * x).clamp_(-SCALE, SCALE).to(torch.int8)
+    return out
+
+
+def serving_requests(rate: float, window_s: float, max_requests: int, nblocks_total: int,
+                     dims=(32, 64, 128), min_entries: int = 10_000, max_entries: int = 10_000_000,
+                     seed: int = 0, n_block: int = 4096):
+    """Poisson arrivals at `rate` per second over `window_s` seconds (at most
+    max_requests).  Each request: arrival time, gallery index (its d drawn
+    uniformly from dims), size uniform in [min_entries, max_entries] entries
+    rounded up to whole blocks, and a uniform start block.  Returns a list of
+    (t_arrival_s, gallery_index, block_begin, block_end)."""
+    rng = np.random.default_rng([seed, 0x73657276])
+    t, out = 0.0, []
+    while len(out) < max_requests:
+        t += rng.exponential(1.0 / rate)
+        if t > window_s:
+            break
+        gi = int(rng.integers(0, len(dims)))
+        size = int(rng.integers(min_entries, max_entries + 1))
+        nb = min(nblocks_total, (size + n_block - 1) // n_block)
+        b0 = int(rng.integers(0, nblocks_total - nb + 1))
+        out.append((t, gi, b0, b0 + nb))
+    return out
+
+
 def batched_workload(total_blocks: int, nprobes: int, seed: int, dims=(32, 64, 128),
                      max_subset=64):
     """Uneven gallery subsets for batched search.
