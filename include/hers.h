@@ -113,8 +113,10 @@ int hers_keys_export(hers_ctx* ctx, const hers_keys* keys, int8_t* sk, uint64_t*
  * becomes the plaintext whose slot j holds feats[b N + j][i] (0 past m),
  * encrypted with randomness stream obj = b d + i.
  * gallery: device, hers_gallery_bytes(ceil(m/N), d) bytes: the resident form
- *   the search streams (NTT domain, extended to the 5-prime basis q1 q2 p1 p2 p3).
- * gallery_ct: device uint64 [ceil(m/N)][d][2][2][N] canonical cts, or NULL.
+ *   the search streams (NTT domain, extended to the 5-prime basis q1 q2 p1 p2 p3),
+ *   or NULL to write the canonical cts only (for hers_search_stream).
+ * gallery_ct: device uint64 [ceil(m/N)][d][2][2][N] canonical cts, or NULL
+ *   (at least one of gallery, gallery_ct is non-NULL).
  * Asynchronous on stream; sampler failures are reported by the next
  * synchronous call on ctx (hers_check).
  */
@@ -276,11 +278,45 @@ int hers_server_create(hers_ctx* ctx, const hers_keys* keys, const hers_server_g
 int hers_server_submit(hers_server* srv, uint32_t gallery, uint64_t block_begin, uint64_t block_end,
                        const uint64_t* probe_ct_host, uint64_t* scores_ct_host, uint64_t* id);
 int hers_server_wait(hers_server* srv, uint64_t id, uint32_t timeout_ms, double* latency_ms);
+/* Holds (paused != 0) or resumes admission: while held, submitted requests
+ * queue and batches already running finish. */
+int hers_server_pause(hers_server* srv, int paused);
 /* Counters since creation; returns a sticky error status (HERS_OK if none). */
 int hers_server_stats(hers_server* srv, uint64_t* submitted, uint64_t* completed, uint64_t* batches,
                       uint64_t* entries, uint64_t* max_batch_seen, uint64_t* pool_bytes);
 /* Finishes in-flight batches, drops queued requests and frees the server. */
 int hers_server_free(hers_server* srv);
+
+/*
+ * Streamed search over a gallery kept in canonical form.  The canonical form
+ * has 2 limbs in the coefficient domain, 32 d bytes per entry, i.e. the
+ * ciphertexts' own size.  It is meant for galleries too large for the 5-prime
+ * resident form: 100M entries at d = 64 are 204.8 GB canonical against 512 GB
+ * resident.
+ *
+ * The gallery is gallery_ct, [nblocks][d][2][2][N], in host memory when
+ * gallery_on_host (pinned for full copy speed) or in device memory.
+ * probes: host array of nprobes device pointers to prepared probes of
+ * dimension d.  scores_ct: device [nprobes][nblocks][2][2][N].
+ *
+ * Per chunk of chunk_blocks blocks the call:
+ *  - copies the chunk in;
+ *  - extends it and NTTs it into the resident form in the workspace;
+ *  - runs one persistent batched tensor launch with every probe (variant as
+ *    hers_batch_variant_name) and the epilogue.
+ * Two chunk slots alternate, so chunk c+1's copy and extension, on the
+ * context's own stream, overlap chunk c's search on `stream`.
+ *
+ * workspace: device, hers_search_stream_workspace_bytes(d, nprobes,
+ * chunk_blocks).  Asynchronous on `stream`: the work on both streams is joined
+ * into `stream`.  Results equal hers_search's.
+ */
+uint64_t hers_search_stream_workspace_bytes(uint32_t d, uint32_t nprobes, uint32_t chunk_blocks);
+int hers_search_stream(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery_ct,
+                       int gallery_on_host, uint64_t nblocks, uint32_t d,
+                       const uint64_t* const* probes, uint32_t nprobes, uint64_t* scores_ct,
+                       uint32_t chunk_blocks, int variant, void* workspace,
+                       uint64_t workspace_bytes, void* stream);
 
 /*
  * End-to-end server step with host buffers: copies the probe's d canonical

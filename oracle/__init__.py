@@ -215,6 +215,18 @@ def encrypt_gallery_block(pk, feats, b, seed, n=N):
     return out
 
 
+def encrypt_gallery_block_rows(pk, rows, b, seed, n=N):
+    """Ciphertexts [d][2][2][n] of gallery block b given only that block's rows
+    (rows[j] = entry b n + j; fewer than n rows pad with zeros)."""
+    d = rows.shape[1]
+    slots = np.zeros((d, n), dtype=np.int64)
+    slots[:, : rows.shape[0]] = rows.T.astype(np.int64)
+    out = np.zeros((d, 2, 2, n), dtype=np.uint64)
+    for i in range(d):
+        out[i] = encrypt(pk, encode(slots[i], n), seed, PURPOSE_GALLERY, b * d + i, n)
+    return out
+
+
 def encrypt_probe(pk, qfeat, seed, n=N):
     """Ciphertexts [d][2][2][n] of a probe (Eq. 2: dimension i in every slot; obj = i)."""
     d = len(qfeat)

@@ -84,10 +84,14 @@ def lib():
                 "hers_batch_info": ([vp, vp, vp, vp, vp, vp], i32),
                 "hers_batch_free": ([vp], i32),
                 "hers_batch_trace": ([vp, vp, vp, vp], i32),
+                "hers_search_stream_workspace_bytes": ([u32, u32, u32], u64),
+                "hers_search_stream": ([vp, vp, vp, i32, u64, u32, vp, u32, vp, u32, i32, vp, u64,
+                                        vp], i32),
                 "hers_server_create": ([vp, vp, vp, u32, u64, u32, i32, vp], i32),
                 "hers_server_submit": ([vp, u32, u64, u64, vp, vp, vp], i32),
                 "hers_server_wait": ([vp, u64, u32, vp], i32),
                 "hers_server_stats": ([vp, vp, vp, vp, vp, vp, vp], i32),
+                "hers_server_pause": ([vp, i32], i32),
                 "hers_server_free": ([vp], i32),
                 "hers_batch_variants": ([], i32),
                 "hers_batch_variant_name": ([i32], ctypes.c_char_p),
@@ -206,14 +210,19 @@ def hers_keys_export(ctx: Context, keys: Keys):
 
 
 def hers_encrypt_gallery(ctx: Context, keys: Keys, feats, seed: int, want_ct: bool = False,
-                         out=None, out_ct=None, stream=None):
-    """feats: cuda int8 [m, d].  Returns (gallery words, canonical cts [nb,d,2,2,N] or None)."""
+                         out=None, out_ct=None, stream=None, resident: bool = True):
+    """feats: cuda int8 [m, d].  Returns (resident gallery words or None,
+    canonical cts [nb,d,2,2,N] or None).  resident=False writes only the
+    canonical cts (for hers_search_stream)."""
     import torch
     assert feats.is_cuda and feats.dtype == torch.int8 and feats.dim() == 2
     feats = feats.contiguous()
     m, d = feats.shape
     nb = hers_blocks_for(m)
-    gal = out if out is not None else _words(hers_gallery_bytes(nb, d), feats.device)
+    want_ct = want_ct or not resident
+    gal = None
+    if resident:
+        gal = out if out is not None else _words(hers_gallery_bytes(nb, d), feats.device)
     cts = out_ct
     if want_ct and cts is None:
         cts = torch.empty((nb, d, 2, 2, N), dtype=torch.int64, device=feats.device)
@@ -262,6 +271,32 @@ def hers_search_host(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, pr
                                      _ptr(scores_host), _ptr(workspace), workspace.numel() * 8,
                                      _stream(stream)), "hers_search_host")
     return scores_host
+
+
+def hers_search_stream(ctx: Context, keys: Keys, gallery_ct, nblocks: int, d: int, probes,
+                       chunk_blocks: int = 32, variant: int = 1, out=None, workspace=None,
+                       stream=None):
+    """Streamed search of a canonical gallery (CPU tensor: from host memory; CUDA
+    tensor: from device memory) with several prepared probes.  Returns score
+    cts [nprobes, nblocks, 2, 2, N] (int64 view) on the probes' device."""
+    import torch
+    dev = probes[0].device
+    on_host = not gallery_ct.is_cuda
+    np_ = len(probes)
+    sc = out if out is not None else torch.empty((np_, nblocks, 2, 2, N), dtype=torch.int64,
+                                                 device=dev)
+    wsb = int(lib().hers_search_stream_workspace_bytes(d, np_, chunk_blocks))
+    ws = workspace if workspace is not None else _words(wsb, dev)
+    ptrs = (ctypes.c_void_p * np_)(*[p.data_ptr() for p in probes])
+    ctx.check(lib().hers_search_stream(ctx.h, keys.h, _ptr(gallery_ct), 1 if on_host else 0,
+                                       nblocks, d, ptrs, np_, _ptr(sc), chunk_blocks, variant,
+                                       _ptr(ws), ws.numel() * 8, _stream(stream)),
+              "hers_search_stream")
+    return sc
+
+
+def hers_search_stream_workspace_bytes(d, nprobes, chunk_blocks):
+    return int(lib().hers_search_stream_workspace_bytes(d, nprobes, chunk_blocks))
 
 
 def hers_decrypt_scores(ctx: Context, keys: Keys, scores_ct, m: int, out=None, stream=None):
@@ -451,6 +486,9 @@ class Server:
         if rc != -4:
             self._bufs.pop(rid, None)
         return rc, lat.value
+
+    def pause(self, paused: bool = True):
+        self.ctx.check(lib().hers_server_pause(self.h, 1 if paused else 0), "hers_server_pause")
 
     def stats(self):
         v = [ctypes.c_uint64() for _ in range(6)]

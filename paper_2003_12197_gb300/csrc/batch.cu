@@ -32,7 +32,7 @@ __device__ __forceinline__ void madw_b(uint64_t& acc, uint32_t a, uint32_t b) {
     asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
-template <int NP, int STAGES, int DPS, int MINB>
+template <int NP, int NB, int STAGES, int DPS, int MINB>
 __global__ void __launch_bounds__(TILE + 32, MINB)
     k_tensor_batched(const BatchChunk* __restrict__ chunks, const BatchUnit* __restrict__ units,
                      uint32_t nunits, uint32_t* counter, uint64_t* __restrict__ X, int* err) {
@@ -41,7 +41,9 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
     __shared__ uint32_t hdr_unit[STAGES], hdr_si[STAGES];
     constexpr int RUN = DPS * 2 * TILE;
-    constexpr int STAGE_WORDS = (NP + 1) * RUN;
+    constexpr int STAGE_WORDS = (NP + NB) * RUN;  // NP probe runs, then NB gallery runs
+    // per-thread running sums of the folded chunks: [q][j][c][TILE] after the ring
+    uint64_t* foldbuf = sm + (size_t)STAGES * STAGE_WORDS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -85,15 +87,16 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
                     const uint32_t nd = min((uint32_t)DPS, Ch.d - si * DPS);
                     const uint32_t bytes = nd * 2 * TILE * 8;
                     uint64_t* dst = sm + (size_t)st * STAGE_WORDS;
-                    mbar_expect_tx(&full[st], bytes * (Ch.np + 1));
+                    mbar_expect_tx(&full[st], bytes * (Ch.np + U.nb));
                     const uint64_t off = resident_offset(0, U.limb, U.tile * TILE, Ch.d, 0, 0) +
                                          (uint64_t)si * RUN;
-                    for (uint32_t p = 0; p < Ch.np; p++)
-                        bulk_g2s(dst + p * RUN, Ch.probe[p] + off, bytes, &full[st], pol_p);
-                    bulk_g2s(dst + NP * RUN,
-                             Ch.gallery + resident_offset(U.block, U.limb, U.tile * TILE, Ch.d, 0, 0) +
-                                 (uint64_t)si * RUN,
-                             bytes, &full[st], pol_g);
+                    for (uint32_t q = 0; q < Ch.np; q++)
+                        bulk_g2s(dst + q * RUN, Ch.probe[q] + off, bytes, &full[st], pol_p);
+                    for (uint32_t j = 0; j < U.nb; j++)
+                        bulk_g2s(dst + (NP + j) * RUN,
+                                 Ch.gallery + resident_offset(U.block + j, U.limb, U.tile * TILE, Ch.d, 0, 0) +
+                                     (uint64_t)si * RUN,
+                                 bytes, &full[st], pol_g);
                 }
                 if (stop || failed) break;
             }
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
 
     // consumers
     const int t = threadIdx.x;
-    uint64_t s[NP][9], fold[NP][3];
+    uint64_t s[NP][NB][9];
     for (uint32_t g = 0;; g++) {
         const int st = (int)(g % STAGES);
         if (!mbar_wait(&full[st], (g / STAGES) & 1)) {
@@ -116,43 +119,58 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
         const uint32_t u = hdr_unit[st], si = hdr_si[st];
         if (u == UNIT_STOP) break;
         const BatchUnit U = units[u];
-        const uint32_t d = chunks[U.chunk].d, np = chunks[U.chunk].np;
+        const uint32_t d = chunks[U.chunk].d, np = chunks[U.chunk].np, nbu = U.nb;
         const int l = U.limb;
         const uint64_t p = c_mod[l];
         if (si == 0) {
 #pragma unroll
-            for (int q = 0; q < NP; q++) {
-                fold[q][0] = fold[q][1] = fold[q][2] = 0;
+            for (int q = 0; q < NP; q++)
 #pragma unroll
-                for (int r = 0; r < 9; r++) s[q][r] = 0;
-            }
+                for (int j = 0; j < NB; j++) {
+#pragma unroll
+                    for (int r = 0; r < 9; r++) s[q][j][r] = 0;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) foldbuf[((q * NB + j) * 3 + c) * TILE + t] = 0;
+                }
         }
         const uint32_t nd = min((uint32_t)DPS, d - si * DPS);
         const uint64_t* base = sm + (size_t)st * STAGE_WORDS + t;
 #pragma unroll
         for (int dd = 0; dd < DPS; dd++) {
             if ((uint32_t)dd < nd) {
-                const uint64_t B0 = base[NP * RUN + dd * 2 * TILE], B1 = base[NP * RUN + dd * 2 * TILE + TILE];
-                const uint32_t b0l = (uint32_t)B0, b0h = (uint32_t)(B0 >> 32);
-                const uint32_t b1l = (uint32_t)B1, b1h = (uint32_t)(B1 >> 32);
-                const uint32_t b0s = b0l + b0h, b1s = b1l + b1h;
-                const uint32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
+                uint32_t a0l[NP], a0h[NP], a1l[NP], a1h[NP];
 #pragma unroll
                 for (int q = 0; q < NP; q++) {
-                    if ((uint32_t)q < np) {
-                        const uint64_t A0 = base[q * RUN + dd * 2 * TILE], A1 = base[q * RUN + dd * 2 * TILE + TILE];
-                        const uint32_t a0l = (uint32_t)A0, a0h = (uint32_t)(A0 >> 32);
-                        const uint32_t a1l = (uint32_t)A1, a1h = (uint32_t)(A1 >> 32);
-                        const uint32_t sal = a0l + a1l, sah = a0h + a1h;
-                        madw_b(s[q][0], a0l, b0l);
-                        madw_b(s[q][1], a0h, b0h);
-                        madw_b(s[q][2], a0l + a0h, b0s);
-                        madw_b(s[q][3], a1l, b1l);
-                        madw_b(s[q][4], a1h, b1h);
-                        madw_b(s[q][5], a1l + a1h, b1s);
-                        madw_b(s[q][6], sal, sbl);
-                        madw_b(s[q][7], sah, sbh);
-                        madw_b(s[q][8], sal + sah, sbs);
+                    const uint64_t A0 = base[q * RUN + dd * 2 * TILE], A1 = base[q * RUN + dd * 2 * TILE + TILE];
+                    a0l[q] = (uint32_t)A0;
+                    a0h[q] = (uint32_t)(A0 >> 32);
+                    a1l[q] = (uint32_t)A1;
+                    a1h[q] = (uint32_t)(A1 >> 32);
+                }
+#pragma unroll
+                for (int j = 0; j < NB; j++) {
+                    if ((uint32_t)j < nbu) {
+                        const uint64_t* gp = base + (NP + j) * RUN + dd * 2 * TILE;
+                        const uint64_t B0 = gp[0], B1 = gp[TILE];
+                        const uint32_t b0l = (uint32_t)B0, b0h = (uint32_t)(B0 >> 32);
+                        const uint32_t b1l = (uint32_t)B1, b1h = (uint32_t)(B1 >> 32);
+                        const uint32_t b0s = b0l + b0h, b1s = b1l + b1h;
+                        const uint32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
+#pragma unroll
+                        for (int q = 0; q < NP; q++) {
+                            if ((uint32_t)q < np) {
+                                const uint32_t sal = a0l[q] + a1l[q], sah = a0h[q] + a1h[q];
+                                madw_b(s[q][j][0], a0l[q], b0l);
+                                madw_b(s[q][j][1], a0h[q], b0h);
+                                madw_b(s[q][j][2], a0l[q] + a0h[q], b0s);
+                                madw_b(s[q][j][3], a1l[q], b1l);
+                                madw_b(s[q][j][4], a1h[q], b1h);
+                                madw_b(s[q][j][5], a1l[q] + a1h[q], b1s);
+                                madw_b(s[q][j][6], sal, sbl);
+                                madw_b(s[q][j][7], sah, sbh);
+                                madw_b(s[q][j][8], sal + sah, sbs);
+                            }
+                        }
                     }
                 }
             }
@@ -162,31 +180,38 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
         const uint32_t done = si * DPS + nd;
         if (done % BKCHUNK == 0 || done == d) {
 #pragma unroll
-            for (int q = 0; q < NP; q++) {
-                uint64_t v[3];
+            for (int q = 0; q < NP; q++)
 #pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    const uint64_t LL = s[q][3 * c], HH = s[q][3 * c + 1], MM = s[q][3 * c + 2];
-                    v[c] = reduce64(shoup_lazy(LL, 1, c_one_s[l], p) +
-                                        shoup_lazy(MM - HH - LL, c_r27[l], c_r27_s[l], p) +
-                                        shoup_lazy(HH, c_r54[l], c_r54_s[l], p),
-                                    l);
-                    s[q][3 * c] = s[q][3 * c + 1] = s[q][3 * c + 2] = 0;
+                for (int j = 0; j < NB; j++) {
+                    uint64_t v[3];
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        const uint64_t LL = s[q][j][3 * c], HH = s[q][j][3 * c + 1], MM = s[q][j][3 * c + 2];
+                        v[c] = reduce64(shoup_lazy(LL, 1, c_one_s[l], p) +
+                                            shoup_lazy(MM - HH - LL, c_r27[l], c_r27_s[l], p) +
+                                            shoup_lazy(HH, c_r54[l], c_r54_s[l], p),
+                                        l);
+                        s[q][j][3 * c] = s[q][j][3 * c + 1] = s[q][j][3 * c + 2] = 0;
+                    }
+                    uint64_t* f = foldbuf + (q * NB + j) * 3 * TILE + t;
+                    f[0] = add_mod(f[0], v[0], p);
+                    f[2 * TILE] = add_mod(f[2 * TILE], v[1], p);
+                    f[TILE] = add_mod(f[TILE], sub_mod(sub_mod(v[2], v[0], p), v[1], p), p);
                 }
-                fold[q][0] = add_mod(fold[q][0], v[0], p);
-                fold[q][2] = add_mod(fold[q][2], v[1], p);
-                fold[q][1] = add_mod(fold[q][1], sub_mod(sub_mod(v[2], v[0], p), v[1], p), p);
-            }
         }
         if (done == d) {
             const int k = U.tile * TILE + t;
 #pragma unroll
             for (int q = 0; q < NP; q++)
-                if ((uint32_t)q < np) {
-                    const uint64_t pair = chunks[U.chunk].pair[q] + U.block;
+                if ((uint32_t)q < np)
 #pragma unroll
-                    for (int c = 0; c < 3; c++) X[((pair * 3 + c) * 5 + l) * N + k] = fold[q][c];
-                }
+                    for (int j = 0; j < NB; j++)
+                        if ((uint32_t)j < nbu) {
+                            const uint64_t pair = chunks[U.chunk].pair[q] + U.block + j;
+                            const uint64_t* f = foldbuf + (q * NB + j) * 3 * TILE + t;
+#pragma unroll
+                            for (int c = 0; c < 3; c++) X[((pair * 3 + c) * 5 + l) * N + k] = f[c * TILE];
+                        }
         }
     }
 }
@@ -195,21 +220,24 @@ using BatchFn = void (*)(const BatchChunk*, const BatchUnit*, uint32_t, uint32_t
 struct BatchVariant {
     const char* name;
     BatchFn fn;
-    int np, stages, dps, minb;
+    int np, nb, stages, dps, minb;
 };
-#define HERS_BV(NP, S, D, M) \
-    {"np" #NP "_s" #S "_d" #D "_m" #M, k_tensor_batched<NP, S, D, M>, NP, S, D, M}
+#define HERS_BV(NP, NB, S, D, M) \
+    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M, k_tensor_batched<NP, NB, S, D, M>, NP, NB, S, D, M}
 static const BatchVariant kBatchVariants[] = {
-    HERS_BV(1, 4, 2, 3), HERS_BV(2, 3, 2, 2), HERS_BV(2, 2, 4, 2),
-    HERS_BV(4, 2, 2, 1), HERS_BV(4, 3, 1, 1),
+    HERS_BV(1, 1, 4, 2, 3), HERS_BV(2, 1, 2, 4, 2), HERS_BV(2, 2, 2, 2, 2),
+    HERS_BV(2, 2, 4, 2, 1), HERS_BV(4, 1, 4, 2, 1), HERS_BV(1, 2, 3, 2, 3),
 };
 #undef HERS_BV
 constexpr int NUM_BATCH_VARIANTS = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
-static int batch_smem(const BatchVariant& v) { return v.stages * (v.np + 1) * v.dps * 2 * TILE * 8; }
+static int batch_smem(const BatchVariant& v) {
+    return v.stages * (v.np + v.nb) * v.dps * 2 * TILE * 8 + v.np * v.nb * 3 * TILE * 8;
+}
 
 int batch_variant_count() { return NUM_BATCH_VARIANTS; }
 int batch_variant_np(int v) { return kBatchVariants[v].np; }
+int batch_variant_nb(int v) { return kBatchVariants[v].nb; }
 
 // Direct launch of the persistent kernel of variant v over device tables.
 cudaError_t launch_batched(int v, const BatchChunk* d_chunks, const BatchUnit* d_units, uint32_t nunits,
@@ -278,8 +306,8 @@ namespace hers {
 // a gallery is streamed once per chunk of NP covering items.  Units are
 // block-major, then limb, tile and chunk, so the chunks of one tile are
 // adjacent and the later ones find the gallery rows in L2.
-void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, std::vector<BatchChunk>& chunks,
-                 std::vector<BatchUnit>& units, uint32_t* ngroups) {
+void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, int nb_max,
+                 std::vector<BatchChunk>& chunks, std::vector<BatchUnit>& units, uint32_t* ngroups) {
     std::map<std::pair<const uint64_t*, uint32_t>, std::vector<uint32_t>> by_gallery;
     std::vector<std::pair<const uint64_t*, uint32_t>> order;
     for (uint32_t i = 0; i < nitems; i++) {
@@ -318,11 +346,13 @@ void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, std::vecto
                 chunks.push_back(ch);
             }
             const uint32_t nch = (uint32_t)chunks.size() - first;
-            for (uint64_t blk = s0; blk < s1; blk++)
+            for (uint64_t blk = s0; blk < s1; blk += nb_max) {
+                const uint32_t nbu = (uint32_t)std::min<uint64_t>(nb_max, s1 - blk);
                 for (uint16_t l = 0; l < 5; l++)
                     for (uint16_t tl = 0; tl < NTILES; tl++)
                         for (uint32_t c2 = 0; c2 < nch; c2++)
-                            units.push_back({first + c2, (uint32_t)blk, l, tl, 0});
+                            units.push_back({first + c2, (uint32_t)blk, l, tl, nbu});
+            }
         }
     }
     if (ngroups) *ngroups = groups;
@@ -332,14 +362,14 @@ void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, std::vecto
 
 namespace {
 
-Plan make_plan(const hers_batch_item* items, uint32_t nitems, int np_max) {
+Plan make_plan(const hers_batch_item* items, uint32_t nitems, int np_max, int nb_max) {
     Plan P;
     std::vector<RangeItem> r(nitems);
     for (uint32_t i = 0; i < nitems; i++) {
         r[i] = {items[i].gallery, 0, items[i].nblocks, items[i].d, items[i].probe, P.npairs};
         P.npairs += items[i].nblocks;
     }
-    plan_ranges(r.data(), nitems, np_max, P.chunks, P.units, &P.ngroups);
+    plan_ranges(r.data(), nitems, np_max, nb_max, P.chunks, P.units, &P.ngroups);
     return P;
 }
 
@@ -373,7 +403,7 @@ cudaError_t batch_launch(hers_batch* B, cudaStream_t st, bool traced) {
 int batch_build(hers_batch* B, const hers_batch_item* items, uint32_t nitems, int v) {
     hers_ctx* ctx = B->ctx;
     const BatchVariant& V = kBatchVariants[v];
-    Plan P = make_plan(items, nitems, V.np);
+    Plan P = make_plan(items, nitems, V.np, V.nb);
     if (P.units.size() >= UNIT_STOP) return fail(ctx, HERS_E_INVAL, "hers_batch_create: too many units");
     const size_t cbytes = P.chunks.size() * sizeof(BatchChunk);
     const size_t ubytes = P.units.size() * sizeof(BatchUnit);
@@ -464,7 +494,7 @@ int hers_batch_create(hers_ctx* ctx, const hers_keys* keys, const hers_batch_ite
     for (int v = 0; v < NUM_BATCH_VARIANTS; v++) B->tune_ms[v] = -1;
     int rc = HERS_OK;
     if (forced >= 0 || !(flags & HERS_BATCH_AUTOTUNE)) {
-        rc = batch_build(B, items, nitems, forced >= 0 ? forced : 1);
+        rc = batch_build(B, items, nitems, forced >= 0 ? forced : DEFAULT_BATCH_VARIANT);
     } else {
         // autotune: build every variant, time 3 graph launches each, keep the fastest
         cudaEvent_t e0, e1;

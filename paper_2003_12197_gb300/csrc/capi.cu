@@ -149,7 +149,8 @@ int hers_create(const hers_params* p, int device, hers_ctx** out) {
         delete ctx;
         return HERS_E_CUDA;
     }
-    // twiddles: [mod][fwd, fwd', inv, inv'][N]
+    // twiddles: [mod][forward, inverse][N] pairs (w, floor(w 2^64 / p)); entry 0
+    // of the inverse table: the last inverse stage's twiddle times N^-1
     const size_t words = (size_t)NUM_MODS * 4 * N;
     uint64_t* h = new (std::nothrow) uint64_t[words];
     if (!h) { cudaStreamDestroy(ctx->stream); delete ctx; return HERS_E_NOMEM; }
@@ -159,11 +160,15 @@ int hers_create(const hers_params* p, int device, hers_ctx** out) {
         for (int k = 0; k < N; k++) {
             const int r = h_brev(k, LOGN);
             const uint64_t w = h_pow(psi, (uint64_t)r, pm), wi = h_pow(psi_inv, (uint64_t)r, pm);
-            f[k] = w;
-            f[N + k] = (uint64_t)(((u128)w << 64) / pm);
-            f[2 * N + k] = wi;
-            f[3 * N + k] = (uint64_t)(((u128)wi << 64) / pm);
+            f[2 * k] = w;
+            f[2 * k + 1] = (uint64_t)(((u128)w << 64) / pm);
+            f[2 * N + 2 * k] = wi;
+            f[2 * N + 2 * k + 1] = (uint64_t)(((u128)wi << 64) / pm);
         }
+        const uint64_t ninv = h_pow((uint64_t)N, pm - 2, pm);
+        const uint64_t wl = h_mulmod(f[2 * N + 2], ninv, pm);  // inverse twiddle 1 times N^-1
+        f[2 * N] = wl;
+        f[2 * N + 1] = (uint64_t)(((u128)wl << 64) / pm);
     }
     cudaError_t e = cudaMalloc(&ctx->tw, words * 8);
     if (e == cudaSuccess) e = cudaMemcpy(ctx->tw, h, words * 8, cudaMemcpyHostToDevice);
@@ -262,7 +267,7 @@ int hers_keys_export(hers_ctx* ctx, const hers_keys* keys, int8_t* sk, uint64_t*
 int hers_encrypt_gallery(hers_ctx* ctx, const hers_keys* keys, const int8_t* feats, uint64_t m,
                          uint32_t d, uint64_t seed, uint64_t* gallery, uint64_t* gallery_ct,
                          void* stream) {
-    if (!ctx || !keys || !feats || !gallery)
+    if (!ctx || !keys || !feats || (!gallery && !gallery_ct))
         return fail(ctx, HERS_E_INVAL, "hers_encrypt_gallery: null argument");
     if (m == 0 || d == 0 || d > HERS_MAX_D)
         return fail(ctx, HERS_E_INVAL, "hers_encrypt_gallery: m = %llu, d = %u", (unsigned long long)m, d);
@@ -282,7 +287,7 @@ int hers_encrypt_gallery(hers_ctx* ctx, const hers_keys* keys, const int8_t* fea
         const uint64_t n = nct - c0 < chunk ? nct - c0 : chunk;
         uint64_t* ct = gallery_ct ? gallery_ct + c0 * 4 * N : tmp;
         e = launch_encrypt(ctx->tw, keys->k, feats, m, d, c0, n, false, seed, ct, ctx->err, st);
-        if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, ct, n, c0, d, gallery, st);
+        if (e == cudaSuccess && gallery) e = launch_extend_ntt(ctx->tw, ct, n, c0, d, gallery, st);
     }
     if (tmp) cudaFreeAsync(tmp, st);
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_encrypt_gallery");

@@ -54,11 +54,16 @@ __host__ __device__ __forceinline__ uint64_t resident_offset(uint64_t b, int lim
 constexpr uint32_t MASK27 = (1u << 27) - 1;
 
 // Twiddle table of modulus i inside the table buffer the context owns:
-// [i][fwd w, fwd w', inv w, inv w'][N], w' = floor(w 2^64 / p) (Shoup).
-__device__ __forceinline__ const uint64_t* tw_fwd(const uint64_t* tw, int i) { return tw + (size_t)(4 * i + 0) * N; }
-__device__ __forceinline__ const uint64_t* tw_fwd_s(const uint64_t* tw, int i) { return tw + (size_t)(4 * i + 1) * N; }
-__device__ __forceinline__ const uint64_t* tw_inv(const uint64_t* tw, int i) { return tw + (size_t)(4 * i + 2) * N; }
-__device__ __forceinline__ const uint64_t* tw_inv_s(const uint64_t* tw, int i) { return tw + (size_t)(4 * i + 3) * N; }
+// [i][forward, inverse][N] pairs (w, w'), w' = floor(w 2^64 / p) (Shoup), so
+// one 16-byte load fetches a twiddle with its companion.  Entry 0 of the
+// inverse table (never used as a butterfly twiddle) holds the last inverse
+// stage's twiddle times N^-1.
+__device__ __forceinline__ const ulonglong2* tw_fwd(const uint64_t* tw, int i) {
+    return (const ulonglong2*)(tw + (size_t)4 * N * i);
+}
+__device__ __forceinline__ const ulonglong2* tw_inv(const uint64_t* tw, int i) {
+    return (const ulonglong2*)(tw + (size_t)4 * N * i + 2 * N);
+}
 
 // ---------------------------------------------------------------- arithmetic
 
@@ -253,15 +258,15 @@ __device__ __forceinline__ void sample_uniform(uint64_t seed, uint32_t purpose, 
 //
 // Forward: Cooley-Tukey with psi-powers in bit-reversed order; input residues
 // < 2p, output fully reduced in bit-reversed order: index j holds the
-// evaluation at psi^(2 brev(j) + 1).  Values stay below 4p between stages.
+// evaluation at psi^(2 brev(j) + 1).
 // Inverse: Gentleman-Sande with inverse psi-powers; bit-reversed input < 2p,
-// natural-order output times N^-1, fully reduced.
+// natural-order output times N^-1 (folded into the last stage), fully reduced.
 // All NTT_THREADS threads must call these; they begin and end with a barrier.
 constexpr int NTT_THREADS = 256;
 
 template <int STRIDE>
-__device__ __forceinline__ void ct_phase(uint64_t v[16], int base, const uint64_t* __restrict__ w,
-                                         const uint64_t* __restrict__ ws, uint64_t p) {
+__device__ __forceinline__ void ct_phase(uint64_t v[16], int base, const ulonglong2* __restrict__ w,
+                                         uint64_t p) {
     const uint64_t two_p = 2 * p;
 #pragma unroll
     for (int h = 8; h >= 1; h >>= 1) {
@@ -271,19 +276,22 @@ __device__ __forceinline__ void ct_phase(uint64_t v[16], int base, const uint64_
         for (int a = 0; a < 16; a++) {
             if (a & h) continue;
             const int i = (base + STRIDE * a) / (2 * t);
-            const uint64_t W = __ldg(w + m + i), Ws = __ldg(ws + m + i);
-            uint64_t U = v[a];
-            U = U >= two_p ? U - two_p : U;
-            const uint64_t V = shoup_lazy(v[a + h], W, Ws, p);
+            const ulonglong2 W = __ldg(w + m + i);
+            // no reduction of U: inputs < 2p grow by < 2p per stage, so every
+            // value stays below 26p < 2^59 over the twelve stages
+            const uint64_t U = v[a];
+            const uint64_t V = shoup_lazy(v[a + h], W.x, W.y, p);
             v[a] = U + V;
             v[a + h] = U - V + two_p;
         }
     }
 }
 
-template <int STRIDE>
-__device__ __forceinline__ void gs_phase(uint64_t v[16], int base, const uint64_t* __restrict__ w,
-                                         const uint64_t* __restrict__ ws, uint64_t p) {
+// LAST: this phase holds the final stage (distance 2048), whose outputs are
+// multiplied by N^-1 on the way (twiddle entry 0 carries W N^-1).
+template <int STRIDE, bool LAST>
+__device__ __forceinline__ void gs_phase(uint64_t v[16], int base, const ulonglong2* __restrict__ w,
+                                         uint64_t p, uint64_t ninv, uint64_t ninv_s) {
     const uint64_t two_p = 2 * p;
 #pragma unroll
     for (int h = 1; h <= 8; h <<= 1) {
@@ -292,18 +300,24 @@ __device__ __forceinline__ void gs_phase(uint64_t v[16], int base, const uint64_
 #pragma unroll
         for (int a = 0; a < 16; a++) {
             if (a & h) continue;
-            const int i = (base + STRIDE * a) / (2 * t);
-            const uint64_t W = __ldg(w + m + i), Ws = __ldg(ws + m + i);
             const uint64_t U = v[a], V = v[a + h];
-            const uint64_t S = U + V;
-            v[a] = S >= two_p ? S - two_p : S;
-            v[a + h] = shoup_lazy(U - V + two_p, W, Ws, p);
+            if (LAST && h == 8) {
+                const ulonglong2 W = __ldg(w);
+                v[a] = shoup(U + V, ninv, ninv_s, p);
+                v[a + h] = shoup(U - V + two_p, W.x, W.y, p);
+            } else {
+                const int i = (base + STRIDE * a) / (2 * t);
+                const ulonglong2 W = __ldg(w + m + i);
+                const uint64_t S = U + V;
+                v[a] = S >= two_p ? S - two_p : S;
+                v[a + h] = shoup_lazy(U - V + two_p, W.x, W.y, p);
+            }
         }
     }
 }
 
-__device__ __forceinline__ void ntt_fwd_smem(uint64_t* sm, const uint64_t* __restrict__ w,
-                                             const uint64_t* __restrict__ ws, uint64_t p) {
+__device__ __forceinline__ void ntt_fwd_smem(uint64_t* sm, const ulonglong2* __restrict__ w, uint64_t p,
+                                             uint64_t one_s) {
     const int t = threadIdx.x;
     uint64_t v[16];
     __syncthreads();
@@ -311,7 +325,7 @@ __device__ __forceinline__ void ntt_fwd_smem(uint64_t* sm, const uint64_t* __res
         const int base = t;
 #pragma unroll
         for (int a = 0; a < 16; a++) v[a] = sm[swz(base + 256 * a)];
-        ct_phase<256>(v, base, w, ws, p);
+        ct_phase<256>(v, base, w, p);
 #pragma unroll
         for (int a = 0; a < 16; a++) sm[swz(base + 256 * a)] = v[a];
     }
@@ -320,29 +334,23 @@ __device__ __forceinline__ void ntt_fwd_smem(uint64_t* sm, const uint64_t* __res
         const int base = 256 * (t >> 4) + (t & 15);
 #pragma unroll
         for (int a = 0; a < 16; a++) v[a] = sm[swz(base + 16 * a)];
-        ct_phase<16>(v, base, w, ws, p);
+        ct_phase<16>(v, base, w, p);
 #pragma unroll
         for (int a = 0; a < 16; a++) sm[swz(base + 16 * a)] = v[a];
     }
     __syncwarp();
-    {   // phase C, then full reduction
+    {   // phase C, then full reduction (values < 26p)
         const int base = 16 * t;
 #pragma unroll
         for (int a = 0; a < 16; a++) v[a] = sm[swz(base + a)];
-        ct_phase<1>(v, base, w, ws, p);
-        const uint64_t two_p = 2 * p;
+        ct_phase<1>(v, base, w, p);
 #pragma unroll
-        for (int a = 0; a < 16; a++) {
-            uint64_t x = v[a];
-            x = x >= two_p ? x - two_p : x;
-            sm[swz(base + a)] = csub(x, p);
-        }
+        for (int a = 0; a < 16; a++) sm[swz(base + a)] = csub(shoup_lazy(v[a], 1, one_s, p), p);
     }
     __syncthreads();
 }
 
-__device__ __forceinline__ void ntt_inv_smem(uint64_t* sm, const uint64_t* __restrict__ w,
-                                             const uint64_t* __restrict__ ws, uint64_t p,
+__device__ __forceinline__ void ntt_inv_smem(uint64_t* sm, const ulonglong2* __restrict__ w, uint64_t p,
                                              uint64_t ninv, uint64_t ninv_s) {
     const int t = threadIdx.x;
     uint64_t v[16];
@@ -351,7 +359,7 @@ __device__ __forceinline__ void ntt_inv_smem(uint64_t* sm, const uint64_t* __res
         const int base = 16 * t;
 #pragma unroll
         for (int a = 0; a < 16; a++) v[a] = sm[swz(base + a)];
-        gs_phase<1>(v, base, w, ws, p);
+        gs_phase<1, false>(v, base, w, p, ninv, ninv_s);
 #pragma unroll
         for (int a = 0; a < 16; a++) sm[swz(base + a)] = v[a];
     }
@@ -360,27 +368,27 @@ __device__ __forceinline__ void ntt_inv_smem(uint64_t* sm, const uint64_t* __res
         const int base = 256 * (t >> 4) + (t & 15);
 #pragma unroll
         for (int a = 0; a < 16; a++) v[a] = sm[swz(base + 16 * a)];
-        gs_phase<16>(v, base, w, ws, p);
+        gs_phase<16, false>(v, base, w, p, ninv, ninv_s);
 #pragma unroll
         for (int a = 0; a < 16; a++) sm[swz(base + 16 * a)] = v[a];
     }
     __syncthreads();
-    {   // distances 256 .. 2048, then N^-1
+    {   // distances 256 .. 2048, the last stage times N^-1: fully reduced
         const int base = t;
 #pragma unroll
         for (int a = 0; a < 16; a++) v[a] = sm[swz(base + 256 * a)];
-        gs_phase<256>(v, base, w, ws, p);
+        gs_phase<256, true>(v, base, w, p, ninv, ninv_s);
 #pragma unroll
-        for (int a = 0; a < 16; a++) sm[swz(base + 256 * a)] = shoup(v[a], ninv, ninv_s, p);
+        for (int a = 0; a < 16; a++) sm[swz(base + 256 * a)] = v[a];
     }
     __syncthreads();
 }
 
 __device__ __forceinline__ void ntt_fwd_mod(uint64_t* a, const uint64_t* tw, int i) {
-    ntt_fwd_smem(a, tw_fwd(tw, i), tw_fwd_s(tw, i), c_mod[i]);
+    ntt_fwd_smem(a, tw_fwd(tw, i), c_mod[i], c_one_s[i]);
 }
 __device__ __forceinline__ void ntt_inv_mod(uint64_t* a, const uint64_t* tw, int i) {
-    ntt_inv_smem(a, tw_inv(tw, i), tw_inv_s(tw, i), c_mod[i], c_ninv[i], c_ninv_s[i]);
+    ntt_inv_smem(a, tw_inv(tw, i), c_mod[i], c_ninv[i], c_ninv_s[i]);
 }
 // Out-of-line versions for kernels that run several NTTs among other work:
 // each call then gets its own register allocation.

@@ -113,15 +113,17 @@ struct BatchChunk {  // up to BATCH_NPMAX probes sharing one gallery segment
     uint64_t pair[BATCH_NPMAX];  // pair of probe q at absolute block b: pair[q] + b (mod 2^64)
     uint32_t d, np;
 };
-struct BatchUnit {  // (chunk, absolute block, limb, tile)
+struct BatchUnit {  // (chunk, first absolute block, limb, tile, blocks in the unit)
     uint32_t chunk, block;
     uint16_t limb, tile;
-    uint32_t pad;
+    uint32_t nb;
 };
-void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, std::vector<BatchChunk>& chunks,
-                 std::vector<BatchUnit>& units, uint32_t* ngroups);
+void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, int nb_max,
+                 std::vector<BatchChunk>& chunks, std::vector<BatchUnit>& units, uint32_t* ngroups);
+constexpr int DEFAULT_BATCH_VARIANT = 2;
 int batch_variant_count();
 int batch_variant_np(int v);
+int batch_variant_nb(int v);
 cudaError_t launch_batched(int v, const BatchChunk* d_chunks, const BatchUnit* d_units, uint32_t nunits,
                            uint32_t* d_counter, uint64_t* X, int* err, int device, cudaStream_t st);
 

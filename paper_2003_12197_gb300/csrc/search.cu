@@ -219,7 +219,7 @@ cudaError_t launch_tensor(int variant, const uint64_t* gallery, uint64_t nblocks
 // CTA per polynomial of a contiguous [npolys][N] array; modulus index
 // mod_off + (P % mod_period).
 template <bool INV>
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_batch(const uint64_t* __restrict__ tw,
+__global__ void __launch_bounds__(NTT_THREADS, 3) k_ntt_batch(const uint64_t* __restrict__ tw,
                                                            uint64_t* __restrict__ data,
                                                            int mod_period, int mod_off) {
     extern __shared__ uint64_t sm[];

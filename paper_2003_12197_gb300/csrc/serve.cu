@@ -100,6 +100,7 @@ struct hers_server {
     std::map<uint64_t, Request*> reqs;
     std::thread thr;
     bool stop = false;
+    bool paused = false;  // admission held (requests queue up)
     uint64_t next_id = 1;
     uint64_t n_submitted = 0, n_completed = 0, n_batches = 0, n_entries = 0, max_batch_seen = 0;
     int error = 0;
@@ -245,7 +246,7 @@ void scheduler(hers_server* srv) {
             }
         bool any_busy = false;
         for (Slot* s : srv->slots) any_busy = any_busy || s->busy;
-        if (freeslot && !srv->pending.empty()) {
+        if (freeslot && !srv->pending.empty() && !srv->paused) {
             // admit from the head of the queue while the batch fits in the pool
             size_t take = std::min<size_t>(srv->pending.size(), srv->max_batch);
             std::vector<BatchChunk> chunks;
@@ -268,7 +269,8 @@ void scheduler(hers_server* srv) {
                     words += request_words(G.d, r->end - r->begin);
                 }
                 uint32_t ng = 0;
-                plan_ranges(items.data(), (uint32_t)items.size(), batch_variant_np(srv->variant), chunks, units, &ng);
+                plan_ranges(items.data(), (uint32_t)items.size(), batch_variant_np(srv->variant),
+                            batch_variant_nb(srv->variant), chunks, units, &ng);
                 bytes = words * 8 + (chunks.size() * sizeof(BatchChunk) + ALIGN) +
                         (units.size() * sizeof(BatchUnit) + ALIGN) + ALIGN;
                 if (srv->pool.alloc(bytes, &off)) {
@@ -415,6 +417,16 @@ int hers_server_wait(hers_server* srv, uint64_t id, uint32_t timeout_ms, double*
     srv->reqs.erase(it);
     delete r;
     return st;
+}
+
+int hers_server_pause(hers_server* srv, int paused) {
+    if (!srv) return HERS_E_INVAL;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->paused = paused != 0;
+    }
+    srv->cv_work.notify_all();
+    return HERS_OK;
 }
 
 int hers_server_stats(hers_server* srv, uint64_t* submitted, uint64_t* completed, uint64_t* batches,

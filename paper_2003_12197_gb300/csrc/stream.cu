@@ -1,0 +1,190 @@
+// Streamed search over a gallery kept in canonical form (two limbs,
+// coefficient domain: 32 d bytes per entry, the ciphertexts' own size) in
+// host or device memory.  This is for galleries too large for the 5-prime
+// resident form: 100M entries at d = 64 are 204.8 GB canonical against
+// 512 GB resident.
+//
+// Per chunk of blocks:
+//   1. copy in (from host memory);
+//   2. extend + NTT to the resident form, into a device chunk buffer;
+//   3. one persistent batched tensor launch with every probe;
+//   4. the epilogue;
+//   5. the score ciphertexts are copied into their [probe][block] places.
+// Two chunk slots alternate: chunk c+1's copy and extension (a side stream)
+// overlap chunk c's search (the caller's stream).
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "hers.h"
+#include "internal.h"
+
+using namespace hers;
+
+namespace {
+
+struct SlotLayout {
+    uint64_t staging, resident, X, C, KS, OUT, tables;  // word offsets in the slot
+    uint64_t words;
+};
+
+SlotLayout slot_layout(uint32_t d, uint32_t nprobes, uint32_t chunk, uint64_t table_bytes) {
+    SlotLayout L;
+    uint64_t w = 0;
+    L.staging = w;
+    w += (uint64_t)chunk * d * 4 * N;
+    L.resident = w;
+    w += (uint64_t)chunk * d * 10 * N;
+    const uint64_t pairs = (uint64_t)nprobes * chunk;
+    L.X = w;
+    w += pairs * 15 * N;
+    L.C = w;
+    w += pairs * 6 * N;
+    L.KS = w;
+    w += pairs * 4 * N;
+    L.OUT = w;
+    w += pairs * 4 * N;
+    L.tables = w;
+    w += (table_bytes + 7) / 8 + 64;
+    L.words = (w + 31) / 32 * 32;  // 256-byte multiples
+    return L;
+}
+
+uint64_t table_bytes_for(uint32_t nprobes, uint32_t chunk) {
+    // at most one chunk record per probe and one unit per (block, limb, tile, probe)
+    return (uint64_t)nprobes * sizeof(BatchChunk) + 256 +
+           (uint64_t)chunk * 5 * NTILES * nprobes * sizeof(BatchUnit) + 256 + 64;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t hers_search_stream_workspace_bytes(uint32_t d, uint32_t nprobes, uint32_t chunk_blocks) {
+    return 2 * slot_layout(d, nprobes, chunk_blocks, table_bytes_for(nprobes, chunk_blocks)).words * 8;
+}
+
+int hers_search_stream(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery_ct,
+                       int gallery_on_host, uint64_t nblocks, uint32_t d,
+                       const uint64_t* const* probes, uint32_t nprobes, uint64_t* scores_ct,
+                       uint32_t chunk_blocks, int variant, void* workspace, uint64_t workspace_bytes,
+                       void* stream) {
+    if (!ctx || !keys || !gallery_ct || !probes || !scores_ct || !workspace || nblocks == 0 ||
+        nprobes == 0 || chunk_blocks == 0)
+        return fail(ctx, HERS_E_INVAL, "hers_search_stream: null argument or empty sizes");
+    if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_search_stream: d = %u", d);
+    if (variant < 0 || variant >= batch_variant_count())
+        return fail(ctx, HERS_E_INVAL, "hers_search_stream: variant %d", variant);
+    for (uint32_t p = 0; p < nprobes; p++)
+        if (!probes[p]) return fail(ctx, HERS_E_INVAL, "hers_search_stream: probe %u is null", p);
+    const uint64_t tbytes = table_bytes_for(nprobes, chunk_blocks);
+    const SlotLayout L = slot_layout(d, nprobes, chunk_blocks, tbytes);
+    if (workspace_bytes < 2 * L.words * 8)
+        return fail(ctx, HERS_E_NOMEM, "hers_search_stream: workspace %llu < %llu bytes",
+                    (unsigned long long)workspace_bytes, (unsigned long long)(2 * L.words * 8));
+    DeviceGuard g(ctx->device);
+    cudaStream_t sm = (cudaStream_t)stream, sc = ctx->stream;
+    uint64_t* slot[2] = {(uint64_t*)workspace, (uint64_t*)workspace + L.words};
+    const int np_var = batch_variant_np(variant);
+
+    // Work tables: the same plan for every full chunk, one copy per slot (the
+    // tables point at the slot's resident buffer); the last chunk may be shorter.
+    auto plan = [&](int s, uint32_t nb, std::vector<BatchChunk>& ch, std::vector<BatchUnit>& un) {
+        std::vector<RangeItem> items(nprobes);
+        for (uint32_t p = 0; p < nprobes; p++)
+            items[p] = {slot[s] + L.resident, 0, nb, d, probes[p], (uint64_t)p * nb};
+        uint32_t ng = 0;
+        plan_ranges(items.data(), nprobes, np_var, batch_variant_nb(variant), ch, un, &ng);
+    };
+    const uint64_t nchunks = (nblocks + chunk_blocks - 1) / chunk_blocks;
+    const uint32_t last_nb = (uint32_t)(nblocks - (nchunks - 1) * chunk_blocks);
+    struct Tables {
+        BatchChunk* chunks;
+        BatchUnit* units;
+        uint32_t* counter;
+        uint32_t nunits;
+    };
+    // table sets: [slot][full, last]; the "last" set lives in the same slot
+    // area after a full chunk finished with it, so each slot holds the set
+    // for the chunk it currently runs (re-uploaded when the size changes)
+    Tables T[2][2];
+    std::vector<BatchChunk> hc[2][2];
+    std::vector<BatchUnit> hu[2][2];
+    for (int s = 0; s < 2; s++) {
+        plan(s, chunk_blocks, hc[s][0], hu[s][0]);
+        plan(s, last_nb, hc[s][1], hu[s][1]);
+        for (int k = 0; k < 2; k++) {
+            uint8_t* tb = (uint8_t*)(slot[s] + L.tables);
+            T[s][k].chunks = (BatchChunk*)tb;
+            T[s][k].units = (BatchUnit*)(tb + (hc[s][k].size() * sizeof(BatchChunk) + 255) / 256 * 256);
+            T[s][k].counter = (uint32_t*)((uint8_t*)T[s][k].units +
+                                          (hu[s][k].size() * sizeof(BatchUnit) + 255) / 256 * 256);
+            T[s][k].nunits = (uint32_t)hu[s][k].size();
+        }
+    }
+
+    cudaEvent_t ev_ext[2], ev_free[2], ev_join;
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < 2 && e == cudaSuccess; s++) {
+        e = cudaEventCreateWithFlags(&ev_ext[s], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_free[s], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_search_stream: events");
+    // the side stream starts after work already queued on the caller's stream
+    cudaEventRecord(ev_join, sm);
+    cudaStreamWaitEvent(sc, ev_join, 0);
+
+    int table_kind[2] = {-1, -1};
+    for (uint64_t c = 0; c < nchunks && e == cudaSuccess; c++) {
+        const int s = (int)(c & 1);
+        const uint64_t b0 = c * chunk_blocks;
+        const uint32_t nb = (uint32_t)std::min<uint64_t>(chunk_blocks, nblocks - b0);
+        const int kind = (c == nchunks - 1 && nb != chunk_blocks) ? 1 : 0;
+        uint64_t* base = slot[s];
+        // side stream: wait until the slot's previous chunk has been searched
+        if (c >= 2) cudaStreamWaitEvent(sc, ev_free[s], 0);
+        const uint64_t* src = gallery_ct + b0 * d * 4 * N;
+        const uint64_t* cts = src;
+        if (gallery_on_host) {
+            e = cudaMemcpyAsync(base + L.staging, src, (uint64_t)nb * d * 4 * N * 8, cudaMemcpyHostToDevice, sc);
+            cts = base + L.staging;
+        }
+        if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, cts, (uint64_t)nb * d, 0, d, base + L.resident, sc);
+        if (e == cudaSuccess && table_kind[s] != kind) {
+            const Tables& t = T[s][kind];
+            e = cudaMemcpyAsync(t.chunks, hc[s][kind].data(), hc[s][kind].size() * sizeof(BatchChunk),
+                                cudaMemcpyHostToDevice, sc);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(t.units, hu[s][kind].data(), hu[s][kind].size() * sizeof(BatchUnit),
+                                    cudaMemcpyHostToDevice, sc);
+            table_kind[s] = kind;  // a pageable source is staged before cudaMemcpyAsync returns
+        }
+        cudaEventRecord(ev_ext[s], sc);
+        // caller's stream: search the chunk
+        cudaStreamWaitEvent(sm, ev_ext[s], 0);
+        const Tables& t = T[s][kind];
+        const uint64_t npairs = (uint64_t)nprobes * nb;
+        if (e == cudaSuccess)
+            e = launch_batched(variant, t.chunks, t.units, t.nunits, t.counter, base + L.X, ctx->err,
+                               ctx->device, sm);
+        cudaEventRecord(ev_free[s], sm);  // the resident chunk buffer may be refilled
+        if (e == cudaSuccess)
+            e = launch_epilogue(ctx->tw, keys->k, npairs, base + L.X, base + L.C, base + L.KS, base + L.OUT, sm);
+        for (uint32_t p = 0; p < nprobes && e == cudaSuccess; p++)
+            e = cudaMemcpyAsync(scores_ct + ((uint64_t)p * nblocks + b0) * 4 * N,
+                                base + L.OUT + (uint64_t)p * nb * 4 * N, (uint64_t)nb * 4 * N * 8,
+                                cudaMemcpyDeviceToDevice, sm);
+    }
+    // join the side stream into the caller's
+    cudaEventRecord(ev_join, sc);
+    cudaStreamWaitEvent(sm, ev_join, 0);
+    for (int s = 0; s < 2; s++) {
+        cudaEventDestroy(ev_ext[s]);
+        cudaEventDestroy(ev_free[s]);
+    }
+    cudaEventDestroy(ev_join);
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search_stream");
+}
+
+}  // extern "C"

@@ -438,3 +438,13 @@ def test_paper_parameter_facts():
     blocks = -(-100_000_000 // 4096)
     assert blocks == facts["table3_blocks_100M"]["value"]
     assert round(blocks * 64 * 2 * 2 * 4096 * 8 / 1e9, 1) == 204.8
+
+
+def test_block_rows_encryption_matches_full_array_form():
+    n, d = 16, 3
+    sk, pk, _ = O.keygen(9, n)
+    feats = np.random.default_rng(4).integers(-127, 128, (3 * n - 5, d)).astype(np.int8)
+    for b in range(3):
+        a = O.encrypt_gallery_block(pk, feats, b, seed=12, n=n)
+        r = O.encrypt_gallery_block_rows(pk, feats[b * n:(b + 1) * n], b, seed=12, n=n)
+        assert np.array_equal(a, r)
