@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--oracle-blocks", type=int, default=4,
                     help="scale: random blocks checked against the oracle (plus the mate blocks "
                          "of the first probes)")
+    ap.add_argument("--batch-variant", default=None,
+                    help="batched: kernel shape by name (skips the batched autotuner)")
     ap.add_argument("--variant", default=None,
                     help="tensor-kernel shape by name (skips the autotuner), e.g. nb2_s2_d4_m2")
     return ap.parse_args()
@@ -481,7 +483,10 @@ def run_batched(args):
     plain_ms = e0.elapsed_time(e1) / args.steps
 
     # the batched plan: one graph launch per step
-    b = H.Batch(ctx, keys, items, flags=H.BATCH_AUTOTUNE)
+    flags = H.BATCH_AUTOTUNE
+    if args.batch_variant:
+        flags = H.batch_variant_flag(H.hers_batch_variants().index(args.batch_variant))
+    b = H.Batch(ctx, keys, items, flags=flags)
     for _ in range(max(1, args.warmup)):
         b.run()
     torch.cuda.synchronize()

@@ -302,10 +302,12 @@ namespace hers {
 // resident gallery at `gallery` (block 0) with dimension d; its pair of
 // block b is pair_base_i + (b - begin_i).  For every gallery, the items' range
 // end points cut the blocks into segments over which the set of covering items
-// is constant; each segment with covering items is a group, so every block of
-// a gallery is streamed once per chunk of NP covering items.  Units are
-// block-major, then limb, tile and chunk, so the chunks of one tile are
-// adjacent and the later ones find the gallery rows in L2.
+// is constant; each segment with covering items is a group.
+// Unit order within a segment: (limb, tile) outermost, then block, then probe
+// chunk.  Units in flight at one time then share one (limb, tile): the probe
+// rows they need (all the segment's probes, d x 4 KiB each) stay in L2 across
+// blocks, and the chunks of one block run back to back, so a gallery run is
+// read from HBM once and from L2 by the other chunks.
 void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, int nb_max,
                  std::vector<BatchChunk>& chunks, std::vector<BatchUnit>& units, uint32_t* ngroups) {
     std::map<std::pair<const uint64_t*, uint32_t>, std::vector<uint32_t>> by_gallery;
@@ -346,13 +348,13 @@ void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, int nb_max
                 chunks.push_back(ch);
             }
             const uint32_t nch = (uint32_t)chunks.size() - first;
-            for (uint64_t blk = s0; blk < s1; blk += nb_max) {
-                const uint32_t nbu = (uint32_t)std::min<uint64_t>(nb_max, s1 - blk);
-                for (uint16_t l = 0; l < 5; l++)
-                    for (uint16_t tl = 0; tl < NTILES; tl++)
+            for (uint16_t l = 0; l < 5; l++)
+                for (uint16_t tl = 0; tl < NTILES; tl++)
+                    for (uint64_t blk = s0; blk < s1; blk += nb_max) {
+                        const uint32_t nbu = (uint32_t)std::min<uint64_t>(nb_max, s1 - blk);
                         for (uint32_t c2 = 0; c2 < nch; c2++)
                             units.push_back({first + c2, (uint32_t)blk, l, tl, nbu});
-            }
+                    }
         }
     }
     if (ngroups) *ngroups = groups;
