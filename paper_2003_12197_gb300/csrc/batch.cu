@@ -28,21 +28,124 @@ namespace hers {
 constexpr uint32_t UNIT_STOP = 0xFFFFFFFFu;
 constexpr int BKCHUNK = 32;  // fold period in dimensions (see k_tensor)
 
+// Stage descriptor flags (written by the producer with each stage).
+constexpr uint32_t F_FIRST = 1;  // first stage of a unit: sums start at zero
+constexpr uint32_t F_FOLD = 2;   // fold the 64-bit sums mod p after this stage
+constexpr uint32_t F_LAST = 4;   // last stage of a unit: store the unit's results
+constexpr uint32_t F_STOP = 8;   // no more units: the consumers leave
+
 __device__ __forceinline__ void madw_b(uint64_t& acc, uint32_t a, uint32_t b) {
     asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
-template <int NP, int NB, int STAGES, int DPS, int MINB>
+// A unit's table entries, held in registers by the producer.
+template <int NP>
+struct UnitRegs {
+    const uint64_t* gallery;
+    const uint64_t* probe[NP];
+    uint64_t pair[NP];  // pair of probe q at the unit's first block
+    uint32_t d, np, nb, block, limb, tile;
+};
+
+template <int NP>
+__device__ __forceinline__ void load_unit(UnitRegs<NP>& r, const BatchChunk* __restrict__ chunks,
+                                          const BatchUnit* __restrict__ units, uint32_t u) {
+    const BatchUnit U = units[u];
+    const BatchChunk* C = chunks + U.chunk;
+    r.gallery = C->gallery;
+    r.d = C->d;
+    r.np = C->np;
+#pragma unroll
+    for (int q = 0; q < NP; q++) {  // entries past np are zero in the table
+        r.probe[q] = C->probe[q];
+        r.pair[q] = C->pair[q] + U.block;
+    }
+    r.nb = U.nb;
+    r.block = U.block;
+    r.limb = U.limb;
+    r.tile = U.tile;
+}
+
+// One stage's products into the 64-bit sums: for dd < nd, probe q < np,
+// block j < nb, the 9 digit products of (probe row q) x (gallery row j).  With
+// FULL (nd = DPS, np = NP, nb = NB) the loops carry no predicates.
+template <int NP, int NB, int DPS, bool FULL>
+__device__ __forceinline__ void stage_products(uint64_t (&s)[NP][NB][9], const uint64_t* base, uint32_t nd,
+                                               uint32_t np, uint32_t nbu) {
+    constexpr int RUN = DPS * 2 * TILE;
+#pragma unroll
+    for (int dd = 0; dd < DPS; dd++) {
+        if (FULL || (uint32_t)dd < nd) {
+            uint32_t a0l[NP], a0h[NP], a1l[NP], a1h[NP];
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                const uint64_t A0 = base[q * RUN + dd * 2 * TILE], A1 = base[q * RUN + dd * 2 * TILE + TILE];
+                a0l[q] = (uint32_t)A0;
+                a0h[q] = (uint32_t)(A0 >> 32);
+                a1l[q] = (uint32_t)A1;
+                a1h[q] = (uint32_t)(A1 >> 32);
+            }
+#pragma unroll
+            for (int j = 0; j < NB; j++) {
+                if (FULL || (uint32_t)j < nbu) {
+                    const uint64_t* gp = base + (NP + j) * RUN + dd * 2 * TILE;
+                    const uint64_t B0 = gp[0], B1 = gp[TILE];
+                    const uint32_t b0l = (uint32_t)B0, b0h = (uint32_t)(B0 >> 32);
+                    const uint32_t b1l = (uint32_t)B1, b1h = (uint32_t)(B1 >> 32);
+                    const uint32_t b0s = b0l + b0h, b1s = b1l + b1h;
+                    const uint32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
+#pragma unroll
+                    for (int q = 0; q < NP; q++) {
+                        if (FULL || (uint32_t)q < np) {
+                            const uint32_t sal = a0l[q] + a1l[q], sah = a0h[q] + a1h[q];
+                            madw_b(s[q][j][0], a0l[q], b0l);
+                            madw_b(s[q][j][1], a0h[q], b0h);
+                            madw_b(s[q][j][2], a0l[q] + a0h[q], b0s);
+                            madw_b(s[q][j][3], a1l[q], b1l);
+                            madw_b(s[q][j][4], a1h[q], b1h);
+                            madw_b(s[q][j][5], a1l[q] + a1h[q], b1s);
+                            madw_b(s[q][j][6], sal, sbl);
+                            madw_b(s[q][j][7], sah, sbh);
+                            madw_b(s[q][j][8], sal + sah, sbs);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Folds the three digit sums of one component, value = LL + (MM - HH - LL) 2^27
+// + HH 2^54, to a residue mod p_l in [0, p).
+__device__ __forceinline__ uint64_t fold3(uint64_t LL, uint64_t HH, uint64_t MM, int l, uint64_t p) {
+    return reduce64(shoup_lazy(LL, 1, c_one_s[l], p) + shoup_lazy(MM - HH - LL, c_r27[l], c_r27_s[l], p) +
+                        shoup_lazy(HH, c_r54[l], c_r54_s[l], p),
+                    l);
+}
+
+// Persistent batched tensor kernel.  A CTA has TILE consumer threads (one
+// coefficient each) and one producer warp.  The producer's elected lane
+// claims units from the atomic counter one unit ahead (the claim and the
+// unit's table reads overlap the current unit's stages), and for each stage
+// writes a descriptor (dimensions, probes, blocks, limb, flags; on the last
+// stage the output pairs) into shared memory before the stage's copies, so
+// the consumers read no tables from global memory.  FREG keeps the folded
+// sums in registers (for 1-CTA/SM shapes); otherwise they live in shared
+// memory after the ring.
+
+template <int NP, int NB, int STAGES, int DPS, int MINB, int FREG>
 __global__ void __launch_bounds__(TILE + 32, MINB)
     k_tensor_batched(const BatchChunk* __restrict__ chunks, const BatchUnit* __restrict__ units,
                      uint32_t nunits, uint32_t* counter, uint64_t* __restrict__ X, int* err) {
     static_assert(BKCHUNK % DPS == 0, "stages must not straddle a fold");
+    static_assert(NP <= BATCH_NPMAX && NB <= 15 && DPS <= 255, "descriptor fields");
     extern __shared__ __align__(128) uint64_t sm[];
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
-    __shared__ uint32_t hdr_unit[STAGES], hdr_si[STAGES];
+    __shared__ uint32_t hdr_info[STAGES], hdr_k0[STAGES];
+    __shared__ uint64_t hdr_pair[STAGES][NP];
     constexpr int RUN = DPS * 2 * TILE;
     constexpr int STAGE_WORDS = (NP + NB) * RUN;  // NP probe runs, then NB gallery runs
-    // per-thread running sums of the folded chunks: [q][j][c][TILE] after the ring
+    // FREG = 0: per-thread folded sums [q][j][c][TILE] after the ring
     uint64_t* foldbuf = sm + (size_t)STAGES * STAGE_WORDS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -55,22 +158,18 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
     }
     __syncthreads();
 
-    if (warp == TILE / 32) {  // producer warp: claims units, streams their stages
+    if (warp == TILE / 32) {  // producer warp
         if (lane == 0) {
             const uint64_t pol_g = policy_evict_first(), pol_p = policy_evict_last();
             uint32_t g = 0;  // stages issued by this CTA
             bool failed = false;
-            for (;;) {
-                const uint32_t u = atomicAdd(counter, 1u);
+            uint32_t u = atomicAdd(counter, 1u);
+            UnitRegs<NP> cur = {}, nxt = {};
+            if (u < nunits) load_unit(cur, chunks, units, u);
+            while (!failed) {
                 const bool stop = u >= nunits;
-                BatchUnit U = {};
-                BatchChunk Ch = {};
-                uint32_t nst = 1;
-                if (!stop) {
-                    U = units[u];
-                    Ch = chunks[U.chunk];
-                    nst = (Ch.d + DPS - 1) / DPS;
-                }
+                const uint32_t un = stop ? UNIT_STOP : atomicAdd(counter, 1u);  // next unit, claimed now
+                const uint32_t nst = stop ? 1 : (cur.d + DPS - 1) / DPS;
                 for (uint32_t si = 0; si < nst; si++, g++) {
                     const int st = (int)(g % STAGES);
                     if (g >= STAGES && !mbar_wait(&empty[st], ((g / STAGES) + 1) & 1)) {
@@ -78,27 +177,42 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
                         failed = true;
                         break;
                     }
-                    hdr_unit[st] = stop ? UNIT_STOP : u;
-                    hdr_si[st] = si;
                     if (stop) {
+                        hdr_info[st] = F_STOP << 20;
                         mbar_arrive(&full[st]);
                         continue;
                     }
-                    const uint32_t nd = min((uint32_t)DPS, Ch.d - si * DPS);
+                    const uint32_t nd = min((uint32_t)DPS, cur.d - si * DPS), done = si * DPS + nd;
+                    const uint32_t flags = (si == 0 ? F_FIRST : 0u) |
+                                           ((done % BKCHUNK == 0 || done == cur.d) ? F_FOLD : 0u) |
+                                           (done == cur.d ? F_LAST : 0u);
+                    hdr_info[st] = nd | (cur.np << 8) | (cur.nb << 12) | (cur.limb << 16) | (flags << 20);
+                    if (flags & F_LAST) {
+                        hdr_k0[st] = cur.tile * TILE;
+#pragma unroll
+                        for (int q = 0; q < NP; q++) hdr_pair[st][q] = cur.pair[q];
+                    }
                     const uint32_t bytes = nd * 2 * TILE * 8;
                     uint64_t* dst = sm + (size_t)st * STAGE_WORDS;
-                    mbar_expect_tx(&full[st], bytes * (Ch.np + U.nb));
-                    const uint64_t off = resident_offset(0, U.limb, U.tile * TILE, Ch.d, 0, 0) +
+                    mbar_expect_tx(&full[st], bytes * (cur.np + cur.nb));
+                    const uint64_t off = resident_offset(0, cur.limb, cur.tile * TILE, cur.d, 0, 0) +
                                          (uint64_t)si * RUN;
-                    for (uint32_t q = 0; q < Ch.np; q++)
-                        bulk_g2s(dst + q * RUN, Ch.probe[q] + off, bytes, &full[st], pol_p);
-                    for (uint32_t j = 0; j < U.nb; j++)
-                        bulk_g2s(dst + (NP + j) * RUN,
-                                 Ch.gallery + resident_offset(U.block + j, U.limb, U.tile * TILE, Ch.d, 0, 0) +
-                                     (uint64_t)si * RUN,
-                                 bytes, &full[st], pol_g);
+#pragma unroll
+                    for (int q = 0; q < NP; q++)
+                        if ((uint32_t)q < cur.np) bulk_g2s(dst + q * RUN, cur.probe[q] + off, bytes, &full[st], pol_p);
+#pragma unroll
+                    for (int j = 0; j < NB; j++)
+                        if ((uint32_t)j < cur.nb)
+                            bulk_g2s(dst + (NP + j) * RUN,
+                                     cur.gallery + resident_offset(cur.block + j, cur.limb, cur.tile * TILE, cur.d, 0, 0) +
+                                         (uint64_t)si * RUN,
+                                     bytes, &full[st], pol_g);
+                    // the next unit's tables, once this unit's first stage is on its way
+                    if (si == 0 && un < nunits) load_unit(nxt, chunks, units, un);
                 }
-                if (stop || failed) break;
+                if (stop) break;
+                u = un;
+                cur = nxt;
             }
             // drain: the copies of the last stages issued land before this thread leaves
             for (uint32_t i = g > STAGES ? g - STAGES : 0; i < g; i++)
@@ -110,19 +224,27 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
     // consumers
     const int t = threadIdx.x;
     uint64_t s[NP][NB][9];
+    uint64_t f[NP][NB][3];  // FREG only
     for (uint32_t g = 0;; g++) {
         const int st = (int)(g % STAGES);
         if (!mbar_wait(&full[st], (g / STAGES) & 1)) {
             atomicOr(err, 2);
             return;
         }
-        const uint32_t u = hdr_unit[st], si = hdr_si[st];
-        if (u == UNIT_STOP) break;
-        const BatchUnit U = units[u];
-        const uint32_t d = chunks[U.chunk].d, np = chunks[U.chunk].np, nbu = U.nb;
-        const int l = U.limb;
-        const uint64_t p = c_mod[l];
-        if (si == 0) {
+        const uint32_t info = hdr_info[st];
+        const uint32_t flags = info >> 20;
+        if (flags & F_STOP) break;
+        const uint32_t nd = info & 0xFF, np = (info >> 8) & 15, nbu = (info >> 12) & 15;
+        const int l = (int)((info >> 16) & 15);
+        // what the last stage stores, read before the stage is handed back
+        uint64_t opair[NP];
+        uint32_t k0 = 0;
+        if (flags & F_LAST) {
+            k0 = hdr_k0[st];
+#pragma unroll
+            for (int q = 0; q < NP; q++) opair[q] = hdr_pair[st][q];
+        }
+        if (flags & F_FIRST) {
 #pragma unroll
             for (int q = 0; q < NP; q++)
 #pragma unroll
@@ -130,87 +252,57 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
 #pragma unroll
                     for (int r = 0; r < 9; r++) s[q][j][r] = 0;
 #pragma unroll
-                    for (int c = 0; c < 3; c++) foldbuf[((q * NB + j) * 3 + c) * TILE + t] = 0;
-                }
-        }
-        const uint32_t nd = min((uint32_t)DPS, d - si * DPS);
-        const uint64_t* base = sm + (size_t)st * STAGE_WORDS + t;
-#pragma unroll
-        for (int dd = 0; dd < DPS; dd++) {
-            if ((uint32_t)dd < nd) {
-                uint32_t a0l[NP], a0h[NP], a1l[NP], a1h[NP];
-#pragma unroll
-                for (int q = 0; q < NP; q++) {
-                    const uint64_t A0 = base[q * RUN + dd * 2 * TILE], A1 = base[q * RUN + dd * 2 * TILE + TILE];
-                    a0l[q] = (uint32_t)A0;
-                    a0h[q] = (uint32_t)(A0 >> 32);
-                    a1l[q] = (uint32_t)A1;
-                    a1h[q] = (uint32_t)(A1 >> 32);
-                }
-#pragma unroll
-                for (int j = 0; j < NB; j++) {
-                    if ((uint32_t)j < nbu) {
-                        const uint64_t* gp = base + (NP + j) * RUN + dd * 2 * TILE;
-                        const uint64_t B0 = gp[0], B1 = gp[TILE];
-                        const uint32_t b0l = (uint32_t)B0, b0h = (uint32_t)(B0 >> 32);
-                        const uint32_t b1l = (uint32_t)B1, b1h = (uint32_t)(B1 >> 32);
-                        const uint32_t b0s = b0l + b0h, b1s = b1l + b1h;
-                        const uint32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
-#pragma unroll
-                        for (int q = 0; q < NP; q++) {
-                            if ((uint32_t)q < np) {
-                                const uint32_t sal = a0l[q] + a1l[q], sah = a0h[q] + a1h[q];
-                                madw_b(s[q][j][0], a0l[q], b0l);
-                                madw_b(s[q][j][1], a0h[q], b0h);
-                                madw_b(s[q][j][2], a0l[q] + a0h[q], b0s);
-                                madw_b(s[q][j][3], a1l[q], b1l);
-                                madw_b(s[q][j][4], a1h[q], b1h);
-                                madw_b(s[q][j][5], a1l[q] + a1h[q], b1s);
-                                madw_b(s[q][j][6], sal, sbl);
-                                madw_b(s[q][j][7], sah, sbh);
-                                madw_b(s[q][j][8], sal + sah, sbs);
-                            }
-                        }
+                    for (int c = 0; c < 3; c++) {
+                        if (FREG) f[q][j][c] = 0;
+                        else foldbuf[((q * NB + j) * 3 + c) * TILE + t] = 0;
                     }
                 }
-            }
         }
+        const uint64_t* base = sm + (size_t)st * STAGE_WORDS + t;
+        if (nd == DPS && np == NP && nbu == NB)
+            stage_products<NP, NB, DPS, true>(s, base, nd, np, nbu);
+        else
+            stage_products<NP, NB, DPS, false>(s, base, nd, np, nbu);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
-        const uint32_t done = si * DPS + nd;
-        if (done % BKCHUNK == 0 || done == d) {
+        if (flags & F_FOLD) {
+            const uint64_t p = c_mod[l];
 #pragma unroll
             for (int q = 0; q < NP; q++)
 #pragma unroll
                 for (int j = 0; j < NB; j++) {
-                    uint64_t v[3];
+                    const uint64_t v0 = fold3(s[q][j][0], s[q][j][1], s[q][j][2], l, p);
+                    const uint64_t v2 = fold3(s[q][j][3], s[q][j][4], s[q][j][5], l, p);
+                    const uint64_t vk = fold3(s[q][j][6], s[q][j][7], s[q][j][8], l, p);
 #pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        const uint64_t LL = s[q][j][3 * c], HH = s[q][j][3 * c + 1], MM = s[q][j][3 * c + 2];
-                        v[c] = reduce64(shoup_lazy(LL, 1, c_one_s[l], p) +
-                                            shoup_lazy(MM - HH - LL, c_r27[l], c_r27_s[l], p) +
-                                            shoup_lazy(HH, c_r54[l], c_r54_s[l], p),
-                                        l);
-                        s[q][j][3 * c] = s[q][j][3 * c + 1] = s[q][j][3 * c + 2] = 0;
+                    for (int r = 0; r < 9; r++) s[q][j][r] = 0;
+                    // T0 = v0, T2 = v2, T1 = vk - T0 - T2
+                    const uint64_t v1 = sub_mod(sub_mod(vk, v0, p), v2, p);
+                    if (FREG) {
+                        f[q][j][0] = add_mod(f[q][j][0], v0, p);
+                        f[q][j][1] = add_mod(f[q][j][1], v1, p);
+                        f[q][j][2] = add_mod(f[q][j][2], v2, p);
+                    } else {
+                        uint64_t* fb = foldbuf + (q * NB + j) * 3 * TILE + t;
+                        fb[0] = add_mod(fb[0], v0, p);
+                        fb[TILE] = add_mod(fb[TILE], v1, p);
+                        fb[2 * TILE] = add_mod(fb[2 * TILE], v2, p);
                     }
-                    uint64_t* f = foldbuf + (q * NB + j) * 3 * TILE + t;
-                    f[0] = add_mod(f[0], v[0], p);
-                    f[2 * TILE] = add_mod(f[2 * TILE], v[1], p);
-                    f[TILE] = add_mod(f[TILE], sub_mod(sub_mod(v[2], v[0], p), v[1], p), p);
                 }
         }
-        if (done == d) {
-            const int k = U.tile * TILE + t;
+        if (flags & F_LAST) {
+            const uint32_t k = k0 + t;
 #pragma unroll
             for (int q = 0; q < NP; q++)
                 if ((uint32_t)q < np)
 #pragma unroll
                     for (int j = 0; j < NB; j++)
                         if ((uint32_t)j < nbu) {
-                            const uint64_t pair = chunks[U.chunk].pair[q] + U.block + j;
-                            const uint64_t* f = foldbuf + (q * NB + j) * 3 * TILE + t;
+                            const uint64_t pair = opair[q] + j;
 #pragma unroll
-                            for (int c = 0; c < 3; c++) X[((pair * 3 + c) * 5 + l) * N + k] = f[c * TILE];
+                            for (int c = 0; c < 3; c++)
+                                X[((pair * 3 + c) * 5 + l) * N + k] =
+                                    FREG ? f[q][j][c] : foldbuf[((q * NB + j) * 3 + c) * TILE + t];
                         }
         }
     }
@@ -220,19 +312,23 @@ using BatchFn = void (*)(const BatchChunk*, const BatchUnit*, uint32_t, uint32_t
 struct BatchVariant {
     const char* name;
     BatchFn fn;
-    int np, nb, stages, dps, minb;
+    int np, nb, stages, dps, minb, freg;
 };
-#define HERS_BV(NP, NB, S, D, M) \
-    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M, k_tensor_batched<NP, NB, S, D, M>, NP, NB, S, D, M}
+// name: np<probes>_nb<blocks>_s<stages>_d<dims per stage>_m<CTAs/SM>, and
+// "r" when the folded sums stay in registers
+#define HERS_BV(NP, NB, S, D, M, FR, SUF) \
+    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M SUF, k_tensor_batched<NP, NB, S, D, M, FR>, NP, NB, S, D, M, FR}
 static const BatchVariant kBatchVariants[] = {
-    HERS_BV(1, 1, 4, 2, 3), HERS_BV(2, 1, 2, 4, 2), HERS_BV(2, 2, 2, 2, 2),
-    HERS_BV(2, 2, 4, 2, 1), HERS_BV(4, 1, 4, 2, 1), HERS_BV(1, 2, 3, 2, 3),
+    HERS_BV(1, 1, 4, 2, 3, 0, ""),  HERS_BV(2, 1, 2, 4, 2, 0, ""),  HERS_BV(2, 1, 3, 2, 2, 0, ""),
+    HERS_BV(2, 2, 4, 2, 1, 1, "r"), HERS_BV(4, 1, 4, 2, 1, 1, "r"), HERS_BV(1, 2, 3, 2, 3, 0, ""),
+    HERS_BV(2, 2, 6, 2, 1, 1, "r"), HERS_BV(2, 1, 4, 4, 1, 1, "r"), HERS_BV(4, 1, 5, 2, 1, 1, "r"),
+    HERS_BV(2, 2, 3, 4, 1, 1, "r"), HERS_BV(1, 2, 2, 4, 2, 0, ""),  HERS_BV(1, 2, 4, 2, 2, 0, ""),
 };
 #undef HERS_BV
 constexpr int NUM_BATCH_VARIANTS = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
 static int batch_smem(const BatchVariant& v) {
-    return v.stages * (v.np + v.nb) * v.dps * 2 * TILE * 8 + v.np * v.nb * 3 * TILE * 8;
+    return v.stages * (v.np + v.nb) * v.dps * 2 * TILE * 8 + (v.freg ? 0 : v.np * v.nb * 3 * TILE * 8);
 }
 
 int batch_variant_count() { return NUM_BATCH_VARIANTS; }
@@ -423,7 +519,14 @@ int batch_build(hers_batch* B, const hers_batch_item* items, uint32_t nitems, in
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, V.fn, TILE + 32, smem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_batch_create: setup");
-    if (per_sm < 1) return fail(ctx, HERS_E_CUDA, "hers_batch_create: variant %s does not fit an SM", V.name);
+    if (per_sm < 1) {
+        cudaFuncAttributes fa = {};
+        cudaFuncGetAttributes(&fa, V.fn);
+        return fail(ctx, HERS_E_CUDA,
+                    "hers_batch_create: variant %s does not fit an SM (%d registers, %d threads max, "
+                    "%d + %d bytes shared)",
+                    V.name, fa.numRegs, fa.maxThreadsPerBlock, (int)fa.sharedSizeBytes, smem);
+    }
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)per_sm * sms, P.units.size());
 
     B->fn = V.fn;

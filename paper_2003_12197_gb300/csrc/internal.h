@@ -120,7 +120,7 @@ struct BatchUnit {  // (chunk, first absolute block, limb, tile, blocks in the u
 };
 void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, int nb_max,
                  std::vector<BatchChunk>& chunks, std::vector<BatchUnit>& units, uint32_t* ngroups);
-constexpr int DEFAULT_BATCH_VARIANT = 2;
+constexpr int DEFAULT_BATCH_VARIANT = 1;
 int batch_variant_count();
 int batch_variant_np(int v);
 int batch_variant_nb(int v);

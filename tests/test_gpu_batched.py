@@ -22,7 +22,7 @@ def setup():
     ctx = H.Context(0)
     keys = H.hers_keygen(ctx, KEY_SEED)
     # three subsets: (entries, d); the middle one has a ragged last block
-    specs = [(2 * 4096, 16), (4096 + 1234, 40), (3 * 4096, 24)]
+    specs = [(2 * 4096, 16), (4096 + 1234, 37), (3 * 4096, 24)]
     nprobes = [3, 1, 5]          # 5 -> chunks of 4 + 1 at NP = 4
     subsets, items, truth = [], [], []
     for s, ((m, d), npb) in enumerate(zip(specs, nprobes)):
@@ -48,7 +48,7 @@ def setup():
     ctx.close()
 
 
-@pytest.mark.parametrize("variant", range(5))
+@pytest.mark.parametrize("variant", range(20))
 def test_batched_variant_equals_plain_search(setup, variant):
     names = H.hers_batch_variants()
     if variant >= len(names):
