@@ -60,7 +60,8 @@ def parse():
                     help="scale: random blocks checked against the oracle (plus the mate blocks "
                          "of the first probes)")
     ap.add_argument("--batch-variant", default=None,
-                    help="batched: kernel shape by name (skips the batched autotuner)")
+                    help="batched: kernel shape by name (skips the batched autotuner); "
+                         "scale: the streamed search's kernel shape (default np2_nb1_s2_d4_m2)")
     ap.add_argument("--variant", default=None,
                     help="tensor-kernel shape by name (skips the autotuner), e.g. nb2_s2_d4_m2")
     return ap.parse_args()
@@ -749,18 +750,21 @@ def run_scale(args):
               for i, q in enumerate(qs)]
     sc = torch.empty((nprobes, nb, 2, 2, N), dtype=torch.int64, device=dev)
     chunk = 32
+    bv_name = args.batch_variant or "np2_nb1_s2_d4_m2"
+    bv = H.hers_batch_variants().index(bv_name)
     ws = torch.empty(H.hers_search_stream_workspace_bytes(d, nprobes, chunk) // 8,
                      dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
     # warm-up on a few chunks, then the timed full pass
-    H.hers_search_stream(ctx, keys, g[: 4 * chunk], 4 * chunk, d, probes, chunk, 1, out=sc[:, : 4 * chunk].contiguous(), workspace=ws)
+    H.hers_search_stream(ctx, keys, g[: 4 * chunk], 4 * chunk, d, probes, chunk, bv,
+                         out=sc[:, : 4 * chunk].contiguous(), workspace=ws)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks.mark_start()
     e0.record(stream)
-    H.hers_search_stream(ctx, keys, g, nb, d, probes, chunk, 1, out=sc, workspace=ws)
+    H.hers_search_stream(ctx, keys, g, nb, d, probes, chunk, bv, out=sc, workspace=ws)
     e1.record(stream)
     torch.cuda.synchronize()
     clocks.mark_stop()
@@ -805,7 +809,7 @@ def run_scale(args):
            "config": {"workload": f"{m} entries ({nb} blocks), d = {d}, {nprobes} probes",
                       "gallery_form": "canonical (2 limbs, coefficient domain)",
                       "gallery_bytes": gal_bytes, "gallery_source": source, "chunk_blocks": chunk,
-                      "setup_s": gen_s},
+                      "batch_variant": bv_name, "setup_s": gen_s},
            "search_s_all_probes": ms / 1e3, "search_s_per_probe": ms / 1e3 / nprobes,
            "paper_100M_d64_s": 1480.0,
            "correct": {"scores_exact_all": exact, "top1": f"{top1}/{nprobes}",

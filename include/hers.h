@@ -394,6 +394,21 @@ int hers_autotune(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
  */
 int hers_probe_int_pipe(int device, uint32_t op, uint64_t iters, double* ops_per_s);
 
+/*
+ * Diagnostic with no counterpart in the paper: exercises the bounded wait
+ * that every streaming kernel's producer and consumers use.  Launches one
+ * CTA on ctx's stream whose thread waits on a shared-memory mbarrier that
+ * nothing completes, with a budget of limit_ns nanoseconds of global time
+ * (1e6 .. 2e9).  When the budget runs out the kernel sets bit 2 of the
+ * context's device error flag and returns; the call then reads and clears the
+ * flag as hers_check does.  Returns HERS_E_TIMEOUT, the expected outcome,
+ * with *elapsed_ms the kernel's duration (CUDA events); HERS_E_INVAL for a
+ * null argument or a limit out of range; HERS_E_CUDA on a CUDA error.  The
+ * context stays usable afterwards.  Nothing faults: the wait is an ordinary
+ * bounded loop that gives up.
+ */
+int hers_selftest_wait_timeout(hers_ctx* ctx, uint64_t limit_ns, double* elapsed_ms);
+
 #ifdef __cplusplus
 }
 #endif

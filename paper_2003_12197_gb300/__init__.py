@@ -19,6 +19,7 @@ import threading
 N = 4096
 MAX_D = 512
 HERS_OK = 0
+HERS_E_TIMEOUT = -4
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhers.so")
 
@@ -73,6 +74,7 @@ def lib():
                 "hers_trace_read": ([vp, vp, vp], i32),
                 "hers_kernel_launches": ([], u64),
                 "hers_probe_int_pipe": ([i32, u32, u64, vp], i32),
+                "hers_selftest_wait_timeout": ([vp, u64, vp], i32),
                 "hers_tensor_variants": ([], i32),
                 "hers_tensor_variant_name": ([i32], ctypes.c_char_p),
                 "hers_get_tensor_variant": ([vp], i32),
@@ -524,6 +526,14 @@ def hers_probe_int_pipe(device: int = 0, iters: int = 1 << 16):
             raise HersError(f"hers_probe_int_pipe({name}): {lib().hers_status_string(rc).decode()}")
         out[name] = v.value
     return out
+
+
+def hers_selftest_wait_timeout(ctx: Context, limit_ns: int):
+    """Runs the bounded-wait self-test: (status, kernel ms).  HERS_E_TIMEOUT is
+    the expected status; this call does not raise on it."""
+    ms = ctypes.c_double()
+    rc = lib().hers_selftest_wait_timeout(ctx.h, limit_ns, ctypes.byref(ms))
+    return rc, ms.value
 
 
 def to_u64(t):

@@ -402,7 +402,8 @@ static __device__ __noinline__ void ntt_inv_call(uint64_t* a, const uint64_t* tw
 // ---------------------------------------------------------------- mbarrier + bulk async copy (TMA engine)
 // Used by the streaming kernels: a producer lane issues cp.async.bulk copies
 // global -> shared that complete on an mbarrier; consumers wait on it.  Every
-// wait is bounded: after WAIT_LIMIT polls the caller gives up and reports.
+// wait is bounded: after WAIT_NS of global time (or WAIT_LIMIT polls) the
+// caller gives up and reports.
 constexpr uint32_t WAIT_LIMIT = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -432,10 +433,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase of parity `parity`; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t it = 0; it < WAIT_LIMIT; it++)
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase of parity `parity`; false if it gave up, after
+// limit_ns of global time or WAIT_LIMIT polls, whichever comes first.
+constexpr uint64_t WAIT_NS = 2000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = WAIT_NS) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0; it < WAIT_LIMIT; it++) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15) == 15 && globaltimer_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 __device__ __forceinline__ uint64_t policy_evict_first() {

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "common.cuh"
 #include "hers.h"
 #include "internal.h"
 
@@ -34,7 +35,47 @@ __global__ void __launch_bounds__(256) k_intpipe(uint64_t iters, uint32_t c, uin
     if (r == 0x123456789ull) sink[0] = r;  // keeps the chains live
 }
 
+// One thread waits on an mbarrier that nothing arrives on, with the same
+// bounded wait the streaming kernels use; the give-up path is theirs too.
+__global__ void k_wait_timeout(uint64_t limit_ns, int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit_ns)) atomicOr(err, 2);
+}
+
 }  // namespace hers
+
+extern "C" int hers_selftest_wait_timeout(hers_ctx* ctx, uint64_t limit_ns, double* elapsed_ms) {
+    using namespace hers;
+    if (!ctx || !elapsed_ms) return fail(ctx, HERS_E_INVAL, "hers_selftest_wait_timeout: null argument");
+    if (limit_ns < 1000000ull || limit_ns > WAIT_NS)
+        return fail(ctx, HERS_E_INVAL, "hers_selftest_wait_timeout: limit %llu ns not in [1e6, 2e9]",
+                    (unsigned long long)limit_ns);
+    DeviceGuard g(ctx->device);
+    int rc = hers_check(ctx, nullptr);  // start from a clear error flag
+    if (rc != HERS_OK) return rc;
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_selftest_wait_timeout: events");
+    cudaEventRecord(e0, ctx->stream);
+    k_wait_timeout<<<1, 32, 0, ctx->stream>>>(limit_ns, ctx->err);
+    count_launches(1);
+    e = cudaGetLastError();
+    cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_selftest_wait_timeout");
+    *elapsed_ms = ms;
+    return hers_check(ctx, ctx->stream);
+}
 
 extern "C" int hers_probe_int_pipe(int device, uint32_t op, uint64_t iters, double* ops_per_s) {
     using namespace hers;

@@ -33,7 +33,7 @@ namespace hers {
 // so each (dimension, coefficient, limb, block) costs 9 32x32->64 multiply-adds
 // (mad.wide.u32) into 64-bit sums without reduction.  The largest partial
 // product is (2^29)^2 = 2^58, so the sums are folded mod p every KCHUNK = 32
-// dimensions.  A wait that exceeds WAIT_LIMIT polls sets bit 2 of *err.
+// dimensions.  A wait that runs out (WAIT_NS, 2 s) sets bit 2 of *err.
 constexpr int KCHUNK = 32;
 
 __device__ __forceinline__ void madw(uint64_t& acc, uint32_t a, uint32_t b) {
