@@ -333,6 +333,21 @@ int hers_search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* galle
                      uint64_t* scores_ct_host, void* workspace, uint64_t workspace_bytes,
                      void* stream);
 uint64_t hers_search_host_workspace_bytes(uint64_t nblocks, uint32_t d);
+/*
+ * hers_search_host without the final wait: the copies and kernels are
+ * enqueued on `stream` (NULL = the CUDA default stream) and the call returns.
+ * The scores are in host memory once `stream` reaches this point; the caller
+ * synchronises (a stream or event wait) before reading them.  probe_ct_host
+ * and scores_ct_host must be pinned host memory (cudaHostAlloc / registered)
+ * and stay valid and unmodified until then; the workspace belongs to this call
+ * until then too.  Calls on different streams with separate workspaces and
+ * score buffers overlap: one call's copies run beside another's kernels.
+ * Returns HERS_E_INVAL if a host buffer is not pinned.
+ */
+int hers_search_host_async(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
+                           uint64_t nblocks, uint32_t d, const uint64_t* probe_ct_host,
+                           uint64_t* scores_ct_host, void* workspace, uint64_t workspace_bytes,
+                           void* stream);
 
 /*
  * Client-side decryption (App. A, Alg 3) and decoding of block score cts

@@ -67,6 +67,7 @@ def lib():
                 "hers_probe_prepare": ([vp, vp, u32, vp, vp], i32),
                 "hers_search": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
                 "hers_search_host": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
+                "hers_search_host_async": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
                 "hers_search_noalloc": ([vp, vp, vp, u64, u32, vp, vp, vp], i32),
                 "hers_decrypt_scores": ([vp, vp, vp, u64, vp, u64, vp], i32),
                 "hers_check": ([vp, vp], i32),
@@ -272,6 +273,17 @@ def hers_search_host(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, pr
     ctx.check(lib().hers_search_host(ctx.h, keys.h, _ptr(gallery), nblocks, d, _ptr(probe_ct_host),
                                      _ptr(scores_host), _ptr(workspace), workspace.numel() * 8,
                                      _stream(stream)), "hers_search_host")
+    return scores_host
+
+
+def hers_search_host_async(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, probe_ct_host,
+                           scores_host, workspace, stream=None):
+    """hers_search_host enqueued on `stream` without waiting: probe_ct_host and
+    scores_host must be pinned CPU tensors; synchronise `stream` before reading
+    scores_host or reusing the buffers or the workspace."""
+    ctx.check(lib().hers_search_host_async(ctx.h, keys.h, _ptr(gallery), nblocks, d, _ptr(probe_ct_host),
+                                           _ptr(scores_host), _ptr(workspace), workspace.numel() * 8,
+                                           _stream(stream)), "hers_search_host_async")
     return scores_host
 
 

@@ -329,16 +329,32 @@ int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search");
 }
 
-int hers_search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
-                     uint64_t nblocks, uint32_t d, const uint64_t* probe_ct_host,
-                     uint64_t* scores_ct_host, void* workspace, uint64_t workspace_bytes,
-                     void* stream) {
+}  // extern "C"
+
+namespace {
+
+// The host-buffer search step; waits for the copy back when `sync`.
+int search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
+                uint32_t d, const uint64_t* probe_ct_host, uint64_t* scores_ct_host, void* workspace,
+                uint64_t workspace_bytes, void* stream, bool sync, const char* name) {
     if (!ctx || !keys || !gallery || !probe_ct_host || !scores_ct_host || !workspace)
-        return fail(ctx, HERS_E_INVAL, "hers_search_host: null argument");
-    if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_search_host: d = %u", d);
+        return fail(ctx, HERS_E_INVAL, "%s: null argument", name);
+    if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "%s: d = %u", name, d);
     if (workspace_bytes < hers_search_host_workspace_bytes(nblocks, d))
-        return fail(ctx, HERS_E_NOMEM, "hers_search_host: workspace too small");
+        return fail(ctx, HERS_E_NOMEM, "%s: workspace too small", name);
     DeviceGuard g(ctx->device);
+    if (!sync) {
+        // an asynchronous copy from or to pageable memory would not overlap
+        // and could outlive the caller's buffer: require pinned memory
+        const void* bufs[2] = {probe_ct_host, scores_ct_host};
+        for (const void* b : bufs) {
+            cudaPointerAttributes pa = {};
+            if (cudaPointerGetAttributes(&pa, b) != cudaSuccess || pa.type != cudaMemoryTypeHost) {
+                cudaGetLastError();
+                return fail(ctx, HERS_E_INVAL, "%s: host buffers must be pinned", name);
+            }
+        }
+    }
     cudaStream_t st = pick(ctx, stream);
     // workspace: [search scratch][probe cts d*4N][probe form d*10N][score cts nblocks*4N]
     uint64_t* ws = (uint64_t*)workspace;
@@ -353,8 +369,28 @@ int hers_search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* galle
                           next_trace(ctx), ctx->tensor_variant);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(scores_ct_host, out_dev, nblocks * 4 * N * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search_host");
+    if (e == cudaSuccess && sync) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, name);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hers_search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
+                     uint64_t nblocks, uint32_t d, const uint64_t* probe_ct_host,
+                     uint64_t* scores_ct_host, void* workspace, uint64_t workspace_bytes,
+                     void* stream) {
+    return search_host(ctx, keys, gallery, nblocks, d, probe_ct_host, scores_ct_host, workspace,
+                       workspace_bytes, stream, true, "hers_search_host");
+}
+
+int hers_search_host_async(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
+                           uint64_t nblocks, uint32_t d, const uint64_t* probe_ct_host,
+                           uint64_t* scores_ct_host, void* workspace, uint64_t workspace_bytes,
+                           void* stream) {
+    return search_host(ctx, keys, gallery, nblocks, d, probe_ct_host, scores_ct_host, workspace,
+                       workspace_bytes, stream, false, "hers_search_host_async");
 }
 
 int hers_decrypt_scores(hers_ctx* ctx, const hers_keys* keys, const uint64_t* scores_ct,

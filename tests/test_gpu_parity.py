@@ -221,3 +221,32 @@ def test_every_tensor_shape_gives_the_same_ciphertexts(ctx, keys, oracle_keys):
     chosen, ms = H.hers_autotune(ctx, keys, gal, 4, d, pr)
     assert 0 <= chosen < len(names) and len(ms) == len(names)
     H.hers_set_tensor_variant(ctx, keep)
+
+
+def test_async_host_search_equals_sync(ctx, keys):
+    """hers_search_host_async on two streams gives the bytes of
+    hers_search_host; unpinned host buffers are refused."""
+    m, d = 3 * 4096 + 17, 8
+    feats = W.gallery_features(m, d, 6161)
+    q = W.probe_for_mate(12, d, 6161, 6262)
+    gal, _ = H.hers_encrypt_gallery(ctx, keys, torch.from_numpy(feats).cuda(), 6363)
+    pct = H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).cuda(), 6464)
+    nb = H.hers_blocks_for(m)
+    ws = [torch.empty(H.hers_search_host_workspace_bytes(nb, d) // 8, dtype=torch.int64, device="cuda")
+          for _ in range(2)]
+    pct_host = pct.cpu().pin_memory()
+    ref = torch.empty((nb, 2, 2, H.N), dtype=torch.int64).pin_memory()
+    H.hers_search_host(ctx, keys, gal, nb, d, pct_host, ref, ws[0])
+    outs = [torch.zeros((nb, 2, 2, H.N), dtype=torch.int64).pin_memory() for _ in range(2)]
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    for k in range(4):
+        H.hers_search_host_async(ctx, keys, gal, nb, d, pct_host, outs[k % 2], ws[k % 2],
+                                 stream=streams[k % 2])
+    torch.cuda.synchronize()
+    for o in outs:
+        assert torch.equal(o, ref)
+    scores = H.hers_decrypt_scores(ctx, keys, ref.cuda(), m).cpu().numpy().astype(np.int64)
+    assert np.array_equal(scores, W.plain_inner_products(feats, q))
+    with pytest.raises(H.HersError):
+        H.hers_search_host_async(ctx, keys, gal, nb, d, pct.cpu(), outs[0], ws[0], stream=streams[0])
+    H.hers_check(ctx)
