@@ -85,6 +85,24 @@ __device__ __forceinline__ uint64_t shoup(uint64_t x, uint64_t w, uint64_t ws, u
     return csub(shoup_lazy(x, w, ws, p), p);
 }
 
+// Shoup multiplication with a truncated quotient, for the NTT butterflies.
+// The high half of x ws is taken from three of the four 32x32 partial
+// products (xh wsh exactly, the high words of xh wsl and xl wsh); the dropped
+// fractions sum to less than 3, so the quotient is short of Shoup's by 0, 1 or
+// 2 and x w - q p lies in [0, 4p) (Shoup's own lies in [0, 2p)).  Needs p <
+// 2^61 so that 4p fits; costs one 32x32->64 and two 32x32-high products in
+// place of a 64x64-high product.
+__device__ __forceinline__ uint64_t shoup4(uint64_t x, uint64_t w, uint64_t ws, uint64_t p) {
+    const uint32_t xl = (uint32_t)x, xh = (uint32_t)(x >> 32);
+    const uint32_t sl = (uint32_t)ws, sh = (uint32_t)(ws >> 32);
+    const uint64_t q = (uint64_t)xh * sh + __umulhi(xh, sl) + __umulhi(xl, sh);
+    return x * w - q * p;
+}
+// shoup4 reduced to [0, p).
+__device__ __forceinline__ uint64_t shoup4_full(uint64_t x, uint64_t w, uint64_t ws, uint64_t p) {
+    return csub(csub(shoup4(x, w, ws, p), 2 * p), p);
+}
+
 // x mod p_i for any 64-bit x (Shoup with w = 1).
 __device__ __forceinline__ uint64_t reduce64(uint64_t x, int i) {
     return csub(shoup_lazy(x, 1, c_one_s[i], c_mod[i]), c_mod[i]);
@@ -264,53 +282,64 @@ __device__ __forceinline__ void sample_uniform(uint64_t seed, uint32_t purpose, 
 // All NTT_THREADS threads must call these; they begin and end with a barrier.
 constexpr int NTT_THREADS = 256;
 
+// Twiddle index of a butterfly.  In every phase, the pairs (a, a + h) of
+// stage h with a = 2h j + r, r < h, share one twiddle: for the three base
+// patterns, base + STRIDE r < 2 STRIDE h whenever base is taken modulo
+// 2 STRIDE h, so i = floor(base / (2 STRIDE h)) + j.  Each stage therefore
+// loads 8 / h twiddles (15 per phase) rather than 8.
 template <int STRIDE>
 __device__ __forceinline__ void ct_phase(uint64_t v[16], int base, const ulonglong2* __restrict__ w,
                                          uint64_t p) {
-    const uint64_t two_p = 2 * p;
+    const uint64_t four_p = 4 * p;
 #pragma unroll
     for (int h = 8; h >= 1; h >>= 1) {
         const int t = STRIDE * h;       // butterfly distance
         const int m = N / (2 * t);      // groups in this stage
+        const int i0 = base / (2 * t);
 #pragma unroll
-        for (int a = 0; a < 16; a++) {
-            if (a & h) continue;
-            const int i = (base + STRIDE * a) / (2 * t);
-            const ulonglong2 W = __ldg(w + m + i);
-            // no reduction of U: inputs < 2p grow by < 2p per stage, so every
-            // value stays below 26p < 2^59 over the twelve stages
-            const uint64_t U = v[a];
-            const uint64_t V = shoup_lazy(v[a + h], W.x, W.y, p);
-            v[a] = U + V;
-            v[a + h] = U - V + two_p;
+        for (int j = 0; j < 8 / h; j++) {
+            const ulonglong2 W = __ldg(w + m + i0 + j);
+#pragma unroll
+            for (int r = 0; r < h; r++) {
+                const int a = 2 * h * j + r;
+                // no reduction of U: inputs < 2p grow by < 4p per stage, so
+                // every value stays below 50p < 2^60 over the twelve stages
+                const uint64_t U = v[a];
+                const uint64_t V = shoup4(v[a + h], W.x, W.y, p);
+                v[a] = U + V;
+                v[a + h] = U - V + four_p;
+            }
         }
     }
 }
 
 // LAST: this phase holds the final stage (distance 2048), whose outputs are
-// multiplied by N^-1 on the way (twiddle entry 0 carries W N^-1).
+// multiplied by N^-1 on the way (twiddle entry 0 carries W N^-1).  Values stay
+// below 4p between stages; the last stage reduces fully.
 template <int STRIDE, bool LAST>
 __device__ __forceinline__ void gs_phase(uint64_t v[16], int base, const ulonglong2* __restrict__ w,
                                          uint64_t p, uint64_t ninv, uint64_t ninv_s) {
-    const uint64_t two_p = 2 * p;
+    const uint64_t four_p = 4 * p;
 #pragma unroll
     for (int h = 1; h <= 8; h <<= 1) {
         const int t = STRIDE * h;
         const int m = N / (2 * t);
+        const int i0 = base / (2 * t);
 #pragma unroll
-        for (int a = 0; a < 16; a++) {
-            if (a & h) continue;
-            const uint64_t U = v[a], V = v[a + h];
-            if (LAST && h == 8) {
-                const ulonglong2 W = __ldg(w);
-                v[a] = shoup(U + V, ninv, ninv_s, p);
-                v[a + h] = shoup(U - V + two_p, W.x, W.y, p);
-            } else {
-                const int i = (base + STRIDE * a) / (2 * t);
-                const ulonglong2 W = __ldg(w + m + i);
-                const uint64_t S = U + V;
-                v[a] = S >= two_p ? S - two_p : S;
-                v[a + h] = shoup_lazy(U - V + two_p, W.x, W.y, p);
+        for (int j = 0; j < 8 / h; j++) {
+            const ulonglong2 W = __ldg(LAST && h == 8 ? w : w + m + i0 + j);
+#pragma unroll
+            for (int r = 0; r < h; r++) {
+                const int a = 2 * h * j + r;
+                const uint64_t U = v[a], V = v[a + h];
+                if (LAST && h == 8) {
+                    v[a] = shoup4_full(U + V, ninv, ninv_s, p);
+                    v[a + h] = shoup4_full(U - V + four_p, W.x, W.y, p);
+                } else {
+                    const uint64_t S = U + V;
+                    v[a] = S >= four_p ? S - four_p : S;
+                    v[a + h] = shoup4(U - V + four_p, W.x, W.y, p);
+                }
             }
         }
     }
@@ -339,7 +368,7 @@ __device__ __forceinline__ void ntt_fwd_smem(uint64_t* sm, const ulonglong2* __r
         for (int a = 0; a < 16; a++) sm[swz(base + 16 * a)] = v[a];
     }
     __syncwarp();
-    {   // phase C, then full reduction (values < 26p)
+    {   // phase C, then full reduction (values < 50p)
         const int base = 16 * t;
 #pragma unroll
         for (int a = 0; a < 16; a++) v[a] = sm[swz(base + a)];
