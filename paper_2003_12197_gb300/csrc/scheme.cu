@@ -207,7 +207,7 @@ cudaError_t launch_encrypt(const uint64_t* tw, const DevKeys& k, const int8_t* f
 // ciphertext ct_begin + P/2 = b d + i.  Exactness of the later tensor product
 // needs the centred lift: the product of two such polynomials over Z, summed
 // over d <= 512 dimensions, stays below q P / 2 (|X| < 2^237).
-__global__ void __launch_bounds__(NTT_THREADS, 2) k_extend_ntt(const uint64_t* __restrict__ tw,
+__global__ void __launch_bounds__(NTT_THREADS, 3) k_extend_ntt(const uint64_t* __restrict__ tw,
                                                             const uint64_t* __restrict__ ct,
                                                             uint64_t ct_begin, uint32_t d,
                                                             uint64_t* __restrict__ out) {
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 2) k_extend_ntt(const uint64_t* _
         const uint64_t a = x1[k], b = x2[k];
         sm[swz(k)] = lifted_mod(lift_q(a, b), limb, b);
     }
-    ntt_fwd_call(sm, tw, limb);
+    ntt_fwd_mod(sm, tw, limb);
     const uint64_t c = ct_begin + P / 2;
     const uint64_t blk = c / d;
     const uint32_t i = (uint32_t)(c % d);
