@@ -48,10 +48,12 @@ def parse():
     ap.add_argument("--m", type=int, default=1 << 20, help="gallery entries per GPU")
     ap.add_argument("--d", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "scale"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "scale", "sweep"],
                     help="plain: 1,048,576 entries, d = 64, one probe (the headline line); "
                          "batched: 64 probes x uneven subsets of 256 blocks, mixed d; "
-                         "serving: Poisson requests against 10M-entry galleries at d 32/64/128")
+                         "serving: Poisson requests against 10M-entry galleries at d 32/64/128; "
+                         "scale: 100M entries, 16 probes, streamed; "
+                         "sweep: search time against d (32..512) and against m (the shape of Table 3)")
     ap.add_argument("--rates", default="50,200,500,1000,2000",
                     help="serving: arrival rates (requests/s) to sweep")
     ap.add_argument("--window", type=float, default=2.0, help="serving: seconds of arrivals per rate")
@@ -847,6 +849,117 @@ def run_scale(args):
     return 0
 
 
+def run_sweep(args):
+    """Search time of one probe against d at m = 1,048,576 and against m at
+    d = 64 (the shape of the paper's Table 3 and Fig. 3, for HERS alone).
+    Each point: a fresh resident gallery of device-drawn features, the
+    autotuned plain kernel shape, `steps` timed steps (probe preparation +
+    search, CUDA events), every decrypted score checked against the plaintext
+    inner products, and the tensor kernel's HBM roofline fraction."""
+    import numpy as np
+    import torch
+
+    import paper_2003_12197_gb300 as H
+    import workloads as W
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    H.build_library()
+    ctx = H.Context(local)
+    keys = H.hers_keygen(ctx, KEY_SEED)
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        peak_src = "measured"
+    except (OSError, ValueError, KeyError):
+        peak, peak_src = 6800.0, "fallback"
+    points = [(1 << 20, d) for d in (32, 64, 128, 256, 512)] + [(m, 64) for m in (1 << 18, 1 << 22)]
+    out_points = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for m, d in points:
+        nb = H.hers_blocks_for(m)
+        feats = W.gallery_features_device(m, d, FEAT_SEED + 900 + d, dev)
+        mate = int(W.mate_indices(m, 1, MATE_SEED + 900 + d)[0])
+        x = feats[mate].float().cpu().numpy().astype("float64")
+        x = x / np.linalg.norm(x)
+        rng = np.random.default_rng(NOISE_SEED + 900 + d)
+        q = W.quantise((x + rng.standard_normal(d) * (W.PROBE_NOISE / np.sqrt(d)))[None, :])[0]
+        gal, _ = H.hers_encrypt_gallery(ctx, keys, feats, GAL_SEED + 900 + d)
+        pct = H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).to(dev), PRB_SEED + 900 + d)
+        pr = H.hers_probe_prepare(ctx, pct)
+        ws = torch.empty(H.hers_search_workspace_bytes(nb) // 8, dtype=torch.int64, device=dev)
+        sc = torch.empty((nb, 2, 2, N), dtype=torch.int64, device=dev)
+        variant, _ = H.hers_autotune(ctx, keys, gal, nb, d, pr, workspace=ws)
+        H.hers_search(ctx, keys, gal, nb, d, pr, out=sc, workspace=ws)
+        scores = H.hers_decrypt_scores(ctx, keys, sc, m)
+        plain = (feats.float() @ torch.from_numpy(q).to(dev).float()).to(torch.int32)  # exact: < 2^24
+        exact = bool(torch.equal(plain, scores))
+        top1 = int(torch.argmax(scores).item()) == mate
+
+        def step():
+            H.hers_probe_prepare(ctx, pct, out=pr)
+            H.hers_search(ctx, keys, gal, nb, d, pr, out=sc, workspace=ws)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        H.hers_trace_enable(ctx, args.steps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        _, phases = H.hers_trace_read(ctx)
+        H.hers_trace_enable(ctx, 0)
+        H.hers_check(ctx)
+        ms = e0.elapsed_time(e1) / args.steps
+        alg = nb * d * 2 * 5 * N * 8 + d * 2 * 5 * N * 8 + nb * 3 * 5 * N * 8
+        gbs = alg / (phases["tensor"] / 1e3) / 1e9
+        out_points.append({"m": m, "d": d, "blocks": nb, "ms_per_step": ms, "entries_per_s": m / (ms / 1e3),
+                           "phases_ms": {k: round(v, 4) for k, v in phases.items()},
+                           "variant": H.hers_tensor_variants()[variant],
+                           "tensor_gbs": gbs, "tensor_frac": gbs / peak,
+                           "exact": exact, "top1": top1})
+        del feats, gal, pct, pr, ws, sc, scores, plain
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+
+    def fit(xs, ys):
+        n = len(xs)
+        mx, my = sum(xs) / n, sum(ys) / n
+        sxx = sum((x - mx) ** 2 for x in xs)
+        sxy = sum((x - mx) * (y - my) for x, y in zip(xs, ys))
+        a = sxy / sxx
+        b = my - a * mx
+        ss = sum((y - my) ** 2 for y in ys)
+        r2 = 1 - sum((y - a * x - b) ** 2 for x, y in zip(xs, ys)) / ss if ss > 0 else 1.0
+        return a, b, r2
+
+    by_d = [p for p in out_points if p["m"] == 1 << 20]
+    by_m = sorted([p for p in out_points if p["d"] == 64], key=lambda p: p["m"])
+    ad, bd, r2d = fit([p["d"] for p in by_d], [p["ms_per_step"] for p in by_d])
+    am, bm, r2m = fit([p["m"] for p in by_m], [p["ms_per_step"] for p in by_m])
+    out = {"metric": "search ms per probe against d and m (N=4096, bit-exact)", "workload": "sweep",
+           "unit": "ms", "n_gpus": 1, "dtype": "u64", "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": False,
+           "data": "synthetic (seeded int8 features drawn on the device, one planted mate per point)",
+           "config": {"workload": "one probe; d in {32,64,128,256,512} at m = 1,048,576; "
+                                  "m in {262144, 1048576, 4194304} at d = 64",
+                      "peak_hbm_gbs": peak, "peak_source": peak_src},
+           "points": out_points,
+           "linear_in_d": {"ms_per_dim": ad, "intercept_ms": bd, "r2": r2d},
+           "linear_in_m": {"ms_per_million_entries": am * 1e6, "intercept_ms": bm, "r2": r2m},
+           "all_exact": all(p["exact"] for p in out_points),
+           "all_top1": all(p["top1"] for p in out_points),
+           "clocks": clk}
+    print(json.dumps(out))
+    keys.close()
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -857,6 +970,8 @@ def main():
         return run_serving(args)
     if args.workload == "scale":
         return run_scale(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_gpu(args)
 
 

@@ -40,7 +40,12 @@ __device__ __forceinline__ void madw(uint64_t& acc, uint32_t a, uint32_t b) {
     asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
-template <int NB, int STAGES, int DPS, int MINB>
+// GORDER: block groups vary fastest over the grid (x = group, y = (limb,
+// tile)), so the CTAs in flight share one (limb, tile) run of the probe and
+// it stays in L2 when the whole probe (d x 320 KiB) does not fit; otherwise
+// tiles vary fastest (x = tile, y = limb, z = group) and the CTAs in flight
+// read neighbouring runs of one block.
+template <int NB, int STAGES, int DPS, int MINB, bool GORDER>
 __global__ void __launch_bounds__(TILE + 32, MINB)
     k_tensor(const uint64_t* __restrict__ gal, const uint64_t* __restrict__ probe,
              uint64_t* __restrict__ acc, uint64_t nblocks, uint32_t d, int* err) {
@@ -49,8 +54,9 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
     constexpr int RUN = DPS * 2 * TILE;         // words of one run per stage
     constexpr int STAGE_WORDS = (1 + NB) * RUN;
-    const int tile = blockIdx.x, l = blockIdx.y;
-    const uint64_t b0 = (uint64_t)blockIdx.z * NB;
+    const int tile = GORDER ? (int)(blockIdx.y % NTILES) : (int)blockIdx.x;
+    const int l = GORDER ? (int)(blockIdx.y / NTILES) : (int)blockIdx.y;
+    const uint64_t b0 = (uint64_t)(GORDER ? blockIdx.x : blockIdx.z) * NB;
     const int nb = (int)((nblocks - b0) < (uint64_t)NB ? (nblocks - b0) : NB);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t nst = (d + DPS - 1) / DPS;
@@ -182,14 +188,19 @@ struct TensorVariant {
     const char* name;
     TensorFn fn;
     int nb, stages, dps;
+    bool gorder;
 };
-#define HERS_TV(NB, S, D, M) \
-    {"nb" #NB "_s" #S "_d" #D "_m" #M, k_tensor<NB, S, D, M>, NB, S, D}
+// name: nb<blocks per CTA>_s<stages>_d<dimensions per stage>_m<CTAs/SM>, and
+// a leading "g" for the group-fastest grid order
+#define HERS_TV(NB, S, D, M) {"nb" #NB "_s" #S "_d" #D "_m" #M, k_tensor<NB, S, D, M, false>, NB, S, D, false}
+#define HERS_TVG(NB, S, D, M) {"gnb" #NB "_s" #S "_d" #D "_m" #M, k_tensor<NB, S, D, M, true>, NB, S, D, true}
 static const TensorVariant kTensorVariants[] = {
-    HERS_TV(2, 6, 1, 1), HERS_TV(2, 4, 2, 2), HERS_TV(2, 3, 2, 3), HERS_TV(1, 4, 2, 3),
-    HERS_TV(1, 6, 2, 2), HERS_TV(2, 2, 4, 2), HERS_TV(4, 3, 2, 1), HERS_TV(1, 3, 4, 3),
+    HERS_TV(2, 6, 1, 1),  HERS_TV(2, 4, 2, 2),  HERS_TV(2, 3, 2, 3),  HERS_TV(1, 4, 2, 3),
+    HERS_TV(1, 6, 2, 2),  HERS_TV(2, 2, 4, 2),  HERS_TV(4, 3, 2, 1),  HERS_TV(1, 3, 4, 3),
+    HERS_TVG(2, 2, 4, 2), HERS_TVG(2, 4, 2, 2), HERS_TVG(1, 3, 4, 3), HERS_TVG(2, 3, 2, 3),
 };
 #undef HERS_TV
+#undef HERS_TVG
 constexpr int NUM_TENSOR_VARIANTS = sizeof(kTensorVariants) / sizeof(kTensorVariants[0]);
 
 int tensor_variant_count() { return NUM_TENSOR_VARIANTS; }
@@ -204,10 +215,12 @@ cudaError_t launch_tensor(int variant, const uint64_t* gallery, uint64_t nblocks
     const int smem = v.stages * (1 + v.nb) * v.dps * 2 * TILE * 8;
     cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const uint64_t max_z = 65535ull * v.nb;
+    const uint64_t max_groups = v.gorder ? 0x7FFFFFFFull : 65535ull;  // grid x or z limit
+    const uint64_t max_z = max_groups * v.nb;
     for (uint64_t g0 = 0; g0 < nblocks; g0 += max_z) {
         const uint64_t nb = nblocks - g0 < max_z ? nblocks - g0 : max_z;
-        dim3 grid(NTILES, 5, (unsigned)((nb + v.nb - 1) / v.nb));
+        const unsigned groups = (unsigned)((nb + v.nb - 1) / v.nb);
+        const dim3 grid = v.gorder ? dim3(groups, NTILES * 5, 1) : dim3(NTILES, 5, groups);
         v.fn<<<grid, TILE + 32, smem, st>>>(gallery + g0 * 10ull * d * N, probe, X + g0 * 15 * N, nb,
                                             d, err);
         count_launches(1);

@@ -250,3 +250,21 @@ def test_async_host_search_equals_sync(ctx, keys):
     with pytest.raises(H.HersError):
         H.hers_search_host_async(ctx, keys, gal, nb, d, pct.cpu(), outs[0], ws[0], stream=streams[0])
     H.hers_check(ctx)
+
+
+def test_maximum_dimension_d512_bit_exact(ctx, keys, oracle_keys):
+    """d = 512, the largest supported dimension (|X| < 2^236 < QP/2): one
+    ragged block, gallery, probe and score ciphertexts against the oracle, and
+    the decrypted scores against Eq. 1."""
+    m, d = 4000, 512
+    feats = W.gallery_features(m, d, 5120)
+    q = W.probe_for_mate(1234, d, 5120, 5121)
+    res = run_search(ctx, keys, feats, q, gal_seed=5122, prb_seed=5123)
+    ogal = O.encrypt_gallery_block(oracle_keys[1], feats, 0, 5122)
+    assert np.array_equal(u64(res["gct"])[0], ogal)
+    oprb = O.encrypt_probe(oracle_keys[1], q, 5123)
+    assert np.array_equal(u64(res["pct"]), oprb)
+    osc, st = O.search_block(oprb, ogal, oracle_keys[2])
+    assert np.array_equal(u64(res["sc"])[0], osc)
+    assert np.array_equal(res["scores"].astype(np.int64), W.plain_inner_products(feats, q))
+    assert int(np.argmax(res["scores"])) == 1234
