@@ -48,12 +48,13 @@ def parse():
     ap.add_argument("--m", type=int, default=1 << 20, help="gallery entries per GPU")
     ap.add_argument("--d", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "scale", "sweep"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "scale", "sweep", "topk"],
                     help="plain: 1,048,576 entries, d = 64, one probe (the headline line); "
                          "batched: 64 probes x uneven subsets of 256 blocks, mixed d; "
                          "serving: Poisson requests against 10M-entry galleries at d 32/64/128; "
                          "scale: 100M entries, 16 probes, streamed; "
-                         "sweep: search time against d (32..512) and against m (the shape of Table 3)")
+                         "sweep: search time against d (32..512) and against m (the shape of Table 3); "
+                         "topk: stage-1 top-K over 100M decrypted-score-sized int32 values")
     ap.add_argument("--rates", default="50,200,500,1000,2000",
                     help="serving: arrival rates (requests/s) to sweep")
     ap.add_argument("--window", type=float, default=2.0, help="serving: seconds of arrivals per rate")
@@ -960,6 +961,58 @@ def run_sweep(args):
     return 0
 
 
+def run_topk(args):
+    """Stage-1 top-K (Sec. 3.2's first stage) over m = 100,000,000 int32
+    scores in the range of d = 64 inner products (|s| <= 64 * 127^2), drawn on
+    the device.  Per K: CUDA-event time over `steps` calls, checked against
+    torch.topk's values and the index order of ties."""
+    import torch
+
+    import paper_2003_12197_gb300 as H
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    H.build_library()
+    ctx = H.Context(local)
+    m = 100_000_000
+    g = torch.Generator(device=dev)
+    g.manual_seed(FEAT_SEED + 77)
+    bound = 64 * 127 * 127
+    s = torch.randint(-bound, bound + 1, (m,), generator=g, device=dev, dtype=torch.int32)
+    ws = torch.empty(H.lib().hers_topk_workspace_bytes(m) // 8 + 1, dtype=torch.int64, device=dev)
+    out = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for k in (16, 100, 1000, 4096):
+        for _ in range(args.warmup):
+            H.hers_topk(ctx, s, k, workspace=ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            idx, val = H.hers_topk(ctx, s, k, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        H.hers_check(ctx)
+        ms = e0.elapsed_time(e1) / args.steps
+        ref = torch.topk(s, k).values
+        ok = bool(torch.equal(val, ref)) and bool(torch.equal(s[idx], val))
+        same = val[1:] == val[:-1]
+        ok = ok and bool(torch.all(idx[1:][same] > idx[:-1][same]))
+        out.append({"k": k, "ms": ms, "scores_per_s": m / (ms / 1e3),
+                    "gbs": m * 4 / (ms / 1e3) / 1e9, "correct": ok})
+    clk = clocks.stop()
+    print(json.dumps({"metric": "stage-1 top-K scores scanned/sec", "workload": "topk", "unit": "scores/s",
+                      "value": out[0]["scores_per_s"], "n_gpus": 1, "dtype": "int32", "steps": args.steps,
+                      "warmup": args.warmup, "higher_is_better": True,
+                      "data": "synthetic (uniform int32 in the d = 64 score range, drawn on the device)",
+                      "config": {"workload": f"m = {m} scores, k in 16/100/1000/4096"},
+                      "points": out, "clocks": clk}))
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -972,6 +1025,8 @@ def main():
         return run_scale(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "topk":
+        return run_topk(args)
     return run_gpu(args)
 
 

@@ -400,6 +400,26 @@ int hers_autotune(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
                   void* stream, int* chosen, double* ms_per_variant);
 
 /*
+ * Stage 1 of the two-stage search (Sec. 3.2): the k entries with the largest
+ * decrypted scores, ordered by score descending and, among equal scores, by
+ * index ascending (the lowest index first).
+ *
+ * scores: device int32[m], e.g. hers_decrypt_scores' output (1 <= m < 2^32 - 1).
+ * k: 1 <= k <= min(m, 4096).
+ * out_idx: device int64[k]; out_scores: device int32[k].
+ * workspace: device, hers_topk_workspace_bytes(m) bytes (selection state,
+ * a histogram, per-CTA tie counts and the k candidates); the call allocates
+ * nothing.  Asynchronous on `stream` (NULL = the CUDA default stream); no
+ * step waits on the host.  Exact radix selection of the k-th largest score,
+ * then a sort of the k candidates.  Returns HERS_E_INVAL for a size out of
+ * range, HERS_E_NOMEM for a short workspace, HERS_E_CUDA on a CUDA error; an
+ * internal count mismatch is reported by hers_check as HERS_E_CUDA.
+ */
+uint64_t hers_topk_workspace_bytes(uint64_t m);
+int hers_topk(hers_ctx* ctx, const int32_t* scores, uint64_t m, uint32_t k, int64_t* out_idx,
+              int32_t* out_scores, void* workspace, uint64_t workspace_bytes, void* stream);
+
+/*
  * Diagnostic with no counterpart in the paper: sustained integer-pipe rate on
  * `device`, in operations per second over all SMs, for op 0 = 32x32 -> 64-bit
  * multiply-add (IMAD.WIDE.U32, the tensor kernel's inner operation), 1 =

@@ -300,3 +300,14 @@ def search_gallery(probe_cts, gal_blocks_cts, evk, n=N):
         outs.append(o)
         tot = st if tot is None else {k: tot[k] + st[k] for k in st}
     return np.stack(outs), tot
+
+
+def topk(scores, k):
+    """Stage 1 of the two-stage search (Sec. 3.2): the k gallery entries with
+    the largest decrypted scores, ordered by score descending and, among equal
+    scores, by index ascending.  Returns (indices int64[k], scores int32[k]).
+    The plain definition: a stable sort of the indices by descending score."""
+    s = np.asarray(scores)
+    k = int(min(k, s.shape[0]))
+    order = np.lexsort((np.arange(s.shape[0], dtype=np.int64), -s.astype(np.int64)))[:k]
+    return order.astype(np.int64), s[order].astype(np.int32)

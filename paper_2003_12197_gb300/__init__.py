@@ -76,6 +76,8 @@ def lib():
                 "hers_kernel_launches": ([], u64),
                 "hers_probe_int_pipe": ([i32, u32, u64, vp], i32),
                 "hers_selftest_wait_timeout": ([vp, u64, vp], i32),
+                "hers_topk_workspace_bytes": ([u64], u64),
+                "hers_topk": ([vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
                 "hers_tensor_variants": ([], i32),
                 "hers_tensor_variant_name": ([i32], ctypes.c_char_p),
                 "hers_get_tensor_variant": ([vp], i32),
@@ -538,6 +540,21 @@ def hers_probe_int_pipe(device: int = 0, iters: int = 1 << 16):
             raise HersError(f"hers_probe_int_pipe({name}): {lib().hers_status_string(rc).decode()}")
         out[name] = v.value
     return out
+
+
+def hers_topk(ctx: Context, scores, k: int, workspace=None, stream=None):
+    """Stage-1 top-k of int32 device scores: (indices int64[k], scores int32[k]),
+    score descending, ties by lowest index."""
+    import torch
+    assert scores.is_cuda and scores.dtype == torch.int32 and scores.dim() == 1
+    m = scores.numel()
+    if workspace is None:
+        workspace = _words(int(lib().hers_topk_workspace_bytes(m)) + 7, scores.device)
+    idx = torch.empty(k, dtype=torch.int64, device=scores.device)
+    val = torch.empty(k, dtype=torch.int32, device=scores.device)
+    ctx.check(lib().hers_topk(ctx.h, _ptr(scores), m, k, _ptr(idx), _ptr(val), _ptr(workspace),
+                              workspace.numel() * 8, _stream(stream)), "hers_topk")
+    return idx, val
 
 
 def hers_selftest_wait_timeout(ctx: Context, limit_ns: int):

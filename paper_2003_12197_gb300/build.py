@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhers.so")
-SOURCES = ["capi.cu", "scheme.cu", "search.cu", "batch.cu", "serve.cu", "stream.cu", "intpipe.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "scheme.cu", "search.cu", "batch.cu", "serve.cu", "stream.cu", "intpipe.cu", "noalloc.cu",
+           "topk.cu"]
 HEADERS = ["common.cuh", "internal.h", "hers_consts.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

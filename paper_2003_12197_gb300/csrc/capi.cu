@@ -211,6 +211,7 @@ int hers_check(hers_ctx* ctx, void* stream) {
     if (flag) {
         cudaMemset(ctx->err, 0, sizeof(int));
         if (flag & 2) return fail(ctx, HERS_E_TIMEOUT, "a bounded device-side wait gave up");
+        if (flag & 8) return fail(ctx, HERS_E_CUDA, "top-K selection: candidate count mismatch");
         return fail(ctx, HERS_E_SAMPLER, "a rejection sampler exhausted its attempts");
     }
     return HERS_OK;

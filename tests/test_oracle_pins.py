@@ -448,3 +448,22 @@ def test_block_rows_encryption_matches_full_array_form():
         a = O.encrypt_gallery_block(pk, feats, b, seed=12, n=n)
         r = O.encrypt_gallery_block_rows(pk, feats[b * n:(b + 1) * n], b, seed=12, n=n)
         assert np.array_equal(a, r)
+
+
+def test_topk_matches_sorted_with_index_ties():
+    """Stage-1 top-K: against Python's sorted() with key (-score, index), on
+    small-range scores full of ties, for every k from 1 to m."""
+    rng = np.random.default_rng(7)
+    for m in (1, 2, 7, 50):
+        s = rng.integers(-3, 4, size=m).astype(np.int32)
+        want_all = sorted(range(m), key=lambda i: (-int(s[i]), i))
+        for k in range(1, m + 1):
+            idx, val = O.topk(s, k)
+            assert list(idx) == want_all[:k]
+            assert list(val) == [int(s[i]) for i in want_all[:k]]
+    # k larger than m is clipped; the planted maximum comes first
+    s = rng.integers(-1000, 1000, size=1000).astype(np.int32)
+    s[617] = 5000
+    idx, val = O.topk(s, 5000)
+    assert len(idx) == 1000 and idx[0] == 617 and val[0] == 5000
+    assert np.all(np.diff(val.astype(np.int64)) <= 0)
