@@ -343,6 +343,23 @@ def run_gpu(args):
     H.hers_trace_enable(ctx, 0)
     clk = clocks.stop()
 
+    # the same step with output re-randomisation (Enc(0) added per block)
+    def step_rerand():
+        H.hers_probe_prepare(ctx, pct, out=pr)
+        H.hers_search_rerand(ctx, keys, gal, nb, d, pr, GAL_SEED + 1, out=sc, workspace=ws)
+
+    for _ in range(args.warmup):
+        step_rerand()
+    torch.cuda.synchronize()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(args.steps):
+        step_rerand()
+    r1.record(stream)
+    torch.cuda.synchronize()
+    rerand_ms = r0.elapsed_time(r1) / args.steps
+    H.hers_check(ctx)
+
     # e2e through the C ABI with host buffers.  Each step copies the probe's
     # cts in from pinned host memory and the score cts back out.  Two streams
     # with their own workspaces and host buffers alternate, so one step's
@@ -441,6 +458,8 @@ def run_gpu(args):
                          "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
                          "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes},
             "phases_ms": {k: round(v, 4) for k, v in phases.items()},
+            "rerandomized": {"ms_per_step": rerand_ms, "entries_per_s": m * world / (rerand_ms / 1e3),
+                             "api": "hers_search_rerand (Enc(0) added to every block's score ciphertext)"},
             "traced_calls": ncalls,
             "correct": {"scores_exact": exact, "top1_planted_mate": top1},
             "clocks": clk,

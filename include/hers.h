@@ -150,6 +150,17 @@ int hers_probe_prepare(hers_ctx* ctx, const uint64_t* probe_ct, uint32_t d, uint
 int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
                 uint32_t d, const uint64_t* probe, uint64_t* scores_ct, void* workspace,
                 uint64_t workspace_bytes, void* stream);
+/*
+ * hers_search with output re-randomisation (Alg 7's s <- Encrypt(0), as an
+ * option): block b's score ciphertext gets a fresh encryption of zero added,
+ * Enc(0) with u, e1, e2 drawn from the streams (rerand_seed, 0x31 + 0/1/2, b),
+ * b counted from the first block of this call.  Decrypts to the same scores;
+ * hides the noise left by the computation.  Same arguments, workspace and
+ * errors as hers_search, plus rerand_seed.
+ */
+int hers_search_rerand(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
+                       uint32_t d, const uint64_t* probe, uint64_t* scores_ct, void* workspace,
+                       uint64_t workspace_bytes, uint64_t rerand_seed, void* stream);
 
 /*
  * hers_search without caller-supplied scratch, for callers that cannot

@@ -35,6 +35,7 @@ Q = Q1 * Q2
 T = 4169729
 PURPOSE_GALLERY = 0x11  # u, e1, e2 streams at 0x11, 0x12, 0x13; obj = block * d + dim
 PURPOSE_PROBE = 0x21    # u, e1, e2 streams at 0x21, 0x22, 0x23; obj = dim
+PURPOSE_RERAND = 0x31   # output re-randomisation Enc(0): u, e1, e2 at 0x31..0x33; obj = block
 
 _lock = threading.Lock()
 _lib = None
@@ -311,3 +312,19 @@ def topk(scores, k):
     k = int(min(k, s.shape[0]))
     order = np.lexsort((np.arange(s.shape[0], dtype=np.int64), -s.astype(np.int64)))[:k]
     return order.astype(np.int64), s[order].astype(np.int32)
+
+
+def ct_add(a, b):
+    """Homomorphic addition (App. A): residue-wise sum of two canonical
+    ciphertexts [2][2][n], mod q1 for limb 0 and q2 for limb 1."""
+    out = np.empty_like(a)
+    for l, q in enumerate((Q1, Q2)):
+        out[:, l] = (a[:, l].astype(object) + b[:, l].astype(object)) % q
+    return out.astype(np.uint64)
+
+
+def rerandomize(pk, ct, seed, block, n=N):
+    """Output re-randomisation (Alg 7 initialises s with Encrypt(0)): ct plus
+    a fresh encryption of zero drawn from the streams (seed, 0x31.., block)."""
+    zero = encrypt(pk, np.zeros(n, dtype=np.uint32), seed, PURPOSE_RERAND, block, n)
+    return ct_add(ct, zero)

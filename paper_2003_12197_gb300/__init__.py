@@ -66,6 +66,7 @@ def lib():
                 "hers_encrypt_probe": ([vp, vp, vp, u32, u64, vp, vp], i32),
                 "hers_probe_prepare": ([vp, vp, u32, vp, vp], i32),
                 "hers_search": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
+                "hers_search_rerand": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, u64, vp], i32),
                 "hers_search_host": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
                 "hers_search_host_async": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
                 "hers_search_noalloc": ([vp, vp, vp, u64, u32, vp, vp, vp], i32),
@@ -267,6 +268,21 @@ def hers_search(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, probe, 
     ctx.check(lib().hers_search(ctx.h, keys.h, _ptr(gallery), nblocks, d, _ptr(probe), _ptr(sc),
                                 _ptr(ws), ws.numel() * 8, _stream(stream)), "hers_search")
     return sc
+
+
+def hers_search_rerand(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, probe, rerand_seed: int,
+                       out=None, workspace=None, stream=None):
+    """hers_search plus a fresh Enc(0) (streams (rerand_seed, 0x31.., block)) on every block."""
+    import torch
+    dev = probe.device
+    if out is None:
+        out = torch.empty((nblocks, 2, 2, N), dtype=torch.int64, device=dev)
+    if workspace is None:
+        workspace = _words(int(lib().hers_search_workspace_bytes(nblocks)), dev)
+    ctx.check(lib().hers_search_rerand(ctx.h, keys.h, _ptr(gallery), nblocks, d, _ptr(probe), _ptr(out),
+                                       _ptr(workspace), workspace.numel() * 8, rerand_seed, _stream(stream)),
+              "hers_search_rerand")
+    return out
 
 
 def hers_search_host(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, probe_ct_host,

@@ -287,7 +287,7 @@ int hers_encrypt_gallery(hers_ctx* ctx, const hers_keys* keys, const int8_t* fea
     for (uint64_t c0 = 0; c0 < nct && e == cudaSuccess; c0 += chunk) {
         const uint64_t n = nct - c0 < chunk ? nct - c0 : chunk;
         uint64_t* ct = gallery_ct ? gallery_ct + c0 * 4 * N : tmp;
-        e = launch_encrypt(ctx->tw, keys->k, feats, m, d, c0, n, false, seed, ct, ctx->err, st);
+        e = launch_encrypt(ctx->tw, keys->k, feats, m, d, c0, n, ENC_GALLERY, seed, ct, ctx->err, st);
         if (e == cudaSuccess && gallery) e = launch_extend_ntt(ctx->tw, ct, n, c0, d, gallery, st);
     }
     if (tmp) cudaFreeAsync(tmp, st);
@@ -299,7 +299,7 @@ int hers_encrypt_probe(hers_ctx* ctx, const hers_keys* keys, const int8_t* q, ui
     if (!ctx || !keys || !q || !probe_ct) return fail(ctx, HERS_E_INVAL, "hers_encrypt_probe: null argument");
     if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_encrypt_probe: d = %u", d);
     DeviceGuard g(ctx->device);
-    cudaError_t e = launch_encrypt(ctx->tw, keys->k, q, 0, d, 0, d, true, seed, probe_ct, ctx->err,
+    cudaError_t e = launch_encrypt(ctx->tw, keys->k, q, 0, d, 0, d, ENC_PROBE, seed, probe_ct, ctx->err,
                                    pick(ctx, stream));
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_encrypt_probe");
 }
@@ -328,6 +328,21 @@ int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
                                   (uint64_t*)workspace, ctx->err, pick(ctx, stream), next_trace(ctx),
                                   ctx->tensor_variant);
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search");
+}
+
+int hers_search_rerand(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
+                       uint32_t d, const uint64_t* probe, uint64_t* scores_ct, void* workspace,
+                       uint64_t workspace_bytes, uint64_t rerand_seed, void* stream) {
+    int rc = hers_search(ctx, keys, gallery, nblocks, d, probe, scores_ct, workspace, workspace_bytes, stream);
+    if (rc != HERS_OK || nblocks == 0) return rc;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick(ctx, stream);
+    // the accumulator area of the workspace is free once the search is done
+    uint64_t* z = (uint64_t*)workspace;
+    cudaError_t e = launch_encrypt(ctx->tw, keys->k, nullptr, 0, 1, 0, nblocks, ENC_ZERO, rerand_seed, z,
+                                   ctx->err, st);
+    if (e == cudaSuccess) e = launch_ct_add(scores_ct, z, nblocks, st);
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search_rerand");
 }
 
 }  // extern "C"

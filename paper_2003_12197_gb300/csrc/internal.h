@@ -59,9 +59,14 @@ struct DeviceGuard {
 
 // scheme.cu
 cudaError_t launch_keygen(const uint64_t* tw, uint64_t seed, DevKeys k, int* err, cudaStream_t st);
+// Encryption modes of launch_encrypt: gallery blocks (Eq. 3), probe dimensions
+// (Eq. 2), or encryptions of zero (output re-randomisation, obj = block).
+constexpr int ENC_GALLERY = 0, ENC_PROBE = 1, ENC_ZERO = 2;
 cudaError_t launch_encrypt(const uint64_t* tw, const DevKeys& k, const int8_t* feats, uint64_t m,
-                           uint32_t d, uint64_t ct_begin, uint64_t nct, bool probe, uint64_t seed,
+                           uint32_t d, uint64_t ct_begin, uint64_t nct, int mode, uint64_t seed,
                            uint64_t* out_ct, int* err, cudaStream_t st);
+// out[c] += add[c] mod q for nct canonical ciphertexts.
+cudaError_t launch_ct_add(uint64_t* out, const uint64_t* add, uint64_t nct, cudaStream_t st);
 // Canonical cts ct[0 .. nct) (global indices ct_begin ..) of dimension d into
 // the resident form at `out` (the base of block 0).
 cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t ct_begin,

@@ -110,13 +110,15 @@ cudaError_t launch_keygen(const uint64_t* tw, uint64_t seed, DevKeys k, int* err
 //   gallery (Eq. 3): ct c = b d + i has slot j = feats[b N + j][i] (0 past m);
 //     slot j is the evaluation at psi_t^(2j+1), which the forward NTT mod t
 //     puts at index brev(j), so m = INTT_t of the slots placed at brev(j).
+//   zero (mode ENC_ZERO): m = 0, an encryption of zero for output
+//     re-randomisation (Alg 7's Encrypt(0)); ciphertext c is block c.
 // Randomness: u, e1, e2 are the streams (seed, base + 0/1/2, obj) with
-// obj = b d + i (gallery) or i (probe).
+// obj = b d + i (gallery), i (probe) or the block (zero).
 __global__ void __launch_bounds__(NTT_THREADS, 2) k_encrypt(const uint64_t* __restrict__ tw,
                                                          const uint64_t* __restrict__ pk_ntt,
                                                          const int8_t* __restrict__ feats,
                                                          uint64_t m, uint32_t d, uint64_t ct_begin,
-                                                         int probe, uint64_t seed,
+                                                         int mode, uint64_t seed,
                                                          uint64_t* __restrict__ out, int* err) {
     extern __shared__ uint64_t sm[];
     uint64_t* U = sm;
@@ -125,11 +127,13 @@ __global__ void __launch_bounds__(NTT_THREADS, 2) k_encrypt(const uint64_t* __re
     const uint64_t c = ct_begin + blockIdx.x;
     const int limb = blockIdx.y;
     const uint64_t p = c_mod[limb];
-    const uint32_t base = probe ? PRF_PROBE : PRF_GALLERY;
-    const uint64_t obj = c;  // gallery: b d + i; probe: i
+    const uint32_t base = mode == ENC_PROBE ? PRF_PROBE : (mode == ENC_ZERO ? PRF_RERAND : PRF_GALLERY);
+    const uint64_t obj = c;  // gallery: b d + i; probe: i; zero: block
 
     // plaintext
-    if (probe) {
+    if (mode == ENC_ZERO) {
+        for (int k = threadIdx.x; k < N; k += blockDim.x) M[swz(k)] = 0;
+    } else if (mode == ENC_PROBE) {
         const int v = feats[c];
         const uint64_t mv = v < 0 ? T_PLAIN - (uint64_t)(-v) : (uint64_t)v;
         for (int k = threadIdx.x; k < N; k += blockDim.x) M[swz(k)] = k == 0 ? mv : 0;
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 2) k_encrypt(const uint64_t* __re
 }
 
 cudaError_t launch_encrypt(const uint64_t* tw, const DevKeys& k, const int8_t* feats, uint64_t m,
-                           uint32_t d, uint64_t ct_begin, uint64_t nct, bool probe, uint64_t seed,
+                           uint32_t d, uint64_t ct_begin, uint64_t nct, int mode, uint64_t seed,
                            uint64_t* out_ct, int* err, cudaStream_t st) {
     const int smem = 3 * N * 8;
     cudaError_t e = cudaFuncSetAttribute(k_encrypt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -192,7 +196,27 @@ cudaError_t launch_encrypt(const uint64_t* tw, const DevKeys& k, const int8_t* f
     for (uint64_t off = 0; off < nct; off += chunk) {
         const uint64_t n = nct - off < chunk ? nct - off : chunk;
         k_encrypt<<<dim3((unsigned)n, 2), NTT_THREADS, smem, st>>>(
-            tw, k.pk_ntt, feats, m, d, ct_begin + off, probe ? 1 : 0, seed, out_ct + off * 4 * N, err);
+            tw, k.pk_ntt, feats, m, d, ct_begin + off, mode, seed, out_ct + off * 4 * N, err);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+// out[c] = out[c] + add[c] (mod q_l, per polynomial and limb) for nct
+// canonical ciphertexts: homomorphic addition (App. A), used to add Enc(0).
+__global__ void __launch_bounds__(256) k_ct_add(uint64_t* __restrict__ out, const uint64_t* __restrict__ add) {
+    const uint64_t c = blockIdx.y;
+    const int row = blockIdx.z;  // poly * 2 + limb
+    const int k = blockIdx.x * 256 + threadIdx.x;
+    const uint64_t q = c_mod[row & 1];
+    const size_t at = (c * 4 + row) * N + k;
+    out[at] = add_mod(out[at], add[at], q);
+}
+
+cudaError_t launch_ct_add(uint64_t* out, const uint64_t* add, uint64_t nct, cudaStream_t st) {
+    for (uint64_t off = 0; off < nct; off += 65535) {
+        const uint64_t n = nct - off < 65535 ? nct - off : 65535;
+        k_ct_add<<<dim3(N / 256, (unsigned)n, 4), 256, 0, st>>>(out + off * 4 * N, add + off * 4 * N);
         count_launches(1);
     }
     return cudaGetLastError();

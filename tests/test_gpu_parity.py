@@ -268,3 +268,28 @@ def test_maximum_dimension_d512_bit_exact(ctx, keys, oracle_keys):
     assert np.array_equal(u64(res["sc"])[0], osc)
     assert np.array_equal(res["scores"].astype(np.int64), W.plain_inner_products(feats, q))
     assert int(np.argmax(res["scores"])) == 1234
+
+
+def test_rerandomized_search_bit_exact(ctx, keys, oracle_keys):
+    """hers_search_rerand: every block's score ciphertext equals the oracle's
+    search output plus its Enc(0) from the streams (seed, 0x31.., block), and
+    decrypts to the plaintext inner products."""
+    m, d = 2 * 4096 + 300, 16
+    feats = W.gallery_features(m, d, 8181)
+    q = W.probe_for_mate(4321, d, 8181, 8282)
+    gal, _ = H.hers_encrypt_gallery(ctx, keys, torch.from_numpy(feats).cuda(), 8383)
+    pr = H.hers_probe_prepare(ctx, H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).cuda(), 8484))
+    nb = H.hers_blocks_for(m)
+    plain = H.hers_search(ctx, keys, gal, nb, d, pr)
+    sc = H.hers_search_rerand(ctx, keys, gal, nb, d, pr, 8585)
+    H.hers_check(ctx)
+    got, plain_u = u64(sc), u64(plain)
+    assert not np.array_equal(got, plain_u)
+    oprb = O.encrypt_probe(oracle_keys[1], q, 8484)
+    for b in range(nb):
+        ogal = O.encrypt_gallery_block(oracle_keys[1], feats, b, 8383)
+        osc, _ = O.search_block(oprb, ogal, oracle_keys[2])
+        assert np.array_equal(plain_u[b], osc), f"block {b}"
+        assert np.array_equal(got[b], O.rerandomize(oracle_keys[1], osc, 8585, b)), f"block {b}"
+    scores = H.hers_decrypt_scores(ctx, keys, sc, m).cpu().numpy().astype(np.int64)
+    assert np.array_equal(scores, W.plain_inner_products(feats, q))

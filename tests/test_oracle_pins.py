@@ -467,3 +467,26 @@ def test_topk_matches_sorted_with_index_ties():
     idx, val = O.topk(s, 5000)
     assert len(idx) == 1000 and idx[0] == 617 and val[0] == 5000
     assert np.all(np.diff(val.astype(np.int64)) <= 0)
+
+
+def test_rerandomization_adds_a_fresh_zero():
+    """Output re-randomisation: the added ciphertext decrypts to 0 with small
+    noise, the sum decrypts to the same message, and different blocks or
+    seeds give different randomness."""
+    n = 4096
+    sk, pk, evk = O.keygen(2222)
+    m = np.arange(n, dtype=np.uint32) % O.T
+    ct = O.encrypt(pk, m, 3333, O.PURPOSE_PROBE, 0)
+    r = O.rerandomize(pk, ct, 4444, 7)
+    zero = O.encrypt(pk, np.zeros(n, dtype=np.uint32), 4444, O.PURPOSE_RERAND, 7)
+    # residue-wise sum, checked against Python integers limb by limb
+    for poly in range(2):
+        for l, q in enumerate((O.Q1, O.Q2)):
+            want = [(int(a) + int(b)) % q for a, b in zip(ct[poly, l], zero[poly, l])]
+            assert list(map(int, r[poly, l])) == want
+    _, pt0, noise0 = O.decrypt(sk, zero)
+    assert not np.any(pt0) and noise0 < O.Q // (2 * O.T) >> 40
+    _, pt, _ = O.decrypt(sk, r)
+    assert np.array_equal(pt, m)
+    assert not np.array_equal(O.rerandomize(pk, ct, 4444, 8), r)
+    assert not np.array_equal(O.rerandomize(pk, ct, 4445, 7), r)
