@@ -125,6 +125,25 @@ int hers_encrypt_gallery(hers_ctx* ctx, const hers_keys* keys, const int8_t* fea
                          void* stream);
 
 /*
+ * Online single-entry enrollment (Alg 6): the entry's d int8 features (device
+ * pointer `feats`) go into slot `slot` of resident block `block` of a gallery
+ * of nblocks blocks and dimension d.  For each dimension i the call encrypts
+ * the plaintext whose slot `slot` holds feats[i] and every other slot 0
+ * (BatchEncode(.; v)), with u, e1, e2 from the streams (seed, 0x41..0x43,
+ * (block N + slot) d + i), adds it to the block's ciphertext (CipherAdd), and
+ * rewrites that ciphertext's resident form.  The block's canonical
+ * ciphertexts are recovered from the resident form, so no canonical copy is
+ * needed.  The slot should be empty (it holds 0 for padded slots); otherwise
+ * its value becomes the sum.  workspace: device, hers_enroll_workspace_bytes(d)
+ * bytes.  Asynchronous on `stream`.  HERS_E_INVAL for a block or slot out of
+ * range.
+ */
+uint64_t hers_enroll_workspace_bytes(uint32_t d);
+int hers_enroll(hers_ctx* ctx, const hers_keys* keys, uint64_t* gallery, uint64_t nblocks, uint32_t d,
+                uint64_t block, uint32_t slot, const int8_t* feats, uint64_t seed, void* workspace,
+                uint64_t workspace_bytes, void* stream);
+
+/*
  * Probe encryption (Alg 7 client side; Eq. 2 encoding; Alg 2).
  * q: device int8 [d].  Dimension i is the constant plaintext q[i] (every slot
  * = q[i]), encrypted under pk with randomness stream obj = i.

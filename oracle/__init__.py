@@ -36,6 +36,7 @@ T = 4169729
 PURPOSE_GALLERY = 0x11  # u, e1, e2 streams at 0x11, 0x12, 0x13; obj = block * d + dim
 PURPOSE_PROBE = 0x21    # u, e1, e2 streams at 0x21, 0x22, 0x23; obj = dim
 PURPOSE_RERAND = 0x31   # output re-randomisation Enc(0): u, e1, e2 at 0x31..0x33; obj = block
+PURPOSE_ENROLL = 0x41   # online enrollment (Alg 6): u, e1, e2 at 0x41..0x43; obj = (b n + v) d + dim
 
 _lock = threading.Lock()
 _lib = None
@@ -328,3 +329,19 @@ def rerandomize(pk, ct, seed, block, n=N):
     a fresh encryption of zero drawn from the streams (seed, 0x31.., block)."""
     zero = encrypt(pk, np.zeros(n, dtype=np.uint32), seed, PURPOSE_RERAND, block, n)
     return ct_add(ct, zero)
+
+
+def enroll(pk, block_cts, b, v, feat, seed, n=N):
+    """Online enrollment (Alg 6): adds one entry with features feat[d] into
+    slot v of gallery block b.  For each dimension i: the plaintext with slot
+    v = feat[i] and every other slot 0 (BatchEncode(.; v)), encrypted with the
+    streams (seed, 0x41.., (b n + v) d + i), is added to the block's
+    ciphertext i (CipherAdd).  block_cts: [d][2][2][n]; returns the updated copy."""
+    d = block_cts.shape[0]
+    out = np.empty_like(block_cts)
+    for i in range(d):
+        slots = np.zeros(n, dtype=np.int64)
+        slots[v] = int(feat[i])
+        z = encrypt(pk, encode(slots, n), seed, PURPOSE_ENROLL, (b * n + v) * d + i, n)
+        out[i] = ct_add(block_cts[i], z)
+    return out

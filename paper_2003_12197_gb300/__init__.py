@@ -78,6 +78,8 @@ def lib():
                 "hers_probe_int_pipe": ([i32, u32, u64, vp], i32),
                 "hers_selftest_wait_timeout": ([vp, u64, vp], i32),
                 "hers_topk_workspace_bytes": ([u64], u64),
+                "hers_enroll_workspace_bytes": ([u32], u64),
+                "hers_enroll": ([vp, vp, vp, u64, u32, u64, u32, vp, u64, vp, u64, vp], i32),
                 "hers_topk": ([vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
                 "hers_tensor_variants": ([], i32),
                 "hers_tensor_variant_name": ([i32], ctypes.c_char_p),
@@ -556,6 +558,20 @@ def hers_probe_int_pipe(device: int = 0, iters: int = 1 << 16):
             raise HersError(f"hers_probe_int_pipe({name}): {lib().hers_status_string(rc).decode()}")
         out[name] = v.value
     return out
+
+
+def hers_enroll(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, block: int, slot: int, feats,
+                seed: int, workspace=None, stream=None):
+    """Online enrollment (Alg 6): int8 device features [d] into slot `slot` of
+    resident block `block`; updates `gallery` in place."""
+    import torch
+    assert feats.is_cuda and feats.dtype == torch.int8 and feats.numel() == d
+    feats = feats.contiguous()
+    if workspace is None:
+        workspace = _words(int(lib().hers_enroll_workspace_bytes(d)), feats.device)
+    ctx.check(lib().hers_enroll(ctx.h, keys.h, _ptr(gallery), nblocks, d, block, slot, _ptr(feats), seed,
+                                _ptr(workspace), workspace.numel() * 8, _stream(stream)), "hers_enroll")
+    return gallery
 
 
 def hers_topk(ctx: Context, scores, k: int, workspace=None, stream=None):

@@ -294,6 +294,31 @@ int hers_encrypt_gallery(hers_ctx* ctx, const hers_keys* keys, const int8_t* fea
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_encrypt_gallery");
 }
 
+uint64_t hers_enroll_workspace_bytes(uint32_t d) { return 2ull * d * 4 * N * 8; }
+
+int hers_enroll(hers_ctx* ctx, const hers_keys* keys, uint64_t* gallery, uint64_t nblocks, uint32_t d,
+                uint64_t block, uint32_t slot, const int8_t* feats, uint64_t seed, void* workspace,
+                uint64_t workspace_bytes, void* stream) {
+    if (!ctx || !keys || !gallery || !feats || !workspace)
+        return fail(ctx, HERS_E_INVAL, "hers_enroll: null argument");
+    if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_enroll: d = %u", d);
+    if (block >= nblocks || slot >= N)
+        return fail(ctx, HERS_E_INVAL, "hers_enroll: block %llu of %llu, slot %u of %d",
+                    (unsigned long long)block, (unsigned long long)nblocks, slot, N);
+    if (workspace_bytes < hers_enroll_workspace_bytes(d))
+        return fail(ctx, HERS_E_NOMEM, "hers_enroll: workspace %llu < %llu bytes",
+                    (unsigned long long)workspace_bytes, (unsigned long long)hers_enroll_workspace_bytes(d));
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick(ctx, stream);
+    uint64_t* enc = (uint64_t*)workspace;        // d fresh ciphertexts of the entry
+    uint64_t* upd = enc + (uint64_t)d * 4 * N;   // block b's updated canonical ciphertexts
+    const uint64_t gslot = block * N + slot;
+    cudaError_t e = launch_encrypt(ctx->tw, keys->k, feats, gslot, d, 0, d, ENC_SLOT, seed, enc, ctx->err, st);
+    if (e == cudaSuccess) e = launch_resident_to_canonical_add(ctx->tw, gallery, block, d, enc, upd, st);
+    if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, upd, d, block * d, d, gallery, st);
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_enroll");
+}
+
 int hers_encrypt_probe(hers_ctx* ctx, const hers_keys* keys, const int8_t* q, uint32_t d,
                        uint64_t seed, uint64_t* probe_ct, void* stream) {
     if (!ctx || !keys || !q || !probe_ct) return fail(ctx, HERS_E_INVAL, "hers_encrypt_probe: null argument");

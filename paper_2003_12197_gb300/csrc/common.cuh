@@ -182,6 +182,7 @@ constexpr uint32_t PRF_KG_EVK_E = 0x05u;  // obj = j
 constexpr uint32_t PRF_GALLERY = 0x11u;   // obj = block * d + dim
 constexpr uint32_t PRF_PROBE = 0x21u;     // obj = dim
 constexpr uint32_t PRF_RERAND = 0x31u;    // output re-randomisation Enc(0); obj = block
+constexpr uint32_t PRF_ENROLL = 0x41u;    // online enrollment (Alg 6); obj = (b N + v) d + dim
 constexpr int MAX_ATTEMPTS = 16;
 
 // One coefficient k of a ternary stream, walking attempts a = 0, 1, ...

@@ -61,12 +61,18 @@ struct DeviceGuard {
 cudaError_t launch_keygen(const uint64_t* tw, uint64_t seed, DevKeys k, int* err, cudaStream_t st);
 // Encryption modes of launch_encrypt: gallery blocks (Eq. 3), probe dimensions
 // (Eq. 2), or encryptions of zero (output re-randomisation, obj = block).
-constexpr int ENC_GALLERY = 0, ENC_PROBE = 1, ENC_ZERO = 2;
+// ENC_SLOT: one entry's d dimensions, each into the single slot `m` mod N of
+// global slot m = b N + v (Alg 6's BatchEncode(.; v)); ciphertext c is dim c.
+constexpr int ENC_GALLERY = 0, ENC_PROBE = 1, ENC_ZERO = 2, ENC_SLOT = 3;
 cudaError_t launch_encrypt(const uint64_t* tw, const DevKeys& k, const int8_t* feats, uint64_t m,
                            uint32_t d, uint64_t ct_begin, uint64_t nct, int mode, uint64_t seed,
                            uint64_t* out_ct, int* err, cudaStream_t st);
 // out[c] += add[c] mod q for nct canonical ciphertexts.
 cudaError_t launch_ct_add(uint64_t* out, const uint64_t* add, uint64_t nct, cudaStream_t st);
+// Canonical ciphertexts of block b (d of them) recovered from the resident
+// form (inverse NTT of the q1, q2 limbs), plus add[i] mod q, into out[i].
+cudaError_t launch_resident_to_canonical_add(const uint64_t* tw, const uint64_t* resident, uint64_t b,
+                                             uint32_t d, const uint64_t* add, uint64_t* out, cudaStream_t st);
 // Canonical cts ct[0 .. nct) (global indices ct_begin ..) of dimension d into
 // the resident form at `out` (the base of block 0).
 cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t ct_begin,

@@ -111,7 +111,9 @@ cudaError_t launch_keygen(const uint64_t* tw, uint64_t seed, DevKeys k, int* err
 //     slot j is the evaluation at psi_t^(2j+1), which the forward NTT mod t
 //     puts at index brev(j), so m = INTT_t of the slots placed at brev(j).
 //   zero (mode ENC_ZERO): m = 0, an encryption of zero for output
-//     re-randomisation (Alg 7's Encrypt(0)); ciphertext c is block c.
+//     re-randomisation (Alg 7's Encrypt(0)); ciphertext c is block c;
+//   slot (mode ENC_SLOT, Alg 6): ciphertext c is dimension c of one entry at
+//     global slot m = b N + v: slot v holds feats[c], every other slot 0.
 // Randomness: u, e1, e2 are the streams (seed, base + 0/1/2, obj) with
 // obj = b d + i (gallery), i (probe) or the block (zero).
 __global__ void __launch_bounds__(NTT_THREADS, 2) k_encrypt(const uint64_t* __restrict__ tw,
@@ -127,12 +129,22 @@ __global__ void __launch_bounds__(NTT_THREADS, 2) k_encrypt(const uint64_t* __re
     const uint64_t c = ct_begin + blockIdx.x;
     const int limb = blockIdx.y;
     const uint64_t p = c_mod[limb];
-    const uint32_t base = mode == ENC_PROBE ? PRF_PROBE : (mode == ENC_ZERO ? PRF_RERAND : PRF_GALLERY);
-    const uint64_t obj = c;  // gallery: b d + i; probe: i; zero: block
+    const uint32_t base = mode == ENC_PROBE  ? PRF_PROBE
+                          : mode == ENC_ZERO ? PRF_RERAND
+                          : mode == ENC_SLOT ? PRF_ENROLL
+                                             : PRF_GALLERY;
+    // gallery: b d + i; probe: i; zero: block; slot: (b N + v) d + i
+    const uint64_t obj = mode == ENC_SLOT ? m * d + c : c;
 
     // plaintext
     if (mode == ENC_ZERO) {
         for (int k = threadIdx.x; k < N; k += blockDim.x) M[swz(k)] = 0;
+    } else if (mode == ENC_SLOT) {
+        const int v = feats[c];
+        const uint32_t slot = (uint32_t)(m % N);
+        for (int s = threadIdx.x; s < N; s += blockDim.x)
+            M[swz(brev12(s))] = s == (int)slot ? (v < 0 ? T_PLAIN - (uint64_t)(-v) : (uint64_t)v) : 0;
+        ntt_inv_call(M, tw, MOD_T);
     } else if (mode == ENC_PROBE) {
         const int v = feats[c];
         const uint64_t mv = v < 0 ? T_PLAIN - (uint64_t)(-v) : (uint64_t)v;
@@ -219,6 +231,31 @@ cudaError_t launch_ct_add(uint64_t* out, const uint64_t* add, uint64_t nct, cuda
         k_ct_add<<<dim3(N / 256, (unsigned)n, 4), 256, 0, st>>>(out + off * 4 * N, add + off * 4 * N);
         count_launches(1);
     }
+    return cudaGetLastError();
+}
+
+// Grid (2 d polys, 2 limbs).  Polynomial P = 2 i + poly of block b: reads its
+// limb-l values from the resident form, undoes the split storage and the
+// NTT (the resident q limbs are NTT_{q_l} of the canonical residues), adds
+// add[i][poly][l] and writes the canonical residues to out[i][poly][l].
+__global__ void __launch_bounds__(NTT_THREADS, 3) k_resident_to_canonical_add(
+    const uint64_t* __restrict__ tw, const uint64_t* __restrict__ resident, uint64_t b, uint32_t d,
+    const uint64_t* __restrict__ add, uint64_t* __restrict__ out) {
+    extern __shared__ uint64_t sm[];
+    const uint32_t i = blockIdx.x >> 1;
+    const int poly = (int)(blockIdx.x & 1), limb = blockIdx.y;
+    for (int k = threadIdx.x; k < N; k += blockDim.x)
+        sm[swz(k)] = split_load(resident[resident_offset(b, limb, k, d, i, poly)]);
+    ntt_inv_mod(sm, tw, limb);
+    const uint64_t q = c_mod[limb];
+    const size_t row = (((size_t)i * 2 + poly) * 2 + limb) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) out[row + k] = add_mod(sm[swz(k)], add[row + k], q);
+}
+
+cudaError_t launch_resident_to_canonical_add(const uint64_t* tw, const uint64_t* resident, uint64_t b,
+                                             uint32_t d, const uint64_t* add, uint64_t* out, cudaStream_t st) {
+    k_resident_to_canonical_add<<<dim3(2 * d, 2), NTT_THREADS, N * 8, st>>>(tw, resident, b, d, add, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 

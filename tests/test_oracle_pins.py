@@ -490,3 +490,26 @@ def test_rerandomization_adds_a_fresh_zero():
     assert np.array_equal(pt, m)
     assert not np.array_equal(O.rerandomize(pk, ct, 4444, 8), r)
     assert not np.array_equal(O.rerandomize(pk, ct, 4445, 7), r)
+
+
+def test_enrollment_changes_only_its_slot():
+    """Alg 6: after enrolling an entry into an empty slot v, every dimension's
+    ciphertext decrypts to the old slots with slot v replaced by the entry's
+    feature; the added ciphertext uses its own randomness stream."""
+    n, d = 4096, 3
+    sk, pk, evk = O.keygen(5151)
+    feats = np.array([[7, -3, 100], [1, 2, 3]], dtype=np.int8)      # two entries, slots 0 and 1
+    blk = O.encrypt_gallery_block(pk, feats, 0, 5252)
+    new = np.array([-127, 55, 0], dtype=np.int8)
+    v = 4000
+    upd = O.enroll(pk, blk, 0, v, new, 5353)
+    for i in range(d):
+        slots, _, noise = O.decrypt(sk, upd[i])
+        want = np.zeros(n, dtype=np.int64)
+        want[:2] = feats[:, i]
+        want[v] = new[i]
+        assert np.array_equal(slots, want)
+        assert noise < O.Q // (2 * O.T) >> 30
+    again = O.enroll(pk, blk, 0, v, new, 5353)
+    assert np.array_equal(again, upd)
+    assert not np.array_equal(O.enroll(pk, blk, 0, v, new, 5354), upd)
