@@ -223,6 +223,34 @@ def cpu_oracle_rate(d, blocks, budget_s=12.0):
     return done * N / t_search, done, t_search
 
 
+def cpu_oracle_rate_single_thread(d):
+    """The oracle's search of one gallery block on one host thread: the
+    OpenMP thread count of the oracle's runtime is set to 1 for the timed
+    call (libgomp's omp_set_num_threads, through ctypes) and restored after."""
+    import ctypes
+
+    import oracle as O
+    import workloads as W
+    O.build()
+    try:
+        gomp = ctypes.CDLL("libgomp.so.1")
+    except OSError:
+        return None
+    _, opk, oevk = O.keygen(KEY_SEED)
+    q = W.probe_for_mate(0, d, FEAT_SEED, NOISE_SEED)
+    oprb = O.encrypt_probe(opk, q, PRB_SEED)
+    ogal = O.encrypt_gallery_block(opk, W.gallery_features(N, d, FEAT_SEED), 0, GAL_SEED)
+    before = gomp.omp_get_max_threads()
+    gomp.omp_set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        O.search_block(oprb, ogal, oevk)
+        dt = time.perf_counter() - t0
+    finally:
+        gomp.omp_set_num_threads(before)
+    return N / dt, dt
+
+
 def omp_threads():
     v = os.environ.get("OMP_NUM_THREADS")
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
@@ -433,6 +461,10 @@ def run_gpu(args):
         cpu = {"value": rate, "unit": "entries/s", "cores": omp_threads(), "kind": "oracle",
                "sample": f"{blocks} block(s) of {N} entries (d = {d}) of this workload searched by "
                          f"the oracle, {secs:.1f} s of search time"}
+        one = cpu_oracle_rate_single_thread(d)
+        if one is not None:
+            cpu["single_thread"] = {"value": one[0], "unit": "entries/s", "cores": 1,
+                                    "sample": f"one block of {N} entries (d = {d}), {one[1]:.1f} s"}
 
     if rank == 0:
         out = {
