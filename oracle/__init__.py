@@ -96,6 +96,9 @@ def lib():
                                                        u64p, sp]
             L.orc_decrypt.argtypes = [c_int, i8p, u64p, c_int, i64p, u32p, u64p]
             L.orc_params.argtypes = [u64p]
+            L.orc_basew_digits.argtypes = [c_int]
+            L.orc_keygen_w.argtypes = [c_int, c_u64, c_u64, c_int, u64p]
+            L.orc_keyswitch_w.argtypes = [c_int, u64p, u64p, c_int, u64p]
             _lib = L
     return _lib
 
@@ -345,3 +348,33 @@ def enroll(pk, block_cts, b, v, feat, seed, n=N):
         z = encrypt(pk, encode(slots, n), seed, PURPOSE_ENROLL, (b * n + v) * d + i, n)
         out[i] = ct_add(block_cts[i], z)
     return out
+
+
+def basew_digits(logw):
+    """Digits l = ceil(bits(q) / logw) of the base-w gadget, w = 2^logw."""
+    return int(lib().orc_basew_digits(logw))
+
+
+def keygen_w(sk_seed, w_seed, logw, n=N):
+    """Base-w evaluation keys (Alg 1 with g_j = w^j): [l][2][2][n]; s from
+    sk_seed's secret-key stream, a_j / e_j from w_seed's streams 0x06 / 0x07."""
+    evkw = np.zeros((basew_digits(logw), 2, 2, n), dtype=np.uint64)
+    _check(lib().orc_keygen_w(n, sk_seed, w_seed, logw, _p(evkw, ctypes.c_uint64)), "keygen_w")
+    return evkw
+
+
+def keyswitch_w(ct3, evkw, logw, n=N):
+    """Relinearisation of (c0, c1, c2) [3][2][n] with the base-w gadget."""
+    c = np.ascontiguousarray(ct3, dtype=np.uint64)
+    ev = np.ascontiguousarray(evkw, dtype=np.uint64)
+    out = np.zeros((2, 2, n), dtype=np.uint64)
+    _check(lib().orc_keyswitch_w(n, _p(c, ctypes.c_uint64), _p(ev, ctypes.c_uint64), logw,
+                                 _p(out, ctypes.c_uint64)), "keyswitch_w")
+    return out
+
+
+def search_block_basew(probe_cts, gal_cts, evk, evkw, logw, n=N):
+    """Score ciphertext of one block with the base-w gadget for the one key
+    switch: the same tensor and scale-and-round as search_block."""
+    _, pre, _ = search_block(probe_cts, gal_cts, evk, n, want_pre=True)
+    return keyswitch_w(pre, evkw, logw, n)

@@ -385,6 +385,8 @@ static void sample_gauss(uint64_t seed, uint32_t purpose, uint64_t obj, int n, i
 #define PRF_KG_PK_E 0x03u
 #define PRF_KG_EVK_A 0x04u /* obj = 2*j + limb */
 #define PRF_KG_EVK_E 0x05u /* obj = j */
+#define PRF_KG_EVKW_A 0x06u /* base-w evaluation keys: obj = 2*j + limb */
+#define PRF_KG_EVKW_E 0x07u /* obj = j */
 /* encryption: base + 0 -> u, base + 1 -> e1, base + 2 -> e2 */
 
 int orc_sample(uint64_t seed, uint32_t purpose, uint64_t obj, int n, int kind, uint64_t qj,
@@ -649,6 +651,55 @@ done:
     return rc;
 }
 
+/*
+ * Number of digits of the base-w gadget with w = 2^logw: l = ceil(bits(q) / logw),
+ * so that c = sum_{j<l} D_j w^j with D_j in [0, w) for every c in [0, q).
+ */
+int orc_basew_digits(int logw) {
+    init_consts();
+    int bits = 0;
+    for (u128 q = orc_q(); q; q >>= 1) bits++;
+    return (bits + logw - 1) / logw;
+}
+
+/*
+ * Base-w evaluation keys (Alg 1 with the power-of-two gadget g_j = w^j,
+ * w = 2^logw, 16 <= logw <= 60): evkw_j = ([-(a_j s + e_j) + w^j s^2]_q, a_j)
+ * for j = 0 .. l-1.  s is the secret key of sk_seed (its stream 0x01);
+ * a_j (uniform mod q, limb by limb) and e_j come from w_seed's streams 0x06
+ * (obj 2j + limb) and 0x07 (obj j).  evkw: [l][2 polys][2 limbs][n].
+ */
+int orc_keygen_w(int n, uint64_t sk_seed, uint64_t w_seed, int logw, uint64_t *evkw) {
+    init_consts();
+    if (!valid_n(n) || logw < 16 || logw > 60) return ORC_E_ARG;
+    int rc = ORC_OK, l = orc_basew_digits(logw);
+    u128 q = orc_q();
+    int8_t *sk = malloc(n), *e8 = malloc(n);
+    int32_t *s = malloc(n * sizeof(int32_t)), *s2 = malloc(n * sizeof(int32_t));
+    uint64_t *r = malloc(2 * n * sizeof(uint64_t));
+    u128 *a = malloc(n * sizeof(u128)), *as = malloc(n * sizeof(u128)), *c0 = malloc(n * sizeof(u128));
+    if ((rc = sample_ternary(sk_seed, PRF_KG_SK, 0, n, sk)) != ORC_OK) goto done;
+    for (int k = 0; k < n; k++) s[k] = sk[k];
+    negacyclic_small_z(n, s, s, s2);
+    for (int j = 0; j < l; j++) {
+        if ((rc = sample_uniform(w_seed, PRF_KG_EVKW_A, 2 * j, n, ORC_Q1, r)) != ORC_OK) goto done;
+        if ((rc = sample_uniform(w_seed, PRF_KG_EVKW_A, 2 * j + 1, n, ORC_Q2, r + n)) != ORC_OK) goto done;
+        poly_from_res(n, r, a);
+        sample_gauss(w_seed, PRF_KG_EVKW_E, (uint64_t)j, n, e8);
+        negacyclic_small_mod_q(n, a, s, as);
+        const u128 g = ((u128)1 << (logw * j)) % q; /* w^j < 2^108 */
+        for (int k = 0; k < n; k++) {
+            u128 gs2 = mod_q_i128((i128)g * s2[k]); /* |g s2| < 2^108 * 2^12 */
+            c0[k] = mod_q_i128(-((i128)as[k] + e8[k]) + (i128)gs2);
+        }
+        poly_to_res(n, c0, evkw + (size_t)j * 4 * n);
+        poly_to_res(n, a, evkw + (size_t)j * 4 * n + 2 * n);
+    }
+done:
+    free(sk); free(e8); free(s); free(s2); free(r); free(a); free(as); free(c0);
+    return rc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Alg 2: encryption                                                        */
 /* ------------------------------------------------------------------------ */
@@ -754,6 +805,55 @@ static void key_switch(int n, const u128 *c0, const u128 *c1, const u128 *c2,
         free(E[j][0]);
         free(E[j][1]);
     }
+}
+
+/*
+ * Relinearisation with the base-w gadget (Alg 5 with g_j = w^j): the
+ * coefficients of c2, as integers in [0, q), are cut into l digits D_j in
+ * [0, w), c2 = sum_j D_j w^j; (c0', c1') = ([c0 + sum_j D_j evkw_j[0]]_q,
+ * [c1 + sum_j D_j evkw_j[1]]_q), products exact over Z.
+ */
+static void key_switch_w(int n, const u128 *c0, const u128 *c1, const u128 *c2, const uint64_t *evkw,
+                         int logw, u128 *o0, u128 *o1) {
+    const int l = orc_basew_digits(logw);
+    const u128 mask = ((u128)1 << logw) - 1;
+    dig *D = malloc((size_t)l * n * sizeof(dig));
+    dig *E0 = malloc((size_t)l * n * sizeof(dig)), *E1 = malloc((size_t)l * n * sizeof(dig));
+    for (int j = 0; j < l; j++) {
+        const uint64_t *e0 = evkw + (size_t)j * 4 * n, *e1 = e0 + 2 * n;
+        for (int k = 0; k < n; k++) {
+            D[(size_t)j * n + k] = to_dig((i128)((c2[k] >> (logw * j)) & mask));
+            E0[(size_t)j * n + k] = to_dig((i128)crt2(e0[k], e0[n + k]));
+            E1[(size_t)j * n + k] = to_dig((i128)crt2(e1[k], e1[n + k]));
+        }
+    }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < n; k++) {
+        bi a0 = bi_from_u128(c0[k]), a1 = bi_from_u128(c1[k]);
+        for (int j = 0; j < l; j++) {
+            part p0 = {0, 0, 0}, p1 = {0, 0, 0};
+            negacyclic_coeff(n, k, D + (size_t)j * n, E0 + (size_t)j * n, &p0);
+            negacyclic_coeff(n, k, D + (size_t)j * n, E1 + (size_t)j * n, &p1);
+            part_flush(&p0, &a0);
+            part_flush(&p1, &a1);
+        }
+        o0[k] = bi_mod_q(&a0);
+        o1[k] = bi_mod_q(&a1);
+    }
+    free(D); free(E0); free(E1);
+}
+
+/* ct3 [3][2][n] canonical (c0, c1, c2) -> out [2][2][n] with the base-w gadget */
+int orc_keyswitch_w(int n, const uint64_t *ct3, const uint64_t *evkw, int logw, uint64_t *out) {
+    init_consts();
+    if (!valid_n(n) || logw < 16 || logw > 60) return ORC_E_ARG;
+    u128 *c = malloc((size_t)3 * n * sizeof(u128)), *o0 = malloc(n * sizeof(u128)), *o1 = malloc(n * sizeof(u128));
+    for (int p = 0; p < 3; p++) poly_from_res(n, ct3 + (size_t)p * 2 * n, c + (size_t)p * n);
+    key_switch_w(n, c, c + n, c + 2 * n, evkw, logw, o0, o1);
+    poly_to_res(n, o0, out);
+    poly_to_res(n, o1, out + 2 * n);
+    free(c); free(o0); free(o1);
+    return ORC_OK;
 }
 
 /* bound B = d * 2n * ((q-1)/2)^2 on |X_k| */

@@ -513,3 +513,53 @@ def test_enrollment_changes_only_its_slot():
     again = O.enroll(pk, blk, 0, v, new, 5353)
     assert np.array_equal(again, upd)
     assert not np.array_equal(O.enroll(pk, blk, 0, v, new, 5354), upd)
+
+
+def test_basew_keys_and_key_switch_identity():
+    """Base-w gadget (w = 2^27, l = 4): each key satisfies
+    evkw_j0 + evkw_j1 s = w^j s^2 - e_j over Z mod q with small e_j; the key
+    switch satisfies c0' + c1' s - (c0 + c1 s + c2 s^2) = -sum_j D_j e_j, with
+    c2 = sum_j D_j w^j, checked with Python integers."""
+    n, logw = 4096, 27
+    assert O.basew_digits(logw) == 4 and O.basew_digits(54) == 2 and O.basew_digits(16) == 7
+    sk, pk, evk = O.keygen(7171)
+    evkw = O.keygen_w(7171, 7272, logw)
+    assert evkw.shape == (4, 2, 2, n)
+    q = O.Q
+    s = [int(x) for x in sk]
+    def val(poly):        # CRT of the two limbs, centred in (-q/2, q/2)
+        return [x - q if x > q // 2 else x for x in O.res_to_int(poly)]
+
+    def mul(a, b):        # negacyclic product over Z (the pinned oracle routine; |a|, |b| < 2^107)
+        return [int(x) for x in O.negacyclic_z(list(a), list(b))]
+    s2 = mul(s, s)
+    errs = []
+    for j in range(4):
+        e0, e1 = val(evkw[j, 0]), val(evkw[j, 1])
+        lhs = [(x + y) % q for x, y in zip(e0, mul(e1, s))]
+        e = [((pow(2, logw * j, q) * z - x) % q) for z, x in zip(s2, lhs)]
+        e = [x - q if x > q // 2 else x for x in e]
+        assert max(abs(x) for x in e) <= 19
+        errs.append(e)
+    # key switch of a random 3-component ciphertext
+    rng = np.random.default_rng(5)
+    ct3 = np.zeros((3, 2, n), dtype=np.uint64)
+    for p in range(3):
+        ct3[p, 0] = rng.integers(0, O.Q1, n, dtype=np.uint64)
+        ct3[p, 1] = rng.integers(0, O.Q2, n, dtype=np.uint64)
+    out = O.keyswitch_w(ct3, evkw, logw)
+    c0, c1, c2 = val(ct3[0]), val(ct3[1]), val(ct3[2])
+    o0, o1 = val(out[0]), val(out[1])
+    lhs = [(a + b) % q for a, b in zip(o0, mul(o1, s))]
+    rhs0 = [(a + b + c) % q for a, b, c in zip(c0, mul(c1, s), mul(c2, s2))]
+    diff = [(x - y) % q for x, y in zip(lhs, rhs0)]
+    diff = [x - q if x > q // 2 else x for x in diff]
+    # exactly -sum_j D_j (*) e_j, with D_j the base-2^27 digits of c2 in [0, q)
+    c2u = O.res_to_int(ct3[2])
+    want = [0] * n
+    for j in range(4):
+        Dj = [(c >> (logw * j)) & ((1 << logw) - 1) for c in c2u]
+        assert sum(Dj) > 0
+        for k, v in enumerate(mul(Dj, errs[j])):
+            want[k] -= v
+    assert diff == want
