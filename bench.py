@@ -390,6 +390,24 @@ def run_gpu(args):
     rerand_ms = r0.elapsed_time(r1) / args.steps
     H.hers_check(ctx)
 
+    # the same step with the base-w relinearisation gadget (w = 2^27, 4 digits)
+    H.hers_keys_add_basew(ctx, keys, KEY_SEED + 27, 27)
+
+    def step_basew():
+        H.hers_probe_prepare(ctx, pct, out=pr)
+        H.hers_search_basew(ctx, keys, gal, nb, d, pr, out=sc, workspace=ws)
+
+    for _ in range(args.warmup):
+        step_basew()
+    torch.cuda.synchronize()
+    r0.record(stream)
+    for _ in range(args.steps):
+        step_basew()
+    r1.record(stream)
+    torch.cuda.synchronize()
+    basew_ms = r0.elapsed_time(r1) / args.steps
+    H.hers_check(ctx)
+
     # e2e through the C ABI with host buffers.  Each step copies the probe's
     # cts in from pinned host memory and the score cts back out.  Two streams
     # with their own workspaces and host buffers alternate, so one step's
@@ -494,6 +512,8 @@ def run_gpu(args):
             "phases_ms": {k: round(v, 4) for k, v in phases.items()},
             "rerandomized": {"ms_per_step": rerand_ms, "entries_per_s": m * world / (rerand_ms / 1e3),
                              "api": "hers_search_rerand (Enc(0) added to every block's score ciphertext)"},
+            "basew_gadget": {"ms_per_step": basew_ms, "entries_per_s": m * world / (basew_ms / 1e3),
+                             "api": "hers_search_basew, w = 2^27 (4 digits) instead of the 2-digit RNS gadget"},
             "traced_calls": ncalls,
             "correct": {"scores_exact": exact, "top1_planted_mate": top1},
             "clocks": clk,

@@ -170,6 +170,30 @@ int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
                 uint32_t d, const uint64_t* probe, uint64_t* scores_ct, void* workspace,
                 uint64_t workspace_bytes, void* stream);
 /*
+ * Base-w relinearisation gadget (Alg 1 / Alg 5 with g_j = w^j, w = 2^logw),
+ * as an option beside the default RNS gadget.
+ *
+ * hers_basew_digits(logw): the number of digits l = ceil(108 / logw) for
+ * 22 <= logw <= 60 (at most 5 digits), else 0.
+ * hers_keys_add_basew: generates evkw_j = ([-(a_j s + e_j) + w^j s^2]_q, a_j),
+ * j < l, for the keys' secret key s, with a_j (uniform mod q, limb by limb)
+ * and e_j from the streams (seed, 0x06, 2 j + limb) and (seed, 0x07, j), and
+ * attaches them to `keys` (replacing earlier base-w keys).  Synchronous.
+ * hers_keys_export_basew: copies them to host memory, [l][2][2][N] canonical.
+ * hers_search_basew: hers_search with the one key switch per block done with
+ * these keys: the coefficients of c2, as integers in [0, q), are cut into l
+ * base-w digits D_j and (c0', c1') = (c0 + sum_j D_j evkw_j0, c1 + sum_j D_j
+ * evkw_j1).  Same arguments, workspace and errors as hers_search;
+ * HERS_E_INVAL when the keys have no base-w keys.
+ */
+uint32_t hers_basew_digits(uint32_t logw);
+int hers_keys_add_basew(hers_ctx* ctx, hers_keys* keys, uint64_t seed, uint32_t logw);
+int hers_keys_export_basew(hers_ctx* ctx, const hers_keys* keys, uint64_t* evkw);
+int hers_search_basew(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
+                      uint32_t d, const uint64_t* probe, uint64_t* scores_ct, void* workspace,
+                      uint64_t workspace_bytes, void* stream);
+
+/*
  * hers_search with output re-randomisation (Alg 7's s <- Encrypt(0), as an
  * option): block b's score ciphertext gets a fresh encryption of zero added,
  * Enc(0) with u, e1, e2 drawn from the streams (rerand_seed, 0x31 + 0/1/2, b),

@@ -67,6 +67,10 @@ def lib():
                 "hers_probe_prepare": ([vp, vp, u32, vp, vp], i32),
                 "hers_search": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
                 "hers_search_rerand": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, u64, vp], i32),
+                "hers_basew_digits": ([u32], u32),
+                "hers_keys_add_basew": ([vp, vp, u64, u32], i32),
+                "hers_keys_export_basew": ([vp, vp, vp], i32),
+                "hers_search_basew": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
                 "hers_search_host": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
                 "hers_search_host_async": ([vp, vp, vp, u64, u32, vp, vp, vp, u64, vp], i32),
                 "hers_search_noalloc": ([vp, vp, vp, u64, u32, vp, vp, vp], i32),
@@ -269,6 +273,31 @@ def hers_search(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, probe, 
     ws = workspace if workspace is not None else _words(wsb, dev)
     ctx.check(lib().hers_search(ctx.h, keys.h, _ptr(gallery), nblocks, d, _ptr(probe), _ptr(sc),
                                 _ptr(ws), ws.numel() * 8, _stream(stream)), "hers_search")
+    return sc
+
+
+def hers_keys_add_basew(ctx: Context, keys: Keys, seed: int, logw: int):
+    """Attach base-w evaluation keys (w = 2^logw) to `keys`."""
+    ctx.check(lib().hers_keys_add_basew(ctx.h, keys.h, seed, logw), "hers_keys_add_basew")
+
+
+def hers_keys_export_basew(ctx: Context, keys: Keys, logw: int):
+    """The base-w evaluation keys, uint64 [l][2][2][N] (canonical)."""
+    import numpy as np
+    out = np.zeros((int(lib().hers_basew_digits(logw)), 2, 2, N), dtype=np.uint64)
+    ctx.check(lib().hers_keys_export_basew(ctx.h, keys.h, out.ctypes.data), "hers_keys_export_basew")
+    return out
+
+
+def hers_search_basew(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, probe, out=None,
+                      workspace=None, stream=None):
+    """hers_search with the base-w gadget for the key switch."""
+    import torch
+    dev = gallery.device
+    sc = out if out is not None else torch.empty((nblocks, 2, 2, N), dtype=torch.int64, device=dev)
+    ws = workspace if workspace is not None else _words(hers_search_workspace_bytes(nblocks), dev)
+    ctx.check(lib().hers_search_basew(ctx.h, keys.h, _ptr(gallery), nblocks, d, _ptr(probe), _ptr(sc),
+                                      _ptr(ws), ws.numel() * 8, _stream(stream)), "hers_search_basew")
     return sc
 
 

@@ -250,9 +250,46 @@ int hers_keys_free(hers_keys* keys) {
         DeviceGuard g(keys->ctx->device);
         cudaStreamSynchronize(keys->ctx->stream);
         cudaFree(keys->base);
+        if (keys->evkw) cudaFree(keys->evkw);  // evkw and evkw_ntt share one allocation
     }
     delete keys;
     return HERS_OK;
+}
+
+uint32_t hers_basew_digits(uint32_t logw) {
+    return (logw >= BASEW_MIN && logw <= BASEW_MAX) ? basew_digits(logw) : 0;
+}
+
+int hers_keys_add_basew(hers_ctx* ctx, hers_keys* keys, uint64_t seed, uint32_t logw) {
+    if (!ctx || !keys) return fail(ctx, HERS_E_INVAL, "hers_keys_add_basew: null argument");
+    if (logw < BASEW_MIN || logw > BASEW_MAX)
+        return fail(ctx, HERS_E_INVAL, "hers_keys_add_basew: log2 w = %u not in [%u, %u]", logw, BASEW_MIN,
+                    BASEW_MAX);
+    DeviceGuard g(ctx->device);
+    const uint32_t nd = basew_digits(logw);
+    uint64_t* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, (size_t)nd * (4 + 8) * N * 8);
+    if (e != cudaSuccess) return fail(ctx, HERS_E_NOMEM, "hers_keys_add_basew: %s", cudaGetErrorString(e));
+    e = launch_keygen_w(ctx->tw, seed, logw, nd, keys->k, mem, mem + (size_t)nd * 4 * N, ctx->err, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        cudaFree(mem);
+        return cuda_fail(ctx, e, "hers_keys_add_basew");
+    }
+    if (keys->evkw) cudaFree(keys->evkw);
+    keys->logw = logw;
+    keys->ndig = nd;
+    keys->evkw = mem;
+    keys->evkw_ntt = mem + (size_t)nd * 4 * N;
+    return HERS_OK;
+}
+
+int hers_keys_export_basew(hers_ctx* ctx, const hers_keys* keys, uint64_t* evkw) {
+    if (!ctx || !keys || !evkw) return fail(ctx, HERS_E_INVAL, "hers_keys_export_basew: null argument");
+    if (!keys->evkw) return fail(ctx, HERS_E_INVAL, "hers_keys_export_basew: no base-w keys");
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaMemcpy(evkw, keys->evkw, (size_t)keys->ndig * 4 * N * 8, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_keys_export_basew");
 }
 
 int hers_keys_export(hers_ctx* ctx, const hers_keys* keys, int8_t* sk, uint64_t* pk, uint64_t* evk) {
@@ -368,6 +405,22 @@ int hers_search_rerand(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gal
                                    ctx->err, st);
     if (e == cudaSuccess) e = launch_ct_add(scores_ct, z, nblocks, st);
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search_rerand");
+}
+
+int hers_search_basew(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
+                      uint32_t d, const uint64_t* probe, uint64_t* scores_ct, void* workspace,
+                      uint64_t workspace_bytes, void* stream) {
+    if (!ctx || !keys || !gallery || !probe || !scores_ct || !workspace)
+        return fail(ctx, HERS_E_INVAL, "hers_search_basew: null argument");
+    if (!keys->evkw) return fail(ctx, HERS_E_INVAL, "hers_search_basew: the keys have no base-w keys");
+    if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_search_basew: d = %u", d);
+    if (workspace_bytes < hers_search_workspace_bytes(nblocks))
+        return fail(ctx, HERS_E_NOMEM, "hers_search_basew: workspace too small");
+    DeviceGuard g(ctx->device);
+    const KeySwitchW ksw = {keys->evkw_ntt, keys->logw, keys->ndig};
+    cudaError_t e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, scores_ct, (uint64_t*)workspace,
+                                  ctx->err, pick(ctx, stream), next_trace(ctx), ctx->tensor_variant, &ksw);
+    return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search_basew");
 }
 
 }  // extern "C"

@@ -179,6 +179,8 @@ constexpr uint32_t PRF_KG_PK_A = 0x02u;   // obj = limb
 constexpr uint32_t PRF_KG_PK_E = 0x03u;
 constexpr uint32_t PRF_KG_EVK_A = 0x04u;  // obj = 2 j + limb
 constexpr uint32_t PRF_KG_EVK_E = 0x05u;  // obj = j
+constexpr uint32_t PRF_KG_EVKW_A = 0x06u; // base-w evaluation keys: obj = 2 j + limb
+constexpr uint32_t PRF_KG_EVKW_E = 0x07u; // obj = j
 constexpr uint32_t PRF_GALLERY = 0x11u;   // obj = block * d + dim
 constexpr uint32_t PRF_PROBE = 0x21u;     // obj = dim
 constexpr uint32_t PRF_RERAND = 0x31u;    // output re-randomisation Enc(0); obj = block

@@ -43,6 +43,10 @@ struct hers_keys {
     hers_ctx* ctx;
     hers::DevKeys k;
     void* base;  // single device allocation holding every key array
+    // base-w gadget keys (hers_keys_add_basew), 0 / null when absent
+    uint32_t logw = 0, ndig = 0;
+    uint64_t* evkw = nullptr;      // [ndig][2 polys][2 limbs][N], canonical
+    uint64_t* evkw_ntt = nullptr;  // [ndig][2][2][2][N]: NTT values and Shoup companions
 };
 
 namespace hers {
@@ -59,6 +63,15 @@ struct DeviceGuard {
 
 // scheme.cu
 cudaError_t launch_keygen(const uint64_t* tw, uint64_t seed, DevKeys k, int* err, cudaStream_t st);
+// Base-w gadget (w = 2^logw): digits and key generation / key switch pieces.
+constexpr uint32_t BASEW_MIN = 22, BASEW_MAX = 60;  // at most 5 digits: they fit the workspace
+uint32_t basew_digits(uint32_t logw);
+cudaError_t launch_keygen_w(const uint64_t* tw, uint64_t seed, uint32_t logw, uint32_t ndig, const DevKeys& k,
+                            uint64_t* evkw, uint64_t* evkw_ntt, int* err, cudaStream_t st);
+struct KeySwitchW {
+    const uint64_t* evkw_ntt;
+    uint32_t logw, ndig;
+};
 // Encryption modes of launch_encrypt: gallery blocks (Eq. 3), probe dimensions
 // (Eq. 2), or encryptions of zero (output re-randomisation, obj = block).
 // ENC_SLOT: one entry's d dimensions, each into the single slot `m` mod N of
@@ -90,16 +103,19 @@ constexpr int SEARCH_EVENTS = 5;
 // `err` receives bit 2 if a bounded wait inside a streaming kernel gave up.
 // `variant` selects the tensor-kernel shape (see tensor_variant_name).
 constexpr int DEFAULT_TENSOR_VARIANT = 1;
+// ksw (optional): key switch with the base-w gadget instead of the RNS one.
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
                           uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev = nullptr,
-                          int variant = DEFAULT_TENSOR_VARIANT);
+                          int variant = DEFAULT_TENSOR_VARIANT, const KeySwitchW* ksw = nullptr);
 // Epilogue over npairs accumulators X [npairs][3][5][N]; workspace C, KS as in
 // launch_search; `ev` (optional) receives the boundaries after the inverse
 // NTTs (ev[0]) and after scale-and-round (ev[1]).
+// With ksw, the key switch uses the base-w gadget: its digits [npairs][ndig]
+// [2][N] go after O in X (O [npairs][4][N] at X; 4 + 2 ndig <= 15 words per N).
 cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npairs, uint64_t* X,
                             uint64_t* C, uint64_t* KS, uint64_t* out, cudaStream_t st,
-                            cudaEvent_t* ev = nullptr);
+                            cudaEvent_t* ev = nullptr, const KeySwitchW* ksw = nullptr);
 // The tensor kernel alone, into X [nblocks][3][5][N].
 cudaError_t launch_tensor(int variant, const uint64_t* gallery, uint64_t nblocks, uint32_t d,
                           const uint64_t* probe, uint64_t* X, int* err, cudaStream_t st);

@@ -101,6 +101,68 @@ cudaError_t launch_keygen(const uint64_t* tw, uint64_t seed, DevKeys k, int* err
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- base-w evaluation keys
+//
+// Grid (2 limbs, ndig digits).  CTA (l, j) writes limb l of
+//   evkw_j = ([-(a_j s + e_j) + w^j s^2]_q, a_j),  w = 2^logw,
+// with a_j uniform mod q_l from the stream (seed, 0x06, 2 j + l) and e_j
+// from (seed, 0x07, j); s from the keys' NTT form.  Products in the NTT
+// domain mod q_l; w^j mod q_l by repeated doubling.
+uint32_t basew_digits(uint32_t logw) {
+    // bits(q1 q2) = 108
+    return (108 + logw - 1) / logw;
+}
+
+__global__ void __launch_bounds__(NTT_THREADS, 2) k_keygen_w(const uint64_t* __restrict__ tw, uint64_t seed,
+                                                          uint32_t logw, DevKeys K, uint64_t* __restrict__ evkw,
+                                                          int* err) {
+    extern __shared__ uint64_t sm[];
+    uint64_t* A = sm;
+    uint64_t* X = sm + N;
+    const int limb = blockIdx.x;
+    const uint32_t j = blockIdx.y;
+    const uint64_t p = c_mod[limb];
+    const uint64_t* s = K.s_ntt + (size_t)limb * 2 * N;  // NTT(s) mod q_l, then companions
+
+    sample_uniform(seed, PRF_KG_EVKW_A, (uint64_t)(2 * j + limb), p, A, err);
+    __syncthreads();
+    uint64_t* out = evkw + (size_t)j * 4 * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) out[(2 + limb) * N + k] = A[swz(k)];
+    ntt_fwd_call(A, tw, limb);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const int x = swz(k);
+        A[x] = mul_mod(A[x], s[k], limb);
+        X[x] = mul_mod(s[k], s[k], limb);
+    }
+    ntt_inv_call(A, tw, limb);
+    ntt_inv_call(X, tw, limb);
+    uint64_t g = 1;  // w^j mod q_l
+    for (uint32_t i = 0; i < logw * j; i++) g = add_mod(g, g, p);
+    for (int c = threadIdx.x; c < N / 8; c += blockDim.x) {
+        uint32_t blk[16];
+        chacha20(seed, PRF_KG_EVKW_E, (uint64_t)j, (uint32_t)c, blk);
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = 8 * c + i;
+            const int e = chi_from_word(((uint64_t)blk[2 * i + 1] << 32) | blk[2 * i]);
+            uint64_t v = add_mod(A[swz(k)], e < 0 ? p - (uint64_t)(-e) : (uint64_t)e, p);
+            v = v == 0 ? 0 : p - v;  // -(a s + e)
+            out[limb * N + k] = add_mod(v, mul_mod(g, X[swz(k)], limb), p);
+        }
+    }
+}
+
+cudaError_t launch_keygen_w(const uint64_t* tw, uint64_t seed, uint32_t logw, uint32_t ndig, const DevKeys& k,
+                            uint64_t* evkw, uint64_t* evkw_ntt, int* err, cudaStream_t st) {
+    const int smem = 2 * N * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_keygen_w, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_keygen_w<<<dim3(2, ndig), NTT_THREADS, smem, st>>>(tw, seed, logw, k, evkw, err);
+    k_key_ntt<<<4 * ndig, NTT_THREADS, N * 8, st>>>(tw, evkw, evkw_ntt);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- encryption
 //
 // Grid (nct, 2 limbs).  CTA (c, l) writes limb l of ciphertext ct_begin + c:

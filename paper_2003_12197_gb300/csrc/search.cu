@@ -341,10 +341,50 @@ __global__ void __launch_bounds__(256) k_ks_finish(const uint64_t* __restrict__ 
 // Epilogue over npairs (probe, block) pairs whose accumulators are in
 // X [npairs][3][5][N] (NTT domain): inverse NTTs, exact scale-and-round into
 // C [npairs][3][2][N] and KS [npairs][4][N], key switch (the output O reuses X),
+// ---------------------------------------------------------------- base-w key switch
+// Digits of c2 (C[b][2], canonical) in base w = 2^logw: the coefficient as an
+// integer c = x1 + q1 h in [0, q) (Garner), D_j = floor(c / w^j) mod w, each
+// stored as a residue in both limbs: W[b][j][l][N] = D_j mod q_l.
+__global__ void __launch_bounds__(256) k_digits_w(const uint64_t* __restrict__ C, uint32_t logw, uint32_t ndig,
+                                                  uint64_t* __restrict__ W) {
+    const int k = blockIdx.x * 256 + threadIdx.x;
+    const uint64_t b = blockIdx.z;
+    const uint64_t* c2 = C + ((b * 3 + 2) * 2) * N;
+    const uint64_t x1 = c2[k], x2 = c2[N + k];
+    const Lifted L = lift_q(x1, x2);
+    const unsigned __int128 c = (unsigned __int128)x1 + (unsigned __int128)c_mod[0] * L.h;
+    const unsigned __int128 mask = ((unsigned __int128)1 << logw) - 1;
+    uint64_t* w = W + b * ndig * 2 * N + k;
+    for (uint32_t j = 0; j < ndig; j++) {
+        const uint64_t dj = (uint64_t)((c >> (logw * j)) & mask);  // < 2^60
+        w[(j * 2 + 0) * N] = dj % c_mod[0];
+        w[(j * 2 + 1) * N] = dj % c_mod[1];
+    }
+}
+
+// O[b][c][l] = sum_j D_j evkw_j[c][l] (NTT domain, Shoup with the keys' companions).
+__global__ void __launch_bounds__(256) k_ks_mul_w(const uint64_t* __restrict__ W,
+                                                  const uint64_t* __restrict__ evkw_ntt, uint32_t ndig,
+                                                  uint64_t* __restrict__ O) {
+    const int k = blockIdx.x * 256 + threadIdx.x;
+    const int l = blockIdx.y;
+    const uint64_t b = blockIdx.z;
+    const uint64_t q = c_mod[l];
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        uint64_t v = 0;  // each term < 2q, at most 5 terms: < 10q < 2^58
+        for (uint32_t j = 0; j < ndig; j++) {
+            const uint64_t* e = evkw_ntt + (size_t)(((j * 2 + c) * 2 + l) * 2) * N;
+            v += shoup_lazy(W[((b * ndig + j) * 2 + l) * N + k], e[k], e[N + k], q);
+        }
+        O[((b * 2 + c) * 2 + l) * N + k] = reduce64(v, l);
+    }
+}
+
 // canonical score ciphertexts into out [npairs][2][2][N].
 cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npairs, uint64_t* X,
                             uint64_t* C, uint64_t* KS, uint64_t* out, cudaStream_t st,
-                            cudaEvent_t* ev) {
+                            cudaEvent_t* ev, const KeySwitchW* ksw) {
     uint64_t nl = 0;
     uint64_t* O = X;
     const uint64_t max_z = 65535;
@@ -362,16 +402,39 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
         nl++;
     }
     if (ev) cudaEventRecord(ev[1], st);
-    for (uint64_t off = 0; off < npairs * 4; off += chunk) {
-        const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
-        k_ntt_batch<false><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, KS + off * N, 2, 0);
-        nl++;
-    }
-    for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
-        const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
-        k_ks_mul<<<dim3(N / 256, 2, (unsigned)nb), 256, 0, st>>>(KS + b0 * 4 * N, k.evk_ntt,
-                                                                 O + b0 * 4 * N);
-        nl++;
+    if (ksw) {
+        // base-w gadget: digits after O in X, NTT, multiply-accumulate with evkw
+        uint64_t* W = X + npairs * 4 * N;
+        const uint64_t per = (uint64_t)ksw->ndig * 2;
+        for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
+            const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
+            k_digits_w<<<dim3(N / 256, 1, (unsigned)nb), 256, 0, st>>>(C + b0 * 6 * N, ksw->logw, ksw->ndig,
+                                                                       W + b0 * per * N);
+            nl++;
+        }
+        for (uint64_t off = 0; off < npairs * per; off += chunk) {
+            const uint64_t n = npairs * per - off < chunk ? npairs * per - off : chunk;
+            k_ntt_batch<false><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, W + off * N, 2, 0);
+            nl++;
+        }
+        for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
+            const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
+            k_ks_mul_w<<<dim3(N / 256, 2, (unsigned)nb), 256, 0, st>>>(W + b0 * per * N, ksw->evkw_ntt,
+                                                                       ksw->ndig, O + b0 * 4 * N);
+            nl++;
+        }
+    } else {
+        for (uint64_t off = 0; off < npairs * 4; off += chunk) {
+            const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
+            k_ntt_batch<false><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, KS + off * N, 2, 0);
+            nl++;
+        }
+        for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
+            const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
+            k_ks_mul<<<dim3(N / 256, 2, (unsigned)nb), 256, 0, st>>>(KS + b0 * 4 * N, k.evk_ntt,
+                                                                     O + b0 * 4 * N);
+            nl++;
+        }
     }
     for (uint64_t off = 0; off < npairs * 4; off += chunk) {
         const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
@@ -391,7 +454,8 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
 // Workspace per block: X [3][5][N] (reused for O [2][2][N]), C [3][2][N], KS [4][N].
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
-                          uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev, int variant) {
+                          uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev, int variant,
+                          const KeySwitchW* ksw) {
     if (nblocks == 0) return cudaSuccess;
     uint64_t* X = ws;
     uint64_t* C = X + nblocks * 15 * N;
@@ -400,7 +464,7 @@ cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* 
     cudaError_t e = launch_tensor(variant, gallery, nblocks, d, probe, X, err, st);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
-    e = launch_epilogue(tw, k, nblocks, X, C, KS, scores_ct, st, ev ? ev + 2 : nullptr);
+    e = launch_epilogue(tw, k, nblocks, X, C, KS, scores_ct, st, ev ? ev + 2 : nullptr, ksw);
     if (ev) cudaEventRecord(ev[4], st);
     return e;
 }
