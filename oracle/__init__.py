@@ -32,7 +32,8 @@ N = 4096
 Q1 = 18014398509309953
 Q2 = 18014398509293569
 Q = Q1 * Q2
-T = 4169729
+T = 4169729            # the default plaintext modulus
+T_PAPER = 1032193      # the paper's (Sec. 4.1); select with set_plain_modulus
 PURPOSE_GALLERY = 0x11  # u, e1, e2 streams at 0x11, 0x12, 0x13; obj = block * d + dim
 PURPOSE_PROBE = 0x21    # u, e1, e2 streams at 0x21, 0x22, 0x23; obj = dim
 PURPOSE_RERAND = 0x31   # output re-randomisation Enc(0): u, e1, e2 at 0x31..0x33; obj = block
@@ -96,6 +97,7 @@ def lib():
                                                        u64p, sp]
             L.orc_decrypt.argtypes = [c_int, i8p, u64p, c_int, i64p, u32p, u64p]
             L.orc_params.argtypes = [u64p]
+            L.orc_set_t.argtypes = [c_u64]
             L.orc_basew_digits.argtypes = [c_int]
             L.orc_keygen_w.argtypes = [c_int, c_u64, c_u64, c_int, u64p]
             L.orc_keyswitch_w.argtypes = [c_int, u64p, u64p, c_int, u64p]
@@ -378,3 +380,15 @@ def search_block_basew(probe_cts, gal_cts, evk, evkw, logw, n=N):
     switch: the same tensor and scale-and-round as search_block."""
     _, pre, _ = search_block(probe_cts, gal_cts, evk, n, want_pre=True)
     return keyswitch_w(pre, evkw, logw, n)
+
+
+def set_plain_modulus(t):
+    """Selects the plaintext modulus for every later call: T (default) or
+    T_PAPER.  Not for use while another thread calls the oracle."""
+    _check(lib().orc_set_t(t), "set_plain_modulus")
+
+
+def plain_modulus():
+    out = np.zeros(4, dtype=np.uint64)
+    lib().orc_params(_p(out, ctypes.c_uint64))
+    return int(out[2])

@@ -38,7 +38,11 @@ typedef __int128 i128;
 
 #define ORC_Q1 18014398509309953ULL
 #define ORC_Q2 18014398509293569ULL
-#define ORC_T 4169729ULL
+/* The plaintext modulus t: 4169729 by default, or the paper's 1032193 (Sec.
+ * 4.1) after orc_set_t; both are primes = 1 (mod 2n).  Set it before any
+ * other call, not while one runs. */
+static uint64_t g_orc_t = 4169729ULL;
+#define ORC_T g_orc_t
 #define ORC_MAXN 4096
 
 /* status codes shared with the Python wrapper */
@@ -61,6 +65,12 @@ static uint64_t mulmod64(uint64_t a, uint64_t b, uint64_t m) {
 
 /* a * b mod t for a, b < t < 2^23 (the product fits in 64 bits) */
 static uint64_t mulmod_t(uint64_t a, uint64_t b) { return (a * b) % ORC_T; }
+
+int orc_set_t(uint64_t t) {
+    if (t != 4169729ULL && t != 1032193ULL) return ORC_E_ARG;
+    g_orc_t = t;
+    return ORC_OK;
+}
 
 static uint64_t powmod64(uint64_t b, uint64_t e, uint64_t m) {
     uint64_t r = 1 % m;

@@ -127,13 +127,29 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-class Context:
-    """A library context on one CUDA device (hers_create / hers_destroy)."""
+class HersParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint32), ("q", ctypes.c_uint64 * 2), ("t", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32)]
 
-    def __init__(self, device: int = 0):
+
+T_DEFAULT = 4169729
+T_PAPER = 1032193
+
+
+class Context:
+    """A library context on one CUDA device (hers_create / hers_destroy).
+    t: the plaintext modulus, T_DEFAULT or the paper's T_PAPER."""
+
+    def __init__(self, device: int = 0, t: int = None):
         self.device = device
         h = ctypes.c_void_p()
-        rc = lib().hers_create(None, device, ctypes.byref(h))
+        params = None
+        if t is not None:
+            params = HersParams()
+            lib().hers_default_params(ctypes.byref(params))
+            params.t = t
+            params = ctypes.byref(params)
+        rc = lib().hers_create(params, device, ctypes.byref(h))
         if rc != HERS_OK:
             raise HersError(f"hers_create: {lib().hers_status_string(rc).decode()}")
         self.h = h

@@ -134,14 +134,19 @@ int hers_create(const hers_params* p, int device, hers_ctx** out) {
     *out = nullptr;
     hers_params def;
     hers_default_params(&def);
-    if (p && (p->n != def.n || p->q[0] != def.q[0] || p->q[1] != def.q[1] || p->t != def.t ||
-              p->flags != 0))
-        return HERS_E_PARAM;
+    // the plaintext modulus: the default t or the paper's (Sec. 4.1)
+    int pm = 0;
+    if (p) {
+        if (p->n != def.n || p->q[0] != def.q[0] || p->q[1] != def.q[1] || p->flags != 0) return HERS_E_PARAM;
+        if (p->t == H_MOD[MOD_T_PAPER]) pm = 1;
+        else if (p->t != def.t) return HERS_E_PARAM;
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return HERS_E_CUDA;
     hers_ctx* ctx = new (std::nothrow) hers_ctx();
     if (!ctx) return HERS_E_NOMEM;
     ctx->device = device;
+    ctx->pm = pm;
     ctx->msg[0] = 0;
     DeviceGuard g(device);
     if (!g.ok) { delete ctx; return HERS_E_CUDA; }
@@ -224,6 +229,7 @@ int hers_keygen(hers_ctx* ctx, uint64_t seed, hers_keys** out) {
     hers_keys* K = new (std::nothrow) hers_keys();
     if (!K) return fail(ctx, HERS_E_NOMEM, "hers_keygen: host allocation");
     K->ctx = ctx;
+    K->k.pm = ctx->pm;
     // sizes in words
     const size_t w_sk = N / 8, w_pk = 4 * N, w_evk = 8 * N, w_pkn = 8 * N, w_evkn = 16 * N, w_sn = 4 * N;
     const size_t total = w_sk + w_pk + w_evk + w_pkn + w_evkn + w_sn;

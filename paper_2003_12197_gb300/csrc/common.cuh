@@ -12,7 +12,8 @@
 namespace hers {
 
 // ---------------------------------------------------------------- constants
-// Modulus index i: 0 = q1, 1 = q2, 2 = p1, 3 = p2, 4 = p3, 5 = t.
+// Modulus index i: 0 = q1, 1 = q2, 2 = p1, 3 = p2, 4 = p3, 5 = the default t,
+// 6 = the paper's t.
 static __constant__ uint64_t c_mod[NUM_MODS] = HERS_MOD_INIT;
 static __constant__ uint64_t c_ninv[NUM_MODS] = HERS_NINV_INIT;
 static __constant__ uint64_t c_ninv_s[NUM_MODS] = HERS_NINV_S_INIT;
@@ -22,7 +23,6 @@ static __constant__ uint64_t c_r27[NUM_MODS] = HERS_R27_INIT;
 static __constant__ uint64_t c_r27_s[NUM_MODS] = HERS_R27_S_INIT;
 static __constant__ uint64_t c_r54[NUM_MODS] = HERS_R54_INIT;
 static __constant__ uint64_t c_r54_s[NUM_MODS] = HERS_R54_S_INIT;
-static __constant__ uint64_t c_t_s[NUM_MODS] = HERS_T_S_INIT;
 static __constant__ uint64_t c_q1_mod[NUM_RNS] = HERS_Q1_MOD_INIT;
 static __constant__ uint64_t c_q1_mod_s[NUM_RNS] = HERS_Q1_MOD_S_INIT;
 static __constant__ uint64_t c_q_mod[NUM_RNS] = HERS_Q_MOD_INIT;
@@ -33,11 +33,19 @@ static __constant__ uint64_t c_p1_mod_q_s[2] = HERS_P1_MOD_Q_S_INIT;
 static __constant__ uint64_t c_p1p2_mod_q[2] = HERS_P1P2_MOD_Q_INIT;
 static __constant__ uint64_t c_p1p2_mod_q_s[2] = HERS_P1P2_MOD_Q_S_INIT;
 static __constant__ uint64_t c_p_mod_q[2] = HERS_P_MOD_Q_INIT;
-static __constant__ uint64_t c_delta[2] = HERS_DELTA_MOD_Q_INIT;
-static __constant__ uint64_t c_delta_s[2] = HERS_DELTA_MOD_Q_S_INIT;
 static __constant__ uint64_t c_chi_cdt[CHI_LEN] = HERS_CHI_CDT_INIT;
 
-constexpr uint64_t T_PLAIN = 4169729ULL;
+// Plaintext modulus t and what depends on it; a context uses entry 0 (the
+// default t = 4169729) or entry 1 (the paper's t = 1032193), and its keys
+// carry the index (DevKeys::pm).
+struct PlainMod {
+    uint64_t t;
+    int mod;                                 // index of t in the modulus arrays
+    uint64_t q1_mod_t, q_mod_t, qinv_t;      // decryption: pt = [-r q^-1]_t
+    uint64_t t_mod[NUM_RNS], t_s[NUM_RNS];   // t mod p and its Shoup companion
+    uint64_t delta[2], delta_s[2];           // Delta = floor(q / t) mod q_l
+};
+static __constant__ PlainMod c_plain[2] = HERS_PLAIN_INIT;
 
 // Resident (search) form of ciphertexts: NTT domain over the five primes, split
 // storage, tiled so that everything one search CTA streams is contiguous:
@@ -123,7 +131,7 @@ __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, int i) {
 }
 
 // mod-t arithmetic (t < 2^23): products fit in 64 bits
-__device__ __forceinline__ uint64_t mul_mod_t(uint64_t a, uint64_t b) { return (a * b) % T_PLAIN; }
+__device__ __forceinline__ uint64_t mul_mod_t(uint64_t a, uint64_t b, uint64_t t) { return (a * b) % t; }
 
 // value of a split-stored residue (hi27 << 32 | lo27)
 __device__ __forceinline__ uint64_t split_store(uint64_t v) {

@@ -6,7 +6,10 @@ to the library, used for the exact ciphertext product and rounding of Alg 5)
 uses the next three.  The plaintext modulus t = 4169729 is the smallest prime
 = 1 (mod 2N) above 2 * 128 * 127^2, so that every score |<q, p_j>| <= d 127^2
 of a d <= 128 int8 search stays below t/2 (Sec. 3.2: the plaintext ring must
-hold the result of the computation).
+hold the result of the computation).  The paper's own t = 1032193 (Sec. 4.1),
+also = 1 (mod 2N), is the second plaintext modulus: it holds the scores of
+L2-normalised features quantised at scale 127 (|score| < 131^2 for d <= 64),
+which is the regime the paper uses it in.
 
 Roots.  For t the 2N-th root psi_t is the smallest x >= 2 with x^N = -1: it
 fixes which evaluation point psi_t^(2j+1) each plaintext slot j is.  For the
@@ -24,6 +27,7 @@ import sys
 N = 4096
 LOGN = 12
 T = 4169729
+T_PAPER = 1032193
 SIGMA = decimal.Decimal("3.2")
 CHI_BOUND = 19
 
@@ -118,13 +122,14 @@ def build():
     q1, q2, p1, p2, p3 = primes
     q = q1 * q2
     P = p1 * p2 * p3
-    mods = primes + [T]
+    mods = primes + [T, T_PAPER]
     assert is_prime(T) and T % (2 * N) == 1 and T > 2 * 128 * 127 ** 2
+    assert is_prime(T_PAPER) and T_PAPER % (2 * N) == 1
     C = []  # (name, value) scalar uint64 constants
     arrays = []  # (name, list)
 
     arrays.append(("MOD", mods))
-    psis = [first_psi(p) for p in primes] + [smallest_psi(T)]
+    psis = [first_psi(p) for p in primes] + [smallest_psi(T), smallest_psi(T_PAPER)]
     arrays.append(("PSI", psis))
     arrays.append(("NINV", [pow(N, -1, p) for p in mods]))
     arrays.append(("NINV_S", [shoup(pow(N, -1, p), p) for p in mods]))
@@ -134,7 +139,6 @@ def build():
     arrays.append(("R27_S", [shoup((1 << 27) % p, p) for p in mods]))
     arrays.append(("R54", [(1 << 54) % p for p in mods]))
     arrays.append(("R54_S", [shoup((1 << 54) % p, p) for p in mods]))
-    arrays.append(("T_S", [shoup(T % p, p) for p in mods]))           # t as a Shoup multiplier
 
     # base extension Q -> {q1, q2, p1, p2, p3} of a centred x in (-q/2, q/2)
     C.append(("Q1INV_Q2", pow(q1, -1, q2)))
@@ -167,15 +171,20 @@ def build():
     arrays.append(("P1P2_MOD_Q_S", [shoup((p1 * p2) % x, x) for x in (q1, q2)]))
     arrays.append(("P_MOD_Q", [P % x for x in (q1, q2)]))
 
-    # encryption: Delta = floor(q / t)
-    delta = q // T
-    arrays.append(("DELTA_MOD_Q", [delta % x for x in (q1, q2)]))
-    arrays.append(("DELTA_MOD_Q_S", [shoup(delta % x, x) for x in (q1, q2)]))
-
-    # decryption: pt = [-r q^-1]_t with r = [t v]_q centred
-    C.append(("Q1_MOD_T", q1 % T))
-    C.append(("Q_MOD_T", q % T))
-    C.append(("QINV_T", pow(q % T, -1, T)))
+    # per plaintext modulus: {t, modulus index, q1 mod t, q mod t, q^-1 mod t
+    # (decryption: pt = [-r q^-1]_t with r = [t v]_q centred), t mod p and its
+    # Shoup companion for the five RNS primes (t x in scale-and-round and
+    # decryption), Delta = floor(q / t) mod q_l and companions (encryption)}
+    plains = []
+    for idx, t in ((5, T), (6, T_PAPER)):
+        delta = q // t
+        plains.append("{ %dULL, %d, %dULL, %dULL, %dULL, { %s }, { %s }, { %s }, { %s } }" % (
+            t, idx, q1 % t, q % t, pow(q % t, -1, t),
+            ", ".join(f"{t % p}ULL" for p in primes),
+            ", ".join(f"{shoup(t % p, p)}ULL" for p in primes),
+            ", ".join(f"{delta % x}ULL" for x in (q1, q2)),
+            ", ".join(f"{shoup(delta % x, x)}ULL" for x in (q1, q2))))
+    arrays.append(("PLAIN", plains))
 
     # sanity of the ranges the kernels rely on
     assert q1 > q2 > p1 > p2 > p3 and q1 < 2 * p3
@@ -196,8 +205,9 @@ def header():
          f"constexpr int N = {N};",
          f"constexpr int LOGN = {LOGN};",
          "constexpr int NUM_RNS = 5;     /* q1, q2, p1, p2, p3 */",
-         "constexpr int MOD_T = 5;       /* index of t in the modulus arrays */",
-         "constexpr int NUM_MODS = 6;",
+         "constexpr int MOD_T = 5;       /* index of the default t in the modulus arrays */",
+         "constexpr int MOD_T_PAPER = 6; /* index of the paper's t */",
+         "constexpr int NUM_MODS = 7;",
          "constexpr int CHI_MIN = -19;",
          "constexpr int CHI_LEN = 38;",
          ""]
@@ -205,7 +215,7 @@ def header():
         o.append(f"constexpr uint64_t {name} = {v}ULL;")
     o.append("")
     for name, vals in arrays:
-        body = ", ".join(f"{v}ULL" for v in vals)
+        body = ", ".join(v if isinstance(v, str) else f"{v}ULL" for v in vals)
         o.append(f"#define HERS_{name}_INIT {{ {body} }}")
     o.append("#define HERS_CHI_CDT_INIT { " + ", ".join(f"{v}ULL" for v in cdt) + " }")
     o += ["}  // namespace hers", ""]

@@ -17,6 +17,7 @@ struct hers_ctx {
     std::vector<cudaEvent_t> tev;
     uint32_t tcap = 0, tn = 0;
     int tensor_variant = 1;  // tensor-kernel shape used by searches on this context
+    int pm = 0;              // plaintext modulus: 0 the default t, 1 the paper's t
 };
 
 namespace hers {
@@ -29,6 +30,7 @@ namespace hers {
 //   evk_ntt   [2 j][2 polys][2 limbs][2][N] NTT form + Shoup (key switch)
 //   s_ntt     [2 limbs][2][N]           NTT form of s + Shoup (decryption)
 struct DevKeys {
+    int pm;  // plaintext modulus of the context: index into c_plain (0 default t, 1 the paper's t)
     int8_t* sk;
     uint64_t* pk;
     uint64_t* evk;

@@ -182,8 +182,9 @@ __global__ void __launch_bounds__(NTT_THREADS, 2) k_encrypt(const uint64_t* __re
                                                          const uint64_t* __restrict__ pk_ntt,
                                                          const int8_t* __restrict__ feats,
                                                          uint64_t m, uint32_t d, uint64_t ct_begin,
-                                                         int mode, uint64_t seed,
+                                                         int mode, uint64_t seed, int pm,
                                                          uint64_t* __restrict__ out, int* err) {
+    const PlainMod& P = c_plain[pm];
     extern __shared__ uint64_t sm[];
     uint64_t* U = sm;
     uint64_t* B = sm + N;
@@ -205,20 +206,20 @@ __global__ void __launch_bounds__(NTT_THREADS, 2) k_encrypt(const uint64_t* __re
         const int v = feats[c];
         const uint32_t slot = (uint32_t)(m % N);
         for (int s = threadIdx.x; s < N; s += blockDim.x)
-            M[swz(brev12(s))] = s == (int)slot ? (v < 0 ? T_PLAIN - (uint64_t)(-v) : (uint64_t)v) : 0;
-        ntt_inv_call(M, tw, MOD_T);
+            M[swz(brev12(s))] = s == (int)slot ? (v < 0 ? P.t - (uint64_t)(-v) : (uint64_t)v) : 0;
+        ntt_inv_call(M, tw, P.mod);
     } else if (mode == ENC_PROBE) {
         const int v = feats[c];
-        const uint64_t mv = v < 0 ? T_PLAIN - (uint64_t)(-v) : (uint64_t)v;
+        const uint64_t mv = v < 0 ? P.t - (uint64_t)(-v) : (uint64_t)v;
         for (int k = threadIdx.x; k < N; k += blockDim.x) M[swz(k)] = k == 0 ? mv : 0;
     } else {
         const uint64_t b = c / d, i = c % d;
         for (int s = threadIdx.x; s < N; s += blockDim.x) {
             const uint64_t e = b * N + (uint64_t)s;
             const int v = e < m ? feats[e * d + i] : 0;
-            M[swz(brev12(s))] = v < 0 ? T_PLAIN - (uint64_t)(-v) : (uint64_t)v;
+            M[swz(brev12(s))] = v < 0 ? P.t - (uint64_t)(-v) : (uint64_t)v;
         }
-        ntt_inv_call(M, tw, MOD_T);
+        ntt_inv_call(M, tw, P.mod);
     }
 
     // u, NTT, products with the public key
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 2) k_encrypt(const uint64_t* __re
             const int k = 8 * cb + j;
             const int e1 = chi_from_word(((uint64_t)blk[2 * j + 1] << 32) | blk[2 * j]);
             const int x = swz(k);
-            uint64_t v0 = add_mod(U[x], shoup(M[x], c_delta[limb], c_delta_s[limb], p), p);
+            uint64_t v0 = add_mod(U[x], shoup(M[x], P.delta[limb], P.delta_s[limb], p), p);
             o0[k] = e1 < 0 ? sub_mod(v0, (uint64_t)(-e1), p) : add_mod(v0, (uint64_t)e1, p);
         }
         chacha20(seed, base + 2, obj, (uint32_t)cb, blk);
@@ -270,7 +271,7 @@ cudaError_t launch_encrypt(const uint64_t* tw, const DevKeys& k, const int8_t* f
     for (uint64_t off = 0; off < nct; off += chunk) {
         const uint64_t n = nct - off < chunk ? nct - off : chunk;
         k_encrypt<<<dim3((unsigned)n, 2), NTT_THREADS, smem, st>>>(
-            tw, k.pk_ntt, feats, m, d, ct_begin + off, mode, seed, out_ct + off * 4 * N, err);
+            tw, k.pk_ntt, feats, m, d, ct_begin + off, mode, seed, k.pm, out_ct + off * 4 * N, err);
         count_launches(1);
     }
     return cudaGetLastError();
@@ -373,8 +374,10 @@ cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t n
 __global__ void __launch_bounds__(NTT_THREADS, 2) k_decrypt(const uint64_t* __restrict__ tw,
                                                          const uint64_t* __restrict__ s_ntt,
                                                          const uint64_t* __restrict__ cts,
-                                                         int32_t* __restrict__ scores, uint64_t m) {
+                                                         int32_t* __restrict__ scores, uint64_t m, int pm) {
     extern __shared__ uint64_t sm[];
+    const PlainMod& P = c_plain[pm];
+    const uint64_t t = P.t;
     uint64_t* V0 = sm;
     uint64_t* V1 = sm + N;
     uint64_t* PT = sm + 2 * N;
@@ -392,19 +395,19 @@ __global__ void __launch_bounds__(NTT_THREADS, 2) k_decrypt(const uint64_t* __re
     }
     __syncthreads();
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const uint64_t a1 = shoup(V0[swz(k)], T_PLAIN, c_t_s[0], c_mod[0]);
-        const uint64_t a2 = shoup(V1[swz(k)], T_PLAIN, c_t_s[1], c_mod[1]);
+        const uint64_t a1 = shoup(V0[swz(k)], P.t_mod[0], P.t_s[0], c_mod[0]);
+        const uint64_t a2 = shoup(V1[swz(k)], P.t_mod[1], P.t_s[1], c_mod[1]);
         const Lifted L = lift_q(a1, a2);
-        uint64_t r = (a1 % T_PLAIN + mul_mod_t(Q1_MOD_T, L.h % T_PLAIN)) % T_PLAIN;
-        if (L.neg) r = (r + T_PLAIN - Q_MOD_T) % T_PLAIN;
-        PT[swz(k)] = mul_mod_t((T_PLAIN - r) % T_PLAIN, QINV_T);
+        uint64_t r = (a1 % t + mul_mod_t(P.q1_mod_t, L.h % t, t)) % t;
+        if (L.neg) r = (r + t - P.q_mod_t) % t;
+        PT[swz(k)] = mul_mod_t((t - r) % t, P.qinv_t, t);
     }
-    ntt_fwd_call(PT, tw, MOD_T);
+    ntt_fwd_call(PT, tw, P.mod);
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
         const uint64_t e = b * N + (uint64_t)brev12(j);
         if (e < m) {
             const uint64_t v = PT[swz(j)];
-            scores[e] = v > (T_PLAIN - 1) / 2 ? (int32_t)((int64_t)v - (int64_t)T_PLAIN) : (int32_t)v;
+            scores[e] = v > (t - 1) / 2 ? (int32_t)((int64_t)v - (int64_t)t) : (int32_t)v;
         }
     }
 }
@@ -418,7 +421,7 @@ cudaError_t launch_decrypt(const uint64_t* tw, const DevKeys& k, const uint64_t*
     for (uint64_t off = 0; off < nblocks; off += chunk) {
         const uint64_t n = nblocks - off < chunk ? nblocks - off : chunk;
         k_decrypt<<<(unsigned)n, NTT_THREADS, smem, st>>>(tw, k.s_ntt, scores_ct + off * 4 * N,
-                                                          scores + off * N, m > off * N ? m - off * N : 0);
+                                                          scores + off * N, m > off * N ? m - off * N : 0, k.pm);
         count_launches(1);
     }
     return cudaGetLastError();

@@ -258,7 +258,8 @@ __global__ void __launch_bounds__(NTT_THREADS, 3) k_ntt_batch(const uint64_t* __
 // KS[b][0] = D_1 mod q1, [1] = D_1 mod q2, [2] = D_2 mod q1, [3] = D_2 mod q2.
 __global__ void __launch_bounds__(256) k_scale_round(const uint64_t* __restrict__ X,
                                                      uint64_t* __restrict__ C,
-                                                     uint64_t* __restrict__ KS) {
+                                                     uint64_t* __restrict__ KS, int pm) {
+    const PlainMod& P = c_plain[pm];
     const int k = blockIdx.x * 256 + threadIdx.x;
     const int c = blockIdx.y;
     const uint64_t b = blockIdx.z;
@@ -267,8 +268,8 @@ __global__ void __launch_bounds__(256) k_scale_round(const uint64_t* __restrict_
     const uint64_t q1 = c_mod[0], q2 = c_mod[1];
 
     // r = [t X]_q
-    const uint64_t a1 = shoup(x0, T_PLAIN, c_t_s[0], q1);
-    const uint64_t a2 = shoup(x1, T_PLAIN, c_t_s[1], q2);
+    const uint64_t a1 = shoup(x0, P.t_mod[0], P.t_s[0], q1);
+    const uint64_t a2 = shoup(x1, P.t_mod[1], P.t_s[1], q2);
     const Lifted R = lift_q(a1, a2);
     uint64_t y[3];
 #pragma unroll
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(256) k_scale_round(const uint64_t* __restrict_
         const uint64_t p = c_mod[mi];
         const uint64_t xi = i == 0 ? x2 : (i == 1 ? x3 : x4);
         const uint64_t rm = lifted_mod(R, mi, a2);
-        const uint64_t tx = shoup(xi, T_PLAIN, c_t_s[mi], p);
+        const uint64_t tx = shoup(xi, P.t_mod[mi], P.t_s[mi], p);
         y[i] = shoup(sub_mod(tx, rm, p), c_qinv_p[i], c_qinv_p_s[i], p);
     }
     // mixed radix Y = y1 + p1 z2 + p1 p2 z3
@@ -398,7 +399,7 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
     for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
         const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
         k_scale_round<<<dim3(N / 256, 3, (unsigned)nb), 256, 0, st>>>(X + b0 * 15 * N, C + b0 * 6 * N,
-                                                                     KS + b0 * 4 * N);
+                                                                     KS + b0 * 4 * N, k.pm);
         nl++;
     }
     if (ev) cudaEventRecord(ev[1], st);

@@ -60,7 +60,7 @@ def test_status_strings_and_param_check(libhers):
     assert libhers.hers_default_params(ctypes.byref(p)) == 0
     assert p.n == 4096 and p.t == 4169729
     assert p.q[0] == 18014398509309953 and p.q[1] == 18014398509293569
-    p.t = 1032193  # the paper's t: not supported by this build (see the reading of t)
+    p.t = 65537    # a prime t that is not = 1 (mod 2N): no plaintext NTT, not supported
     h = ctypes.c_void_p()
     assert libhers.hers_create(ctypes.byref(p), 0, ctypes.byref(h)) == -5
     assert libhers.hers_keygen(None, 1, ctypes.byref(h)) == -1

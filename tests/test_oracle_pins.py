@@ -563,3 +563,36 @@ def test_basew_keys_and_key_switch_identity():
         for k, v in enumerate(mul(Dj, errs[j])):
             want[k] -= v
     assert diff == want
+
+
+def test_paper_plain_modulus_t1032193():
+    """The paper's t = 1,032,193 (Sec. 4.1), selected at run time: psi_t by
+    brute force, the encode/decode round trip and the slot-wise product, and a
+    full block whose decrypted scores equal the plaintext inner products
+    (L2-normalised int8 features keep |score| < 131^2 < t/2)."""
+    tp = O.T_PAPER
+    assert tp % (2 * 4096) == 1 and all(tp % p for p in range(2, 1016))
+    O.set_plain_modulus(tp)
+    try:
+        assert O.plain_modulus() == tp
+        psi = O.psi_t()
+        assert pow(psi, 4096, tp) == tp - 1
+        assert all(pow(x, 4096, tp) != tp - 1 for x in range(2, psi))
+        rng = np.random.default_rng(9)
+        slots = rng.integers(-(tp - 1) // 2, (tp - 1) // 2 + 1, 4096)
+        assert np.array_equal(O.decode(O.encode(slots)), slots)
+        sk, pk, evk = O.keygen(4242)
+        m, d = 4096, 64
+        feats = W.gallery_features(m, d, 4343)
+        mate = int(W.mate_indices(m, 1, 4444)[0])
+        q = W.probe_for_mate(mate, d, 4343, 4545)
+        plain = W.plain_inner_products(feats, q)
+        assert np.abs(plain).max() < 131 ** 2 < tp // 2
+        osc, st = O.search_block(O.encrypt_probe(pk, q, 4646), O.encrypt_gallery_block(pk, feats, 0, 4747), evk)
+        slots_out, _, noise = O.decrypt(sk, osc)
+        assert np.array_equal(slots_out, plain)
+        assert int(np.argmax(slots_out)) == mate
+        assert noise < O.Q // (2 * tp) >> 16
+    finally:
+        O.set_plain_modulus(O.T)
+    assert O.plain_modulus() == O.T
