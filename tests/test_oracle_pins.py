@@ -430,9 +430,10 @@ def test_paper_parameter_facts():
     tp = facts["paper_t"]["value"]
     assert tp % (2 * facts["paper_n"]["value"]) == 1
     assert all(tp % p for p in range(2, int(tp ** 0.5) + 1))
-    # why the paper's t is not used: 2 d 127^2 exceeds it for d >= 32 (int8 features)
-    assert 2 * 32 * 127 ** 2 > tp
-    # this build's t covers |score| <= d 127^2 < t/2 for d <= 128
+    # the paper's t cannot hold every score of arbitrary int8 vectors (2 d 127^2 > t
+    # for d >= 32), only those of L2-normalised features (|score| < 131^2 < t/2)
+    assert 2 * 32 * 127 ** 2 > tp and 131 ** 2 < tp // 2
+    # the default t holds |score| <= d 127^2 < t/2 for any int8 vectors, d <= 128
     assert 128 * 127 ** 2 < T // 2
     # gallery sizes: 100M entries, d = 64, two 64-bit limbs per coefficient
     blocks = -(-100_000_000 // 4096)
