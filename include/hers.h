@@ -8,7 +8,8 @@
  *
  * Scheme: FV (App. A, Algs 1-5) over R_q = Z_q[x]/(x^N + 1), N = 4096,
  * q = q1 q2 (two 54-bit NTT primes, 108 bits), plaintext modulus t = 4169729
- * (prime, t = 1 mod 2N, so plaintexts have N SIMD slots).  Gallery dimension
+ * by default or the paper's t = 1032193 (Sec. 4.1) as a context option (both
+ * prime, t = 1 mod 2N, so plaintexts have N SIMD slots).  Gallery dimension
  * i of entries bN .. bN+N-1 is one plaintext (Eq. 3, one "block" b); probe
  * dimension i fills every slot (Eq. 2).  A block's score ciphertext is
  * sum_i ct_i (x) D_i^b (Eq. 4, Alg 7), with the degree-2 tensor accumulated
@@ -59,8 +60,11 @@ extern "C" {
 typedef struct hers_ctx hers_ctx;
 typedef struct hers_keys hers_keys;
 
-/* Scheme parameters (App. A; Sec. 4.1 fixes n, the rest is this library's
- * reading).  Only the default set is supported; hers_create() checks. */
+/* Scheme parameters (App. A; Sec. 4.1 fixes n and the paper's t, the rest is
+ * this library's reading).  n and q must be the defaults; t is 4169729 (the
+ * default: it holds every score of any int8 vectors, |score| <= d 127^2 < t/2
+ * for d <= 128) or 1032193 (the paper's: it holds the scores of L2-normalised
+ * int8 features, |score| < 131^2).  hers_create() checks. */
 typedef struct hers_params {
     uint32_t n;       /* ring degree, 4096 */
     uint64_t q[2];    /* ciphertext modulus primes q1, q2 */
@@ -68,12 +72,14 @@ typedef struct hers_params {
     uint32_t flags;   /* reserved, 0 */
 } hers_params;
 
-/* Fills *out with the supported parameter set. */
+/* Fills *out with the default parameter set. */
 int hers_default_params(hers_params* out);
 
-/* Creates a context on CUDA device `device`: uploads NTT twiddle tables and
- * creates the context stream.  *out is owned by the caller, freed by
- * hers_destroy. */
+/* Creates a context on CUDA device `device` with parameters p (NULL: the
+ * defaults): uploads NTT twiddle tables and creates the context stream.  Keys
+ * made on the context, and every call with them, use its plaintext modulus.
+ * *out is owned by the caller, freed by hers_destroy.  HERS_E_PARAM for an
+ * unsupported parameter set. */
 int hers_create(const hers_params* p, int device, hers_ctx** out);
 int hers_destroy(hers_ctx* ctx);
 
