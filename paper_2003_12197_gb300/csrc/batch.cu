@@ -26,7 +26,7 @@
 namespace hers {
 
 constexpr uint32_t UNIT_STOP = 0xFFFFFFFFu;
-constexpr int BKCHUNK = 32;  // fold period in dimensions (see k_tensor)
+constexpr int BKCHUNK = 64;  // fold period in dimensions (see k_tensor)
 
 // Stage descriptor flags (written by the producer with each stage).
 constexpr uint32_t F_FIRST = 1;  // first stage of a unit: sums start at zero
@@ -34,8 +34,8 @@ constexpr uint32_t F_FOLD = 2;   // fold the 64-bit sums mod p after this stage
 constexpr uint32_t F_LAST = 4;   // last stage of a unit: store the unit's results
 constexpr uint32_t F_STOP = 8;   // no more units: the consumers leave
 
-__device__ __forceinline__ void madw_b(uint64_t& acc, uint32_t a, uint32_t b) {
-    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+__device__ __forceinline__ void madw_b(int64_t& acc, int32_t a, int32_t b) {
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
 // A unit's table entries, held in registers by the producer.
@@ -70,34 +70,34 @@ __device__ __forceinline__ void load_unit(UnitRegs<NP>& r, const BatchChunk* __r
 // block j < nb, the 9 digit products of (probe row q) x (gallery row j).  With
 // FULL (nd = DPS, np = NP, nb = NB) the loops carry no predicates.
 template <int NP, int NB, int DPS, bool FULL>
-__device__ __forceinline__ void stage_products(uint64_t (&s)[NP][NB][9], const uint64_t* base, uint32_t nd,
+__device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][9], const uint64_t* base, uint32_t nd,
                                                uint32_t np, uint32_t nbu) {
     constexpr int RUN = DPS * 2 * TILE;
 #pragma unroll
     for (int dd = 0; dd < DPS; dd++) {
         if (FULL || (uint32_t)dd < nd) {
-            uint32_t a0l[NP], a0h[NP], a1l[NP], a1h[NP];
+            int32_t a0l[NP], a0h[NP], a1l[NP], a1h[NP];  // signed digits (split_store)
 #pragma unroll
             for (int q = 0; q < NP; q++) {
                 const uint64_t A0 = base[q * RUN + dd * 2 * TILE], A1 = base[q * RUN + dd * 2 * TILE + TILE];
-                a0l[q] = (uint32_t)A0;
-                a0h[q] = (uint32_t)(A0 >> 32);
-                a1l[q] = (uint32_t)A1;
-                a1h[q] = (uint32_t)(A1 >> 32);
+                a0l[q] = (int32_t)(uint32_t)A0;
+                a0h[q] = (int32_t)(uint32_t)(A0 >> 32);
+                a1l[q] = (int32_t)(uint32_t)A1;
+                a1h[q] = (int32_t)(uint32_t)(A1 >> 32);
             }
 #pragma unroll
             for (int j = 0; j < NB; j++) {
                 if (FULL || (uint32_t)j < nbu) {
                     const uint64_t* gp = base + (NP + j) * RUN + dd * 2 * TILE;
                     const uint64_t B0 = gp[0], B1 = gp[TILE];
-                    const uint32_t b0l = (uint32_t)B0, b0h = (uint32_t)(B0 >> 32);
-                    const uint32_t b1l = (uint32_t)B1, b1h = (uint32_t)(B1 >> 32);
-                    const uint32_t b0s = b0l + b0h, b1s = b1l + b1h;
-                    const uint32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
+                    const int32_t b0l = (int32_t)(uint32_t)B0, b0h = (int32_t)(uint32_t)(B0 >> 32);
+                    const int32_t b1l = (int32_t)(uint32_t)B1, b1h = (int32_t)(uint32_t)(B1 >> 32);
+                    const int32_t b0s = b0l + b0h, b1s = b1l + b1h;
+                    const int32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
 #pragma unroll
                     for (int q = 0; q < NP; q++) {
                         if (FULL || (uint32_t)q < np) {
-                            const uint32_t sal = a0l[q] + a1l[q], sah = a0h[q] + a1h[q];
+                            const int32_t sal = a0l[q] + a1l[q], sah = a0h[q] + a1h[q];
                             madw_b(s[q][j][0], a0l[q], b0l);
                             madw_b(s[q][j][1], a0h[q], b0h);
                             madw_b(s[q][j][2], a0l[q] + a0h[q], b0s);
@@ -115,11 +115,12 @@ __device__ __forceinline__ void stage_products(uint64_t (&s)[NP][NB][9], const u
     }
 }
 
-// Folds the three digit sums of one component, value = LL + (MM - HH - LL) 2^27
-// + HH 2^54, to a residue mod p_l in [0, p).
-__device__ __forceinline__ uint64_t fold3(uint64_t LL, uint64_t HH, uint64_t MM, int l, uint64_t p) {
-    return reduce64(shoup_lazy(LL, 1, c_one_s[l], p) + shoup_lazy(MM - HH - LL, c_r27[l], c_r27_s[l], p) +
-                        shoup_lazy(HH, c_r54[l], c_r54_s[l], p),
+// Folds the three signed digit sums of one component, value = LL + (MM - HH -
+// LL) 2^27 + HH 2^54, to a residue mod p_l in [0, p).
+__device__ __forceinline__ uint64_t fold3(int64_t LL, int64_t HH, int64_t MM, int l, uint64_t p) {
+    return reduce64(shoup_lazy(signed_to_unsigned(LL, l), 1, c_one_s[l], p) +
+                        shoup_lazy(signed_to_unsigned(MM - HH - LL, l), c_r27[l], c_r27_s[l], p) +
+                        shoup_lazy(signed_to_unsigned(HH, l), c_r54[l], c_r54_s[l], p),
                     l);
 }
 
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
 
     // consumers
     const int t = threadIdx.x;
-    uint64_t s[NP][NB][9];
+    int64_t s[NP][NB][9];
     uint64_t f[NP][NB][3];  // FREG only
     for (uint32_t g = 0;; g++) {
         const int st = (int)(g % STAGES);

@@ -19,6 +19,7 @@ static __constant__ uint64_t c_ninv[NUM_MODS] = HERS_NINV_INIT;
 static __constant__ uint64_t c_ninv_s[NUM_MODS] = HERS_NINV_S_INIT;
 static __constant__ uint64_t c_one_s[NUM_MODS] = HERS_ONE_S_INIT;
 static __constant__ uint64_t c_barrett[NUM_RNS] = HERS_BARRETT_INIT;
+static __constant__ uint64_t c_off63[NUM_RNS] = HERS_OFF63_INIT;
 static __constant__ uint64_t c_r27[NUM_MODS] = HERS_R27_INIT;
 static __constant__ uint64_t c_r27_s[NUM_MODS] = HERS_R27_S_INIT;
 static __constant__ uint64_t c_r54[NUM_MODS] = HERS_R54_INIT;
@@ -133,13 +134,24 @@ __device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, int i) {
 // mod-t arithmetic (t < 2^23): products fit in 64 bits
 __device__ __forceinline__ uint64_t mul_mod_t(uint64_t a, uint64_t b, uint64_t t) { return (a * b) % t; }
 
-// value of a split-stored residue (hi27 << 32 | lo27)
-__device__ __forceinline__ uint64_t split_store(uint64_t v) {
-    return ((v >> 27) << 32) | (v & MASK27);
+// Split storage of a residue v in [0, p), p < 2^54, for the tensor product:
+// the centred value c (|c| <= (p-1)/2 < 2^53) as two signed 27-bit digits,
+// c = hi 2^27 + lo with lo in [-2^26, 2^26) and |hi| <= 2^26, stored as the
+// 32-bit words (hi, lo).  Every digit sum the Karatsuba products use then
+// stays below 2^28 in magnitude and every partial product below 2^56.
+__device__ __forceinline__ uint64_t split_store(uint64_t v, uint64_t p) {
+    const int64_t c = v > (p - 1) / 2 ? (int64_t)v - (int64_t)p : (int64_t)v;
+    const int64_t lo = ((c + (1 << 26)) & (int64_t)MASK27) - (1 << 26);
+    const int64_t hi = (c - lo) >> 27;  // exact
+    return ((uint64_t)(uint32_t)(int32_t)hi << 32) | (uint32_t)(int32_t)lo;
 }
-__device__ __forceinline__ uint64_t split_load(uint64_t s) {
-    return ((s >> 32) << 27) | (s & 0xFFFFFFFFull);
+__device__ __forceinline__ uint64_t split_load(uint64_t s, uint64_t p) {
+    const int64_t c = (int64_t)(int32_t)(uint32_t)(s >> 32) * (1 << 27) + (int64_t)(int32_t)(uint32_t)s;
+    return c < 0 ? (uint64_t)(c + (int64_t)p) : (uint64_t)c;
 }
+// Residue mod p_l of a signed 64-bit sum x with |x| < 2^63 - p: adding
+// c_off63[l] (a multiple of p_l just below 2^63) makes it non-negative.
+__device__ __forceinline__ uint64_t signed_to_unsigned(int64_t x, int l) { return (uint64_t)x + c_off63[l]; }
 
 __device__ __forceinline__ int brev12(int x) { return (int)(__brev((unsigned)x) >> (32 - LOGN)); }
 

@@ -135,6 +135,7 @@ def build():
     arrays.append(("NINV_S", [shoup(pow(N, -1, p), p) for p in mods]))
     arrays.append(("ONE_S", [shoup(1, p) for p in mods]))              # floor(2^64 / p)
     arrays.append(("BARRETT", [(1 << 108) // p for p in primes]))     # floor(2^108 / p)
+    arrays.append(("OFF63", [p * ((1 << 63) // p) for p in primes]))  # multiple of p just below 2^63
     arrays.append(("R27", [(1 << 27) % p for p in mods]))
     arrays.append(("R27_S", [shoup((1 << 27) % p, p) for p in mods]))
     arrays.append(("R54", [(1 << 54) % p for p in mods]))

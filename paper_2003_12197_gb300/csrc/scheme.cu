@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 3) k_resident_to_canonical_add(
     const uint32_t i = blockIdx.x >> 1;
     const int poly = (int)(blockIdx.x & 1), limb = blockIdx.y;
     for (int k = threadIdx.x; k < N; k += blockDim.x)
-        sm[swz(k)] = split_load(resident[resident_offset(b, limb, k, d, i, poly)]);
+        sm[swz(k)] = split_load(resident[resident_offset(b, limb, k, d, i, poly)], c_mod[limb]);
     ntt_inv_mod(sm, tw, limb);
     const uint64_t q = c_mod[limb];
     const size_t row = (((size_t)i * 2 + poly) * 2 + limb) * N;
@@ -327,7 +327,7 @@ cudaError_t launch_resident_to_canonical_add(const uint64_t* tw, const uint64_t*
 // Grid (2 n polys, 5 limbs).  Reads a canonical ciphertext polynomial
 // (residues mod q1, q2), takes its centred representative x in (-q/2, q/2]
 // (App. A) and writes NTT_{p_l}(x mod p_l) for l = 0..4 in split storage
-// (high 27 bits << 32 | low 27 bits) at the resident (tiled) position of
+// (signed 27-bit digits, see split_store) at the resident (tiled) position of
 // ciphertext ct_begin + P/2 = b d + i.  Exactness of the later tensor product
 // needs the centred lift: the product of two such polynomials over Z, summed
 // over d <= 512 dimensions, stays below q P / 2 (|X| < 2^237).
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 3) k_extend_ntt(const uint64_t* _
     const uint32_t i = (uint32_t)(c % d);
     const int poly = (int)(P & 1);
     for (int k = threadIdx.x; k < N; k += blockDim.x)
-        out[resident_offset(blk, limb, k, d, i, poly)] = split_store(sm[swz(k)]);
+        out[resident_offset(blk, limb, k, d, i, poly)] = split_store(sm[swz(k)], c_mod[limb]);
 }
 
 cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t ct_begin,

@@ -27,17 +27,28 @@ namespace hers {
 // STAGES-deep shared-memory ring; "full" mbarriers track the copies and
 // "empty" mbarriers (one arrival per consumer warp) hand stages back.
 //
-// Arithmetic: operands are split-stored 27-bit digits, x = xh 2^27 + xl, and
+// Arithmetic: operands are split-stored signed 27-bit digits of the centred
+// residue, x = xh 2^27 + xl with |xh|, |xl| <= 2^26 (split_store), and
 //   x y = xh yh 2^54 + ((xh+xl)(yh+yl) - xh yh - xl yl) 2^27 + xl yl,
 //   T1 = (a0+a1)(b0+b1) - T0 - T2,
-// so each (dimension, coefficient, limb, block) costs 9 32x32->64 multiply-adds
-// (mad.wide.u32) into 64-bit sums without reduction.  The largest partial
-// product is (2^29)^2 = 2^58, so the sums are folded mod p every KCHUNK = 32
-// dimensions.  A wait that runs out (WAIT_NS, 2 s) sets bit 2 of *err.
-constexpr int KCHUNK = 32;
+// so each (dimension, coefficient, limb, block) costs 9 32x32->64 signed
+// multiply-adds (mad.wide.s32) into 64-bit sums without reduction.  The
+// largest partial product is (2^28)^2 = 2^56, so 64 dimensions sum to at most
+// 2^62 and the sums are folded mod p every KCHUNK = 64 dimensions.  A wait
+// that runs out (WAIT_NS, 2 s) sets bit 2 of *err.
+constexpr int KCHUNK = 64;
 
-__device__ __forceinline__ void madw(uint64_t& acc, uint32_t a, uint32_t b) {
-    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+__device__ __forceinline__ void madw(int64_t& acc, int32_t a, int32_t b) {
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+// Residue mod p_l of the digit sums of one component:
+// value = LL + (MM - HH - LL) 2^27 + HH 2^54, each term a signed 64-bit sum.
+__device__ __forceinline__ uint64_t fold_signed(int64_t LL, int64_t HH, int64_t MM, int l, uint64_t p) {
+    return reduce64(shoup_lazy(signed_to_unsigned(LL, l), 1, c_one_s[l], p) +
+                        shoup_lazy(signed_to_unsigned(MM - HH - LL, l), c_r27[l], c_r27_s[l], p) +
+                        shoup_lazy(signed_to_unsigned(HH, l), c_r54[l], c_r54_s[l], p),
+                    l);
 }
 
 // GORDER: block groups vary fastest over the grid (x = group, y = (limb,
@@ -106,7 +117,7 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
     uint64_t fold[NB][3];
 #pragma unroll
     for (int j = 0; j < NB; j++) fold[j][0] = fold[j][1] = fold[j][2] = 0;
-    uint64_t s[NB][9];  // per block: LL0 HH0 MM0 | LL2 HH2 MM2 | LLk HHk MMk
+    int64_t s[NB][9];  // per block: LL0 HH0 MM0 | LL2 HH2 MM2 | LLk HHk MMk
 #pragma unroll
     for (int j = 0; j < NB; j++)
 #pragma unroll
@@ -123,19 +134,19 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
         for (int dd = 0; dd < DPS; dd++) {
             if ((uint32_t)dd < nd) {
                 const uint64_t A0 = base[dd * 2 * TILE], A1 = base[dd * 2 * TILE + TILE];
-                const uint32_t a0l = (uint32_t)A0, a0h = (uint32_t)(A0 >> 32);
-                const uint32_t a1l = (uint32_t)A1, a1h = (uint32_t)(A1 >> 32);
-                const uint32_t a0s = a0l + a0h, a1s = a1l + a1h;
-                const uint32_t sal = a0l + a1l, sah = a0h + a1h, sas = sal + sah;
+                const int32_t a0l = (int32_t)(uint32_t)A0, a0h = (int32_t)(uint32_t)(A0 >> 32);
+                const int32_t a1l = (int32_t)(uint32_t)A1, a1h = (int32_t)(uint32_t)(A1 >> 32);
+                const int32_t a0s = a0l + a0h, a1s = a1l + a1h;
+                const int32_t sal = a0l + a1l, sah = a0h + a1h, sas = sal + sah;
 #pragma unroll
                 for (int j = 0; j < NB; j++) {
                     if (j < nb) {
                         const uint64_t* g = base + (1 + j) * RUN + dd * 2 * TILE;
                         const uint64_t B0 = g[0], B1 = g[TILE];
-                        const uint32_t b0l = (uint32_t)B0, b0h = (uint32_t)(B0 >> 32);
-                        const uint32_t b1l = (uint32_t)B1, b1h = (uint32_t)(B1 >> 32);
-                        const uint32_t b0s = b0l + b0h, b1s = b1l + b1h;
-                        const uint32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
+                        const int32_t b0l = (int32_t)(uint32_t)B0, b0h = (int32_t)(uint32_t)(B0 >> 32);
+                        const int32_t b1l = (int32_t)(uint32_t)B1, b1h = (int32_t)(uint32_t)(B1 >> 32);
+                        const int32_t b0s = b0l + b0h, b1s = b1l + b1h;
+                        const int32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
                         madw(s[j][0], a0l, b0l);
                         madw(s[j][1], a0h, b0h);
                         madw(s[j][2], a0s, b0s);
@@ -159,11 +170,7 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
                 uint64_t v[3];
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    const uint64_t LL = s[j][3 * c], HH = s[j][3 * c + 1], MM = s[j][3 * c + 2];
-                    v[c] = reduce64(shoup_lazy(LL, 1, c_one_s[l], p) +
-                                        shoup_lazy(MM - HH - LL, c_r27[l], c_r27_s[l], p) +
-                                        shoup_lazy(HH, c_r54[l], c_r54_s[l], p),
-                                    l);
+                    v[c] = fold_signed(s[j][3 * c], s[j][3 * c + 1], s[j][3 * c + 2], l, p);
                     s[j][3 * c] = s[j][3 * c + 1] = s[j][3 * c + 2] = 0;
                 }
                 // T0 = v0, T2 = v1, T1 = K - T0 - T2 with K = v2
