@@ -17,7 +17,7 @@ scored per second = 1,048,576 per step / step time.
          the other's kernels; the synchronous call (hers_search_host, one
          step at a time) is reported beside it.
 
-The gallery (5 GiB resident) is larger than L2 (129 MB), so no flush is needed
+The gallery (4 GiB resident) is larger than L2 (129 MB), so no flush is needed
 between steps.  Multi-GPU: each rank searches its own 256-block gallery (the
 blocks are independent, Sec. 3.2 footnote), no data-path collective: weak
 scaling.  `--impl reference` times the CPU oracle on the host cores instead.
@@ -38,7 +38,23 @@ N = 4096
 FEAT_SEED, MATE_SEED, NOISE_SEED, KEY_SEED, GAL_SEED, PRB_SEED = 1001, 1002, 1003, 1004, 1005, 1006
 ENROLL_SEED = 1007
 METRIC = "encrypted gallery entries scored/sec at N=4096, d=64 (bit-exact)"
+# the resident form the committed DRAM-traffic capture was taken on
+RESIDENT_FORM = "search basis of 8 primes below 2^30, centred int32 residues"
 
+
+def search_limbs():
+    """Primes of the resident search basis (the resident form holds two
+    polynomials of N int32 residues per prime, block and dimension)."""
+    import paper_2003_12197_gb300 as H
+    return H.hers_gallery_bytes(1, 1) // (2 * N * 4)
+
+
+def tensor_alg_bytes(nb, d):
+    """Algorithmic bytes of one tensor-kernel launch over nb blocks at
+    dimension d: the resident gallery read once, the prepared probe read once,
+    and the uint32 accumulators [nb][3][limbs][N] written once."""
+    import paper_2003_12197_gb300 as H
+    return H.hers_gallery_bytes(nb, d) + H.hers_probe_bytes(d) + nb * 3 * search_limbs() * N * 4
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -69,9 +85,9 @@ def parse():
                          "of the first probes)")
     ap.add_argument("--batch-variant", default=None,
                     help="batched: kernel shape by name (skips the batched autotuner); "
-                         "scale: the streamed search's kernel shape (default np2_nb1_s2_d4_m2)")
+                         "scale: the streamed search's kernel shape (default np4_nb1_s2_d4_m2)")
     ap.add_argument("--variant", default=None,
-                    help="tensor-kernel shape by name (skips the autotuner), e.g. nb2_s2_d4_m2")
+                    help="tensor-kernel shape by name (skips the autotuner), e.g. nb2_s3_d4_m3")
     return ap.parse_args()
 
 
@@ -455,10 +471,7 @@ def run_gpu(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    gal_bytes = nb * d * 2 * 5 * N * 8
-    probe_bytes = d * 2 * 5 * N * 8
-    acc_bytes = nb * 3 * 5 * N * 8
-    alg_bytes = gal_bytes + probe_bytes + acc_bytes
+    alg_bytes = tensor_alg_bytes(nb, d)
     t_tensor = phases["tensor"] / 1e3
     achieved = alg_bytes / t_tensor / 1e9 if t_tensor > 0 else 0.0
     # DRAM traffic of the same kernel shape from a committed ncu capture, scaled
@@ -468,7 +481,8 @@ def run_gpu(args):
     if os.path.exists(prof):
         try:
             tj = json.load(open(prof))
-            if tj.get("variant") == variant_name and tj.get("d") == d:
+            if (tj.get("variant") == variant_name and tj.get("d") == d
+                    and tj.get("resident_form") == RESIDENT_FORM):
                 traffic = tj["bytes_per_block"] * nb + tj.get("bytes_fixed", 0)
         except (OSError, ValueError, KeyError):
             traffic = None
@@ -493,7 +507,7 @@ def run_gpu(args):
             "config": {"workload": f"plain single-probe search, m={m} entries per GPU "
                                    f"({nb} blocks), d={d}, N={N}, q=2x54-bit, t=4169729",
                        "global_batch": m * world, "parallelism": f"dp{world}",
-                       "l2": "inputs larger than L2 (5 GiB resident gallery per GPU), no flush"},
+                       "l2": "inputs larger than L2 (4 GiB resident gallery per GPU), no flush"},
             "gpu_launches": launches,
             "e2e": {"value": e2e_value, "unit": "entries/s",
                     "h2d_bytes_per_step": d * 4 * N * 8, "d2h_bytes_per_step": nb * 4 * N * 8,
@@ -623,10 +637,10 @@ def run_batched(args):
     if not exact:
         raise SystemExit("batched search is not bit-exact against the plain path")
 
-    imad = sum(nb * d for _, nb, d, _ in items) * N * 5 * 9
+    imad = sum(nb * d for _, nb, d, _ in items) * N * search_limbs() * 4
     pipe = H.hers_probe_int_pipe(local)["imad_wide_u32"]
     t_tensor = min(tensor_ms) / 1e3
-    gal_bytes = sum(nb * d * 10 * N * 8 for _, _, nb, d in gals)
+    gal_bytes = sum(H.hers_gallery_bytes(nb, d) for _, _, nb, d in gals)
     out = {
         "metric": METRIC.replace("d=64", "d in {32,64,128}"), "workload": "batched",
         "value": entries / (batch_ms / 1e3), "unit": "entries/s", "n_gpus": 1,
@@ -767,7 +781,7 @@ def run_serving(args):
     plain_entries = 0
     for _, gi, b0, b1 in reqs:
         g, _, d = gals[gi]
-        view = g[b0 * 10 * d * N:]
+        view = g[b0 * H.hers_gallery_bytes(1, d) // 8:]
         H.hers_search(ctx, keys, view, b1 - b0, d, prepared[gi][int(prng.integers(0, 8))],
                       out=sc[: b1 - b0], workspace=ws)
         plain_entries += (b1 - b0) * N
@@ -852,7 +866,7 @@ def run_scale(args):
               for i, q in enumerate(qs)]
     sc = torch.empty((nprobes, nb, 2, 2, N), dtype=torch.int64, device=dev)
     chunk = 32
-    bv_name = args.batch_variant or "np2_nb1_s2_d4_m2"
+    bv_name = args.batch_variant or "np4_nb1_s2_d4_m2"
     bv = H.hers_batch_variants().index(bv_name)
     ws = torch.empty(H.hers_search_stream_workspace_bytes(d, nprobes, chunk) // 8,
                      dtype=torch.int64, device=dev)
@@ -989,7 +1003,7 @@ def run_sweep(args):
         H.hers_trace_enable(ctx, 0)
         H.hers_check(ctx)
         ms = e0.elapsed_time(e1) / args.steps
-        alg = nb * d * 2 * 5 * N * 8 + d * 2 * 5 * N * 8 + nb * 3 * 5 * N * 8
+        alg = tensor_alg_bytes(nb, d)
         gbs = alg / (phases["tensor"] / 1e3) / 1e9
         out_points.append({"m": m, "d": d, "blocks": nb, "ms_per_step": ms, "entries_per_s": m / (ms / 1e3),
                            "phases_ms": {k: round(v, 4) for k, v in phases.items()},

@@ -26,11 +26,11 @@
 namespace hers {
 
 constexpr uint32_t UNIT_STOP = 0xFFFFFFFFu;
-constexpr int BKCHUNK = 64;  // fold period in dimensions (see k_tensor)
+constexpr int BPFOLD = 8;  // partial-fold period in dimensions (see k_tensor)
 
 // Stage descriptor flags (written by the producer with each stage).
 constexpr uint32_t F_FIRST = 1;  // first stage of a unit: sums start at zero
-constexpr uint32_t F_FOLD = 2;   // fold the 64-bit sums mod p after this stage
+constexpr uint32_t F_FOLD = 2;   // partial fold of the 64-bit sums after this stage
 constexpr uint32_t F_LAST = 4;   // last stage of a unit: store the unit's results
 constexpr uint32_t F_STOP = 8;   // no more units: the consumers leave
 
@@ -67,46 +67,34 @@ __device__ __forceinline__ void load_unit(UnitRegs<NP>& r, const BatchChunk* __r
 }
 
 // One stage's products into the 64-bit sums: for dd < nd, probe q < np,
-// block j < nb, the 9 digit products of (probe row q) x (gallery row j).  With
-// FULL (nd = DPS, np = NP, nb = NB) the loops carry no predicates.
+// block j < nb, the four products of (probe row q) x (gallery row j) (centred
+// int32 residues, see k_tensor).  With FULL (nd = DPS, np = NP, nb = NB) the
+// loops carry no predicates.
 template <int NP, int NB, int DPS, bool FULL>
-__device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][9], const uint64_t* base, uint32_t nd,
+__device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const int32_t* base, uint32_t nd,
                                                uint32_t np, uint32_t nbu) {
     constexpr int RUN = DPS * 2 * TILE;
 #pragma unroll
     for (int dd = 0; dd < DPS; dd++) {
         if (FULL || (uint32_t)dd < nd) {
-            int32_t a0l[NP], a0h[NP], a1l[NP], a1h[NP];  // signed digits (split_store)
+            int32_t a0[NP], a1[NP];
 #pragma unroll
             for (int q = 0; q < NP; q++) {
-                const uint64_t A0 = base[q * RUN + dd * 2 * TILE], A1 = base[q * RUN + dd * 2 * TILE + TILE];
-                a0l[q] = (int32_t)(uint32_t)A0;
-                a0h[q] = (int32_t)(uint32_t)(A0 >> 32);
-                a1l[q] = (int32_t)(uint32_t)A1;
-                a1h[q] = (int32_t)(uint32_t)(A1 >> 32);
+                a0[q] = base[q * RUN + dd * 2 * TILE];
+                a1[q] = base[q * RUN + dd * 2 * TILE + TILE];
             }
 #pragma unroll
             for (int j = 0; j < NB; j++) {
                 if (FULL || (uint32_t)j < nbu) {
-                    const uint64_t* gp = base + (NP + j) * RUN + dd * 2 * TILE;
-                    const uint64_t B0 = gp[0], B1 = gp[TILE];
-                    const int32_t b0l = (int32_t)(uint32_t)B0, b0h = (int32_t)(uint32_t)(B0 >> 32);
-                    const int32_t b1l = (int32_t)(uint32_t)B1, b1h = (int32_t)(uint32_t)(B1 >> 32);
-                    const int32_t b0s = b0l + b0h, b1s = b1l + b1h;
-                    const int32_t sbl = b0l + b1l, sbh = b0h + b1h, sbs = sbl + sbh;
+                    const int32_t* gp = base + (NP + j) * RUN + dd * 2 * TILE;
+                    const int32_t g0 = gp[0], g1 = gp[TILE];
 #pragma unroll
                     for (int q = 0; q < NP; q++) {
                         if (FULL || (uint32_t)q < np) {
-                            const int32_t sal = a0l[q] + a1l[q], sah = a0h[q] + a1h[q];
-                            madw_b(s[q][j][0], a0l[q], b0l);
-                            madw_b(s[q][j][1], a0h[q], b0h);
-                            madw_b(s[q][j][2], a0l[q] + a0h[q], b0s);
-                            madw_b(s[q][j][3], a1l[q], b1l);
-                            madw_b(s[q][j][4], a1h[q], b1h);
-                            madw_b(s[q][j][5], a1l[q] + a1h[q], b1s);
-                            madw_b(s[q][j][6], sal, sbl);
-                            madw_b(s[q][j][7], sah, sbh);
-                            madw_b(s[q][j][8], sal + sah, sbs);
+                            madw_b(s[q][j][0], a0[q], g0);
+                            madw_b(s[q][j][1], a0[q], g1);
+                            madw_b(s[q][j][1], a1[q], g0);
+                            madw_b(s[q][j][2], a1[q], g1);
                         }
                     }
                 }
@@ -115,39 +103,27 @@ __device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][9], const ui
     }
 }
 
-// Folds the three signed digit sums of one component, value = LL + (MM - HH -
-// LL) 2^27 + HH 2^54, to a residue mod p_l in [0, p).
-__device__ __forceinline__ uint64_t fold3(int64_t LL, int64_t HH, int64_t MM, int l, uint64_t p) {
-    return reduce64(shoup_lazy(signed_to_unsigned(LL, l), 1, c_one_s[l], p) +
-                        shoup_lazy(signed_to_unsigned(MM - HH - LL, l), c_r27[l], c_r27_s[l], p) +
-                        shoup_lazy(signed_to_unsigned(HH, l), c_r54[l], c_r54_s[l], p),
-                    l);
-}
-
 // Persistent batched tensor kernel.  A CTA has TILE consumer threads (one
 // coefficient each) and one producer warp.  The producer's elected lane
 // claims units from the atomic counter one unit ahead (the claim and the
 // unit's table reads overlap the current unit's stages), and for each stage
 // writes a descriptor (dimensions, probes, blocks, limb, flags; on the last
 // stage the output pairs) into shared memory before the stage's copies, so
-// the consumers read no tables from global memory.  FREG keeps the folded
-// sums in registers (for 1-CTA/SM shapes); otherwise they live in shared
-// memory after the ring.
+// the consumers read no tables from global memory.  Each consumer keeps the
+// NP x NB x 3 sums of its coefficient in registers.
 
-template <int NP, int NB, int STAGES, int DPS, int MINB, int FREG>
+template <int NP, int NB, int STAGES, int DPS, int MINB>
 __global__ void __launch_bounds__(TILE + 32, MINB)
     k_tensor_batched(const BatchChunk* __restrict__ chunks, const BatchUnit* __restrict__ units,
-                     uint32_t nunits, uint32_t* counter, uint64_t* __restrict__ X, int* err) {
-    static_assert(BKCHUNK % DPS == 0, "stages must not straddle a fold");
-    static_assert(NP <= BATCH_NPMAX && NB <= 15 && DPS <= 255, "descriptor fields");
-    extern __shared__ __align__(128) uint64_t sm[];
+                     uint32_t nunits, uint32_t* counter, uint32_t* __restrict__ X, int* err) {
+    static_assert(BPFOLD % DPS == 0, "stages must not straddle a partial fold");
+    static_assert(NP <= BATCH_NPMAX && NB <= 15 && DPS <= 255 && NUM_S <= 16, "descriptor fields");
+    extern __shared__ __align__(128) int32_t smr[];
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
     __shared__ uint32_t hdr_info[STAGES], hdr_k0[STAGES];
     __shared__ uint64_t hdr_pair[STAGES][NP];
     constexpr int RUN = DPS * 2 * TILE;
-    constexpr int STAGE_WORDS = (NP + NB) * RUN;  // NP probe runs, then NB gallery runs
-    // FREG = 0: per-thread folded sums [q][j][c][TILE] after the ring
-    uint64_t* foldbuf = sm + (size_t)STAGES * STAGE_WORDS;
+    constexpr int STAGE_ELEMS = (NP + NB) * RUN;  // NP probe runs, then NB gallery runs
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -185,7 +161,7 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
                     }
                     const uint32_t nd = min((uint32_t)DPS, cur.d - si * DPS), done = si * DPS + nd;
                     const uint32_t flags = (si == 0 ? F_FIRST : 0u) |
-                                           ((done % BKCHUNK == 0 || done == cur.d) ? F_FOLD : 0u) |
+                                           ((done % BPFOLD == 0 && done < cur.d) ? F_FOLD : 0u) |
                                            (done == cur.d ? F_LAST : 0u);
                     hdr_info[st] = nd | (cur.np << 8) | (cur.nb << 12) | (cur.limb << 16) | (flags << 20);
                     if (flags & F_LAST) {
@@ -193,19 +169,21 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
 #pragma unroll
                         for (int q = 0; q < NP; q++) hdr_pair[st][q] = cur.pair[q];
                     }
-                    const uint32_t bytes = nd * 2 * TILE * 8;
-                    uint64_t* dst = sm + (size_t)st * STAGE_WORDS;
+                    const uint32_t bytes = nd * 2 * TILE * 4;
+                    int32_t* dst = smr + (size_t)st * STAGE_ELEMS;
                     mbar_expect_tx(&full[st], bytes * (cur.np + cur.nb));
                     const uint64_t off = resident_offset(0, cur.limb, cur.tile * TILE, cur.d, 0, 0) +
                                          (uint64_t)si * RUN;
 #pragma unroll
                     for (int q = 0; q < NP; q++)
-                        if ((uint32_t)q < cur.np) bulk_g2s(dst + q * RUN, cur.probe[q] + off, bytes, &full[st], pol_p);
+                        if ((uint32_t)q < cur.np)
+                            bulk_g2s(dst + q * RUN, (const int32_t*)cur.probe[q] + off, bytes, &full[st], pol_p);
 #pragma unroll
                     for (int j = 0; j < NB; j++)
                         if ((uint32_t)j < cur.nb)
                             bulk_g2s(dst + (NP + j) * RUN,
-                                     cur.gallery + resident_offset(cur.block + j, cur.limb, cur.tile * TILE, cur.d, 0, 0) +
+                                     (const int32_t*)cur.gallery +
+                                         resident_offset(cur.block + j, cur.limb, cur.tile * TILE, cur.d, 0, 0) +
                                          (uint64_t)si * RUN,
                                      bytes, &full[st], pol_g);
                     // the next unit's tables, once this unit's first stage is on its way
@@ -224,8 +202,7 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
 
     // consumers
     const int t = threadIdx.x;
-    int64_t s[NP][NB][9];
-    uint64_t f[NP][NB][3];  // FREG only
+    int64_t s[NP][NB][3];
     for (uint32_t g = 0;; g++) {
         const int st = (int)(g % STAGES);
         if (!mbar_wait(&full[st], (g / STAGES) & 1)) {
@@ -249,17 +226,9 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
 #pragma unroll
             for (int q = 0; q < NP; q++)
 #pragma unroll
-                for (int j = 0; j < NB; j++) {
-#pragma unroll
-                    for (int r = 0; r < 9; r++) s[q][j][r] = 0;
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        if (FREG) f[q][j][c] = 0;
-                        else foldbuf[((q * NB + j) * 3 + c) * TILE + t] = 0;
-                    }
-                }
+                for (int j = 0; j < NB; j++) s[q][j][0] = s[q][j][1] = s[q][j][2] = 0;
         }
-        const uint64_t* base = sm + (size_t)st * STAGE_WORDS + t;
+        const int32_t* base = smr + (size_t)st * STAGE_ELEMS + t;
         if (nd == DPS && np == NP && nbu == NB)
             stage_products<NP, NB, DPS, true>(s, base, nd, np, nbu);
         else
@@ -267,29 +236,13 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
         if (flags & F_FOLD) {
-            const uint64_t p = c_mod[l];
+            const int32_t r32 = (int32_t)c_sr32[l];
 #pragma unroll
             for (int q = 0; q < NP; q++)
 #pragma unroll
-                for (int j = 0; j < NB; j++) {
-                    const uint64_t v0 = fold3(s[q][j][0], s[q][j][1], s[q][j][2], l, p);
-                    const uint64_t v2 = fold3(s[q][j][3], s[q][j][4], s[q][j][5], l, p);
-                    const uint64_t vk = fold3(s[q][j][6], s[q][j][7], s[q][j][8], l, p);
+                for (int j = 0; j < NB; j++)
 #pragma unroll
-                    for (int r = 0; r < 9; r++) s[q][j][r] = 0;
-                    // T0 = v0, T2 = v2, T1 = vk - T0 - T2
-                    const uint64_t v1 = sub_mod(sub_mod(vk, v0, p), v2, p);
-                    if (FREG) {
-                        f[q][j][0] = add_mod(f[q][j][0], v0, p);
-                        f[q][j][1] = add_mod(f[q][j][1], v1, p);
-                        f[q][j][2] = add_mod(f[q][j][2], v2, p);
-                    } else {
-                        uint64_t* fb = foldbuf + (q * NB + j) * 3 * TILE + t;
-                        fb[0] = add_mod(fb[0], v0, p);
-                        fb[TILE] = add_mod(fb[TILE], v1, p);
-                        fb[2 * TILE] = add_mod(fb[2 * TILE], v2, p);
-                    }
-                }
+                    for (int c = 0; c < 3; c++) s[q][j][c] = pfold(s[q][j][c], r32);
         }
         if (flags & F_LAST) {
             const uint32_t k = k0 + t;
@@ -302,35 +255,30 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
                             const uint64_t pair = opair[q] + j;
 #pragma unroll
                             for (int c = 0; c < 3; c++)
-                                X[((pair * 3 + c) * 5 + l) * N + k] =
-                                    FREG ? f[q][j][c] : foldbuf[((q * NB + j) * 3 + c) * TILE + t];
+                                X[((pair * 3 + c) * NUM_S + l) * N + k] = fold_full(s[q][j][c], l);
                         }
         }
     }
 }
 
-using BatchFn = void (*)(const BatchChunk*, const BatchUnit*, uint32_t, uint32_t*, uint64_t*, int*);
+using BatchFn = void (*)(const BatchChunk*, const BatchUnit*, uint32_t, uint32_t*, uint32_t*, int*);
 struct BatchVariant {
     const char* name;
     BatchFn fn;
-    int np, nb, stages, dps, minb, freg;
+    int np, nb, stages, dps, minb;
 };
-// name: np<probes>_nb<blocks>_s<stages>_d<dims per stage>_m<CTAs/SM>, and
-// "r" when the folded sums stay in registers
-#define HERS_BV(NP, NB, S, D, M, FR, SUF) \
-    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M SUF, k_tensor_batched<NP, NB, S, D, M, FR>, NP, NB, S, D, M, FR}
+// name: np<probes>_nb<blocks>_s<stages>_d<dims per stage>_m<CTAs/SM>
+#define HERS_BV(NP, NB, S, D, M) \
+    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M, k_tensor_batched<NP, NB, S, D, M>, NP, NB, S, D, M}
 static const BatchVariant kBatchVariants[] = {
-    HERS_BV(1, 1, 4, 2, 3, 0, ""),  HERS_BV(2, 1, 2, 4, 2, 0, ""),  HERS_BV(2, 1, 3, 2, 2, 0, ""),
-    HERS_BV(2, 2, 4, 2, 1, 1, "r"), HERS_BV(4, 1, 4, 2, 1, 1, "r"), HERS_BV(1, 2, 3, 2, 3, 0, ""),
-    HERS_BV(2, 2, 6, 2, 1, 1, "r"), HERS_BV(2, 1, 4, 4, 1, 1, "r"), HERS_BV(4, 1, 5, 2, 1, 1, "r"),
-    HERS_BV(2, 2, 3, 4, 1, 1, "r"), HERS_BV(1, 2, 2, 4, 2, 0, ""),  HERS_BV(1, 2, 4, 2, 2, 0, ""),
+    HERS_BV(1, 2, 4, 4, 2), HERS_BV(2, 1, 4, 4, 2), HERS_BV(2, 2, 3, 4, 2), HERS_BV(2, 2, 4, 2, 2),
+    HERS_BV(4, 1, 2, 4, 2), HERS_BV(4, 2, 2, 4, 2), HERS_BV(4, 2, 3, 2, 2), HERS_BV(2, 1, 3, 4, 3),
+    HERS_BV(1, 1, 4, 4, 3), HERS_BV(2, 2, 2, 4, 3), HERS_BV(4, 1, 4, 2, 2), HERS_BV(1, 2, 3, 4, 3),
 };
 #undef HERS_BV
 constexpr int NUM_BATCH_VARIANTS = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
-static int batch_smem(const BatchVariant& v) {
-    return v.stages * (v.np + v.nb) * v.dps * 2 * TILE * 8 + (v.freg ? 0 : v.np * v.nb * 3 * TILE * 8);
-}
+static int batch_smem(const BatchVariant& v) { return v.stages * (v.np + v.nb) * v.dps * 2 * TILE * 4; }
 
 int batch_variant_count() { return NUM_BATCH_VARIANTS; }
 int batch_variant_np(int v) { return kBatchVariants[v].np; }
@@ -339,6 +287,8 @@ int batch_variant_nb(int v) { return kBatchVariants[v].nb; }
 // Direct launch of the persistent kernel of variant v over device tables.
 cudaError_t launch_batched(int v, const BatchChunk* d_chunks, const BatchUnit* d_units, uint32_t nunits,
                            uint32_t* d_counter, uint64_t* X, int* err, int device, cudaStream_t st) {
+    // X: the X area of the pairs' workspace; the kernel writes uint32 accumulators
+    // [pair][3][NUM_S][N] at its start
     if (v < 0 || v >= NUM_BATCH_VARIANTS) return cudaErrorInvalidValue;
     const BatchVariant& V = kBatchVariants[v];
     const int smem = batch_smem(V);
@@ -351,7 +301,7 @@ cudaError_t launch_batched(int v, const BatchChunk* d_chunks, const BatchUnit* d
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)per_sm * sms, nunits ? nunits : 1);
     e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    V.fn<<<grid, TILE + 32, smem, st>>>(d_chunks, d_units, nunits, d_counter, X, err);
+    V.fn<<<grid, TILE + 32, smem, st>>>(d_chunks, d_units, nunits, d_counter, (uint32_t*)X, err);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -445,7 +395,7 @@ void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, int nb_max
                 chunks.push_back(ch);
             }
             const uint32_t nch = (uint32_t)chunks.size() - first;
-            for (uint16_t l = 0; l < 5; l++)
+            for (uint16_t l = 0; l < NUM_S; l++)
                 for (uint16_t tl = 0; tl < NTILES; tl++)
                     for (uint64_t blk = s0; blk < s1; blk += nb_max) {
                         const uint32_t nbu = (uint32_t)std::min<uint64_t>(nb_max, s1 - blk);
@@ -489,8 +439,8 @@ cudaError_t batch_launch(hers_batch* B, cudaStream_t st, bool traced) {
     uint64_t* KS = C + B->npairs * 6 * N;
     cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(uint32_t), st);
     if (traced) cudaEventRecord(B->ev[0], st);
-    B->fn<<<B->grid, TILE + 32, B->smem, st>>>(B->d_chunks, B->d_units, B->nunits, B->d_counter, X,
-                                                B->ctx->err);
+    B->fn<<<B->grid, TILE + 32, B->smem, st>>>(B->d_chunks, B->d_units, B->nunits, B->d_counter,
+                                                (uint32_t*)X, B->ctx->err);
     if (traced) cudaEventRecord(B->ev[1], st);
     if (e == cudaSuccess) e = cudaGetLastError();
     cudaError_t el = launch_epilogue(B->ctx->tw, B->keys->k, B->npairs, X, C, KS, B->scores, st);

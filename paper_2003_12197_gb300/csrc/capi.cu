@@ -51,6 +51,8 @@ namespace {
 
 const uint64_t H_MOD[NUM_MODS] = HERS_MOD_INIT;
 const uint64_t H_PSI[NUM_MODS] = HERS_PSI_INIT;
+const uint64_t H_SMOD[NUM_S] = HERS_SMOD_INIT;
+const uint64_t H_SPSI[NUM_S] = HERS_SPSI_INIT;
 
 typedef unsigned __int128 u128;
 
@@ -120,8 +122,8 @@ const char* hers_status_string(int s) {
 const char* hers_last_error(const hers_ctx* ctx) { return ctx ? ctx->msg : "null context"; }
 
 uint64_t hers_ct_bytes(void) { return 4ull * N * 8; }
-uint64_t hers_gallery_bytes(uint64_t nblocks, uint32_t d) { return nblocks * d * 10ull * N * 8; }
-uint64_t hers_probe_bytes(uint32_t d) { return (uint64_t)d * 10ull * N * 8; }
+uint64_t hers_gallery_bytes(uint64_t nblocks, uint32_t d) { return nblocks * d * RES_WORDS_PER_DIM * 8; }
+uint64_t hers_probe_bytes(uint32_t d) { return (uint64_t)d * RES_WORDS_PER_DIM * 8; }
 uint64_t hers_search_workspace_bytes(uint64_t nblocks) { return nblocks * SEARCH_WS_WORDS_PER_BLOCK * 8; }
 uint64_t hers_blocks_for(uint64_t m) { return (m + N - 1) / N; }
 uint64_t hers_search_host_workspace_bytes(uint64_t nblocks, uint32_t d) {
@@ -156,7 +158,7 @@ int hers_create(const hers_params* p, int device, hers_ctx** out) {
     }
     // twiddles: [mod][forward, inverse][N] pairs (w, floor(w 2^64 / p)); entry 0
     // of the inverse table: the last inverse stage's twiddle times N^-1
-    const size_t words = (size_t)NUM_MODS * 4 * N;
+    const size_t words = TW_WORDS;
     uint64_t* h = new (std::nothrow) uint64_t[words];
     if (!h) { cudaStreamDestroy(ctx->stream); delete ctx; return HERS_E_NOMEM; }
     for (int i = 0; i < NUM_MODS; i++) {
@@ -174,6 +176,24 @@ int hers_create(const hers_params* p, int device, hers_ctx** out) {
         const uint64_t wl = h_mulmod(f[2 * N + 2], ninv, pm);  // inverse twiddle 1 times N^-1
         f[2 * N] = wl;
         f[2 * N + 1] = (uint64_t)(((u128)wl << 64) / pm);
+    }
+    // search basis: [i][forward, inverse][N] pairs of 32-bit words (w, floor(w 2^32 / r))
+    uint32_t* h32 = (uint32_t*)(h + (size_t)NUM_MODS * 4 * N);
+    for (int i = 0; i < NUM_S; i++) {
+        const uint64_t r = H_SMOD[i], psi = H_SPSI[i], psi_inv = h_pow(psi, r - 2, r);
+        uint32_t* f = h32 + (size_t)(4 * i) * N;
+        for (int k = 0; k < N; k++) {
+            const int b = h_brev(k, LOGN);
+            const uint64_t w = h_pow(psi, (uint64_t)b, r), wi = h_pow(psi_inv, (uint64_t)b, r);
+            f[2 * k] = (uint32_t)w;
+            f[2 * k + 1] = (uint32_t)((w << 32) / r);
+            f[2 * N + 2 * k] = (uint32_t)wi;
+            f[2 * N + 2 * k + 1] = (uint32_t)((wi << 32) / r);
+        }
+        const uint64_t ninv = h_pow((uint64_t)N, r - 2, r);
+        const uint64_t wl = h_mulmod(f[2 * N + 2], ninv, r);  // inverse twiddle 1 times N^-1
+        f[2 * N] = (uint32_t)wl;
+        f[2 * N + 1] = (uint32_t)((wl << 32) / r);
     }
     cudaError_t e = cudaMalloc(&ctx->tw, words * 8);
     if (e == cudaSuccess) e = cudaMemcpy(ctx->tw, h, words * 8, cudaMemcpyHostToDevice);
@@ -456,11 +476,12 @@ int search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
         }
     }
     cudaStream_t st = pick(ctx, stream);
-    // workspace: [search scratch][probe cts d*4N][probe form d*10N][score cts nblocks*4N]
+    // workspace: [search scratch][probe cts d*4N][probe form d*RES_WORDS_PER_DIM][score cts nblocks*4N]
+    // (hers_search_host_workspace_bytes sums the same parts)
     uint64_t* ws = (uint64_t*)workspace;
     uint64_t* probe_ct = ws + nblocks * SEARCH_WS_WORDS_PER_BLOCK;
     uint64_t* probe = probe_ct + (uint64_t)d * 4 * N;
-    uint64_t* out_dev = probe + (uint64_t)d * 10 * N;
+    uint64_t* out_dev = probe + (uint64_t)d * RES_WORDS_PER_DIM;
     cudaError_t e = cudaMemcpyAsync(probe_ct, probe_ct_host, (uint64_t)d * 4 * N * 8,
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, probe_ct, d, 0, d, probe, st);
@@ -583,11 +604,11 @@ int hers_autotune(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
     float best_ms = 0;
     cudaError_t e = cudaSuccess;
     for (int v = 0; v < tensor_variant_count() && e == cudaSuccess; v++) {
-        e = launch_tensor(v, gallery, nblocks, d, probe, (uint64_t*)workspace, ctx->err, st);  // warm
+        e = launch_tensor(v, gallery, nblocks, d, probe, (uint32_t*)workspace, ctx->err, st);  // warm
         float vbest = 0;
         for (int rep = 0; rep < 3 && e == cudaSuccess; rep++) {
             cudaEventRecord(e0, st);
-            e = launch_tensor(v, gallery, nblocks, d, probe, (uint64_t*)workspace, ctx->err, st);
+            e = launch_tensor(v, gallery, nblocks, d, probe, (uint32_t*)workspace, ctx->err, st);
             cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0;

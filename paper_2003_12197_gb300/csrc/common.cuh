@@ -12,29 +12,34 @@
 namespace hers {
 
 // ---------------------------------------------------------------- constants
-// Modulus index i: 0 = q1, 1 = q2, 2 = p1, 3 = p2, 4 = p3, 5 = the default t,
-// 6 = the paper's t.
+// Modulus index i: 0 = q1, 1 = q2, 2 = the default t, 3 = the paper's t.
 static __constant__ uint64_t c_mod[NUM_MODS] = HERS_MOD_INIT;
 static __constant__ uint64_t c_ninv[NUM_MODS] = HERS_NINV_INIT;
 static __constant__ uint64_t c_ninv_s[NUM_MODS] = HERS_NINV_S_INIT;
 static __constant__ uint64_t c_one_s[NUM_MODS] = HERS_ONE_S_INIT;
-static __constant__ uint64_t c_barrett[NUM_RNS] = HERS_BARRETT_INIT;
-static __constant__ uint64_t c_off63[NUM_RNS] = HERS_OFF63_INIT;
-static __constant__ uint64_t c_r27[NUM_MODS] = HERS_R27_INIT;
-static __constant__ uint64_t c_r27_s[NUM_MODS] = HERS_R27_S_INIT;
-static __constant__ uint64_t c_r54[NUM_MODS] = HERS_R54_INIT;
-static __constant__ uint64_t c_r54_s[NUM_MODS] = HERS_R54_S_INIT;
-static __constant__ uint64_t c_q1_mod[NUM_RNS] = HERS_Q1_MOD_INIT;
-static __constant__ uint64_t c_q1_mod_s[NUM_RNS] = HERS_Q1_MOD_S_INIT;
-static __constant__ uint64_t c_q_mod[NUM_RNS] = HERS_Q_MOD_INIT;
-static __constant__ uint64_t c_qinv_p[3] = HERS_QINV_P_INIT;
-static __constant__ uint64_t c_qinv_p_s[3] = HERS_QINV_P_S_INIT;
-static __constant__ uint64_t c_p1_mod_q[2] = HERS_P1_MOD_Q_INIT;
-static __constant__ uint64_t c_p1_mod_q_s[2] = HERS_P1_MOD_Q_S_INIT;
-static __constant__ uint64_t c_p1p2_mod_q[2] = HERS_P1P2_MOD_Q_INIT;
-static __constant__ uint64_t c_p1p2_mod_q_s[2] = HERS_P1P2_MOD_Q_S_INIT;
-static __constant__ uint64_t c_p_mod_q[2] = HERS_P_MOD_Q_INIT;
+static __constant__ uint64_t c_barrett[NUM_Q] = HERS_BARRETT_INIT;
 static __constant__ uint64_t c_chi_cdt[CHI_LEN] = HERS_CHI_CDT_INIT;
+
+// Search basis r_0 .. r_7 (primes below 2^30, = 1 mod 2N; M = their product):
+// the basis of the resident form and of the exact tensor sums.
+static __constant__ uint32_t c_smod[NUM_S] = HERS_SMOD_INIT;
+static __constant__ uint32_t c_sninv[NUM_S] = HERS_SNINV_INIT;      // N^-1 mod r
+static __constant__ uint32_t c_sninv_s[NUM_S] = HERS_SNINV_S_INIT;  // its Shoup companion (2^32)
+static __constant__ uint64_t c_smu[NUM_S] = HERS_SMU_INIT;          // floor(2^64 / r)
+static __constant__ uint32_t c_sr32[NUM_S] = HERS_SR32_INIT;        // 2^32 mod r
+static __constant__ uint64_t c_soff63[NUM_S] = HERS_SOFF63_INIT;    // multiple of r just below 2^63
+static __constant__ uint32_t c_q1_mod_r[NUM_S] = HERS_Q1_MOD_R_INIT;
+static __constant__ uint32_t c_q1_mod_r_s[NUM_S] = HERS_Q1_MOD_R_S_INIT;
+static __constant__ uint32_t c_q_mod_r[NUM_S] = HERS_Q_MOD_R_INIT;
+// CRT of X' = X + q 2^129: y_i = x_i Minv_i + HM_i mod r_i, Minv_i = (M / r_i)^-1
+// mod r_i, HM_i = (q 2^129 mod r_i) Minv_i; alpha = floor(sum y_i PHI_i / 2^60).
+static __constant__ uint32_t c_minv[NUM_S] = HERS_MINV_INIT;
+static __constant__ uint32_t c_minv_s[NUM_S] = HERS_MINV_S_INIT;
+static __constant__ uint32_t c_hm[NUM_S] = HERS_HM_INIT;
+static __constant__ uint32_t c_phi[NUM_S] = HERS_PHI_INIT;  // floor(2^60 / r) < 2^31
+// 27-bit digits of (M / r_i) mod q_j, [i][j][2], and of M mod q_j, [j][2].
+static __constant__ uint32_t c_mi_q_cols[NUM_S * 4] = HERS_MI_Q_COLS_INIT;
+static __constant__ uint32_t c_m_q_cols[4] = HERS_M_Q_COLS_INIT;
 
 // Plaintext modulus t and what depends on it; a context uses entry 0 (the
 // default t = 4169729) or entry 1 (the paper's t = 1032193), and its keys
@@ -43,35 +48,49 @@ struct PlainMod {
     uint64_t t;
     int mod;                                 // index of t in the modulus arrays
     uint64_t q1_mod_t, q_mod_t, qinv_t;      // decryption: pt = [-r q^-1]_t
-    uint64_t t_mod[NUM_RNS], t_s[NUM_RNS];   // t mod p and its Shoup companion
+    uint64_t t_mod[NUM_Q], t_s[NUM_Q];       // t mod q_l and its Shoup companion
     uint64_t delta[2], delta_s[2];           // Delta = floor(q / t) mod q_l
+    // scale-and-round (t M_i = A_i q + B_i, t M = A_M q + B_M), 27-bit digits:
+    uint32_t b_cols[NUM_S * 4];              // B_i, [i][4]
+    uint32_t bm_cols[4];                     // B_M
+    uint32_t a_cols[NUM_S * 4];              // A_i mod q_j, [i][j][2]
+    uint32_t am_cols[4];                     // A_M mod q_j, [j][2]
+    uint64_t dshift[2];                      // [8 + t 2^129] mod q_j
 };
 static __constant__ PlainMod c_plain[2] = HERS_PLAIN_INIT;
 
-// Resident (search) form of ciphertexts: NTT domain over the five primes, split
-// storage, tiled so that everything one search CTA streams is contiguous:
-//   [block][limb][tile][dim][poly][TILE]   (TILE coefficients per tile)
-// A gallery block occupies 10 d N words; a prepared probe is block 0 of it.
+// Resident (search) form of ciphertexts: NTT domain over the search basis,
+// each residue as its centred value (one int32, |v| < 2^29), tiled so that
+// everything one search CTA streams is contiguous:
+//   [block][limb r_l][tile][dim][poly][TILE]   (TILE coefficients per tile)
+// A gallery block occupies 16 d N int32 (8 d N 64-bit words); a prepared
+// probe is block 0 of it.  Offsets below count int32 elements.
 constexpr int TILE = 256;
 constexpr int NTILES = N / TILE;
 __host__ __device__ __forceinline__ uint64_t resident_offset(uint64_t b, int limb, int k, uint32_t d,
                                                              uint32_t i, int poly) {
-    return ((((b * 5 + (uint64_t)limb) * NTILES + (uint64_t)(k / TILE)) * d + i) * 2 + (uint64_t)poly) *
+    return ((((b * NUM_S + (uint64_t)limb) * NTILES + (uint64_t)(k / TILE)) * d + i) * 2 + (uint64_t)poly) *
                TILE +
            (uint64_t)(k % TILE);
 }
-constexpr uint32_t MASK27 = (1u << 27) - 1;
 
 // Twiddle table of modulus i inside the table buffer the context owns:
 // [i][forward, inverse][N] pairs (w, w'), w' = floor(w 2^64 / p) (Shoup), so
 // one 16-byte load fetches a twiddle with its companion.  Entry 0 of the
 // inverse table (never used as a butterfly twiddle) holds the last inverse
-// stage's twiddle times N^-1.
+// stage's twiddle times N^-1.  After the NUM_MODS tables come those of the
+// search basis in the same form with 32-bit words: pairs (w, floor(w 2^32 / r)).
 __device__ __forceinline__ const ulonglong2* tw_fwd(const uint64_t* tw, int i) {
     return (const ulonglong2*)(tw + (size_t)4 * N * i);
 }
 __device__ __forceinline__ const ulonglong2* tw_inv(const uint64_t* tw, int i) {
     return (const ulonglong2*)(tw + (size_t)4 * N * i + 2 * N);
+}
+__device__ __forceinline__ const uint2* tw32_fwd(const uint64_t* tw, int i) {
+    return (const uint2*)(tw + (size_t)4 * N * NUM_MODS) + (size_t)2 * N * i;
+}
+__device__ __forceinline__ const uint2* tw32_inv(const uint64_t* tw, int i) {
+    return (const uint2*)(tw + (size_t)4 * N * NUM_MODS) + (size_t)2 * N * i + N;
 }
 
 // ---------------------------------------------------------------- arithmetic
@@ -117,41 +136,55 @@ __device__ __forceinline__ uint64_t reduce64(uint64_t x, int i) {
     return csub(shoup_lazy(x, 1, c_one_s[i], c_mod[i]), c_mod[i]);
 }
 
-// a b mod p_i for a, b < p_i, i an RNS prime (2^53 < p_i < 2^54): Barrett on
-// the 108-bit product with mu = floor(2^108 / p), quotient estimate
-// floor(floor(x / 2^53) mu / 2^55), which is at most 2 below the true one.
-__device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, int i) {
+// mod-t arithmetic (t < 2^23): products fit in 64 bits
+__device__ __forceinline__ uint64_t mul_mod_t(uint64_t a, uint64_t b, uint64_t t) { return (a * b) % t; }
+
+// ---------------------------------------------------------------- search-basis arithmetic (r < 2^30)
+__device__ __forceinline__ uint32_t csub32(uint32_t x, uint32_t p) { return min(x, x - p); }
+// Shoup with 32-bit words: x w mod r in [0, 2r) for any x < 2^32, w < r, ws = floor(w 2^32 / r).
+__device__ __forceinline__ uint32_t shoup32(uint32_t x, uint32_t w, uint32_t ws, uint32_t r) {
+    return x * w - __umulhi(x, ws) * r;
+}
+// x mod r_i for any 64-bit x (Barrett with mu = floor(2^64 / r): the quotient
+// estimate is at most one short).
+__device__ __forceinline__ uint32_t reduce_r(uint64_t x, int i) {
+    const uint32_t r = c_smod[i];
+    return csub32((uint32_t)x - (uint32_t)__umul64hi(x, c_smu[i]) * r, r);
+}
+// Partial fold of a signed 64-bit sum s: s' = hi(s) (2^32 mod r) + lo(s) = s (mod r)
+// with |s'| < 2^61 + 2^32 (one 32x32->64 multiply-add).
+__device__ __forceinline__ int64_t pfold(int64_t s, int32_t r32) {
+    int64_t out = (int64_t)(uint64_t)(uint32_t)s;
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(out) : "r"((int32_t)(s >> 32)), "r"(r32));
+    return out;
+}
+// Residue in [0, r_i) of a signed 64-bit sum with |s| < 2^63 - r_i.
+__device__ __forceinline__ uint32_t fold_full(int64_t s, int i) { return reduce_r((uint64_t)s + c_soff63[i], i); }
+// Centred value of a residue v in [0, r) (the resident storage), and back.
+__device__ __forceinline__ int32_t centre32(uint32_t v, uint32_t r) {
+    return v > (r - 1) / 2 ? (int32_t)(v - r) : (int32_t)v;
+}
+__device__ __forceinline__ uint32_t uncentre32(int32_t c, uint32_t r) {
+    return c < 0 ? (uint32_t)(c + (int32_t)r) : (uint32_t)c;
+}
+
+// x mod q_i (i = 0, 1) for x = hi 2^64 + lo < 2^108: Barrett with
+// mu = floor(2^108 / q), quotient estimate floor(floor(x / 2^53) mu / 2^55),
+// at most 2 below the true one.
+__device__ __forceinline__ uint64_t reduce128(uint64_t lo, uint64_t hi, int i) {
     const uint64_t p = c_mod[i];
-    uint64_t lo = a * b, hi = __umul64hi(a, b);
-    uint64_t z = (hi << 11) | (lo >> 53);
-    uint64_t mu = c_barrett[i];
-    uint64_t qh = (__umul64hi(z, mu) << 9) | ((z * mu) >> 55);
+    const uint64_t z = (hi << 11) | (lo >> 53);
+    const uint64_t mu = c_barrett[i];
+    const uint64_t qh = (__umul64hi(z, mu) << 9) | ((z * mu) >> 55);
     uint64_t r = lo - qh * p;
     r = csub(r, p);
     return csub(r, p);
 }
 
-// mod-t arithmetic (t < 2^23): products fit in 64 bits
-__device__ __forceinline__ uint64_t mul_mod_t(uint64_t a, uint64_t b, uint64_t t) { return (a * b) % t; }
-
-// Split storage of a residue v in [0, p), p < 2^54, for the tensor product:
-// the centred value c (|c| <= (p-1)/2 < 2^53) as two signed 27-bit digits,
-// c = hi 2^27 + lo with lo in [-2^26, 2^26) and |hi| <= 2^26, stored as the
-// 32-bit words (hi, lo).  Every digit sum the Karatsuba products use then
-// stays below 2^28 in magnitude and every partial product below 2^56.
-__device__ __forceinline__ uint64_t split_store(uint64_t v, uint64_t p) {
-    const int64_t c = v > (p - 1) / 2 ? (int64_t)v - (int64_t)p : (int64_t)v;
-    const int64_t lo = ((c + (1 << 26)) & (int64_t)MASK27) - (1 << 26);
-    const int64_t hi = (c - lo) >> 27;  // exact
-    return ((uint64_t)(uint32_t)(int32_t)hi << 32) | (uint32_t)(int32_t)lo;
+// a b mod q_i for a, b < q_i (i = 0, 1).
+__device__ __forceinline__ uint64_t mul_mod(uint64_t a, uint64_t b, int i) {
+    return reduce128(a * b, __umul64hi(a, b), i);
 }
-__device__ __forceinline__ uint64_t split_load(uint64_t s, uint64_t p) {
-    const int64_t c = (int64_t)(int32_t)(uint32_t)(s >> 32) * (1 << 27) + (int64_t)(int32_t)(uint32_t)s;
-    return c < 0 ? (uint64_t)(c + (int64_t)p) : (uint64_t)c;
-}
-// Residue mod p_l of a signed 64-bit sum x with |x| < 2^63 - p: adding
-// c_off63[l] (a multiple of p_l just below 2^63) makes it non-negative.
-__device__ __forceinline__ uint64_t signed_to_unsigned(int64_t x, int l) { return (uint64_t)x + c_off63[l]; }
 
 __device__ __forceinline__ int brev12(int x) { return (int)(__brev((unsigned)x) >> (32 - LOGN)); }
 
@@ -452,6 +485,147 @@ static __device__ __noinline__ void ntt_inv_call(uint64_t* a, const uint64_t* tw
     ntt_inv_mod(a, tw, i);
 }
 
+// ---------------------------------------------------------------- NTT over the search basis (32-bit words)
+//
+// The same transform, schedule and twiddle order as above on residues mod
+// r < 2^30 held in 32-bit words.  Butterflies keep values below 4r < 2^32
+// (Harvey): forward, U is brought below 2r before U + V and U - V + 2r with
+// V = x w mod r in [0, 2r); inverse, U + V is brought below 2r and
+// (U - V + 2r) w lands in [0, 2r).  Forward input < 4r, output fully reduced
+// in bit-reversed order; inverse input < 2r, output natural order times N^-1,
+// fully reduced.
+//
+// Swizzle for 4-byte words: coefficient x at word swz32(x) = x ^ ((x >> 4) & 15)
+// ^ (((x >> 8) & 1) << 4).  In every access pattern used (t + 256 a, the three
+// phases) each half-warp's 16 words fall in 16 distinct banks and the two
+// halves in opposite halves of the 32 banks: one wavefront per access.
+__device__ __forceinline__ int swz32(int x) { return x ^ ((x >> 4) & 15) ^ (((x >> 8) & 1) << 4); }
+
+template <int STRIDE>
+__device__ __forceinline__ void ct_phase32(uint32_t v[16], int base, const uint2* __restrict__ w, uint32_t r) {
+    const uint32_t two_r = 2 * r;
+#pragma unroll
+    for (int h = 8; h >= 1; h >>= 1) {
+        const int t = STRIDE * h;
+        const int m = N / (2 * t);
+        const int i0 = base / (2 * t);
+#pragma unroll
+        for (int j = 0; j < 8 / h; j++) {
+            const uint2 W = __ldg(w + m + i0 + j);
+#pragma unroll
+            for (int q = 0; q < h; q++) {
+                const int a = 2 * h * j + q;
+                const uint32_t U = csub32(v[a], two_r);
+                const uint32_t V = shoup32(v[a + h], W.x, W.y, r);
+                v[a] = U + V;
+                v[a + h] = U - V + two_r;
+            }
+        }
+    }
+}
+
+template <int STRIDE, bool LAST>
+__device__ __forceinline__ void gs_phase32(uint32_t v[16], int base, const uint2* __restrict__ w, uint32_t r,
+                                           uint32_t ninv, uint32_t ninv_s) {
+    const uint32_t two_r = 2 * r;
+#pragma unroll
+    for (int h = 1; h <= 8; h <<= 1) {
+        const int t = STRIDE * h;
+        const int m = N / (2 * t);
+        const int i0 = base / (2 * t);
+#pragma unroll
+        for (int j = 0; j < 8 / h; j++) {
+            const uint2 W = __ldg(LAST && h == 8 ? w : w + m + i0 + j);
+#pragma unroll
+            for (int q = 0; q < h; q++) {
+                const int a = 2 * h * j + q;
+                const uint32_t U = v[a], V = v[a + h];
+                if (LAST && h == 8) {
+                    v[a] = csub32(shoup32(U + V, ninv, ninv_s, r), r);
+                    v[a + h] = csub32(shoup32(U - V + two_r, W.x, W.y, r), r);
+                } else {
+                    v[a] = csub32(U + V, two_r);
+                    v[a + h] = shoup32(U - V + two_r, W.x, W.y, r);
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void ntt32_fwd_smem(uint32_t* sm, const uint2* __restrict__ w, uint32_t r) {
+    const int t = threadIdx.x;
+    uint32_t v[16];
+    __syncthreads();
+    {
+        const int base = t;
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz32(base + 256 * a)];
+        ct_phase32<256>(v, base, w, r);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz32(base + 256 * a)] = v[a];
+    }
+    __syncthreads();
+    {
+        const int base = 256 * (t >> 4) + (t & 15);
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz32(base + 16 * a)];
+        ct_phase32<16>(v, base, w, r);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz32(base + 16 * a)] = v[a];
+    }
+    __syncwarp();
+    {
+        const int base = 16 * t;
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz32(base + a)];
+        ct_phase32<1>(v, base, w, r);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz32(base + a)] = csub32(csub32(v[a], 2 * r), r);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void ntt32_inv_smem(uint32_t* sm, const uint2* __restrict__ w, uint32_t r,
+                                               uint32_t ninv, uint32_t ninv_s) {
+    const int t = threadIdx.x;
+    uint32_t v[16];
+    __syncthreads();
+    {
+        const int base = 16 * t;
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz32(base + a)];
+        gs_phase32<1, false>(v, base, w, r, ninv, ninv_s);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz32(base + a)] = v[a];
+    }
+    __syncwarp();
+    {
+        const int base = 256 * (t >> 4) + (t & 15);
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz32(base + 16 * a)];
+        gs_phase32<16, false>(v, base, w, r, ninv, ninv_s);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz32(base + 16 * a)] = v[a];
+    }
+    __syncthreads();
+    {
+        const int base = t;
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz32(base + 256 * a)];
+        gs_phase32<256, true>(v, base, w, r, ninv, ninv_s);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz32(base + 256 * a)] = v[a];
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void ntt32_fwd_mod(uint32_t* a, const uint64_t* tw, int i) {
+    ntt32_fwd_smem(a, tw32_fwd(tw, i), c_smod[i]);
+}
+__device__ __forceinline__ void ntt32_inv_mod(uint32_t* a, const uint64_t* tw, int i) {
+    ntt32_inv_smem(a, tw32_inv(tw, i), c_smod[i], c_sninv[i], c_sninv_s[i]);
+}
+
 // ---------------------------------------------------------------- mbarrier + bulk async copy (TMA engine)
 // Used by the streaming kernels: a producer lane issues cp.async.bulk copies
 // global -> shared that complete on an mbarrier; consumers wait on it.  Every
@@ -545,12 +719,52 @@ __device__ __forceinline__ Lifted lift_q(uint64_t x1, uint64_t x2) {
     return L;
 }
 
-__device__ __forceinline__ uint64_t lifted_mod(const Lifted& L, int i, uint64_t x2) {
-    if (i == 0) return L.x1;
-    if (i == 1) return x2;
-    const uint64_t p = c_mod[i];
-    uint64_t v = add_mod(csub(L.x1, p), shoup(L.h, c_q1_mod[i], c_q1_mod_s[i], p), p);
-    return L.neg ? sub_mod(v, c_q_mod[i], p) : v;
+// The centred x (-q/2 < x <= q/2) of a lift, mod r_i: x1 + q1 h - [neg] q.
+__device__ __forceinline__ uint32_t lifted_mod_r(const Lifted& L, int i) {
+    const uint32_t r = c_smod[i];
+    const uint32_t m = shoup32(reduce_r(L.h, i), c_q1_mod_r[i], c_q1_mod_r_s[i], r);  // [0, 2r)
+    uint32_t v = csub32(csub32(reduce_r(L.x1, i) + m, 2 * r), r);
+    if (L.neg) v = v >= c_q_mod_r[i] ? v - c_q_mod_r[i] : v + r - c_q_mod_r[i];
+    return v;
+}
+
+// ---------------------------------------------------------------- CRT over the search basis
+//
+// For residues x_i = X mod r_i of an integer X with X' = X + q 2^129 in
+// [M/16, M/5] (every value this library reconstructs: the tensor sums,
+// |X| < 2^236, and centred lifts, |X| < q/2), the CRT gives
+//   X' = sum_i y_i M_i - alpha M,   y_i = [x'_i M_i^-1]_{r_i},  M_i = M / r_i,
+// with alpha = floor(sum_i y_i / r_i) (as 0 <= X' < M).  That sum is alpha +
+// X'/M with X'/M in [1/16, 1/5]; PHI_i = floor(2^60 / r_i) computes it short by
+// less than 2^-27, so the floor of the fixed-point sum is alpha exactly.
+__device__ __forceinline__ uint32_t crt_y(const uint32_t x[NUM_S], uint32_t y[NUM_S]) {
+    uint64_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < NUM_S; i++) {
+        const uint32_t r = c_smod[i];
+        const uint32_t v = shoup32(x[i], c_minv[i], c_minv_s[i], r) + c_hm[i];  // < 3r
+        y[i] = csub32(csub32(v, 2 * r), r);
+        acc += (uint64_t)y[i] * c_phi[i];
+    }
+    return (uint32_t)(acc >> 60);
+}
+
+// (sum_i y_i A_ij - alpha A_Mj + extra) mod q_j, with A_ij and A_Mj < q_j given as
+// two 27-bit digits (cols [i][j][2], mcols [j][2]) and |extra| < 2^56: column
+// sums of y (< 2^30) times a digit stay below 2^60.
+__device__ __forceinline__ uint64_t crt_combine_q(const uint32_t y[NUM_S], uint32_t alpha, const uint32_t* cols,
+                                                  const uint32_t* mcols, int j, int64_t extra) {
+    uint64_t c0 = 0, c1 = 0;
+#pragma unroll
+    for (int i = 0; i < NUM_S; i++) {
+        c0 += (uint64_t)y[i] * cols[(i * 2 + j) * 2];
+        c1 += (uint64_t)y[i] * cols[(i * 2 + j) * 2 + 1];
+    }
+    const int64_t s0 = (int64_t)c0 - (int64_t)alpha * mcols[j * 2] + extra + (int64_t)(16 * c_mod[j]);
+    const int64_t s1 = (int64_t)c1 - (int64_t)alpha * mcols[j * 2 + 1];
+    // s0 > 0 (16 q_j > 2^58 covers the negative terms), s1 > -2^30
+    const __int128 v = ((__int128)s1 << 27) + s0;  // in (0, 2^88)
+    return reduce128((uint64_t)v, (uint64_t)(v >> 64), j);
 }
 
 }  // namespace hers

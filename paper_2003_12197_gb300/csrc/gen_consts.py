@@ -1,20 +1,29 @@
 """Generates hers_consts.h: every compile-time constant of the CUDA library.
 
 Moduli.  The ciphertext modulus q = q1 q2 uses the two largest primes below
-2^54 with p = 1 (mod 2N), N = 4096; the auxiliary basis P = p1 p2 p3 (private
-to the library, used for the exact ciphertext product and rounding of Alg 5)
-uses the next three.  The plaintext modulus t = 4169729 is the smallest prime
-= 1 (mod 2N) above 2 * 128 * 127^2, so that every score |<q, p_j>| <= d 127^2
-of a d <= 128 int8 search stays below t/2 (Sec. 3.2: the plaintext ring must
-hold the result of the computation).  The paper's own t = 1032193 (Sec. 4.1),
-also = 1 (mod 2N), is the second plaintext modulus: it holds the scores of
-L2-normalised features quantised at scale 127 (|score| < 131^2 for d <= 64),
-which is the regime the paper uses it in.
+2^54 with p = 1 (mod 2N), N = 4096.  The plaintext modulus t = 4169729 is the
+smallest prime = 1 (mod 2N) above 2 * 128 * 127^2, so that every score
+|<q, p_j>| <= d 127^2 of a d <= 128 int8 search stays below t/2 (Sec. 3.2: the
+plaintext ring must hold the result of the computation).  The paper's own
+t = 1032193 (Sec. 4.1), also = 1 (mod 2N), is the second plaintext modulus: it
+holds the scores of L2-normalised features quantised at scale 127
+(|score| < 131^2 for d <= 64), which is the regime the paper uses it in.
+
+Search basis.  The exact ciphertext product of Alg 5, summed over the d
+dimensions, is computed in a basis private to the library: the eight largest
+primes r_0 > ... > r_7 below 2^30 with r = 1 (mod 2N), M = r_0 ... r_7
+(about 2^240).  Both operands are centred lifts, |x| <= q/2, so the sum X of
+d <= 512 negacyclic products has |X| <= d N q^2 / 2 < 2^236.  Scale-and-round
+and the return to mod q use X' = X + H with H = q 2^129 (a multiple of q),
+which lies in [0.06 M, 0.19 M]: the CRT sum of X' then wraps M a number of
+times alpha that a 60-bit fixed-point sum of y_i / r_i decides exactly.
+Residues of the basis are below 2^30, so a resident value is one centred
+int32 and a product of two is below 2^58.
 
 Roots.  For t the 2N-th root psi_t is the smallest x >= 2 with x^N = -1: it
 fixes which evaluation point psi_t^(2j+1) each plaintext slot j is.  For the
-RNS primes any primitive 2N-th root serves (their NTT domain never leaves the
-library); psi = x^((p-1)/2N) for the first x that gives one.
+other primes any primitive 2N-th root serves (their NTT domain never leaves
+the library); psi = x^((p-1)/2N) for the first x that gives one.
 
 The chi table (truncated discrete Gaussian, sigma 3.2, |e| <= 19) is computed
 with 80-digit decimal arithmetic.  Run `python gen_consts.py` to rewrite the
@@ -117,80 +126,128 @@ def mixed_radix(x, radices):
     return digs
 
 
+def columns(x, n, bits=27):
+    """x as n digits of `bits` bits, least significant first (x < 2^(n bits))."""
+    assert 0 <= x < 1 << (n * bits)
+    return [(x >> (bits * i)) & ((1 << bits) - 1) for i in range(n)]
+
+
+def shoup32(w, p):
+    return (w << 32) // p
+
+
 def build():
-    primes = ntt_primes(5)
-    q1, q2, p1, p2, p3 = primes
+    q1, q2 = ntt_primes(2)
     q = q1 * q2
-    P = p1 * p2 * p3
-    mods = primes + [T, T_PAPER]
+    R = ntt_primes(8, bits=30)
+    M = 1
+    for r in R:
+        M *= r
+    H = q << 129
+    mods = [q1, q2, T, T_PAPER]
     assert is_prime(T) and T % (2 * N) == 1 and T > 2 * 128 * 127 ** 2
     assert is_prime(T_PAPER) and T_PAPER % (2 * N) == 1
     C = []  # (name, value) scalar uint64 constants
     arrays = []  # (name, list)
 
     arrays.append(("MOD", mods))
-    psis = [first_psi(p) for p in primes] + [smallest_psi(T), smallest_psi(T_PAPER)]
+    psis = [first_psi(p) for p in (q1, q2)] + [smallest_psi(T), smallest_psi(T_PAPER)]
     arrays.append(("PSI", psis))
     arrays.append(("NINV", [pow(N, -1, p) for p in mods]))
     arrays.append(("NINV_S", [shoup(pow(N, -1, p), p) for p in mods]))
     arrays.append(("ONE_S", [shoup(1, p) for p in mods]))              # floor(2^64 / p)
-    arrays.append(("BARRETT", [(1 << 108) // p for p in primes]))     # floor(2^108 / p)
-    arrays.append(("OFF63", [p * ((1 << 63) // p) for p in primes]))  # multiple of p just below 2^63
-    arrays.append(("R27", [(1 << 27) % p for p in mods]))
-    arrays.append(("R27_S", [shoup((1 << 27) % p, p) for p in mods]))
-    arrays.append(("R54", [(1 << 54) % p for p in mods]))
-    arrays.append(("R54_S", [shoup((1 << 54) % p, p) for p in mods]))
+    arrays.append(("BARRETT", [(1 << 108) // p for p in (q1, q2)]))   # floor(2^108 / p)
 
-    # base extension Q -> {q1, q2, p1, p2, p3} of a centred x in (-q/2, q/2)
+    # lift of a residue pair (mod q1, q2) to x = x1 + q1 h in [0, q) (Garner)
     C.append(("Q1INV_Q2", pow(q1, -1, q2)))
     C.append(("Q1INV_Q2_S", shoup(pow(q1, -1, q2), q2)))
     half_q = (q - 1) // 2
     C.append(("HALFQ_LO", half_q % q1))
     C.append(("HALFQ_HI", half_q // q1))
-    arrays.append(("Q1_MOD", [q1 % p for p in primes]))
-    arrays.append(("Q1_MOD_S", [shoup(q1 % p, p) for p in primes]))
-    arrays.append(("Q_MOD", [q % p for p in primes]))
+    C.append(("Q_LO", q & ((1 << 64) - 1)))
+    C.append(("Q_HI", q >> 64))
 
-    # exact scale-and-round round(t X / q), with P
-    arrays.append(("QINV_P", [pow(q, -1, p) for p in (p1, p2, p3)]))
-    arrays.append(("QINV_P_S", [shoup(pow(q, -1, p), p) for p in (p1, p2, p3)]))
-    C.append(("P1INV_P2", pow(p1, -1, p2)))
-    C.append(("P1INV_P2_S", shoup(pow(p1, -1, p2), p2)))
-    C.append(("P1INV_P3", pow(p1, -1, p3)))
-    C.append(("P1INV_P3_S", shoup(pow(p1, -1, p3), p3)))
-    C.append(("P2INV_P3", pow(p2, -1, p3)))
-    C.append(("P2INV_P3_S", shoup(pow(p2, -1, p3), p3)))
-    half_P = (P - 1) // 2
-    z = mixed_radix(half_P, (p1, p2, p3))
-    assert z[0] + p1 * z[1] + p1 * p2 * z[2] == half_P
-    C.append(("HALFP_D1", z[0]))
-    C.append(("HALFP_D2", z[1]))
-    C.append(("HALFP_D3", z[2]))
-    arrays.append(("P1_MOD_Q", [p1 % x for x in (q1, q2)]))
-    arrays.append(("P1_MOD_Q_S", [shoup(p1 % x, x) for x in (q1, q2)]))
-    arrays.append(("P1P2_MOD_Q", [(p1 * p2) % x for x in (q1, q2)]))
-    arrays.append(("P1P2_MOD_Q_S", [shoup((p1 * p2) % x, x) for x in (q1, q2)]))
-    arrays.append(("P_MOD_Q", [P % x for x in (q1, q2)]))
+    # search basis r_0..r_7: NTT and reduction constants
+    arrays.append(("SMOD", R))
+    arrays.append(("SPSI", [first_psi(r) for r in R]))
+    arrays.append(("SNINV", [pow(N, -1, r) for r in R]))
+    arrays.append(("SNINV_S", [shoup32(pow(N, -1, r), r) for r in R]))   # floor(w 2^32 / r)
+    arrays.append(("SMU", [(1 << 64) // r for r in R]))                  # Barrett, 64-bit inputs
+    arrays.append(("SR32", [(1 << 32) % r for r in R]))                  # partial folds
+    arrays.append(("SOFF63", [r * ((1 << 63) // r) for r in R]))         # multiple of r just below 2^63
+    # extension: x mod r from the lift (x1, h, sign): (q1 mod r), (q mod r)
+    arrays.append(("Q1_MOD_R", [q1 % r for r in R]))
+    arrays.append(("Q1_MOD_R_S", [shoup32(q1 % r, r) for r in R]))
+    arrays.append(("Q_MOD_R", [q % r for r in R]))
+    # CRT of X' = X + H: y_i = x_i Minv_i + HM_i (mod r_i), alpha = floor(sum y_i phi_i / 2^60)
+    minv = [pow(M // r, -1, r) for r in R]
+    arrays.append(("MINV", minv))
+    arrays.append(("MINV_S", [shoup32(m, r) for m, r in zip(minv, R)]))
+    arrays.append(("HM", [(H % r) * m % r for m, r in zip(minv, R)]))
+    arrays.append(("PHI", [(1 << 60) // r for r in R]))
+    # X' mod q_j = sum y_i [M_i]_qj - alpha [M]_qj (return of a resident value to mod q)
+    mi_cols = []
+    for r in R:
+        for qj in (q1, q2):
+            mi_cols += columns((M // r) % qj, 2)
+    arrays.append(("MI_Q_COLS", mi_cols))          # [i][j][2] 27-bit digits
+    m_cols = []
+    for qj in (q1, q2):
+        m_cols += columns(M % qj, 2)
+    arrays.append(("M_Q_COLS", m_cols))            # [j][2]
+    C.append(("MU_Q144", (1 << 144) // q))
+    K = (q - 1) // 2 + 8 * q
+    C.append(("KROUND_LO", K & ((1 << 64) - 1)))
+    C.append(("KROUND_HI", K >> 64))
 
     # per plaintext modulus: {t, modulus index, q1 mod t, q mod t, q^-1 mod t
-    # (decryption: pt = [-r q^-1]_t with r = [t v]_q centred), t mod p and its
-    # Shoup companion for the five RNS primes (t x in scale-and-round and
-    # decryption), Delta = floor(q / t) mod q_l and companions (encryption)}
+    # (decryption: pt = [-r q^-1]_t with r = [t v]_q centred), t mod q_l and
+    # its Shoup companion (decryption), Delta = floor(q / t) mod q_l and
+    # companions (encryption), and the scale-and-round tables: with
+    # t M_i = A_i q + B_i and t M = A_M q + B_M, the 27-bit digits of B_i, B_M
+    # and of A_i, A_M mod q_j, and D_j = [8 + t 2^129]_qj}
     plains = []
-    for idx, t in ((5, T), (6, T_PAPER)):
+    for idx, t in ((2, T), (3, T_PAPER)):
         delta = q // t
-        plains.append("{ %dULL, %d, %dULL, %dULL, %dULL, { %s }, { %s }, { %s }, { %s } }" % (
-            t, idx, q1 % t, q % t, pow(q % t, -1, t),
-            ", ".join(f"{t % p}ULL" for p in primes),
-            ", ".join(f"{shoup(t % p, p)}ULL" for p in primes),
-            ", ".join(f"{delta % x}ULL" for x in (q1, q2)),
-            ", ".join(f"{shoup(delta % x, x)}ULL" for x in (q1, q2))))
+        b_cols, a_cols = [], []
+        for r in R:
+            A, B = divmod(t * (M // r), q)
+            b_cols += columns(B, 4)
+            for qj in (q1, q2):
+                a_cols += columns(A % qj, 2)
+        AM, BM = divmod(t * M, q)
+        am_cols = []
+        for qj in (q1, q2):
+            am_cols += columns(AM % qj, 2)
+        dj = [(8 + (t << 129)) % qj for qj in (q1, q2)]
+        u32 = lambda xs: ", ".join(f"{x}u" for x in xs)
+        plains.append(
+            "{ %dULL, %d, %dULL, %dULL, %dULL, { %s }, { %s }, { %s }, { %s }, { %s }, { %s }, { %s }, { %s }, { %s } }" % (
+                t, idx, q1 % t, q % t, pow(q % t, -1, t),
+                ", ".join(f"{t % x}ULL" for x in (q1, q2)),
+                ", ".join(f"{shoup(t % x, x)}ULL" for x in (q1, q2)),
+                ", ".join(f"{delta % x}ULL" for x in (q1, q2)),
+                ", ".join(f"{shoup(delta % x, x)}ULL" for x in (q1, q2)),
+                u32(b_cols), u32(columns(BM, 4)), u32(a_cols), u32(am_cols),
+                ", ".join(f"{x}ULL" for x in dj)))
     arrays.append(("PLAIN", plains))
 
     # sanity of the ranges the kernels rely on
-    assert q1 > q2 > p1 > p2 > p3 and q1 < 2 * p3
-    assert q.bit_length() == 108 and P.bit_length() == 162
-    assert (q * P).bit_length() == 270
+    assert q1 > q2 and q.bit_length() == 108 and q > 1 << 107
+    assert all(r < 1 << 30 and r > 1 << 29 for r in R) and len(set(R)) == 8
+    assert max(R) < 2 * min(R)  # a residue mod r_i is reduced mod r_k by one subtraction
+    xmax = 512 * N * q * q // 2  # |X| for d <= 512
+    assert H - xmax > M // 16 and H + xmax < M // 5  # X'/M in [1/16, 1/5]
+    # alpha from 60-bit fixed point: error below 2^-27, far inside the margins above
+    assert sum(((1 << 60) // r) * (r - 1) for r in R) < 1 << 64
+    # scale-and-round magnitudes: column sums below 2^61, R below 2^142
+    assert 8 * (1 << 30) * (1 << 27) < 1 << 61
+    assert 8 * (1 << 30) * q + K < 1 << 142
+    assert (1 << 144) // q < 1 << 37
+    # tensor: centred residues below 2^29, products below 2^58; a partial fold
+    # leaves |s| < 2^61 + 2^32, then 8 dimensions add below 2^62 (middle term)
+    assert all((r - 1) // 2 < 1 << 29 for r in R)
+    assert (1 << 61) + (1 << 32) + 8 * (1 << 59) < 1 << 63
 
     cdt = chi_cdt()
     return mods, psis, C, arrays, cdt
@@ -205,10 +262,11 @@ def header():
          "namespace hers {",
          f"constexpr int N = {N};",
          f"constexpr int LOGN = {LOGN};",
-         "constexpr int NUM_RNS = 5;     /* q1, q2, p1, p2, p3 */",
-         "constexpr int MOD_T = 5;       /* index of the default t in the modulus arrays */",
-         "constexpr int MOD_T_PAPER = 6; /* index of the paper's t */",
-         "constexpr int NUM_MODS = 7;",
+         "constexpr int NUM_Q = 2;       /* q1, q2 */",
+         "constexpr int MOD_T = 2;       /* index of the default t in the modulus arrays */",
+         "constexpr int MOD_T_PAPER = 3; /* index of the paper's t */",
+         "constexpr int NUM_MODS = 4;",
+         "constexpr int NUM_S = 8;       /* search basis r_0 .. r_7 */",
          "constexpr int CHI_MIN = -19;",
          "constexpr int CHI_LEN = 38;",
          ""]

@@ -6,6 +6,8 @@
 
 #include <vector>
 
+#include "hers_consts.h"
+
 // The opaque context handle of include/hers.h.
 struct hers_ctx {
     int device;
@@ -21,6 +23,13 @@ struct hers_ctx {
 };
 
 namespace hers {
+
+// 64-bit words of the resident form per (gallery block, dimension): two
+// polynomials of N int32 residues for each of the NUM_S primes of the search basis.
+constexpr uint64_t RES_WORDS_PER_DIM = (uint64_t)NUM_S * N;
+// Words of a context's twiddle tables: NUM_MODS moduli x (forward, inverse) x
+// N pairs of 64-bit words, then NUM_S x 2 x N pairs of 32-bit words.
+constexpr uint64_t TW_WORDS = (uint64_t)NUM_MODS * 4 * N + (uint64_t)NUM_S * 2 * N;
 
 // Key material in device memory (all uint64 unless noted):
 //   sk        int8 [N]                  ternary secret
@@ -85,11 +94,13 @@ cudaError_t launch_encrypt(const uint64_t* tw, const DevKeys& k, const int8_t* f
 // out[c] += add[c] mod q for nct canonical ciphertexts.
 cudaError_t launch_ct_add(uint64_t* out, const uint64_t* add, uint64_t nct, cudaStream_t st);
 // Canonical ciphertexts of block b (d of them) recovered from the resident
-// form (inverse NTT of the q1, q2 limbs), plus add[i] mod q, into out[i].
+// form (inverse NTTs and the CRT of the search basis), plus add[i] mod q,
+// into out[i].
 cudaError_t launch_resident_to_canonical_add(const uint64_t* tw, const uint64_t* resident, uint64_t b,
                                              uint32_t d, const uint64_t* add, uint64_t* out, cudaStream_t st);
 // Canonical cts ct[0 .. nct) (global indices ct_begin ..) of dimension d into
-// the resident form at `out` (the base of block 0).
+// the resident form at `out` (the base of block 0; RES_WORDS_PER_DIM words per
+// (block, dimension)).
 cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t ct_begin,
                               uint32_t d, uint64_t* out, cudaStream_t st);
 cudaError_t launch_decrypt(const uint64_t* tw, const DevKeys& k, const uint64_t* scores_ct,
@@ -110,7 +121,8 @@ cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* 
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
                           uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev = nullptr,
                           int variant = DEFAULT_TENSOR_VARIANT, const KeySwitchW* ksw = nullptr);
-// Epilogue over npairs accumulators X [npairs][3][5][N]; workspace C, KS as in
+// Epilogue over npairs accumulators X (uint32 [npairs][3][NUM_S][N] at the
+// start of the X area, 15 N words per pair); workspace C, KS as in
 // launch_search; `ev` (optional) receives the boundaries after the inverse
 // NTTs (ev[0]) and after scale-and-round (ev[1]).
 // With ksw, the key switch uses the base-w gadget: its digits [npairs][ndig]
@@ -118,9 +130,9 @@ cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* 
 cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npairs, uint64_t* X,
                             uint64_t* C, uint64_t* KS, uint64_t* out, cudaStream_t st,
                             cudaEvent_t* ev = nullptr, const KeySwitchW* ksw = nullptr);
-// The tensor kernel alone, into X [nblocks][3][5][N].
+// The tensor kernel alone, into X [nblocks][3][NUM_S][N] (uint32).
 cudaError_t launch_tensor(int variant, const uint64_t* gallery, uint64_t nblocks, uint32_t d,
-                          const uint64_t* probe, uint64_t* X, int* err, cudaStream_t st);
+                          const uint64_t* probe, uint32_t* X, int* err, cudaStream_t st);
 int tensor_variant_count();
 const char* tensor_variant_name(int v);
 

@@ -297,69 +297,100 @@ cudaError_t launch_ct_add(uint64_t* out, const uint64_t* add, uint64_t nct, cuda
     return cudaGetLastError();
 }
 
-// Grid (2 d polys, 2 limbs).  Polynomial P = 2 i + poly of block b: reads its
-// limb-l values from the resident form, undoes the split storage and the
-// NTT (the resident q limbs are NTT_{q_l} of the canonical residues), adds
-// add[i][poly][l] and writes the canonical residues to out[i][poly][l].
-__global__ void __launch_bounds__(NTT_THREADS, 3) k_resident_to_canonical_add(
+// One CTA per polynomial P = 2 i + poly of block b: reads its eight limbs
+// from the resident form (centred values, NTT domain over the search basis),
+// undoes the NTTs, recovers the canonical residues mod q1, q2 by the CRT of
+// the search basis (the resident value is the centred lift x, |x| < q/2, so
+// x' = x + q 2^129 is in range and x' = x mod q), adds add[i][poly][l] and
+// writes out[i][poly][l].
+constexpr int R2C_SMEM = NUM_S * N * 4;
+__global__ void __launch_bounds__(NTT_THREADS, 1) k_resident_to_canonical_add(
     const uint64_t* __restrict__ tw, const uint64_t* __restrict__ resident, uint64_t b, uint32_t d,
     const uint64_t* __restrict__ add, uint64_t* __restrict__ out) {
-    extern __shared__ uint64_t sm[];
+    extern __shared__ uint32_t sm32[];
     const uint32_t i = blockIdx.x >> 1;
-    const int poly = (int)(blockIdx.x & 1), limb = blockIdx.y;
-    for (int k = threadIdx.x; k < N; k += blockDim.x)
-        sm[swz(k)] = split_load(resident[resident_offset(b, limb, k, d, i, poly)], c_mod[limb]);
-    ntt_inv_mod(sm, tw, limb);
-    const uint64_t q = c_mod[limb];
-    const size_t row = (((size_t)i * 2 + poly) * 2 + limb) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) out[row + k] = add_mod(sm[swz(k)], add[row + k], q);
+    const int poly = (int)(blockIdx.x & 1);
+    const int32_t* res = (const int32_t*)resident;
+    for (int l = 0; l < NUM_S; l++) {
+        uint32_t* s = sm32 + l * N;
+        const uint32_t r = c_smod[l];
+        for (int k = threadIdx.x; k < N; k += blockDim.x)
+            s[swz32(k)] = uncentre32(res[resident_offset(b, l, k, d, i, poly)], r);
+        ntt32_inv_mod(s, tw, l);
+    }
+    const size_t row = (((size_t)i * 2 + poly) * 2) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        uint32_t x[NUM_S], y[NUM_S];
+#pragma unroll
+        for (int l = 0; l < NUM_S; l++) x[l] = sm32[l * N + swz32(k)];
+        const uint32_t alpha = crt_y(x, y);
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            const uint64_t v = crt_combine_q(y, alpha, c_mi_q_cols, c_m_q_cols, j, 0);
+            out[row + j * N + k] = add_mod(v, add[row + j * N + k], c_mod[j]);
+        }
+    }
 }
 
 cudaError_t launch_resident_to_canonical_add(const uint64_t* tw, const uint64_t* resident, uint64_t b,
                                              uint32_t d, const uint64_t* add, uint64_t* out, cudaStream_t st) {
-    k_resident_to_canonical_add<<<dim3(2 * d, 2), NTT_THREADS, N * 8, st>>>(tw, resident, b, d, add, out);
+    cudaError_t e = cudaFuncSetAttribute(k_resident_to_canonical_add, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         R2C_SMEM);
+    if (e != cudaSuccess) return e;
+    k_resident_to_canonical_add<<<2 * d, NTT_THREADS, R2C_SMEM, st>>>(tw, resident, b, d, add, out);
     count_launches(1);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- extension to the search form
 //
-// Grid (2 n polys, 5 limbs).  Reads a canonical ciphertext polynomial
-// (residues mod q1, q2), takes its centred representative x in (-q/2, q/2]
-// (App. A) and writes NTT_{p_l}(x mod p_l) for l = 0..4 in split storage
-// (signed 27-bit digits, see split_store) at the resident (tiled) position of
-// ciphertext ct_begin + P/2 = b d + i.  Exactness of the later tensor product
-// needs the centred lift: the product of two such polynomials over Z, summed
-// over d <= 512 dimensions, stays below q P / 2 (|X| < 2^237).
+// Grid (2 n polys, 2 groups of EXT_LIMBS limbs).  Reads a canonical ciphertext
+// polynomial (residues mod q1, q2), takes its centred representative x in
+// (-q/2, q/2] (App. A) and writes NTT_{r_l}(x mod r_l) for the group's limbs,
+// as centred int32, at the resident (tiled) position of ciphertext
+// ct_begin + P/2 = b d + i.  Exactness of the later tensor product needs the
+// centred lift: the product of two such polynomials over Z, summed over
+// d <= 512 dimensions, stays below 2^236 < M / 2^4.
+constexpr int EXT_LIMBS = NUM_S / 2;
 __global__ void __launch_bounds__(NTT_THREADS, 3) k_extend_ntt(const uint64_t* __restrict__ tw,
                                                             const uint64_t* __restrict__ ct,
                                                             uint64_t ct_begin, uint32_t d,
                                                             uint64_t* __restrict__ out) {
-    extern __shared__ uint64_t sm[];
+    extern __shared__ uint32_t sm32[];
     const uint64_t P = blockIdx.x;
-    const int limb = blockIdx.y;
+    const int l0 = (int)blockIdx.y * EXT_LIMBS;
     const uint64_t* x1 = ct + (P * 2 + 0) * N;
     const uint64_t* x2 = ct + (P * 2 + 1) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const uint64_t a = x1[k], b = x2[k];
-        sm[swz(k)] = lifted_mod(lift_q(a, b), limb, b);
+        const Lifted L = lift_q(x1[k], x2[k]);
+#pragma unroll
+        for (int g = 0; g < EXT_LIMBS; g++) sm32[g * N + swz32(k)] = lifted_mod_r(L, l0 + g);
     }
-    ntt_fwd_mod(sm, tw, limb);
     const uint64_t c = ct_begin + P / 2;
     const uint64_t blk = c / d;
     const uint32_t i = (uint32_t)(c % d);
     const int poly = (int)(P & 1);
-    for (int k = threadIdx.x; k < N; k += blockDim.x)
-        out[resident_offset(blk, limb, k, d, i, poly)] = split_store(sm[swz(k)], c_mod[limb]);
+    int32_t* o = (int32_t*)out;
+    for (int g = 0; g < EXT_LIMBS; g++) {
+        uint32_t* s = sm32 + g * N;
+        const int l = l0 + g;
+        ntt32_fwd_mod(s, tw, l);
+        const uint32_t r = c_smod[l];
+        for (int k = threadIdx.x; k < N; k += blockDim.x)
+            o[resident_offset(blk, l, k, d, i, poly)] = centre32(s[swz32(k)], r);
+    }
 }
 
 cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t ct_begin,
                               uint32_t d, uint64_t* out, cudaStream_t st) {
+    const int smem = EXT_LIMBS * N * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_extend_ntt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
     const uint64_t chunk = 1u << 30;
     for (uint64_t off = 0; off < 2 * nct; off += chunk) {
         const uint64_t n = 2 * nct - off < chunk ? 2 * nct - off : chunk;
-        k_extend_ntt<<<dim3((unsigned)n, 5), NTT_THREADS, N * 8, st>>>(tw, ct + off * 2 * N,
-                                                                      ct_begin + off / 2, d, out);
+        k_extend_ntt<<<dim3((unsigned)n, NUM_S / EXT_LIMBS), NTT_THREADS, smem, st>>>(tw, ct + off * 2 * N,
+                                                                                       ct_begin + off / 2, d, out);
         count_launches(1);
     }
     return cudaGetLastError();

@@ -135,7 +135,7 @@ void CUDART_CB on_batch_done(void* arg) {
 
 uint64_t request_words(uint32_t d, uint64_t nblocks) {
     // probe cts + prepared probe + X/C/KS + output score cts
-    return (uint64_t)d * 14 * N + nblocks * (SEARCH_WS_WORDS_PER_BLOCK + 4 * N);
+    return (uint64_t)d * (4 * N + RES_WORDS_PER_DIM) + nblocks * (SEARCH_WS_WORDS_PER_BLOCK + 4 * N);
 }
 
 bool ensure_staging(Slot* s, size_t nchunks, size_t nunits) {
@@ -168,13 +168,13 @@ cudaError_t issue_batch(hers_server* srv, Slot* s, std::vector<BatchChunk>& chun
     hers_ctx* ctx = srv->ctx;
     cudaStream_t st = srv->streams[s->index];
     uint64_t* base = (uint64_t*)(srv->pool_base + s->off);
-    // layout: per request [probe cts d*4N][probe d*10N]; then X, C, KS, OUT; then tables
+    // layout: per request [probe cts d*4N][probe d*RES_WORDS_PER_DIM]; then X, C, KS, OUT; then tables
     uint64_t* w = base;
     std::vector<uint64_t*> pct(s->reqs.size());
     for (size_t i = 0; i < s->reqs.size(); i++) {
         const uint32_t d = items[i].d;
         pct[i] = w;
-        w += (uint64_t)d * 14 * N;
+        w += (uint64_t)d * (4 * N + RES_WORDS_PER_DIM);
     }
     uint64_t* X = w;
     uint64_t* C = X + npairs * 15 * N;

@@ -1,8 +1,8 @@
 // Streamed search over a gallery kept in canonical form (two limbs,
 // coefficient domain: 32 d bytes per entry, the ciphertexts' own size) in
-// host or device memory.  This is for galleries too large for the 5-prime
-// resident form: 100M entries at d = 64 are 204.8 GB canonical against
-// 512 GB resident.
+// host or device memory.  This is for galleries too large for the resident
+// form: 100M entries at d = 64 are 204.8 GB canonical against 409.6 GB
+// resident.
 //
 // Per chunk of blocks:
 //   1. copy in (from host memory);
@@ -34,7 +34,7 @@ SlotLayout slot_layout(uint32_t d, uint32_t nprobes, uint32_t chunk, uint64_t ta
     L.staging = w;
     w += (uint64_t)chunk * d * 4 * N;
     L.resident = w;
-    w += (uint64_t)chunk * d * 10 * N;
+    w += (uint64_t)chunk * d * RES_WORDS_PER_DIM;
     const uint64_t pairs = (uint64_t)nprobes * chunk;
     L.X = w;
     w += pairs * 15 * N;
@@ -53,7 +53,7 @@ SlotLayout slot_layout(uint32_t d, uint32_t nprobes, uint32_t chunk, uint64_t ta
 uint64_t table_bytes_for(uint32_t nprobes, uint32_t chunk) {
     // at most one chunk record per probe and one unit per (block, limb, tile, probe)
     return (uint64_t)nprobes * sizeof(BatchChunk) + 256 +
-           (uint64_t)chunk * 5 * NTILES * nprobes * sizeof(BatchUnit) + 256 + 64;
+           (uint64_t)chunk * NUM_S * NTILES * nprobes * sizeof(BatchUnit) + 256 + 64;
 }
 
 }  // namespace

@@ -43,9 +43,9 @@ def test_size_helpers(libhers):
     assert H.hers_ct_bytes() == 2 * 2 * 4096 * 8
     assert H.hers_blocks_for(1) == 1 and H.hers_blocks_for(4096) == 1
     assert H.hers_blocks_for(4097) == 2 and H.hers_blocks_for(100_000_000) == 24415
-    # resident gallery: 2 polys x 5 limbs x N words per (block, dimension)
-    assert H.hers_gallery_bytes(256, 64) == 256 * 64 * 10 * 4096 * 8
-    assert H.hers_probe_bytes(64) == 64 * 10 * 4096 * 8
+    # resident gallery: 2 polys x 8 limbs x N int32 per (block, dimension)
+    assert H.hers_gallery_bytes(256, 64) == 256 * 64 * 2 * 8 * 4096 * 4
+    assert H.hers_probe_bytes(64) == 64 * 2 * 8 * 4096 * 4
 
 
 def test_status_strings_and_param_check(libhers):

@@ -46,7 +46,7 @@ def env():
 
 def alone(env, gi, b0, b1, probe_idx):
     g, nb, d, _ = env["gals"][gi]
-    view = g[b0 * 10 * d * N:]
+    view = g[b0 * H.hers_gallery_bytes(1, d) // 8:]
     out = H.hers_search(env["ctx"], env["keys"], view, b1 - b0, d, env["probes"][probe_idx][2])
     torch.cuda.synchronize()
     return out.cpu().numpy()
