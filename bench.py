@@ -85,7 +85,8 @@ def parse():
                          "of the first probes)")
     ap.add_argument("--batch-variant", default=None,
                     help="batched: kernel shape by name (skips the batched autotuner); "
-                         "scale: the streamed search's kernel shape (default np4_nb1_s2_d4_m2)")
+                         "scale and serving: the kernel shape of the streamed search / the server's "
+                         "batches (defaults np4_nb1_s2_d4_m2 / np2_nb2_s2_d4_m3)")
     ap.add_argument("--variant", default=None,
                     help="tensor-kernel shape by name (skips the autotuner), e.g. nb2_s3_d4_m3")
     return ap.parse_args()
@@ -389,6 +390,10 @@ def run_gpu(args):
     H.hers_trace_enable(ctx, 0)
     clk = clocks.stop()
 
+    # the plain step's score ciphertexts: the e2e results below must equal them
+    # (the re-randomised and base-w steps write other, equally valid, ciphertexts)
+    sc_plain = sc.clone()
+
     # the same step with output re-randomisation (Enc(0) added per block)
     def step_rerand():
         H.hers_probe_prepare(ctx, pct, out=pr)
@@ -449,7 +454,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = dist.max(time.perf_counter() - t0, dev)
     dist.barrier()
-    e2e_ok = all(bool(np.array_equal(h.numpy(), sc.cpu().numpy())) for h in sc_host)
+    e2e_ok = all(bool(np.array_equal(h.numpy(), sc_plain.cpu().numpy())) for h in sc_host)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -457,7 +462,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_sync_s = dist.max(time.perf_counter() - t0, dev)
     dist.barrier()
-    e2e_ok = e2e_ok and bool(np.array_equal(sc_host[0].numpy(), sc.cpu().numpy()))
+    e2e_ok = e2e_ok and bool(np.array_equal(sc_host[0].numpy(), sc_plain.cpu().numpy()))
+    if not e2e_ok:
+        raise SystemExit("the host-buffer search does not equal the device search bit for bit")
 
     entries_total = m * world * args.steps
     value = entries_total / (ms_total / 1e3)
@@ -481,9 +488,9 @@ def run_gpu(args):
     if os.path.exists(prof):
         try:
             tj = json.load(open(prof))
-            if (tj.get("variant") == variant_name and tj.get("d") == d
-                    and tj.get("resident_form") == RESIDENT_FORM):
-                traffic = tj["bytes_per_block"] * nb + tj.get("bytes_fixed", 0)
+            cap = tj.get("captures", {}).get(variant_name)
+            if cap and tj.get("d") == d and tj.get("resident_form") == RESIDENT_FORM:
+                traffic = cap["bytes_per_block"] * nb + cap.get("bytes_fixed", 0)
         except (OSError, ValueError, KeyError):
             traffic = None
 
@@ -710,7 +717,9 @@ def run_serving(args):
             probes[gi].append(pct.cpu().pin_memory())
     free_b, _ = torch.cuda.mem_get_info(dev)
     pool = max(1 << 30, free_b - (8 << 30))
-    srv = H.Server(ctx, keys, gals, workspace_bytes=pool, max_batch=16, variant=1)
+    sv_name = args.batch_variant or "np2_nb2_s2_d4_m3"
+    srv = H.Server(ctx, keys, gals, workspace_bytes=pool, max_batch=16,
+                   variant=H.hers_batch_variants().index(sv_name))
     # pinned host arena for score ciphertexts, handed out as a ring
     ct_bytes = 4 * N * 8
     arena_blocks = 4 * nblocks * 16
@@ -794,7 +803,7 @@ def run_serving(args):
            "config": {"galleries": "3 x 10,000,000 entries (2,442 blocks) at d = 32, 64, 128",
                       "resident_gallery_bytes": resident, "pool_bytes": st["pool_bytes"],
                       "request_size_entries": "uniform [10k, 10M]", "max_batch": 16,
-                      "setup_s": setup_s},
+                      "batch_variant": sv_name, "setup_s": setup_s},
            "value": max(r["entries_per_s"] for r in results), "higher_is_better": True,
            "rates": results, "server": st,
            "plain_sequential": {"requests": len(reqs), "entries_per_s": plain_entries / plain_s,

@@ -271,9 +271,9 @@ struct BatchVariant {
 #define HERS_BV(NP, NB, S, D, M) \
     {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M, k_tensor_batched<NP, NB, S, D, M>, NP, NB, S, D, M}
 static const BatchVariant kBatchVariants[] = {
-    HERS_BV(1, 2, 4, 4, 2), HERS_BV(2, 1, 4, 4, 2), HERS_BV(2, 2, 3, 4, 2), HERS_BV(2, 2, 4, 2, 2),
+    HERS_BV(1, 2, 4, 4, 2), HERS_BV(2, 2, 2, 4, 3), HERS_BV(2, 2, 3, 4, 2), HERS_BV(2, 2, 4, 2, 2),
     HERS_BV(4, 1, 2, 4, 2), HERS_BV(4, 2, 2, 4, 2), HERS_BV(4, 2, 3, 2, 2), HERS_BV(2, 1, 3, 4, 3),
-    HERS_BV(1, 1, 4, 4, 3), HERS_BV(2, 2, 2, 4, 3), HERS_BV(4, 1, 4, 2, 2), HERS_BV(1, 2, 3, 4, 3),
+    HERS_BV(1, 1, 4, 4, 3), HERS_BV(2, 1, 4, 4, 2), HERS_BV(4, 1, 4, 2, 2), HERS_BV(1, 2, 3, 4, 3),
 };
 #undef HERS_BV
 constexpr int NUM_BATCH_VARIANTS = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);

@@ -552,8 +552,11 @@ __device__ __forceinline__ void gs_phase32(uint32_t v[16], int base, const uint2
     }
 }
 
-__device__ __forceinline__ void ntt32_fwd_smem(uint32_t* sm, const uint2* __restrict__ w, uint32_t r) {
-    const int t = threadIdx.x;
+// t: the calling thread's index among the NTT_THREADS threads that run the
+// transform (a CTA may run several transforms side by side, one per group of
+// NTT_THREADS threads; every group takes the same path through the barriers).
+__device__ __forceinline__ void ntt32_fwd_smem(uint32_t* sm, const uint2* __restrict__ w, uint32_t r,
+                                               int t = threadIdx.x) {
     uint32_t v[16];
     __syncthreads();
     {
@@ -586,8 +589,7 @@ __device__ __forceinline__ void ntt32_fwd_smem(uint32_t* sm, const uint2* __rest
 }
 
 __device__ __forceinline__ void ntt32_inv_smem(uint32_t* sm, const uint2* __restrict__ w, uint32_t r,
-                                               uint32_t ninv, uint32_t ninv_s) {
-    const int t = threadIdx.x;
+                                               uint32_t ninv, uint32_t ninv_s, int t = threadIdx.x) {
     uint32_t v[16];
     __syncthreads();
     {
@@ -619,11 +621,11 @@ __device__ __forceinline__ void ntt32_inv_smem(uint32_t* sm, const uint2* __rest
     __syncthreads();
 }
 
-__device__ __forceinline__ void ntt32_fwd_mod(uint32_t* a, const uint64_t* tw, int i) {
-    ntt32_fwd_smem(a, tw32_fwd(tw, i), c_smod[i]);
+__device__ __forceinline__ void ntt32_fwd_mod(uint32_t* a, const uint64_t* tw, int i, int t = threadIdx.x) {
+    ntt32_fwd_smem(a, tw32_fwd(tw, i), c_smod[i], t);
 }
-__device__ __forceinline__ void ntt32_inv_mod(uint32_t* a, const uint64_t* tw, int i) {
-    ntt32_inv_smem(a, tw32_inv(tw, i), c_smod[i], c_sninv[i], c_sninv_s[i]);
+__device__ __forceinline__ void ntt32_inv_mod(uint32_t* a, const uint64_t* tw, int i, int t = threadIdx.x) {
+    ntt32_inv_smem(a, tw32_inv(tw, i), c_smod[i], c_sninv[i], c_sninv_s[i], t);
 }
 
 // ---------------------------------------------------------------- mbarrier + bulk async copy (TMA engine)

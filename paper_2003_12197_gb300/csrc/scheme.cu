@@ -299,24 +299,27 @@ cudaError_t launch_ct_add(uint64_t* out, const uint64_t* add, uint64_t nct, cuda
 
 // One CTA per polynomial P = 2 i + poly of block b: reads its eight limbs
 // from the resident form (centred values, NTT domain over the search basis),
-// undoes the NTTs, recovers the canonical residues mod q1, q2 by the CRT of
-// the search basis (the resident value is the centred lift x, |x| < q/2, so
-// x' = x + q 2^129 is in range and x' = x mod q), adds add[i][poly][l] and
-// writes out[i][poly][l].
+// undoes the NTTs (R2C_GROUPS groups of NTT_THREADS threads, each for
+// NUM_S / R2C_GROUPS limbs), recovers the canonical residues mod q1, q2 by the
+// CRT of the search basis (the resident value is the centred lift x,
+// |x| < q/2, so x' = x + q 2^129 is in range and x' = x mod q), adds
+// add[i][poly][l] and writes out[i][poly][l].
+constexpr int R2C_GROUPS = 4;
 constexpr int R2C_SMEM = NUM_S * N * 4;
-__global__ void __launch_bounds__(NTT_THREADS, 1) k_resident_to_canonical_add(
+__global__ void __launch_bounds__(NTT_THREADS * R2C_GROUPS, 1) k_resident_to_canonical_add(
     const uint64_t* __restrict__ tw, const uint64_t* __restrict__ resident, uint64_t b, uint32_t d,
     const uint64_t* __restrict__ add, uint64_t* __restrict__ out) {
     extern __shared__ uint32_t sm32[];
     const uint32_t i = blockIdx.x >> 1;
     const int poly = (int)(blockIdx.x & 1);
     const int32_t* res = (const int32_t*)resident;
-    for (int l = 0; l < NUM_S; l++) {
+    const int grp = threadIdx.x / NTT_THREADS, t = threadIdx.x % NTT_THREADS;
+    for (int lg = 0; lg < NUM_S / R2C_GROUPS; lg++) {
+        const int l = grp * (NUM_S / R2C_GROUPS) + lg;
         uint32_t* s = sm32 + l * N;
         const uint32_t r = c_smod[l];
-        for (int k = threadIdx.x; k < N; k += blockDim.x)
-            s[swz32(k)] = uncentre32(res[resident_offset(b, l, k, d, i, poly)], r);
-        ntt32_inv_mod(s, tw, l);
+        for (int k = t; k < N; k += NTT_THREADS) s[swz32(k)] = uncentre32(res[resident_offset(b, l, k, d, i, poly)], r);
+        ntt32_inv_mod(s, tw, l, t);
     }
     const size_t row = (((size_t)i * 2 + poly) * 2) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
@@ -337,60 +340,60 @@ cudaError_t launch_resident_to_canonical_add(const uint64_t* tw, const uint64_t*
     cudaError_t e = cudaFuncSetAttribute(k_resident_to_canonical_add, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          R2C_SMEM);
     if (e != cudaSuccess) return e;
-    k_resident_to_canonical_add<<<2 * d, NTT_THREADS, R2C_SMEM, st>>>(tw, resident, b, d, add, out);
+    k_resident_to_canonical_add<<<2 * d, NTT_THREADS * R2C_GROUPS, R2C_SMEM, st>>>(tw, resident, b, d, add, out);
     count_launches(1);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- extension to the search form
 //
-// Grid (2 n polys, 2 groups of EXT_LIMBS limbs).  Reads a canonical ciphertext
-// polynomial (residues mod q1, q2), takes its centred representative x in
-// (-q/2, q/2] (App. A) and writes NTT_{r_l}(x mod r_l) for the group's limbs,
-// as centred int32, at the resident (tiled) position of ciphertext
-// ct_begin + P/2 = b d + i.  Exactness of the later tensor product needs the
-// centred lift: the product of two such polynomials over Z, summed over
-// d <= 512 dimensions, stays below 2^236 < M / 2^4.
-constexpr int EXT_LIMBS = NUM_S / 2;
-__global__ void __launch_bounds__(NTT_THREADS, 3) k_extend_ntt(const uint64_t* __restrict__ tw,
-                                                            const uint64_t* __restrict__ ct,
-                                                            uint64_t ct_begin, uint32_t d,
-                                                            uint64_t* __restrict__ out) {
+// One CTA per canonical ciphertext polynomial P (residues mod q1, q2): takes
+// its centred representative x in (-q/2, q/2] (App. A) once per coefficient,
+// reduces it mod every prime of the search basis, and writes NTT_{r_l}(x mod
+// r_l), as centred int32, at the resident (tiled) position of ciphertext
+// ct_begin + P/2 = b d + i.  EXT_GROUPS groups of NTT_THREADS threads run
+// NUM_S / EXT_GROUPS of the transforms each.  Exactness of the later tensor
+// product needs the centred lift: the product of two such polynomials over
+// Z, summed over d <= 512 dimensions, stays below 2^236 < M / 2^4.
+constexpr int EXT_GROUPS = 4;
+constexpr int EXT_SMEM = NUM_S * N * 4;
+__global__ void __launch_bounds__(NTT_THREADS * EXT_GROUPS, 1) k_extend_ntt(const uint64_t* __restrict__ tw,
+                                                                          const uint64_t* __restrict__ ct,
+                                                                          uint64_t ct_begin, uint32_t d,
+                                                                          uint64_t* __restrict__ out) {
     extern __shared__ uint32_t sm32[];
     const uint64_t P = blockIdx.x;
-    const int l0 = (int)blockIdx.y * EXT_LIMBS;
     const uint64_t* x1 = ct + (P * 2 + 0) * N;
     const uint64_t* x2 = ct + (P * 2 + 1) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const Lifted L = lift_q(x1[k], x2[k]);
 #pragma unroll
-        for (int g = 0; g < EXT_LIMBS; g++) sm32[g * N + swz32(k)] = lifted_mod_r(L, l0 + g);
+        for (int l = 0; l < NUM_S; l++) sm32[l * N + swz32(k)] = lifted_mod_r(L, l);
     }
     const uint64_t c = ct_begin + P / 2;
     const uint64_t blk = c / d;
     const uint32_t i = (uint32_t)(c % d);
     const int poly = (int)(P & 1);
     int32_t* o = (int32_t*)out;
-    for (int g = 0; g < EXT_LIMBS; g++) {
-        uint32_t* s = sm32 + g * N;
-        const int l = l0 + g;
-        ntt32_fwd_mod(s, tw, l);
+    const int grp = threadIdx.x / NTT_THREADS, t = threadIdx.x % NTT_THREADS;
+    for (int lg = 0; lg < NUM_S / EXT_GROUPS; lg++) {
+        const int l = grp * (NUM_S / EXT_GROUPS) + lg;
+        uint32_t* s = sm32 + l * N;
+        ntt32_fwd_mod(s, tw, l, t);  // begins with a CTA barrier: the lift above is complete
         const uint32_t r = c_smod[l];
-        for (int k = threadIdx.x; k < N; k += blockDim.x)
-            o[resident_offset(blk, l, k, d, i, poly)] = centre32(s[swz32(k)], r);
+        for (int k = t; k < N; k += NTT_THREADS) o[resident_offset(blk, l, k, d, i, poly)] = centre32(s[swz32(k)], r);
     }
 }
 
 cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t ct_begin,
                               uint32_t d, uint64_t* out, cudaStream_t st) {
-    const int smem = EXT_LIMBS * N * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_extend_ntt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_extend_ntt, cudaFuncAttributeMaxDynamicSharedMemorySize, EXT_SMEM);
     if (e != cudaSuccess) return e;
     const uint64_t chunk = 1u << 30;
     for (uint64_t off = 0; off < 2 * nct; off += chunk) {
         const uint64_t n = 2 * nct - off < chunk ? 2 * nct - off : chunk;
-        k_extend_ntt<<<dim3((unsigned)n, NUM_S / EXT_LIMBS), NTT_THREADS, smem, st>>>(tw, ct + off * 2 * N,
-                                                                                       ct_begin + off / 2, d, out);
+        k_extend_ntt<<<(unsigned)n, NTT_THREADS * EXT_GROUPS, EXT_SMEM, st>>>(tw, ct + off * 2 * N,
+                                                                              ct_begin + off / 2, d, out);
         count_launches(1);
     }
     return cudaGetLastError();
