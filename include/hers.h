@@ -119,8 +119,10 @@ int hers_keys_export(hers_ctx* ctx, const hers_keys* keys, int8_t* sk, uint64_t*
  * becomes the plaintext whose slot j holds feats[b N + j][i] (0 past m),
  * encrypted with randomness stream obj = b d + i.
  * gallery: device, hers_gallery_bytes(ceil(m/N), d) bytes: the resident form
- *   the search streams (NTT domain, extended to the 5-prime basis q1 q2 p1 p2 p3),
- *   or NULL to write the canonical cts only (for hers_search_stream).
+ *   the search streams (the centred lift of every ciphertext coefficient, in
+ *   the NTT domain of each of the library's eight 30-bit search primes, one
+ *   int32 per residue; the layout is private to the library), or NULL to
+ *   write the canonical cts only (for hers_search_stream).
  * gallery_ct: device uint64 [ceil(m/N)][d][2][2][N] canonical cts, or NULL
  *   (at least one of gallery, gallery_ct is non-NULL).
  * Asynchronous on stream; sampler failures are reported by the next
@@ -225,7 +227,7 @@ int hers_search_rerand(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gal
  * passes the gallery, the probe and scores_ct (device, [nblocks][2][2][N]).
  *  - nblocks above HERS_NOALLOC_MAX_BLOCKS is rejected with HERS_E_INVAL.
  *    Larger galleries are searched by calling once per range of at most
- *    that many blocks: gallery + b*d*10*N words, scores_ct + b*4*N words.
+ *    that many blocks: gallery + b*hers_gallery_bytes(1, d)/8 words, scores_ct + b*4*N words.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current.  Make that first call
  *    before any stream capture.
