@@ -12,9 +12,11 @@ The functions keep the C names:
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 import threading
+import weakref
 
 N = 4096
 MAX_D = 512
@@ -29,6 +31,31 @@ _lib = None
 
 class HersError(RuntimeError):
     pass
+
+
+# Live handles (contexts, keys, batches, servers), oldest first.  At
+# interpreter exit they are closed newest first, while the CUDA runtime and
+# this module are still whole, so a program that leaves them to the garbage
+# collector ends the same way as one that closes them.
+_live = []
+
+
+def _register(obj):
+    with _lock:
+        _live[:] = [r for r in _live if r() is not None]
+        _live.append(weakref.ref(obj))
+
+
+@atexit.register
+def _close_live_handles():
+    for r in reversed(_live):
+        obj = r()
+        if obj is not None:
+            try:
+                obj.close()
+            except Exception:
+                pass
+    _live.clear()
 
 
 def build_library(force: bool = False) -> str:
@@ -153,6 +180,7 @@ class Context:
         if rc != HERS_OK:
             raise HersError(f"hers_create: {lib().hers_status_string(rc).decode()}")
         self.h = h
+        _register(self)
 
     def check(self, rc, what):
         if rc != HERS_OK:
@@ -174,6 +202,7 @@ class Context:
 class Keys:
     def __init__(self, ctx: Context, h):
         self.ctx, self.h = ctx, h
+        _register(self)
 
     def close(self):
         if getattr(self, "h", None):
@@ -489,6 +518,7 @@ class Batch:
                                           _ptr(self.workspace), wsb, flags, ctypes.byref(h)),
                   "hers_batch_create")
         self.h = h
+        _register(self)
 
     def run(self, stream=None):
         self.ctx.check(lib().hers_batch_run(self.h, _stream(stream)), "hers_batch_run")
@@ -539,7 +569,7 @@ class Server:
 
     def __init__(self, ctx: Context, keys: Keys, galleries, workspace_bytes=0, max_batch=16,
                  variant=1):
-        self.ctx = ctx
+        self.ctx, self.keys = ctx, keys  # the server uses both until it is closed
         self._keep = [g for g, _, _ in galleries]
         arr = (ServerGallery * len(galleries))()
         for i, (g, nb, d) in enumerate(galleries):
@@ -548,6 +578,7 @@ class Server:
         ctx.check(lib().hers_server_create(ctx.h, keys.h, arr, len(galleries), workspace_bytes,
                                            max_batch, variant, ctypes.byref(h)), "hers_server_create")
         self.h = h
+        _register(self)
         self._bufs = {}
 
     def submit(self, gallery: int, begin: int, end: int, probe_ct_host, scores_host) -> int:
