@@ -292,22 +292,48 @@ __global__ void __launch_bounds__(256) k_scale_round(const uint32_t* __restrict_
 }
 
 // ---------------------------------------------------------------- key switch
-// KS (NTT domain) x evk_j (NTT, Shoup): O[b][c][l] = sum_j D_j evk_j[c][l].
-__global__ void __launch_bounds__(256) k_ks_mul(const uint64_t* __restrict__ KS,
-                                                const uint64_t* __restrict__ evk_ntt,
-                                                uint64_t* __restrict__ O) {
-    const int k = blockIdx.x * 256 + threadIdx.x;
-    const int l = blockIdx.y;
-    const uint64_t b = blockIdx.z;
+// RNS gadget (Alg 5's relinearisation with one digit per prime): for output
+// c = 0, 1 and limb l, O_cl = sum_j D_j evk_j[c][l], D_j = c2 mod q_j.
+// k_ks_fwd_mul: CTA per (b, j, l) = row of KS: D_j mod q_l to the NTT domain,
+// times evk_j[c][l] (NTT values with Shoup companions) for both c, into
+// P[b][j][c][l] (reduced).  k_ks_inv_finish: CTA per (b, c, l):
+// P[b][0][c][l] + P[b][1][c][l] back to coefficients, plus C[b][c][l], into
+// out[b][c][l].
+__global__ void __launch_bounds__(NTT_THREADS, 3) k_ks_fwd_mul(const uint64_t* __restrict__ tw,
+                                                            const uint64_t* __restrict__ KS,
+                                                            const uint64_t* __restrict__ evk_ntt,
+                                                            uint64_t* __restrict__ P) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t x = blockIdx.x;  // (b * 2 + j) * 2 + l
+    const uint64_t b = x >> 2;
+    const int j = (int)((x >> 1) & 1), l = (int)(x & 1);
     const uint64_t q = c_mod[l];
-    const uint64_t D1 = KS[(b * 4 + l) * N + k], D2 = KS[(b * 4 + 2 + l) * N + k];
+    const uint64_t* src = KS + x * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) sm[swz(k)] = src[k];
+    ntt_fwd_mod(sm, tw, l);
 #pragma unroll
     for (int c = 0; c < 2; c++) {
-        const uint64_t* e1 = evk_ntt + (size_t)(((0 * 2 + c) * 2 + l) * 2) * N;
-        const uint64_t* e2 = evk_ntt + (size_t)(((1 * 2 + c) * 2 + l) * 2) * N;
-        const uint64_t v = shoup_lazy(D1, e1[k], e1[N + k], q) + shoup_lazy(D2, e2[k], e2[N + k], q);
-        O[((b * 2 + c) * 2 + l) * N + k] = reduce64(v, l);
+        const uint64_t* e = evk_ntt + (size_t)(((j * 2 + c) * 2 + l) * 2) * N;
+        uint64_t* dst = P + (((b * 2 + j) * 2 + c) * 2 + l) * N;
+        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = shoup(sm[swz(k)], e[k], e[N + k], q);
     }
+}
+
+__global__ void __launch_bounds__(NTT_THREADS, 3) k_ks_inv_finish(const uint64_t* __restrict__ tw,
+                                                               const uint64_t* __restrict__ P,
+                                                               const uint64_t* __restrict__ C,
+                                                               uint64_t* __restrict__ out) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t x = blockIdx.x;  // (b * 2 + c) * 2 + l
+    const uint64_t b = x >> 2;
+    const int c = (int)((x >> 1) & 1), l = (int)(x & 1);
+    const uint64_t q = c_mod[l];
+    const uint64_t* p0 = P + (((b * 2 + 0) * 2 + c) * 2 + l) * N;
+    const uint64_t* p1 = P + (((b * 2 + 1) * 2 + c) * 2 + l) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) sm[swz(k)] = add_mod(p0[k], p1[k], q);
+    ntt_inv_mod(sm, tw, l);
+    const uint64_t* cc = C + ((b * 3 + c) * 2 + l) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) out[x * N + k] = add_mod(cc[k], sm[swz(k)], q);
 }
 
 // out[b][c][l] = C[b][c][l] + O[b][c][l] mod q_l (O in the coefficient domain)
@@ -366,8 +392,9 @@ __global__ void __launch_bounds__(256) k_ks_mul_w(const uint64_t* __restrict__ W
 // Epilogue over npairs (probe, block) pairs whose accumulators are in X as
 // uint32 [npairs][3][NUM_S][N] (NTT domain): inverse NTTs, exact
 // scale-and-round into C [npairs][3][2][N] and KS [npairs][4][N], key switch
-// (the output O [npairs][2][2][N] reuses X), canonical score ciphertexts into
-// out [npairs][2][2][N].
+// (its intermediates reuse the X area: the partial products P [npairs][8][N],
+// or with the base-w gadget O [npairs][2][2][N] and the digits), canonical
+// score ciphertexts into out [npairs][2][2][N].
 cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npairs, uint64_t* X,
                             uint64_t* C, uint64_t* KS, uint64_t* out, cudaStream_t st,
                             cudaEvent_t* ev, const KeySwitchW* ksw) {
@@ -411,36 +438,39 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
                                                                        ksw->ndig, O + b0 * 4 * N);
             nl++;
         }
-    } else {
         for (uint64_t off = 0; off < npairs * 4; off += chunk) {
             const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
-            k_ntt_batch<false><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, KS + off * N, 2, 0);
+            k_ntt_batch<true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, O + off * N, 2, 0);
             nl++;
         }
         for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
             const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
-            k_ks_mul<<<dim3(N / 256, 2, (unsigned)nb), 256, 0, st>>>(KS + b0 * 4 * N, k.evk_ntt,
-                                                                     O + b0 * 4 * N);
+            k_ks_finish<<<dim3(N / 256, 4, (unsigned)nb), 256, 0, st>>>(C + b0 * 6 * N, O + b0 * 4 * N,
+                                                                        out + b0 * 4 * N);
             nl++;
         }
-    }
-    for (uint64_t off = 0; off < npairs * 4; off += chunk) {
-        const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
-        k_ntt_batch<true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, O + off * N, 2, 0);
-        nl++;
-    }
-    for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
-        const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
-        k_ks_finish<<<dim3(N / 256, 4, (unsigned)nb), 256, 0, st>>>(C + b0 * 6 * N, O + b0 * 4 * N,
-                                                                    out + b0 * 4 * N);
-        nl++;
+    } else {
+        // RNS gadget: partial products P [npairs][2 j][2 c][2 l][N] in the X area
+        uint64_t* P = X;
+        for (uint64_t off = 0; off < npairs * 4; off += chunk) {  // chunk: a multiple of 4 rows
+            const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
+            k_ks_fwd_mul<<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, KS + off * N, k.evk_ntt, P + off * 2 * N);
+            nl++;
+        }
+        for (uint64_t off = 0; off < npairs * 4; off += chunk) {
+            const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
+            k_ks_inv_finish<<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, P + off * 2 * N, C + off / 4 * 6 * N,
+                                                                     out + off * N);
+            nl++;
+        }
     }
     count_launches(nl);
     return cudaGetLastError();
 }
 
 // Workspace per block (64-bit words): X, 15 N, holding the accumulators
-// [3][NUM_S][N] as uint32 (12 N words) and later O [2][2][N]; C [3][2][N]; KS [4][N].
+// [3][NUM_S][N] as uint32 (12 N words), later the key switch's intermediates
+// (8 N words); C [3][2][N]; KS [4][N].
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
                           uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev, int variant,
