@@ -621,6 +621,32 @@ __device__ __forceinline__ void ntt32_inv_smem(uint32_t* sm, const uint2* __rest
     __syncthreads();
 }
 
+// The inverse transform with its first and last phases on registers: v holds
+// the bit-reversed inputs at coefficients 16 t + a on entry and the outputs
+// (natural order, times N^-1, fully reduced) at coefficients t + 256 a on
+// exit, so the caller loads and stores them directly; sm (N words) carries
+// only the middle phase.  Ends with no barrier after its last shared-memory
+// read; a caller that reuses sm synchronises first.
+__device__ __forceinline__ void ntt32_inv_regs(uint32_t v[16], uint32_t* sm, const uint2* __restrict__ w,
+                                               uint32_t r, uint32_t ninv, uint32_t ninv_s, int t) {
+    gs_phase32<1, false>(v, 16 * t, w, r, ninv, ninv_s);
+#pragma unroll
+    for (int a = 0; a < 16; a++) sm[swz32(16 * t + a)] = v[a];
+    __syncwarp();
+    {
+        const int base = 256 * (t >> 4) + (t & 15);
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz32(base + 16 * a)];
+        gs_phase32<16, false>(v, base, w, r, ninv, ninv_s);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz32(base + 16 * a)] = v[a];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 16; a++) v[a] = sm[swz32(t + 256 * a)];
+    gs_phase32<256, true>(v, t, w, r, ninv, ninv_s);
+}
+
 __device__ __forceinline__ void ntt32_fwd_mod(uint32_t* a, const uint64_t* tw, int i, int t = threadIdx.x) {
     ntt32_fwd_smem(a, tw32_fwd(tw, i), c_smod[i], t);
 }

@@ -214,19 +214,30 @@ __global__ void __launch_bounds__(NTT_THREADS, 3) k_ntt_batch(const uint64_t* __
     for (int k = threadIdx.x; k < N; k += blockDim.x) g[k] = sm[swz(k)];
 }
 
-// The same over the search basis: polynomial P of [npolys][N] uint32 is mod
-// r_(P % NUM_S).
-template <bool INV>
-__global__ void __launch_bounds__(NTT_THREADS, 4) k_ntt32_batch(const uint64_t* __restrict__ tw,
-                                                             uint32_t* __restrict__ data) {
+// Inverse NTTs over the search basis: polynomial P of [npolys][N] uint32 is
+// mod r_(P % NUM_S).  Each thread loads its 16 phase-one coefficients (16 t ..
+// 16 t + 15, four 16-byte loads) and stores its 16 outputs (t + 256 a,
+// coalesced) directly; shared memory carries only the middle phase.
+__global__ void __launch_bounds__(NTT_THREADS, 4) k_intt32_batch(const uint64_t* __restrict__ tw,
+                                                              uint32_t* __restrict__ data) {
     __shared__ uint32_t sm32[N];
     const uint64_t P = blockIdx.x;
     const int mi = (int)(P % NUM_S);
+    const int t = threadIdx.x;
     uint32_t* g = data + P * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) sm32[swz32(k)] = g[k];
-    if (INV) ntt32_inv_mod(sm32, tw, mi);
-    else ntt32_fwd_mod(sm32, tw, mi);
-    for (int k = threadIdx.x; k < N; k += blockDim.x) g[k] = sm32[swz32(k)];
+    uint32_t v[16];
+    const uint4* g4 = (const uint4*)(g + 16 * t);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const uint4 u = g4[i];
+        v[4 * i] = u.x;
+        v[4 * i + 1] = u.y;
+        v[4 * i + 2] = u.z;
+        v[4 * i + 3] = u.w;
+    }
+    ntt32_inv_regs(v, sm32, tw32_inv(tw, mi), c_smod[mi], c_sninv[mi], c_sninv_s[mi], t);
+#pragma unroll
+    for (int a = 0; a < 16; a++) g[t + 256 * a] = v[a];
 }
 
 // ---------------------------------------------------------------- exact scale-and-round
@@ -406,7 +417,7 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
     const uint64_t npolys = npairs * 3 * NUM_S;  // chunks are multiples of NUM_S
     for (uint64_t off = 0; off < npolys; off += chunk) {
         const uint64_t n = npolys - off < chunk ? npolys - off : chunk;
-        k_ntt32_batch<true><<<(unsigned)n, NTT_THREADS, 0, st>>>(tw, X32 + off * N);
+        k_intt32_batch<<<(unsigned)n, NTT_THREADS, 0, st>>>(tw, X32 + off * N);
         nl++;
     }
     if (ev) cudaEventRecord(ev[0], st);
