@@ -86,7 +86,7 @@ def parse():
     ap.add_argument("--batch-variant", default=None,
                     help="batched: kernel shape by name (skips the batched autotuner); "
                          "scale and serving: the kernel shape of the streamed search / the server's "
-                         "batches (defaults np4_nb1_s2_d4_m2 / np2_nb2_s2_d4_m3)")
+                         "batches (defaults np4_nb2_s2_d4_m2 / np2_nb2_s2_d4_m3)")
     ap.add_argument("--variant", default=None,
                     help="tensor-kernel shape by name (skips the autotuner), e.g. nb2_s3_d4_m3")
     return ap.parse_args()
@@ -929,7 +929,7 @@ def run_scale(args):
               for i, q in enumerate(qs)]
     sc = torch.empty((nprobes, nb, 2, 2, N), dtype=torch.int64, device=dev)
     chunk = 32
-    bv_name = args.batch_variant or "np4_nb1_s2_d4_m2"
+    bv_name = args.batch_variant or "np4_nb2_s2_d4_m2"
     bv = H.hers_batch_variants().index(bv_name)
     ws = torch.empty(H.hers_search_stream_workspace_bytes(d, nprobes, chunk) // 8,
                      dtype=torch.int64, device=dev)

@@ -71,23 +71,24 @@ __device__ __forceinline__ void load_unit(UnitRegs<NP>& r, const BatchChunk* __r
 // int32 residues, see k_tensor).  With FULL (nd = DPS, np = NP, nb = NB) the
 // loops carry no predicates.
 template <int NP, int NB, int DPS, bool FULL>
-__device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const int32_t* base, uint32_t nd,
+__device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const int2* base, uint32_t nd,
                                                uint32_t np, uint32_t nbu) {
-    constexpr int RUN = DPS * 2 * TILE;
+    constexpr int RUN2 = DPS * TILE;  // (poly 0, poly 1) pairs of one run
 #pragma unroll
     for (int dd = 0; dd < DPS; dd++) {
         if (FULL || (uint32_t)dd < nd) {
             int32_t a0[NP], a1[NP];
 #pragma unroll
             for (int q = 0; q < NP; q++) {
-                a0[q] = base[q * RUN + dd * 2 * TILE];
-                a1[q] = base[q * RUN + dd * 2 * TILE + TILE];
+                const int2 A = base[q * RUN2 + dd * TILE];
+                a0[q] = A.x;
+                a1[q] = A.y;
             }
 #pragma unroll
             for (int j = 0; j < NB; j++) {
                 if (FULL || (uint32_t)j < nbu) {
-                    const int32_t* gp = base + (NP + j) * RUN + dd * 2 * TILE;
-                    const int32_t g0 = gp[0], g1 = gp[TILE];
+                    const int2 G = base[(NP + j) * RUN2 + dd * TILE];
+                    const int32_t g0 = G.x, g1 = G.y;
 #pragma unroll
                     for (int q = 0; q < NP; q++) {
                         if (FULL || (uint32_t)q < np) {
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
 #pragma unroll
                 for (int j = 0; j < NB; j++) s[q][j][0] = s[q][j][1] = s[q][j][2] = 0;
         }
-        const int32_t* base = smr + (size_t)st * STAGE_ELEMS + t;
+        const int2* base = (const int2*)(smr + (size_t)st * STAGE_ELEMS) + t;  // (poly 0, poly 1) pairs
         if (nd == DPS && np == NP && nbu == NB)
             stage_products<NP, NB, DPS, true>(s, base, nd, np, nbu);
         else

@@ -61,17 +61,17 @@ static __constant__ PlainMod c_plain[2] = HERS_PLAIN_INIT;
 
 // Resident (search) form of ciphertexts: NTT domain over the search basis,
 // each residue as its centred value (one int32, |v| < 2^29), tiled so that
-// everything one search CTA streams is contiguous:
-//   [block][limb r_l][tile][dim][poly][TILE]   (TILE coefficients per tile)
+// everything one search CTA streams is contiguous, with the two polynomials
+// of a ciphertext interleaved per coefficient (one 8-byte load gives both):
+//   [block][limb r_l][tile][dim][TILE coefficients][poly]
 // A gallery block occupies 16 d N int32 (8 d N 64-bit words); a prepared
 // probe is block 0 of it.  Offsets below count int32 elements.
 constexpr int TILE = 256;
 constexpr int NTILES = N / TILE;
 __host__ __device__ __forceinline__ uint64_t resident_offset(uint64_t b, int limb, int k, uint32_t d,
                                                              uint32_t i, int poly) {
-    return ((((b * NUM_S + (uint64_t)limb) * NTILES + (uint64_t)(k / TILE)) * d + i) * 2 + (uint64_t)poly) *
-               TILE +
-           (uint64_t)(k % TILE);
+    return ((((b * NUM_S + (uint64_t)limb) * NTILES + (uint64_t)(k / TILE)) * d + i) * TILE +
+            (uint64_t)(k % TILE)) * 2 + (uint64_t)poly;
 }
 
 // Twiddle table of modulus i inside the table buffer the context owns:

@@ -113,16 +113,17 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
             return;
         }
         const uint32_t nd = min((uint32_t)DPS, d - si * DPS);
-        const int32_t* base = smr + (size_t)st * STAGE_ELEMS + t;
+        const int2* base = (const int2*)(smr + (size_t)st * STAGE_ELEMS) + t;  // (poly 0, poly 1) pairs
 #pragma unroll
         for (int dd = 0; dd < DPS; dd++) {
             if ((uint32_t)dd < nd) {
-                const int32_t a0 = base[dd * 2 * TILE], a1 = base[dd * 2 * TILE + TILE];
+                const int2 A = base[dd * TILE];
+                const int32_t a0 = A.x, a1 = A.y;
 #pragma unroll
                 for (int j = 0; j < NB; j++) {
                     if (j < nb) {
-                        const int32_t* g = base + (1 + j) * RUN + dd * 2 * TILE;
-                        const int32_t g0 = g[0], g1 = g[TILE];
+                        const int2 G = base[(1 + j) * (RUN / 2) + dd * TILE];
+                        const int32_t g0 = G.x, g1 = G.y;
                         madw(s[j][0], a0, g0);
                         madw(s[j][1], a0, g1);
                         madw(s[j][1], a1, g0);
