@@ -26,13 +26,14 @@
 namespace hers {
 
 constexpr uint32_t UNIT_STOP = 0xFFFFFFFFu;
-constexpr int BPFOLD = 8;  // partial-fold period in dimensions (see k_tensor)
+constexpr int BPFOLD = 8;  // partial-fold period of T1 in dimensions, 2 BPFOLD for T0, T2 (see k_tensor)
 
 // Stage descriptor flags (written by the producer with each stage).
 constexpr uint32_t F_FIRST = 1;  // first stage of a unit: sums start at zero
-constexpr uint32_t F_FOLD = 2;   // partial fold of the 64-bit sums after this stage
+constexpr uint32_t F_FOLD = 2;   // partial fold of the T1 sums after this stage
 constexpr uint32_t F_LAST = 4;   // last stage of a unit: store the unit's results
 constexpr uint32_t F_STOP = 8;   // no more units: the consumers leave
+constexpr uint32_t F_FOLD02 = 16;  // partial fold of the T0 and T2 sums after this stage
 
 __device__ __forceinline__ void madw_b(int64_t& acc, int32_t a, int32_t b) {
     asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
                     const uint32_t nd = min((uint32_t)DPS, cur.d - si * DPS), done = si * DPS + nd;
                     const uint32_t flags = (si == 0 ? F_FIRST : 0u) |
                                            ((done % BPFOLD == 0 && done < cur.d) ? F_FOLD : 0u) |
+                                           ((done % (2 * BPFOLD) == 0 && done < cur.d) ? F_FOLD02 : 0u) |
                                            (done == cur.d ? F_LAST : 0u);
                     hdr_info[st] = nd | (cur.np << 8) | (cur.nb << 12) | (cur.limb << 16) | (flags << 20);
                     if (flags & F_LAST) {
@@ -238,12 +240,17 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
         if (lane == 0) mbar_arrive(&empty[st]);
         if (flags & F_FOLD) {
             const int32_t r32 = (int32_t)c_sr32[l];
+            const bool all = (flags & F_FOLD02) != 0;
 #pragma unroll
             for (int q = 0; q < NP; q++)
 #pragma unroll
-                for (int j = 0; j < NB; j++)
-#pragma unroll
-                    for (int c = 0; c < 3; c++) s[q][j][c] = pfold(s[q][j][c], r32);
+                for (int j = 0; j < NB; j++) {
+                    s[q][j][1] = pfold(s[q][j][1], r32);
+                    if (all) {
+                        s[q][j][0] = pfold(s[q][j][0], r32);
+                        s[q][j][2] = pfold(s[q][j][2], r32);
+                    }
+                }
         }
         if (flags & F_LAST) {
             const uint32_t k = k0 + t;

@@ -29,11 +29,12 @@ namespace hers {
 //
 // Arithmetic: operands are the centred residues (|a|, |b| < 2^29), so each
 // (dimension, coefficient, limb, block) costs four 32x32->64 signed
-// multiply-adds (mad.wide.s32) into 64-bit sums, T1 growing by less than 2^59
-// per dimension.  Every PFOLD = 8 dimensions a partial fold (pfold) brings a
-// sum back below 2^61 + 2^32 in magnitude, so sums stay below 2^63; the last
-// dimension ends with a full reduction mod r_l.  A wait that runs out
-// (WAIT_NS, 2 s) sets bit 2 of *err.
+// multiply-adds (mad.wide.s32) into 64-bit sums: T1 grows by less than 2^59
+// per dimension, T0 and T2 by less than 2^58.  A partial fold (pfold) brings a
+// sum back below 2^61 + 2^32 in magnitude: T1 every PFOLD = 8 dimensions and
+// T0, T2 every 2 PFOLD, so every sum stays below 2^63 (2^61 + 2^32 + 8 2^59
+// and 2^61 + 2^32 + 16 2^58); the last dimension ends with a full reduction
+// mod r_l.  A wait that runs out (WAIT_NS, 2 s) sets bit 2 of *err.
 constexpr int PFOLD = 8;
 
 __device__ __forceinline__ void madw(int64_t& acc, int32_t a, int32_t b) {
@@ -136,10 +137,15 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
         if (lane == 0) mbar_arrive(&empty[st]);
         const uint32_t done = si * DPS + nd;
         if (done % PFOLD == 0 && done < d) {
+            const bool all = done % (2 * PFOLD) == 0;
 #pragma unroll
-            for (int j = 0; j < NB; j++)
-#pragma unroll
-                for (int c = 0; c < 3; c++) s[j][c] = pfold(s[j][c], r32);
+            for (int j = 0; j < NB; j++) {
+                s[j][1] = pfold(s[j][1], r32);
+                if (all) {
+                    s[j][0] = pfold(s[j][0], r32);
+                    s[j][2] = pfold(s[j][2], r32);
+                }
+            }
         }
     }
     const int k = tile * TILE + t;

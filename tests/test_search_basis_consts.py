@@ -199,8 +199,9 @@ def test_partial_fold_keeps_the_residue(c):
             hi, lo = s >> 32, s & 0xFFFFFFFF
             f = hi * c["SR32"][i] + lo  # the kernels' pfold
             assert f % r == s % r and abs(f) < (1 << 61) + (1 << 32)
-            # 8 dimensions of the middle product sum (each below 2^59) stay below 2^63
-            assert abs(f) + 8 * (1 << 59) < 1 << 63
+            # 8 dimensions of the middle sum (2 products, below 2^59) and 16 of
+            # the outer ones (1 product, below 2^58) stay below 2^63
+            assert abs(f) + 8 * (1 << 59) < 1 << 63 and abs(f) + 16 * (1 << 58) < 1 << 63
             u = (f + c["SOFF63"][i]) & ((1 << 64) - 1)
             qe = (u * c["SMU"][i]) >> 64
             rr = (u - qe * r) & 0xFFFFFFFF
