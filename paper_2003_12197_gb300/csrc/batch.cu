@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], TILE / 32);
+            mbar_init(&empty[s], TILE);  // every consumer thread arrives
         }
         mbar_fence_init();
     }
@@ -236,8 +236,7 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
             stage_products<NP, NB, DPS, true>(s, base, nd, np, nbu);
         else
             stage_products<NP, NB, DPS, false>(s, base, nd, np, nbu);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[st]);
+        mbar_arrive(&empty[st]);
         if (flags & F_FOLD) {
             const int32_t r32 = (int32_t)c_sr32[l];
             const bool all = (flags & F_FOLD02) != 0;

@@ -25,7 +25,8 @@ namespace hers {
 // [dim][poly][TILE] run and one such run per block.  The producer's elected
 // lane streams DPS dimensions per stage with one cp.async.bulk per run into a
 // STAGES-deep shared-memory ring; "full" mbarriers track the copies and
-// "empty" mbarriers (one arrival per consumer warp) hand stages back.
+// "empty" mbarriers (one arrival per consumer thread, no lane test) hand
+// stages back.
 //
 // Arithmetic: operands are the centred residues (|a|, |b| < 2^29), so each
 // (dimension, coefficient, limb, block) costs four 32x32->64 signed
@@ -39,6 +40,29 @@ constexpr int PFOLD = 8;
 
 __device__ __forceinline__ void madw(int64_t& acc, int32_t a, int32_t b) {
     asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+
+// One stage's products: for dd < nd and block j < nb, the four products of
+// the probe row and gallery row j.  With FULL (nd = DPS, nb = NB) the loops
+// carry no predicates.
+template <int NB, int DPS, int RUN, bool FULL>
+__device__ __forceinline__ void tensor_stage(int64_t (&s)[NB][3], const int2* base, uint32_t nd, int nb) {
+#pragma unroll
+    for (int dd = 0; dd < DPS; dd++) {
+        if (FULL || (uint32_t)dd < nd) {
+            const int2 A = base[dd * TILE];
+#pragma unroll
+            for (int j = 0; j < NB; j++) {
+                if (FULL || j < nb) {
+                    const int2 G = base[(1 + j) * (RUN / 2) + dd * TILE];
+                    madw(s[j][0], A.x, G.x);
+                    madw(s[j][1], A.x, G.y);
+                    madw(s[j][1], A.y, G.x);
+                    madw(s[j][2], A.y, G.y);
+                }
+            }
+        }
+    }
 }
 
 // GORDER: block groups vary fastest over the grid (x = group, y = (limb,
@@ -65,7 +89,7 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], TILE / 32);
+            mbar_init(&empty[s], TILE);  // every consumer thread arrives
         }
         mbar_fence_init();
     }
@@ -101,49 +125,38 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
         return;
     }
 
-    // consumers
+    // consumers: the ring is walked STAGES stages per lap, so stage indices are
+    // constants and the phase parity flips once per lap
     const int t = threadIdx.x;
     const int32_t r32 = (int32_t)c_sr32[l];
     int64_t s[NB][3];
 #pragma unroll
     for (int j = 0; j < NB; j++) s[j][0] = s[j][1] = s[j][2] = 0;
-    for (uint32_t si = 0; si < nst; si++) {
-        const int st = (int)(si % STAGES);
-        if (!mbar_wait(&full[st], (si / STAGES) & 1)) {
-            atomicOr(err, 2);
-            return;
-        }
-        const uint32_t nd = min((uint32_t)DPS, d - si * DPS);
-        const int2* base = (const int2*)(smr + (size_t)st * STAGE_ELEMS) + t;  // (poly 0, poly 1) pairs
+    for (uint32_t s0 = 0; s0 < nst; s0 += STAGES) {
+        const uint32_t parity = (s0 / STAGES) & 1;
 #pragma unroll
-        for (int dd = 0; dd < DPS; dd++) {
-            if ((uint32_t)dd < nd) {
-                const int2 A = base[dd * TILE];
-                const int32_t a0 = A.x, a1 = A.y;
+        for (int st = 0; st < STAGES; st++) {
+            const uint32_t si = s0 + st;
+            if (si >= nst) break;
+            if (!mbar_wait(&full[st], parity)) {
+                atomicOr(err, 2);
+                return;
+            }
+            const uint32_t nd = min((uint32_t)DPS, d - si * DPS);
+            const int2* base = (const int2*)(smr + st * STAGE_ELEMS) + t;  // (poly 0, poly 1) pairs
+            if (nd == DPS && nb == NB) tensor_stage<NB, DPS, RUN, true>(s, base, nd, nb);
+            else tensor_stage<NB, DPS, RUN, false>(s, base, nd, nb);
+            mbar_arrive(&empty[st]);
+            const uint32_t done = si * DPS + nd;
+            if (done % PFOLD == 0 && done < d) {
+                const bool all = done % (2 * PFOLD) == 0;
 #pragma unroll
                 for (int j = 0; j < NB; j++) {
-                    if (j < nb) {
-                        const int2 G = base[(1 + j) * (RUN / 2) + dd * TILE];
-                        const int32_t g0 = G.x, g1 = G.y;
-                        madw(s[j][0], a0, g0);
-                        madw(s[j][1], a0, g1);
-                        madw(s[j][1], a1, g0);
-                        madw(s[j][2], a1, g1);
+                    s[j][1] = pfold(s[j][1], r32);
+                    if (all) {
+                        s[j][0] = pfold(s[j][0], r32);
+                        s[j][2] = pfold(s[j][2], r32);
                     }
-                }
-            }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[st]);
-        const uint32_t done = si * DPS + nd;
-        if (done % PFOLD == 0 && done < d) {
-            const bool all = done % (2 * PFOLD) == 0;
-#pragma unroll
-            for (int j = 0; j < NB; j++) {
-                s[j][1] = pfold(s[j][1], r32);
-                if (all) {
-                    s[j][0] = pfold(s[j][0], r32);
-                    s[j][2] = pfold(s[j][2], r32);
                 }
             }
         }
