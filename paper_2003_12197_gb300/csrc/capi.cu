@@ -86,6 +86,14 @@ cudaEvent_t* next_trace(hers_ctx* ctx) {
     return &ctx->tev[(size_t)(ctx->tn++) * SEARCH_EVENTS];
 }
 
+void ep_free(hers_ctx* ctx) {
+    if (ctx->ep_ev[0]) cudaEventDestroy(ctx->ep_ev[0]);
+    if (ctx->ep_ev[1]) cudaEventDestroy(ctx->ep_ev[1]);
+    if (ctx->ep) cudaStreamDestroy(ctx->ep);
+    ctx->ep = nullptr;
+    ctx->ep_ev[0] = ctx->ep_ev[1] = nullptr;
+}
+
 void trace_free(hers_ctx* ctx) {
     for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
     ctx->tev.clear();
@@ -156,11 +164,23 @@ int hers_create(const hers_params* p, int device, hers_ctx** out) {
         delete ctx;
         return HERS_E_CUDA;
     }
+    {   // the epilogue stream: the device's highest priority
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&ctx->ep, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ep_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ep_ev[1], cudaEventDisableTiming) != cudaSuccess) {
+            ep_free(ctx);
+            cudaStreamDestroy(ctx->stream);
+            delete ctx;
+            return HERS_E_CUDA;
+        }
+    }
     // twiddles: [mod][forward, inverse][N] pairs (w, floor(w 2^64 / p)); entry 0
     // of the inverse table: the last inverse stage's twiddle times N^-1
     const size_t words = TW_WORDS;
     uint64_t* h = new (std::nothrow) uint64_t[words];
-    if (!h) { cudaStreamDestroy(ctx->stream); delete ctx; return HERS_E_NOMEM; }
+    if (!h) { ep_free(ctx); cudaStreamDestroy(ctx->stream); delete ctx; return HERS_E_NOMEM; }
     for (int i = 0; i < NUM_MODS; i++) {
         const uint64_t pm = H_MOD[i], psi = H_PSI[i], psi_inv = h_pow(psi, pm - 2, pm);
         uint64_t* f = h + (size_t)(4 * i) * N;
@@ -202,6 +222,7 @@ int hers_create(const hers_params* p, int device, hers_ctx** out) {
     if (e == cudaSuccess) e = cudaMemset(ctx->err, 0, sizeof(int));
     if (e != cudaSuccess) {
         cudaFree(ctx->tw);
+        ep_free(ctx);
         cudaStreamDestroy(ctx->stream);
         delete ctx;
         return HERS_E_CUDA;
@@ -215,9 +236,11 @@ int hers_destroy(hers_ctx* ctx) {
     {
         DeviceGuard g(ctx->device);
         cudaStreamSynchronize(ctx->stream);
+        cudaStreamSynchronize(ctx->ep);
         cudaFree(ctx->tw);
         cudaFree(ctx->err);
         trace_free(ctx);
+        ep_free(ctx);
         cudaStreamDestroy(ctx->stream);
     }
     delete ctx;
@@ -412,9 +435,10 @@ int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
                     (unsigned long long)workspace_bytes,
                     (unsigned long long)hers_search_workspace_bytes(nblocks));
     DeviceGuard g(ctx->device);
+    const EpilogueStream ep = {ctx->ep, {ctx->ep_ev[0], ctx->ep_ev[1]}};
     cudaError_t e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, scores_ct,
                                   (uint64_t*)workspace, ctx->err, pick(ctx, stream), next_trace(ctx),
-                                  ctx->tensor_variant);
+                                  ctx->tensor_variant, nullptr, &ep);
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search");
 }
 
@@ -476,6 +500,7 @@ int search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
         }
     }
     cudaStream_t st = pick(ctx, stream);
+    const EpilogueStream ep = {ctx->ep, {ctx->ep_ev[0], ctx->ep_ev[1]}};
     // workspace: [search scratch][probe cts d*4N][probe form d*RES_WORDS_PER_DIM][score cts nblocks*4N]
     // (hers_search_host_workspace_bytes sums the same parts)
     uint64_t* ws = (uint64_t*)workspace;
@@ -487,7 +512,7 @@ int search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
     if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, probe_ct, d, 0, d, probe, st);
     if (e == cudaSuccess)
         e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, out_dev, ws, ctx->err, st,
-                          next_trace(ctx), ctx->tensor_variant);
+                          next_trace(ctx), ctx->tensor_variant, nullptr, &ep);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(scores_ct_host, out_dev, nblocks * 4 * N * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && sync) e = cudaStreamSynchronize(st);

@@ -20,6 +20,10 @@ struct hers_ctx {
     uint32_t tcap = 0, tn = 0;
     int tensor_variant = 1;  // tensor-kernel shape used by searches on this context
     int pm = 0;              // plaintext modulus: 0 the default t, 1 the paper's t
+    // the epilogue of a search runs on ep (the device's highest stream priority),
+    // after ep_ev[0] (tensor done) and before ep_ev[1] (joined back to the caller)
+    cudaStream_t ep = nullptr;
+    cudaEvent_t ep_ev[2] = {nullptr, nullptr};
 };
 
 namespace hers {
@@ -117,10 +121,18 @@ constexpr int SEARCH_EVENTS = 5;
 // `variant` selects the tensor-kernel shape (see tensor_variant_name).
 constexpr int DEFAULT_TENSOR_VARIANT = 1;
 // ksw (optional): key switch with the base-w gadget instead of the RNS one.
+// ep (optional): the epilogue runs on ep.stream (a high-priority stream), so
+// that its CTAs are dispatched ahead of pending CTAs of another search's
+// tensor kernel; ep.ev[0] and ep.ev[1] fork from and join back to st.
+struct EpilogueStream {
+    cudaStream_t stream;
+    cudaEvent_t ev[2];
+};
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
                           uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev = nullptr,
-                          int variant = DEFAULT_TENSOR_VARIANT, const KeySwitchW* ksw = nullptr);
+                          int variant = DEFAULT_TENSOR_VARIANT, const KeySwitchW* ksw = nullptr,
+                          const EpilogueStream* ep = nullptr);
 // Epilogue over npairs accumulators X (uint32 [npairs][3][NUM_S][N] at the
 // start of the X area, 15 N words per pair); workspace C, KS as in
 // launch_search; `ev` (optional) receives the boundaries after the inverse

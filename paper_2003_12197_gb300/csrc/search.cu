@@ -505,7 +505,7 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
                           uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev, int variant,
-                          const KeySwitchW* ksw) {
+                          const KeySwitchW* ksw, const EpilogueStream* ep) {
     if (nblocks == 0) return cudaSuccess;
     uint64_t* X = ws;
     uint64_t* C = X + nblocks * 15 * N;
@@ -514,8 +514,20 @@ cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* 
     cudaError_t e = launch_tensor(variant, gallery, nblocks, d, probe, (uint32_t*)X, err, st);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
-    e = launch_epilogue(tw, k, nblocks, X, C, KS, scores_ct, st, ev ? ev + 2 : nullptr, ksw);
-    if (ev) cudaEventRecord(ev[4], st);
+    cudaStream_t es = st;
+    if (ep) {
+        e = cudaEventRecord(ep->ev[0], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ep->stream, ep->ev[0], 0);
+        if (e != cudaSuccess) return e;
+        es = ep->stream;
+    }
+    e = launch_epilogue(tw, k, nblocks, X, C, KS, scores_ct, es, ev ? ev + 2 : nullptr, ksw);
+    if (ev) cudaEventRecord(ev[4], es);
+    if (ep) {
+        cudaError_t ej = cudaEventRecord(ep->ev[1], es);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(st, ep->ev[1], 0);
+        if (e == cudaSuccess) e = ej;
+    }
     return e;
 }
 
