@@ -1,9 +1,9 @@
 """Host check of the search basis: the generated constants and the exact
 scale-and-round / CRT they drive (CPU, exact Python integers).
 
-The library computes the tensor sums X of a search mod eight primes below
-2^30 and reconstructs X + q 2^129 by the CRT (R16 of the design notes; Alg 5's
-exact product before rounding).  This test reads hers_consts.h, re-derives
+The library computes the tensor sums X of a search (Alg 5's exact product
+before rounding, summed over the dimensions) mod eight primes below 2^30 and
+reconstructs X + q 2^129 by the CRT.  This test reads hers_consts.h, re-derives
 every search-basis constant from its definition, and runs the kernels'
 arithmetic step by step (the 32-bit Shoup products, the fixed-point overflow
 count alpha, the 27-bit digit columns, the quotient estimate and its
