@@ -198,8 +198,10 @@ def test_inline_temporaries_on_default_stream(ctx, keys):
 
 def test_every_tensor_shape_gives_the_same_ciphertexts(ctx, keys, oracle_keys):
     """Exact integer arithmetic makes the result independent of the kernel's
-    tiling: every autotuner candidate must give the oracle's score ciphertexts."""
-    m, d = 3 * 4096 + 17, 40   # d not a multiple of the stage depth: ragged last stage
+    tiling: every autotuner candidate must give the oracle's score ciphertexts,
+    over 4 blocks and over the first 3 (a partial block group for the 2- and
+    4-block shapes)."""
+    m, d = 3 * 4096 + 17, 41   # 41: a ragged last stage at every stage depth (2, 4, 8), past 5 fold points
     feats = W.gallery_features(m, d, 99)
     q = W.probe_for_mate(4100, d, 99, 98)
     gal, _ = H.hers_encrypt_gallery(ctx, keys, torch.from_numpy(feats).cuda(), GAL_SEED)
@@ -207,10 +209,11 @@ def test_every_tensor_shape_gives_the_same_ciphertexts(ctx, keys, oracle_keys):
     names = H.hers_tensor_variants()
     assert len(names) >= 4
     keep = H.hers_get_tensor_variant(ctx)
-    outs = []
+    outs, outs3 = [], []
     for v in range(len(names)):
         H.hers_set_tensor_variant(ctx, v)
         outs.append(u64(H.hers_search(ctx, keys, gal, 4, d, pr)))
+        outs3.append(u64(H.hers_search(ctx, keys, gal, 3, d, pr)))
     H.hers_set_tensor_variant(ctx, keep)
     oprb = O.encrypt_probe(oracle_keys[1], q, PRB_SEED)
     ogal = O.encrypt_gallery_block(oracle_keys[1], feats, 3, GAL_SEED)
@@ -218,6 +221,7 @@ def test_every_tensor_shape_gives_the_same_ciphertexts(ctx, keys, oracle_keys):
     for v, o in enumerate(outs):
         assert np.array_equal(o, outs[0]), names[v]
         assert np.array_equal(o[3], osc), names[v]
+        assert np.array_equal(outs3[v], outs[0][:3]), names[v]
     chosen, ms = H.hers_autotune(ctx, keys, gal, 4, d, pr)
     assert 0 <= chosen < len(names) and len(ms) == len(names)
     H.hers_set_tensor_variant(ctx, keep)
