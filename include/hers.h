@@ -172,7 +172,13 @@ int hers_probe_prepare(hers_ctx* ctx, const uint64_t* probe_ct, uint32_t d, uint
  * c_k = [round(t X_k / q)]_q, then one relinearisation with evk.
  * scores_ct: device uint64 [nblocks][2][2][N] canonical score cts.
  * workspace: device scratch of at least hers_search_workspace_bytes(nblocks).
- * Reads only the evaluation key of `keys`.  Asynchronous on stream.
+ * Reads only the evaluation key of `keys`.  Asynchronous on stream: the
+ * tensor kernel runs on `stream`; the rounding and relinearisation run on a
+ * high-priority stream of the context, forked after the tensor kernel and
+ * joined back to `stream` with events, so work enqueued on `stream` after
+ * the call (or a synchronisation of `stream`) sees the finished scores.
+ * Searches on several streams of one context may be in flight at once;
+ * calls on one context must come from one host thread at a time.
  */
 int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
                 uint32_t d, const uint64_t* probe, uint64_t* scores_ct, void* workspace,

@@ -297,3 +297,27 @@ def test_rerandomized_search_bit_exact(ctx, keys, oracle_keys):
         assert np.array_equal(got[b], O.rerandomize(oracle_keys[1], osc, 8585, b)), f"block {b}"
     scores = H.hers_decrypt_scores(ctx, keys, sc, m).cpu().numpy().astype(np.int64)
     assert np.array_equal(scores, W.plain_inner_products(feats, q))
+
+
+def test_searches_on_several_streams_in_flight(ctx, keys, config1):
+    """Searches issued back to back on three streams of one context (their
+    epilogues share the context's high-priority stream) each equal the
+    sequential search; and a kernel enqueued on a caller's stream after the
+    call sees the finished scores."""
+    res = config1["res"]
+    nb = res["nb"]
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    outs = [torch.empty_like(res["sc"]) for _ in range(6)]
+    wss = [torch.empty(H.hers_search_workspace_bytes(nb) // 8, dtype=torch.int64, device="cuda")
+           for _ in range(3)]
+    torch.cuda.synchronize()
+    copies = []
+    for k in range(6):
+        st = streams[k % 3]
+        H.hers_search(ctx, keys, res["gal"], nb, 64, res["pr"], out=outs[k], workspace=wss[k % 3], stream=st)
+        with torch.cuda.stream(st):
+            copies.append(outs[k].clone())  # ordered after the search on st
+    torch.cuda.synchronize()
+    for k in range(6):
+        assert torch.equal(outs[k], res["sc"]), f"search {k}"
+        assert torch.equal(copies[k], res["sc"]), f"copy after search {k}"
