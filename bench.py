@@ -522,6 +522,13 @@ def run_gpu(args):
     achieved = alg_bytes / t_tensor / 1e9 if t_tensor > 0 else 0.0
     t_tensor_if = phases["tensor"] / 1e3
     achieved_if = alg_bytes / t_tensor_if / 1e9 if t_tensor_if > 0 else 0.0
+    # the same launch against the canonical-ciphertext minimum (32 d bytes per
+    # entry: the gallery as the client encrypted it) and against the measured
+    # rate of the 32x32->64 multiply-adds it performs (4 per dimension,
+    # coefficient, search prime and block)
+    canon_bytes = nb * d * 4 * N * 8
+    madw = 4 * d * N * search_limbs() * nb
+    imad_rate = H.hers_probe_int_pipe(local)["imad_wide_u32"]
     # DRAM traffic of the same kernel shape from a committed ncu capture, scaled
     # to this launch by blocks (null when no capture matches the current shape)
     traffic = None
@@ -580,7 +587,15 @@ def run_gpu(args):
                                         "CUDA events around each tensor launch on its stream",
                          "in_flight": {"achieved": achieved_if, "frac": achieved_if / peak,
                                        "note": "the same events in the two-in-flight timed region; they also "
-                                               "span the other search's kernels holding SMs"}},
+                                               "span the other search's kernels holding SMs"},
+                         "canonical_min": {"bytes_per_launch": canon_bytes,
+                                           "gbs": canon_bytes / t_tensor / 1e9 if t_tensor > 0 else 0.0,
+                                           "note": "the gallery as canonical ciphertexts (32 d bytes per entry), "
+                                                   "the byte floor of any form"},
+                         "int_pipe": {"mad_wide_per_launch": madw,
+                                      "frac": madw / t_tensor / imad_rate if t_tensor > 0 else 0.0,
+                                      "peak_per_s": imad_rate,
+                                      "peak_source": "measured in this run (hers_probe_int_pipe)"}},
             "phases_ms": {k: round(v, 4) for k, v in phases.items()},
             "phases_note": "per-phase CUDA-event times of the timed searches, each on its own stream; "
                            "with two searches in flight a phase's time includes the other search's "
