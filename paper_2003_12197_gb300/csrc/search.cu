@@ -20,9 +20,11 @@ namespace hers {
 //   T0 = sum a0 b0,  T1 = sum (a0 b1 + a1 b0),  T2 = sum a1 b1.
 //
 // Organisation (sm_103a): CTA (tile, l, group) has TILE consumer threads, one
-// coefficient each, for NB gallery blocks, plus one producer warp.  In the
+// coefficient each, for NB gallery blocks, plus one producer warp.  The
+// consumers walk the ring a lap (STAGES stages) per iteration, with constant
+// stage indices, and take an unpredicated path for full stages.  In the
 // resident layout everything a CTA reads is contiguous: the probe's
-// [dim][poly][TILE] run and one such run per block.  The producer's elected
+// [dim][TILE][poly] run and one such run per block.  The producer's elected
 // lane streams DPS dimensions per stage with one cp.async.bulk per run into a
 // STAGES-deep shared-memory ring; "full" mbarriers track the copies and
 // "empty" mbarriers (one arrival per consumer thread, no lane test) hand
