@@ -28,9 +28,11 @@ static __constant__ uint32_t c_sninv_s[NUM_S] = HERS_SNINV_S_INIT;  // its Shoup
 static __constant__ uint64_t c_smu[NUM_S] = HERS_SMU_INIT;          // floor(2^64 / r)
 static __constant__ uint32_t c_sr32[NUM_S] = HERS_SR32_INIT;        // 2^32 mod r
 static __constant__ uint64_t c_soff63[NUM_S] = HERS_SOFF63_INIT;    // multiple of r just below 2^63
+// Extension: [q1]_r, [q1 2^27]_r, [-q]_r and floor(2^59 / r) (see lift_mod_r).
 static __constant__ uint32_t c_q1_mod_r[NUM_S] = HERS_Q1_MOD_R_INIT;
-static __constant__ uint32_t c_q1_mod_r_s[NUM_S] = HERS_Q1_MOD_R_S_INIT;
-static __constant__ uint32_t c_q_mod_r[NUM_S] = HERS_Q_MOD_R_INIT;
+static __constant__ uint32_t c_lift_b[NUM_S] = HERS_LIFT_B_INIT;
+static __constant__ uint32_t c_lift_nq[NUM_S] = HERS_LIFT_NQ_INIT;
+static __constant__ uint32_t c_mu59[NUM_S] = HERS_MU59_INIT;
 // CRT of X' = X + q 2^129: y_i = x_i Minv_i + HM_i mod r_i, Minv_i = (M / r_i)^-1
 // mod r_i, HM_i = (q 2^129 mod r_i) Minv_i; alpha = floor(sum y_i PHI_i / 2^60).
 static __constant__ uint32_t c_minv[NUM_S] = HERS_MINV_INIT;
@@ -647,6 +649,38 @@ __device__ __forceinline__ void ntt32_inv_regs(uint32_t v[16], uint32_t* sm, con
     gs_phase32<256, true>(v, t, w, r, ninv, ninv_s);
 }
 
+// The forward transform with its first phase on registers: v holds the
+// inputs (below 2r) at coefficients t + 256 a on entry; the outputs
+// (bit-reversed order, fully reduced) are in sm at swz32(k) on exit, after a
+// CTA barrier.  The barrier before the first shared-memory store lets a
+// caller still reading sm's previous contents (in other threads) finish.
+__device__ __forceinline__ void ntt32_fwd_regs(uint32_t v[16], uint32_t* sm, const uint2* __restrict__ w,
+                                               uint32_t r, int t) {
+    ct_phase32<256>(v, t, w, r);
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 16; a++) sm[swz32(t + 256 * a)] = v[a];
+    __syncthreads();
+    {
+        const int base = 256 * (t >> 4) + (t & 15);
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz32(base + 16 * a)];
+        ct_phase32<16>(v, base, w, r);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz32(base + 16 * a)] = v[a];
+    }
+    __syncwarp();
+    {
+        const int base = 16 * t;
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = sm[swz32(base + a)];
+        ct_phase32<1>(v, base, w, r);
+#pragma unroll
+        for (int a = 0; a < 16; a++) sm[swz32(base + a)] = csub32(csub32(v[a], 2 * r), r);
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ void ntt32_fwd_mod(uint32_t* a, const uint64_t* tw, int i, int t = threadIdx.x) {
     ntt32_fwd_smem(a, tw32_fwd(tw, i), c_smod[i], t);
 }
@@ -726,10 +760,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-// ---------------------------------------------------------------- base extension Q -> p_i
+// ---------------------------------------------------------------- base extension Q -> r_i
 // x given by its residues (x1 mod q1, x2 mod q2), read as the centred integer
-// in (-q/2, q/2] (App. A's symmetric representative); returns x mod p_i,
-// exactly, for i in 0..4.
+// in (-q/2, q/2] (App. A's symmetric representative), and reduced mod each
+// prime r_i of the search basis, exactly.
 struct Lifted {
     uint64_t x1;   // x1 in [0, q1)
     uint64_t h;    // Garner digit in [0, q2): x = x1 + q1 h in [0, q)
@@ -747,13 +781,28 @@ __device__ __forceinline__ Lifted lift_q(uint64_t x1, uint64_t x2) {
     return L;
 }
 
-// The centred x (-q/2 < x <= q/2) of a lift, mod r_i: x1 + q1 h - [neg] q.
-__device__ __forceinline__ uint32_t lifted_mod_r(const Lifted& L, int i) {
+// A lift packed for reduction mod many r_i: {x1 low word, x1 high word,
+// h mod 2^27, floor(h / 2^27) | neg << 31} (h < 2^54, so the top digit
+// leaves bit 31 free).
+__device__ __forceinline__ uint4 lift_pack(uint64_t x1, uint64_t x2) {
+    const Lifted L = lift_q(x1, x2);
+    return make_uint4((uint32_t)L.x1, (uint32_t)(L.x1 >> 32), (uint32_t)L.h & ((1u << 27) - 1),
+                      (uint32_t)(L.h >> 27) | ((uint32_t)L.neg << 31));
+}
+
+// The centred lift mod r_i from its packed form: with h = hl + 2^27 hh,
+//   x - [neg] q = x1 + hl [q1]_r + hh [q1 2^27]_r + [neg] [-q]_r  (mod r),
+// a sum S below 2^59 (x1 < 2^54, each product below 2^57).  Barrett with
+// mu = floor(2^59 / r): est = floor(floor(S / 2^27) mu / 2^32) is short of
+// floor(S / r) by at most 2, so S - est r lies in [0, 3r) and is computed in
+// 32 bits.
+__device__ __forceinline__ uint32_t lift_mod_r(uint4 g, int i) {
     const uint32_t r = c_smod[i];
-    const uint32_t m = shoup32(reduce_r(L.h, i), c_q1_mod_r[i], c_q1_mod_r_s[i], r);  // [0, 2r)
-    uint32_t v = csub32(csub32(reduce_r(L.x1, i) + m, 2 * r), r);
-    if (L.neg) v = v >= c_q_mod_r[i] ? v - c_q_mod_r[i] : v + r - c_q_mod_r[i];
-    return v;
+    uint64_t s = ((uint64_t)g.y << 32 | g.x) + ((g.w >> 31) ? c_lift_nq[i] : 0u);
+    s += (uint64_t)g.z * c_q1_mod_r[i];
+    s += (uint64_t)(g.w & ((1u << 27) - 1)) * c_lift_b[i];
+    const uint32_t est = __umulhi((uint32_t)(s >> 27), c_mu59[i]);
+    return csub32(csub32((uint32_t)s - est * r, 2 * r), r);
 }
 
 // ---------------------------------------------------------------- CRT over the search basis

@@ -175,10 +175,13 @@ def build():
     arrays.append(("SMU", [(1 << 64) // r for r in R]))                  # Barrett, 64-bit inputs
     arrays.append(("SR32", [(1 << 32) % r for r in R]))                  # partial folds
     arrays.append(("SOFF63", [r * ((1 << 63) // r) for r in R]))         # multiple of r just below 2^63
-    # extension: x mod r from the lift (x1, h, sign): (q1 mod r), (q mod r)
+    # extension: the centred lift x = x1 + q1 h - [neg] q mod r from x1 and the
+    # 27-bit digits of h: [q1]_r, [q1 2^27]_r, [-q]_r, and the Barrett factor
+    # floor(2^59 / r) of the sum
     arrays.append(("Q1_MOD_R", [q1 % r for r in R]))
-    arrays.append(("Q1_MOD_R_S", [shoup32(q1 % r, r) for r in R]))
-    arrays.append(("Q_MOD_R", [q % r for r in R]))
+    arrays.append(("LIFT_B", [(q1 << 27) % r for r in R]))
+    arrays.append(("LIFT_NQ", [(-q) % r for r in R]))
+    arrays.append(("MU59", [(1 << 59) // r for r in R]))
     # CRT of X' = X + H: y_i = x_i Minv_i + HM_i (mod r_i), alpha = floor(sum y_i phi_i / 2^60)
     minv = [pow(M // r, -1, r) for r in R]
     arrays.append(("MINV", minv))
@@ -248,6 +251,12 @@ def build():
     # leaves |s| < 2^61 + 2^32, then 8 dimensions add below 2^62 (middle term)
     assert all((r - 1) // 2 < 1 << 29 for r in R)
     assert (1 << 61) + (1 << 32) + 8 * (1 << 59) < 1 << 63
+    # extension: the sum S = x1 + hl [q1]_r + hh [q1 2^27]_r (+ [-q]_r) of
+    # x1, h < 2^54 stays below 2^59, so S >> 27 and floor(2^59 / r) fit 32
+    # bits, and S - est r lies in [0, 3r) with 3r < 2^32
+    assert q1 < 1 << 54 and q2 < 1 << 54
+    assert all((1 << 54) + r + 2 * ((1 << 27) - 1) * (r - 1) < 1 << 59 for r in R)
+    assert all((1 << 59) // r < 1 << 32 and 3 * r < 1 << 32 for r in R)
 
     cdt = chi_cdt()
     return mods, psis, C, arrays, cdt

@@ -347,41 +347,63 @@ cudaError_t launch_resident_to_canonical_add(const uint64_t* tw, const uint64_t*
 
 // ---------------------------------------------------------------- extension to the search form
 //
-// One CTA per canonical ciphertext polynomial P (residues mod q1, q2): takes
-// its centred representative x in (-q/2, q/2] (App. A) once per coefficient,
-// reduces it mod every prime of the search basis, and writes NTT_{r_l}(x mod
-// r_l), as centred int32, at the resident (tiled) position of ciphertext
-// ct_begin + P/2 = b d + i.  EXT_GROUPS groups of NTT_THREADS threads run
-// NUM_S / EXT_GROUPS of the transforms each.  Exactness of the later tensor
-// product needs the centred lift: the product of two such polynomials over
-// Z, summed over d <= 512 dimensions, stays below 2^236 < M / 2^4.
-constexpr int EXT_GROUPS = 4;
-constexpr int EXT_SMEM = NUM_S * N * 4;
-__global__ void __launch_bounds__(NTT_THREADS * EXT_GROUPS, 1) k_extend_ntt(const uint64_t* __restrict__ tw,
-                                                                          const uint64_t* __restrict__ ct,
-                                                                          uint64_t ct_begin, uint32_t d,
-                                                                          uint64_t* __restrict__ out) {
-    extern __shared__ uint32_t sm32[];
+// Takes each coefficient of a canonical ciphertext polynomial P (residues mod
+// q1, q2) to its centred representative x in (-q/2, q/2] (App. A), reduces it
+// mod the primes of the search basis, and writes NTT_{r_l}(x mod r_l), as
+// centred int32, at the resident (tiled) position of ciphertext
+// ct_begin + P/2 = b d + i.  Exactness of the later tensor product needs the
+// centred lift: the product of two such polynomials over Z, summed over
+// d <= 512 dimensions, stays below 2^236 < M / 2^4.
+//
+// A CTA covers all NUM_S primes of one polynomial.  It lifts every
+// coefficient once, into shared memory in the packed form of lift_pack (16
+// bytes per coefficient); then EXT_GROUPS groups of NTT_THREADS threads run
+// NUM_S / EXT_GROUPS transforms each.  A thread reduces its 16 first-phase
+// coefficients (t + 256 a) mod r_l straight into registers, the other two
+// phases pass through the group's own N words of shared memory, and the
+// outputs go from there to the resident form: coefficient t + 256 a lies in
+// tile a at position t, so a thread's 16 outputs of one prime are one base
+// address and a fixed stride apart.  96 KiB of shared memory and 64
+// registers give two CTAs per SM.
+constexpr int EXT_GROUPS = 2;
+constexpr int EXT_THREADS = NTT_THREADS * EXT_GROUPS;
+constexpr int EXT_SMEM = N * 16 + EXT_GROUPS * N * 4;
+__global__ void __launch_bounds__(EXT_THREADS, 2) k_extend_ntt(const uint64_t* __restrict__ tw,
+                                                              const uint64_t* __restrict__ ct, uint64_t ct_begin,
+                                                              uint32_t d, uint64_t* __restrict__ out) {
+    extern __shared__ uint4 smx[];  // [N] packed lifts, then [EXT_GROUPS][N] transform words
     const uint64_t P = blockIdx.x;
-    const uint64_t* x1 = ct + (P * 2 + 0) * N;
-    const uint64_t* x2 = ct + (P * 2 + 1) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const Lifted L = lift_q(x1[k], x2[k]);
+    {
+        const uint64_t* x1 = ct + (P * 2 + 0) * N;
+        const uint64_t* x2 = ct + (P * 2 + 1) * N;
+        uint64_t a[N / EXT_THREADS], b[N / EXT_THREADS];
 #pragma unroll
-        for (int l = 0; l < NUM_S; l++) sm32[l * N + swz32(k)] = lifted_mod_r(L, l);
+        for (int j = 0; j < N / EXT_THREADS; j++) {
+            a[j] = x1[threadIdx.x + j * EXT_THREADS];
+            b[j] = x2[threadIdx.x + j * EXT_THREADS];
+        }
+#pragma unroll
+        for (int j = 0; j < N / EXT_THREADS; j++) smx[threadIdx.x + j * EXT_THREADS] = lift_pack(a[j], b[j]);
     }
+    __syncthreads();
     const uint64_t c = ct_begin + P / 2;
     const uint64_t blk = c / d;
     const uint32_t i = (uint32_t)(c % d);
     const int poly = (int)(P & 1);
-    int32_t* o = (int32_t*)out;
     const int grp = threadIdx.x / NTT_THREADS, t = threadIdx.x % NTT_THREADS;
+    uint32_t* buf = (uint32_t*)(smx + N) + grp * N;
+    const uint64_t tile_stride = (uint64_t)d * TILE * 2;  // int32 words from tile a to a + 1
+#pragma unroll 1
     for (int lg = 0; lg < NUM_S / EXT_GROUPS; lg++) {
-        const int l = grp * (NUM_S / EXT_GROUPS) + lg;
-        uint32_t* s = sm32 + l * N;
-        ntt32_fwd_mod(s, tw, l, t);  // begins with a CTA barrier: the lift above is complete
+        const int l = lg * EXT_GROUPS + grp;
         const uint32_t r = c_smod[l];
-        for (int k = t; k < N; k += NTT_THREADS) o[resident_offset(blk, l, k, d, i, poly)] = centre32(s[swz32(k)], r);
+        uint32_t v[16];
+#pragma unroll
+        for (int a = 0; a < 16; a++) v[a] = lift_mod_r(smx[t + 256 * a], l);
+        ntt32_fwd_regs(v, buf, tw32_fwd(tw, l), r, t);  // ends with a CTA barrier
+        int32_t* o = (int32_t*)out + resident_offset(blk, l, t, d, i, poly);
+#pragma unroll
+        for (int a = 0; a < 16; a++) o[a * tile_stride] = centre32(buf[swz32(t + 256 * a)], r);
     }
 }
 
@@ -389,11 +411,10 @@ cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t n
                               uint32_t d, uint64_t* out, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_extend_ntt, cudaFuncAttributeMaxDynamicSharedMemorySize, EXT_SMEM);
     if (e != cudaSuccess) return e;
-    const uint64_t chunk = 1u << 30;
+    const uint64_t chunk = 1u << 30;  // polynomials per launch
     for (uint64_t off = 0; off < 2 * nct; off += chunk) {
         const uint64_t n = 2 * nct - off < chunk ? 2 * nct - off : chunk;
-        k_extend_ntt<<<(unsigned)n, NTT_THREADS * EXT_GROUPS, EXT_SMEM, st>>>(tw, ct + off * 2 * N,
-                                                                              ct_begin + off / 2, d, out);
+        k_extend_ntt<<<(unsigned)n, EXT_THREADS, EXT_SMEM, st>>>(tw, ct + off * 2 * N, ct_begin + off / 2, d, out);
         count_launches(1);
     }
     return cudaGetLastError();

@@ -9,7 +9,8 @@ arithmetic step by step (the 32-bit Shoup products, the fixed-point overflow
 count alpha, the 27-bit digit columns, the quotient estimate and its
 correction) against exact rounding round(t X / q) for both plaintext moduli,
 at the bound |X| = d N q^2 / 2 of d <= 512, on rounding boundaries, and on
-random values; and the return of centred lifts to mod q (enrollment).
+random values; the return of centred lifts to mod q (enrollment); and the
+extension's reduction of a centred lift mod each r_i.
 """
 import os
 import random
@@ -45,7 +46,9 @@ def consts():
     return dict(q1=mods[0], q2=mods[1], R=arr("SMOD"), MINV=arr("MINV"), MINV_S=arr("MINV_S"), HM=arr("HM"),
                 PHI=arr("PHI"), MIQ=arr("MI_Q_COLS"), MQ=arr("M_Q_COLS"), SR32=arr("SR32"), SMU=arr("SMU"),
                 SOFF63=arr("SOFF63"), MU=scal("MU_Q144"), K=(scal("KROUND_HI") << 64) | scal("KROUND_LO"),
-                Q=(scal("Q_HI") << 64) | scal("Q_LO"), plains=plains)
+                Q=(scal("Q_HI") << 64) | scal("Q_LO"), plains=plains, Q1R=arr("Q1_MOD_R"),
+                LB=arr("LIFT_B"), LNQ=arr("LIFT_NQ"), MU59=arr("MU59"), Q1INV=scal("Q1INV_Q2"),
+                HQLO=scal("HALFQ_LO"), HQHI=scal("HALFQ_HI"))
 
 
 def is_prime(n):
@@ -206,3 +209,29 @@ def test_partial_fold_keeps_the_residue(c):
             qe = (u * c["SMU"][i]) >> 64
             rr = (u - qe * r) & 0xFFFFFFFF
             assert rr < 2 * r and (rr if rr < r else rr - r) == s % r
+
+
+def test_extension_reduces_the_centred_lift(c):
+    """The extension kernel's steps: Garner digit h of the residue pair, the sign
+    of x = x1 + q1 h against (q-1)/2 from the stored (q-1)/2 = HI q1 + LO, and
+    x - [neg] q mod r_i from x1 and the 27-bit digits of h (sum below 2^59,
+    Barrett estimate short by at most 2), against v mod r_i for the centred v."""
+    q, q1, q2 = c["Q"], c["q1"], c["q2"]
+    assert c["Q1INV"] == pow(q1, -1, q2) and c["HQHI"] * q1 + c["HQLO"] == (q - 1) // 2
+    rng = random.Random(5)
+    half = (q - 1) // 2
+    vals = [0, 1, -1, half, -half, half - 1, -half + 1, q1, -q1, q2, -q2, q1 - 1, 1 << 100, -(1 << 100)]
+    vals += [rng.randint(-half, half) for _ in range(2000)]
+    for v in vals:
+        x1, x2 = v % q1, v % q2
+        h = (x2 - x1 % q2) * c["Q1INV"] % q2
+        neg = h > c["HQHI"] or (h == c["HQHI"] and x1 > c["HQLO"])
+        assert x1 + q1 * h - neg * q == v
+        hl, hh = h & ((1 << 27) - 1), h >> 27
+        for i, r in enumerate(c["R"]):
+            s = x1 + hl * c["Q1R"][i] + hh * c["LB"][i] + (c["LNQ"][i] if neg else 0)
+            assert s < 1 << 59
+            est = ((s >> 27) * c["MU59"][i]) >> 32
+            rem = s - est * r
+            assert 0 <= rem < 3 * r
+            assert rem % r == v % r, (v, i)
