@@ -26,11 +26,16 @@
 namespace hers {
 
 constexpr uint32_t UNIT_STOP = 0xFFFFFFFFu;
-constexpr int BPFOLD = 8;  // partial-fold period of T1 in dimensions, 2 BPFOLD for T0, T2 (see k_tensor)
+// Partial-fold periods in dimensions: the Karatsuba sums S (products below
+// 2^60) every BPFOLD_S, T0 and T2 (below 2^58) every BPFOLD_02.  A folded sum
+// is below 2^61 + 2^32, so 4 more S products stay below 7 2^60 + 2^32 and 16
+// more T0/T2 products below 2^62 + 2^61 + 2^32, both inside a signed 64-bit.
+constexpr int BPFOLD_S = 4;
+constexpr int BPFOLD_02 = 16;
 
 // Stage descriptor flags (written by the producer with each stage).
 constexpr uint32_t F_FIRST = 1;  // first stage of a unit: sums start at zero
-constexpr uint32_t F_FOLD = 2;   // partial fold of the T1 sums after this stage
+constexpr uint32_t F_FOLD = 2;   // partial fold of the S sums after this stage
 constexpr uint32_t F_LAST = 4;   // last stage of a unit: store the unit's results
 constexpr uint32_t F_STOP = 8;   // no more units: the consumers leave
 constexpr uint32_t F_FOLD02 = 16;  // partial fold of the T0 and T2 sums after this stage
@@ -68,9 +73,13 @@ __device__ __forceinline__ void load_unit(UnitRegs<NP>& r, const BatchChunk* __r
 }
 
 // One stage's products into the 64-bit sums: for dd < nd, probe q < np,
-// block j < nb, the four products of (probe row q) x (gallery row j) (centred
-// int32 residues, see k_tensor).  With FULL (nd = DPS, np = NP, nb = NB) the
-// loops carry no predicates.
+// block j < nb, the tensor of (probe row q) x (gallery row j) (centred int32
+// residues, see k_tensor) by Karatsuba's three products: T0 += a0 g0,
+// T2 += a1 g1 and S += (a0 + a1)(g0 + g1), so that the middle component
+// a0 g1 + a1 g0 of Alg 5's tensor is S - T0 - T2 (formed mod r_l at the end).
+// The sums a0 + a1 and g0 + g1 are below r < 2^30 in magnitude, their
+// product below 2^60.  With FULL (nd = DPS, np = NP, nb = NB) the loops carry
+// no predicates.
 template <int NP, int NB, int DPS, bool FULL>
 __device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const int2* base, uint32_t nd,
                                                uint32_t np, uint32_t nbu) {
@@ -78,24 +87,24 @@ __device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const in
 #pragma unroll
     for (int dd = 0; dd < DPS; dd++) {
         if (FULL || (uint32_t)dd < nd) {
-            int32_t a0[NP], a1[NP];
+            int32_t a0[NP], a1[NP], as[NP];
 #pragma unroll
             for (int q = 0; q < NP; q++) {
                 const int2 A = base[q * RUN2 + dd * TILE];
                 a0[q] = A.x;
                 a1[q] = A.y;
+                as[q] = A.x + A.y;
             }
 #pragma unroll
             for (int j = 0; j < NB; j++) {
                 if (FULL || (uint32_t)j < nbu) {
                     const int2 G = base[(NP + j) * RUN2 + dd * TILE];
-                    const int32_t g0 = G.x, g1 = G.y;
+                    const int32_t g0 = G.x, g1 = G.y, gs = G.x + G.y;
 #pragma unroll
                     for (int q = 0; q < NP; q++) {
                         if (FULL || (uint32_t)q < np) {
                             madw_b(s[q][j][0], a0[q], g0);
-                            madw_b(s[q][j][1], a0[q], g1);
-                            madw_b(s[q][j][1], a1[q], g0);
+                            madw_b(s[q][j][1], as[q], gs);
                             madw_b(s[q][j][2], a1[q], g1);
                         }
                     }
@@ -118,7 +127,7 @@ template <int NP, int NB, int STAGES, int DPS, int MINB>
 __global__ void __launch_bounds__(TILE + 32, MINB)
     k_tensor_batched(const BatchChunk* __restrict__ chunks, const BatchUnit* __restrict__ units,
                      uint32_t nunits, uint32_t* counter, uint32_t* __restrict__ X, int* err) {
-    static_assert(BPFOLD % DPS == 0, "stages must not straddle a partial fold");
+    static_assert(BPFOLD_S % DPS == 0 && BPFOLD_02 % BPFOLD_S == 0, "stages must not straddle a partial fold");
     static_assert(NP <= BATCH_NPMAX && NB <= 15 && DPS <= 255 && NUM_S <= 16, "descriptor fields");
     extern __shared__ __align__(128) int32_t smr[];
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
@@ -163,8 +172,8 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
                     }
                     const uint32_t nd = min((uint32_t)DPS, cur.d - si * DPS), done = si * DPS + nd;
                     const uint32_t flags = (si == 0 ? F_FIRST : 0u) |
-                                           ((done % BPFOLD == 0 && done < cur.d) ? F_FOLD : 0u) |
-                                           ((done % (2 * BPFOLD) == 0 && done < cur.d) ? F_FOLD02 : 0u) |
+                                           ((done % BPFOLD_S == 0 && done < cur.d) ? F_FOLD : 0u) |
+                                           ((done % BPFOLD_02 == 0 && done < cur.d) ? F_FOLD02 : 0u) |
                                            (done == cur.d ? F_LAST : 0u);
                     hdr_info[st] = nd | (cur.np << 8) | (cur.nb << 12) | (cur.limb << 16) | (flags << 20);
                     if (flags & F_LAST) {
@@ -260,9 +269,12 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
                     for (int j = 0; j < NB; j++)
                         if ((uint32_t)j < nbu) {
                             const uint64_t pair = opair[q] + j;
-#pragma unroll
-                            for (int c = 0; c < 3; c++)
-                                X[((pair * 3 + c) * NUM_S + l) * N + k] = fold_full(s[q][j][c], l);
+                            const uint32_t r = c_smod[l];
+                            const uint32_t x0 = fold_full(s[q][j][0], l), x2 = fold_full(s[q][j][2], l);
+                            const uint32_t x1 = csub32(csub32(fold_full(s[q][j][1], l) + 2 * r - x0 - x2, 2 * r), r);
+                            X[((pair * 3 + 0) * NUM_S + l) * N + k] = x0;
+                            X[((pair * 3 + 1) * NUM_S + l) * N + k] = x1;
+                            X[((pair * 3 + 2) * NUM_S + l) * N + k] = x2;
                         }
         }
     }

@@ -251,6 +251,11 @@ def build():
     # leaves |s| < 2^61 + 2^32, then 8 dimensions add below 2^62 (middle term)
     assert all((r - 1) // 2 < 1 << 29 for r in R)
     assert (1 << 61) + (1 << 32) + 8 * (1 << 59) < 1 << 63
+    # batched tensor (Karatsuba): S sums products of two sums of centred
+    # residues, |(a0 + a1)(b0 + b1)| <= (r - 1)^2 < 2^60; 4 dimensions after a
+    # partial fold, or 7 from zero, stay below 2^63 - r (fold_full's range)
+    assert all((1 << 61) + (1 << 32) + 4 * (r - 1) ** 2 < (1 << 63) - r for r in R)
+    assert all(7 * (r - 1) ** 2 < (1 << 63) - r for r in R)
     # extension: the sum S = x1 + hl [q1]_r + hh [q1 2^27]_r (+ [-q]_r) of
     # x1, h < 2^54 stays below 2^59, so S >> 27 and floor(2^59 / r) fit 32
     # bits, and S - est r lies in [0, 3r) with 3r < 2^32

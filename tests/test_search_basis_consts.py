@@ -205,6 +205,8 @@ def test_partial_fold_keeps_the_residue(c):
             # 8 dimensions of the middle sum (2 products, below 2^59) and 16 of
             # the outer ones (1 product, below 2^58) stay below 2^63
             assert abs(f) + 8 * (1 << 59) < 1 << 63 and abs(f) + 16 * (1 << 58) < 1 << 63
+            # the batched kernel's Karatsuba sums: 4 products of (a0 + a1)(b0 + b1)
+            assert abs(f) + 4 * (r - 1) ** 2 < (1 << 63) - r
             u = (f + c["SOFF63"][i]) & ((1 << 64) - 1)
             qe = (u * c["SMU"][i]) >> 64
             rr = (u - qe * r) & 0xFFFFFFFF
@@ -235,3 +237,27 @@ def test_extension_reduces_the_centred_lift(c):
             rem = s - est * r
             assert 0 <= rem < 3 * r
             assert rem % r == v % r, (v, i)
+
+
+def test_karatsuba_middle_term(c):
+    """The batched kernel's middle tensor component: with T0 = sum a0 b0,
+    T2 = sum a1 b1 and S = sum (a0 + a1)(b0 + b1) reduced to [0, r) (x0, x2,
+    xs), x1 = ((xs + 2r - x0 - x2) - 2r if >= 2r) - r if >= r equals
+    sum (a0 b1 + a1 b0) mod r, at the extreme centred residues and at random."""
+    rng = random.Random(13)
+    for r in c["R"]:
+        h = (r - 1) // 2
+        for _ in range(300):
+            d = rng.randint(1, 16)
+            pick = lambda: rng.choice([h, -h, 0, 1, -1, rng.randint(-h, h)])
+            a = [(pick(), pick()) for _ in range(d)]
+            b = [(pick(), pick()) for _ in range(d)]
+            t0 = sum(x[0] * y[0] for x, y in zip(a, b))
+            t2 = sum(x[1] * y[1] for x, y in zip(a, b))
+            s = sum((x[0] + x[1]) * (y[0] + y[1]) for x, y in zip(a, b))
+            x0, x2, xs = t0 % r, t2 % r, s % r
+            v = xs + 2 * r - x0 - x2
+            assert 0 < v < 3 * r and v < 1 << 32
+            v = v - 2 * r if v >= 2 * r else v
+            v = v - r if v >= r else v
+            assert v == sum(x[0] * y[1] + x[1] * y[0] for x, y in zip(a, b)) % r
