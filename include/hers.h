@@ -358,9 +358,9 @@ int hers_server_free(hers_server* srv);
 /*
  * Streamed search over a gallery kept in canonical form.  The canonical form
  * has 2 limbs in the coefficient domain, 32 d bytes per entry, i.e. the
- * ciphertexts' own size.  It is meant for galleries too large for the 5-prime
- * resident form: 100M entries at d = 64 are 204.8 GB canonical against 512 GB
- * resident.
+ * ciphertexts' own size.  It is meant for galleries too large for the
+ * resident form (64 d bytes per entry): 100M entries at d = 64 are 204.8 GB
+ * canonical against 409.6 GB resident.
  *
  * The gallery is gallery_ct, [nblocks][d][2][2][N], in host memory when
  * gallery_on_host (pinned for full copy speed) or in device memory.
