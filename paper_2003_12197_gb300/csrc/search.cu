@@ -277,10 +277,13 @@ __global__ void __launch_bounds__(NTT_THREADS, 4) k_intt32_batch(const uint64_t*
 // Writes c to C[b][c][l][N] and, for c = 2, the relinearisation digits
 // D_1 = c2 mod q1, D_2 = c2 mod q2 reduced into both limbs:
 // KS[b][0] = D_1 mod q1, [1] = D_1 mod q2, [2] = D_2 mod q1, [3] = D_2 mod q2.
+// PM: the context's plaintext modulus entry, a template argument so that the
+// digit tables are read as constant operands at fixed offsets.
+template <int PM>
 __global__ void __launch_bounds__(256) k_scale_round(const uint32_t* __restrict__ X,
                                                      uint64_t* __restrict__ C,
-                                                     uint64_t* __restrict__ KS, int pm) {
-    const PlainMod& P = c_plain[pm];
+                                                     uint64_t* __restrict__ KS) {
+    const PlainMod& P = c_plain[PM];
     const int k = blockIdx.x * 256 + threadIdx.x;
     const int c = blockIdx.y;
     const uint64_t b = blockIdx.z;
@@ -445,8 +448,11 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
     if (ev) cudaEventRecord(ev[0], st);
     for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
         const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
-        k_scale_round<<<dim3(N / 256, 3, (unsigned)nb), 256, 0, st>>>(X32 + b0 * 3 * NUM_S * N, C + b0 * 6 * N,
-                                                                     KS + b0 * 4 * N, k.pm);
+        const dim3 grid(N / 256, 3, (unsigned)nb);
+        if (k.pm == 0)
+            k_scale_round<0><<<grid, 256, 0, st>>>(X32 + b0 * 3 * NUM_S * N, C + b0 * 6 * N, KS + b0 * 4 * N);
+        else
+            k_scale_round<1><<<grid, 256, 0, st>>>(X32 + b0 * 3 * NUM_S * N, C + b0 * 6 * N, KS + b0 * 4 * N);
         nl++;
     }
     if (ev) cudaEventRecord(ev[1], st);
