@@ -457,9 +457,10 @@ __global__ void __cluster_dims__(NUM_S, 1, 1) __launch_bounds__(NTT_THREADS, 4)
 }
 
 // Up to this many polynomials per call take the cluster form: probes of
-// d <= 32.  Measured (probe preparation in a CUDA graph): d = 16, 14.2 us
-// against 27.3 us for one CTA per polynomial; d = 64, 38.6 us against 27.9
-// us, as its 8 CTAs per polynomial no longer fit one wave.
+// d <= 32.  Measured (probe preparation in a CUDA graph, cluster form against
+// one CTA per polynomial): d = 16, 14.2 against 27.3 us; d = 32, 23.2 against
+// 27.6 us; d = 48, equal; d = 64, 38.9 against 28.3 us, as 8 CTAs per
+// polynomial no longer fit one wave.
 constexpr uint64_t EXT_CLUSTER_MAX_POLYS = 64;
 
 cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t ct_begin,
