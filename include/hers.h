@@ -179,6 +179,8 @@ int hers_probe_prepare(hers_ctx* ctx, const uint64_t* probe_ct, uint32_t d, uint
  * the call (or a synchronisation of `stream`) sees the finished scores.
  * Searches on several streams of one context may be in flight at once;
  * calls on one context must come from one host thread at a time.
+ * nblocks = 0 is accepted and enqueues nothing (the pointers must still be
+ * non-null).
  */
 int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
                 uint32_t d, const uint64_t* probe, uint64_t* scores_ct, void* workspace,

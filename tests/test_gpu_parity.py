@@ -161,6 +161,19 @@ def test_invalid_arguments_are_rejected(ctx, keys):
                                                                          device="cuda"))
 
 
+def test_empty_inputs(ctx, keys):
+    """An empty gallery is refused at encryption; a search over zero blocks is
+    accepted and writes nothing."""
+    with pytest.raises(H.HersError):
+        H.hers_encrypt_gallery(ctx, keys, torch.zeros((0, 16), dtype=torch.int8, device="cuda"), 1)
+    out = torch.full((16,), 0x5A5A, dtype=torch.int64, device="cuda")
+    dummy = torch.zeros(16, dtype=torch.int64, device="cuda")
+    H.hers_search(ctx, keys, dummy, 0, 16, dummy, out=out, workspace=dummy)
+    torch.cuda.synchronize()
+    H.hers_check(ctx)
+    assert bool((out == 0x5A5A).all())
+
+
 @pytest.mark.slow
 def test_config2_full_size(ctx, keys, oracle_keys):
     """1,048,576 entries (256 blocks), d = 64, one planted mate: every decrypted
