@@ -101,7 +101,9 @@ uint64_t hers_blocks_for(uint64_t m);                            /* ceil(m / N) 
  * evk_j = ([-(a_j s + e_j) + g_j s^2]_q, a_j), g_j = (q/q_j) [(q/q_j)^-1]_{q_j}
  * (an RNS gadget: the base-w decomposition of Alg 1 with one digit per prime).
  * All key material stays in device memory inside *out (freed by
- * hers_keys_free).  Synchronous.  HERS_E_SAMPLER if a sampler ran out of
+ * hers_keys_free): this is the client's handle, secret key included.  A
+ * server builds its own handle from pk and evk alone (hers_keys_export on
+ * the client, hers_keys_import on the server).  Synchronous.  HERS_E_SAMPLER if a sampler ran out of
  * attempts (probability below 2^-400).
  */
 int hers_keygen(hers_ctx* ctx, uint64_t seed, hers_keys** out);
@@ -112,6 +114,23 @@ int hers_keys_free(hers_keys* keys);
  * ([digit j][poly][limb][N]).  Any pointer may be NULL to skip it. */
 int hers_keys_export(hers_ctx* ctx, const hers_keys* keys, int8_t* sk, uint64_t* pk,
                      uint64_t* evk);
+
+/*
+ * Server-side keys (Sec. 3.1: the server holds pk and evk, never sk; Alg 7's
+ * server loop uses only evk, Alg 6's server side only pk).  Builds a key
+ * handle on ctx from the canonical public key pk, host uint64 [2][2][N], and
+ * relinearisation keys evk, host uint64 [2][2][2][N] ([digit j][poly][limb][N]),
+ * as hers_keys_export writes them on the client.  Every residue must lie in
+ * [0, q_l) (HERS_E_INVAL otherwise).  The handle serves every call that
+ * encrypts or searches (hers_encrypt_*, hers_enroll, hers_search*,
+ * hers_batch_*, hers_server_*, hers_search_stream); calls that need the secret
+ * key (hers_decrypt_scores*, hers_keys_add_basew, hers_keys_export of sk)
+ * return HERS_E_INVAL with it.  Synchronous; freed by hers_keys_free.
+ * hers_keys_has_secret: 1 if the handle holds a secret key (hers_keygen), 0
+ * if not (hers_keys_import) or keys is NULL.
+ */
+int hers_keys_import(hers_ctx* ctx, const uint64_t* pk, const uint64_t* evk, hers_keys** out);
+int hers_keys_has_secret(const hers_keys* keys);
 
 /*
  * Enrollment, batch form (Alg 6; Eq. 3 encoding; Alg 2 encryption).
@@ -131,6 +150,39 @@ int hers_keys_export(hers_ctx* ctx, const hers_keys* keys, int8_t* sk, uint64_t*
 int hers_encrypt_gallery(hers_ctx* ctx, const hers_keys* keys, const int8_t* feats, uint64_t m,
                          uint32_t d, uint64_t seed, uint64_t* gallery, uint64_t* gallery_ct,
                          void* stream);
+
+/*
+ * hers_encrypt_gallery with the features in host memory: feats_host, host
+ * int8 [m][d] row-major, pageable or pinned.  The call stages them in a
+ * temporary device buffer of m d bytes (stream-ordered allocation on
+ * `stream`, freed before it returns), encrypts as hers_encrypt_gallery does,
+ * and returns after the gallery is written (synchronous; sampler failures are
+ * reported as HERS_E_SAMPLER).  Same gallery and gallery_ct arguments.
+ */
+int hers_encrypt_gallery_host(hers_ctx* ctx, const hers_keys* keys, const int8_t* feats_host, uint64_t m,
+                              uint32_t d, uint64_t seed, uint64_t* gallery, uint64_t* gallery_ct,
+                              void* stream);
+
+/*
+ * Persistence and transfer of a resident gallery in the exchange form (Alg 6:
+ * the server stores the enrolled ciphertexts; a ciphertext is a pair of
+ * polynomials in R_q, App. A).  The resident form is private to the library;
+ * these calls convert blocks [block_begin, block_end) of a resident gallery of
+ * nblocks blocks and dimension d to and from canonical ciphertexts in host
+ * memory, ct_host uint64 [block_end - block_begin][d][2][2][N] (the layout of
+ * hers_encrypt_gallery's gallery_ct).
+ * hers_export_ct: resident -> canonical (inverse NTTs and the CRT of the
+ *   search basis on the device), exactly the ciphertexts that were enrolled.
+ * hers_import_ct: canonical -> resident (the extension of
+ *   hers_encrypt_gallery); HERS_E_INVAL if a residue is not in [0, q_l).
+ * Both are synchronous on the context's stream and use a device staging
+ * buffer of at most 256 MiB for the duration of the call; host buffers may be
+ * pageable.  An empty range does nothing.
+ */
+int hers_export_ct(hers_ctx* ctx, const uint64_t* gallery, uint64_t nblocks, uint32_t d, uint64_t block_begin,
+                   uint64_t block_end, uint64_t* ct_host);
+int hers_import_ct(hers_ctx* ctx, const uint64_t* ct_host, uint64_t nblocks, uint32_t d, uint64_t block_begin,
+                   uint64_t block_end, uint64_t* gallery);
 
 /*
  * Online single-entry enrollment (Alg 6): the entry's d int8 features (device
@@ -186,6 +238,18 @@ int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
                 uint32_t d, const uint64_t* probe, uint64_t* scores_ct, void* workspace,
                 uint64_t workspace_bytes, void* stream);
 /*
+ * hers_search over blocks [block_begin, block_end) of a resident gallery of
+ * nblocks blocks (Alg 7's loop over the gallery's blocks, restricted to a
+ * range): scores_ct receives [block_end - block_begin][2][2][N], the score
+ * ciphertext of block block_begin first; the workspace is sized for
+ * block_end - block_begin blocks.  HERS_E_INVAL if the range is not inside
+ * [0, nblocks).  Otherwise as hers_search.
+ */
+int hers_search_range(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
+                      uint32_t d, uint64_t block_begin, uint64_t block_end, const uint64_t* probe,
+                      uint64_t* scores_ct, void* workspace, uint64_t workspace_bytes, void* stream);
+
+/*
  * Base-w relinearisation gadget (Alg 1 / Alg 5 with g_j = w^j, w = 2^logw),
  * as an option beside the default RNS gadget.
  *
@@ -238,7 +302,10 @@ int hers_search_rerand(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gal
  *    that many blocks: gallery + b*hers_gallery_bytes(1, d)/8 words, scores_ct + b*4*N words.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current.  Make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address belongs to the CUDA context it
+ *    was looked up in: after a device reset (cudaDeviceReset), or with
+ *    another context current on the device, the next call looks it up again,
+ *    so that call too should come before any stream capture.
  *  - Every call shares the one array and leaves its contents behind.
  *    Nothing in it needs to start at zero.  Calls that overlap on the GPU
  *    (other streams, other contexts on the same device, other host threads)
@@ -354,6 +421,13 @@ int hers_server_pause(hers_server* srv, int paused);
 /* Counters since creation; returns a sticky error status (HERS_OK if none). */
 int hers_server_stats(hers_server* srv, uint64_t* submitted, uint64_t* completed, uint64_t* batches,
                       uint64_t* entries, uint64_t* max_batch_seen, uint64_t* pool_bytes);
+/* Where the server's time went, summed over its finished batches: device
+ * time of each batch's kernels (probe preparation, tensor kernel, epilogue)
+ * and of its score copies to host memory (CUDA events on the batch's stream;
+ * batches on the two streams overlap, so the sums can exceed wall time), and
+ * host time the scheduler spent planning and issuing batches.  Any pointer
+ * may be NULL. */
+int hers_server_timing(hers_server* srv, double* kernels_ms, double* copies_ms, double* plan_ms);
 /* Finishes in-flight batches, drops queued requests and frees the server. */
 int hers_server_free(hers_server* srv);
 
@@ -429,6 +503,17 @@ int hers_search_host_async(hers_ctx* ctx, const hers_keys* keys, const uint64_t*
 int hers_decrypt_scores(hers_ctx* ctx, const hers_keys* keys, const uint64_t* scores_ct,
                         uint64_t nblocks, int32_t* scores, uint64_t m, void* stream);
 
+/*
+ * Client-side decryption with host buffers (Alg 3; Alg 7's client side after
+ * the server's response, Sec. 3.1's g with sk): scores_ct_host, host
+ * [nblocks][2][2][N] (as hers_search_host writes them); scores_host, host
+ * int32 [m], m <= nblocks N.  Synchronous on the context's stream, with a
+ * device staging buffer of at most 256 MiB.  HERS_E_INVAL for keys without a
+ * secret key.
+ */
+int hers_decrypt_scores_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* scores_ct_host,
+                             uint64_t nblocks, int32_t* scores_host, uint64_t m);
+
 /* Synchronises `stream` and the context's own stream, then reports deferred
  * device-side errors (sampler exhaustion) as a status. */
 int hers_check(hers_ctx* ctx, void* stream);
@@ -468,6 +553,30 @@ int hers_set_tensor_variant(hers_ctx* ctx, int v);
 int hers_autotune(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
                   uint32_t d, const uint64_t* probe, void* workspace, uint64_t workspace_bytes,
                   void* stream, int* chosen, double* ms_per_variant);
+
+/*
+ * Epilogue forms (no counterpart in the paper).  After the tensor kernel every
+ * search runs the same epilogue arithmetic (inverse NTTs, exact
+ * scale-and-round, key switch) in one of hers_epilogue_variants() forms, all
+ * giving the same bytes: 0 "split" (one kernel per step), 1
+ * "intt_scale_cluster" (inverse NTTs and scale-and-round in one kernel: a
+ * cluster of eight CTAs per accumulator polynomial, residues exchanged in
+ * distributed shared memory), 2 "ks_fused" (the key switch in one kernel per
+ * block and limb), 3 both.  The context's form applies to every search on it
+ * (hers_search*, hers_batch_*, hers_server_*, hers_search_stream).
+ * hers_autotune_epilogue times each form's epilogue after the tensor kernel
+ * of the given search (1 warm-up, 3 timed, minimum kept), keeps the fastest
+ * on ctx and, if ms_per_variant is non-null, writes hers_epilogue_variants()
+ * timings in ms.  It holds a temporary device buffer for nblocks score
+ * ciphertexts during the call.  Synchronous.
+ */
+int hers_epilogue_variants(void);
+const char* hers_epilogue_variant_name(int v);
+int hers_get_epilogue_variant(const hers_ctx* ctx);
+int hers_set_epilogue_variant(hers_ctx* ctx, int v);
+int hers_autotune_epilogue(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
+                           uint32_t d, const uint64_t* probe, void* workspace, uint64_t workspace_bytes,
+                           void* stream, int* chosen, double* ms_per_variant);
 
 /*
  * Stage 1 of the two-stage search (Sec. 3.2): the k entries with the largest

@@ -132,8 +132,21 @@ def lib():
                 "hers_server_stats": ([vp, vp, vp, vp, vp, vp, vp], i32),
                 "hers_server_pause": ([vp, i32], i32),
                 "hers_server_free": ([vp], i32),
+                "hers_server_timing": ([vp, vp, vp, vp], i32),
+                "hers_epilogue_variants": ([], i32),
+                "hers_epilogue_variant_name": ([i32], ctypes.c_char_p),
+                "hers_get_epilogue_variant": ([vp], i32),
+                "hers_set_epilogue_variant": ([vp, i32], i32),
+                "hers_autotune_epilogue": ([vp, vp, vp, u64, u32, vp, vp, u64, vp, vp, vp], i32),
                 "hers_batch_variants": ([], i32),
                 "hers_batch_variant_name": ([i32], ctypes.c_char_p),
+                "hers_keys_import": ([vp, vp, vp, vp], i32),
+                "hers_keys_has_secret": ([vp], i32),
+                "hers_search_range": ([vp, vp, vp, u64, u32, u64, u64, vp, vp, vp, u64, vp], i32),
+                "hers_encrypt_gallery_host": ([vp, vp, vp, u64, u32, u64, vp, vp, vp], i32),
+                "hers_decrypt_scores_host": ([vp, vp, vp, u64, vp, u64], i32),
+                "hers_export_ct": ([vp, vp, u64, u32, u64, u64, vp], i32),
+                "hers_import_ct": ([vp, vp, u64, u32, u64, u64, vp], i32),
             }
             for name, (args, res) in sigs.items():
                 f = getattr(L, name)
@@ -264,6 +277,64 @@ def hers_keys_export(ctx: Context, keys: Keys):
     ctx.check(lib().hers_keys_export(ctx.h, keys.h, sk.ctypes.data, pk.ctypes.data,
                                      evk.ctypes.data), "hers_keys_export")
     return sk, pk, evk
+
+
+def hers_keys_import(ctx: Context, pk, evk) -> Keys:
+    """A server-side key handle from the client's canonical pk [2,2,N] and
+    evk [2,2,2,N] (uint64 numpy arrays, as hers_keys_export returns them):
+    no secret key on it."""
+    import numpy as np
+    pk = np.ascontiguousarray(pk, dtype=np.uint64)
+    evk = np.ascontiguousarray(evk, dtype=np.uint64)
+    assert pk.shape == (2, 2, N) and evk.shape == (2, 2, 2, N)
+    h = ctypes.c_void_p()
+    ctx.check(lib().hers_keys_import(ctx.h, pk.ctypes.data, evk.ctypes.data, ctypes.byref(h)),
+              "hers_keys_import")
+    return Keys(ctx, h)
+
+
+def hers_keys_has_secret(keys: Keys) -> bool:
+    return bool(lib().hers_keys_has_secret(keys.h))
+
+
+def hers_encrypt_gallery_host(ctx: Context, keys: Keys, feats, seed: int, want_ct: bool = False,
+                              resident: bool = True, device=None, stream=None):
+    """feats: host int8 [m, d] (numpy).  Returns (resident gallery words or
+    None, canonical cts [nb,d,2,2,N] or None), on `device` (default: the
+    context's CUDA device)."""
+    import numpy as np
+    import torch
+    feats = np.ascontiguousarray(feats, dtype=np.int8)
+    assert feats.ndim == 2
+    m, d = feats.shape
+    nb = hers_blocks_for(m)
+    dev = device if device is not None else torch.device("cuda", ctx.device)
+    want_ct = want_ct or not resident
+    gal = _words(hers_gallery_bytes(nb, d), dev) if resident else None
+    cts = torch.empty((nb, d, 2, 2, N), dtype=torch.int64, device=dev) if want_ct else None
+    ctx.check(lib().hers_encrypt_gallery_host(ctx.h, keys.h, feats.ctypes.data, m, d, seed, _ptr(gal),
+                                              _ptr(cts), _stream(stream)), "hers_encrypt_gallery_host")
+    return gal, cts
+
+
+def hers_export_ct(ctx: Context, gallery, nblocks: int, d: int, begin: int = 0, end: int = None):
+    """Canonical cts of resident blocks [begin, end) as numpy uint64 [end-begin, d, 2, 2, N]."""
+    import numpy as np
+    end = nblocks if end is None else end
+    out = np.zeros((max(0, end - begin), d, 2, 2, N), dtype=np.uint64)
+    ctx.check(lib().hers_export_ct(ctx.h, _ptr(gallery), nblocks, d, begin, end, out.ctypes.data),
+              "hers_export_ct")
+    return out
+
+
+def hers_import_ct(ctx: Context, ct_host, gallery, nblocks: int, d: int, begin: int = 0):
+    """Canonical cts (numpy uint64 [k, d, 2, 2, N]) into resident blocks [begin, begin + k)."""
+    import numpy as np
+    ct_host = np.ascontiguousarray(ct_host, dtype=np.uint64)
+    k = ct_host.shape[0]
+    ctx.check(lib().hers_import_ct(ctx.h, ct_host.ctypes.data, nblocks, d, begin, begin + k, _ptr(gallery)),
+              "hers_import_ct")
+    return gallery
 
 
 def hers_encrypt_gallery(ctx: Context, keys: Keys, feats, seed: int, want_ct: bool = False,
@@ -417,6 +488,34 @@ def hers_decrypt_scores(ctx: Context, keys: Keys, scores_ct, m: int, out=None, s
     return out
 
 
+def hers_decrypt_scores_host(ctx: Context, keys: Keys, scores_ct_host, m: int):
+    """int32 [m] scores (numpy) from host score cts [nb, 2, 2, N] (int64 or uint64)."""
+    import numpy as np
+    import torch
+    if isinstance(scores_ct_host, torch.Tensor):
+        scores_ct_host = scores_ct_host.numpy()
+    cts = np.ascontiguousarray(scores_ct_host).view(np.uint64)
+    nb = cts.shape[0]
+    out = np.zeros(m, dtype=np.int32)
+    ctx.check(lib().hers_decrypt_scores_host(ctx.h, keys.h, cts.ctypes.data, nb, out.ctypes.data, m),
+              "hers_decrypt_scores_host")
+    return out
+
+
+def hers_search_range(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, begin: int, end: int, probe,
+                      out=None, workspace=None, stream=None):
+    """Score cts [end - begin, 2, 2, N] of blocks [begin, end) of a resident gallery."""
+    import torch
+    dev = gallery.device
+    n = max(0, end - begin)
+    # an empty range still passes non-null buffers (the call checks them)
+    sc = out if out is not None else torch.empty((max(n, 1), 2, 2, N), dtype=torch.int64, device=dev)
+    ws = workspace if workspace is not None else _words(max(8, hers_search_workspace_bytes(n)), dev)
+    ctx.check(lib().hers_search_range(ctx.h, keys.h, _ptr(gallery), nblocks, d, begin, end, _ptr(probe),
+                                      _ptr(sc), _ptr(ws), ws.numel() * 8, _stream(stream)), "hers_search_range")
+    return sc[:n]
+
+
 def hers_check(ctx: Context, stream=None):
     ctx.check(lib().hers_check(ctx.h, _stream(stream)), "hers_check")
 
@@ -452,6 +551,32 @@ def hers_get_tensor_variant(ctx: Context) -> int:
 
 def hers_set_tensor_variant(ctx: Context, v: int):
     ctx.check(lib().hers_set_tensor_variant(ctx.h, v), "hers_set_tensor_variant")
+
+
+def hers_epilogue_variants():
+    L = lib()
+    return [L.hers_epilogue_variant_name(v).decode() for v in range(L.hers_epilogue_variants())]
+
+
+def hers_get_epilogue_variant(ctx: Context) -> int:
+    return int(lib().hers_get_epilogue_variant(ctx.h))
+
+
+def hers_set_epilogue_variant(ctx: Context, v: int):
+    ctx.check(lib().hers_set_epilogue_variant(ctx.h, v), "hers_set_epilogue_variant")
+
+
+def hers_autotune_epilogue(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, probe, workspace=None,
+                           stream=None):
+    """(chosen epilogue form, {name: ms}) for this search; the context keeps the fastest form."""
+    names = hers_epilogue_variants()
+    ws = workspace if workspace is not None else _words(hers_search_workspace_bytes(nblocks), gallery.device)
+    chosen = ctypes.c_int()
+    ms = (ctypes.c_double * len(names))()
+    ctx.check(lib().hers_autotune_epilogue(ctx.h, keys.h, _ptr(gallery), nblocks, d, _ptr(probe), _ptr(ws),
+                                           ws.numel() * 8, _stream(stream), ctypes.byref(chosen), ms),
+              "hers_autotune_epilogue")
+    return chosen.value, {names[i]: ms[i] for i in range(len(names))}
 
 
 def hers_autotune(ctx: Context, keys: Keys, gallery, nblocks: int, d: int, probe, workspace=None,
@@ -607,6 +732,12 @@ class Server:
         out = dict(zip(keys, [x.value for x in v]))
         out["status"] = rc
         return out
+
+    def timing(self):
+        """Summed ms over finished batches: kernels and copies (device), plan (host)."""
+        v = [ctypes.c_double() for _ in range(3)]
+        self.ctx.check(lib().hers_server_timing(self.h, *[ctypes.byref(x) for x in v]), "hers_server_timing")
+        return dict(zip(("kernels_ms", "copies_ms", "plan_ms"), [x.value for x in v]))
 
     def close(self):
         if getattr(self, "h", None):

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhers.so")
 SOURCES = ["capi.cu", "scheme.cu", "search.cu", "batch.cu", "serve.cu", "stream.cu", "intpipe.cu", "noalloc.cu",
-           "topk.cu"]
+           "topk.cu", "exchange.cu"]
 HEADERS = ["common.cuh", "internal.h", "hers_consts.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

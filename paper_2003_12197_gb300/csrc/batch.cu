@@ -4,13 +4,14 @@
 // once; the result for every (probe, block) pair is the one hers_search gives).
 //
 // Items (probe, subset) that share a resident gallery form a group.  A group's
-// probes are cut into chunks of NP; a work unit is (chunk, block, limb, tile).
-// The persistent tensor kernel's producer warp claims units from an atomic
-// counter and streams, per stage, the NP probes' rows and the block's gallery
-// rows into a shared-memory ring (cp.async.bulk + mbarriers, as in k_tensor);
-// the consumers accumulate all NP products from the one copy of the gallery
-// rows, so each gallery byte read from HBM serves NP probes.  The epilogue
-// (inverse NTTs, exact scale-and-round, key switch) then runs over all pairs.
+// probes are cut into chunks of G NP; a work unit is (chunk, block, limb,
+// tile).  The persistent tensor kernel's producer warp claims units from an
+// atomic counter and streams, per stage, the chunk's probe rows and the
+// block's gallery rows into a shared-memory ring (cp.async.bulk + mbarriers,
+// as in k_tensor).  The CTA's G groups of consumers each take NP of the
+// chunk's probes against the one copy of the gallery rows, so each gallery
+// byte read from HBM serves up to G NP probes.  The epilogue (inverse NTTs,
+// exact scale-and-round, key switch) then runs over all pairs.
 #include <stdio.h>
 
 #include <algorithm>
@@ -33,6 +34,9 @@ constexpr uint32_t UNIT_STOP = 0xFFFFFFFFu;
 constexpr int BPFOLD_S = 4;
 constexpr int BPFOLD_02 = 16;
 
+// Stage descriptor word: dimensions (8 bits), probes (5), blocks (4), limb
+// (4), flags (5).
+constexpr int HD_NP = 8, HD_NB = 13, HD_LIMB = 17, HD_FLAGS = 21;
 // Stage descriptor flags (written by the producer with each stage).
 constexpr uint32_t F_FIRST = 1;  // first stage of a unit: sums start at zero
 constexpr uint32_t F_FOLD = 2;   // partial fold of the S sums after this stage
@@ -44,17 +48,17 @@ __device__ __forceinline__ void madw_b(int64_t& acc, int32_t a, int32_t b) {
     asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
-// A unit's table entries, held in registers by the producer.
-template <int NP>
+// A unit's table entries.  The scalars stay in the producer's registers; the
+// probe pointers and output pairs (NPC = G NP of each) go to a shared-memory
+// slot, so the producer's register count does not grow with the chunk size.
 struct UnitRegs {
     const uint64_t* gallery;
-    const uint64_t* probe[NP];
-    uint64_t pair[NP];  // pair of probe q at the unit's first block
     uint32_t d, np, nb, block, limb, tile;
 };
 
-template <int NP>
-__device__ __forceinline__ void load_unit(UnitRegs<NP>& r, const BatchChunk* __restrict__ chunks,
+template <int NPC>
+__device__ __forceinline__ void load_unit(UnitRegs& r, const uint64_t** probe_slot, uint64_t* pair_slot,
+                                          const BatchChunk* __restrict__ chunks,
                                           const BatchUnit* __restrict__ units, uint32_t u) {
     const BatchUnit U = units[u];
     const BatchChunk* C = chunks + U.chunk;
@@ -62,9 +66,9 @@ __device__ __forceinline__ void load_unit(UnitRegs<NP>& r, const BatchChunk* __r
     r.d = C->d;
     r.np = C->np;
 #pragma unroll
-    for (int q = 0; q < NP; q++) {  // entries past np are zero in the table
-        r.probe[q] = C->probe[q];
-        r.pair[q] = C->pair[q] + U.block;
+    for (int q = 0; q < NPC; q++) {  // entries past np are zero in the table
+        probe_slot[q] = C->probe[q];
+        pair_slot[q] = C->pair[q] + U.block;
     }
     r.nb = U.nb;
     r.block = U.block;
@@ -80,9 +84,11 @@ __device__ __forceinline__ void load_unit(UnitRegs<NP>& r, const BatchChunk* __r
 // The sums a0 + a1 and g0 + g1 are below r < 2^30 in magnitude, their
 // product below 2^60.  With FULL (nd = DPS, np = NP, nb = NB) the loops carry
 // no predicates.
+// pb: this group's first probe run; gb: the first gallery run (both already
+// offset to the thread's coefficient).
 template <int NP, int NB, int DPS, bool FULL>
-__device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const int2* base, uint32_t nd,
-                                               uint32_t np, uint32_t nbu) {
+__device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const int2* pb, const int2* gb,
+                                               uint32_t nd, uint32_t np, uint32_t nbu) {
     constexpr int RUN2 = DPS * TILE;  // (poly 0, poly 1) pairs of one run
 #pragma unroll
     for (int dd = 0; dd < DPS; dd++) {
@@ -90,7 +96,7 @@ __device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const in
             int32_t a0[NP], a1[NP], as[NP];
 #pragma unroll
             for (int q = 0; q < NP; q++) {
-                const int2 A = base[q * RUN2 + dd * TILE];
+                const int2 A = pb[q * RUN2 + dd * TILE];
                 a0[q] = A.x;
                 a1[q] = A.y;
                 as[q] = A.x + A.y;
@@ -98,7 +104,7 @@ __device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const in
 #pragma unroll
             for (int j = 0; j < NB; j++) {
                 if (FULL || (uint32_t)j < nbu) {
-                    const int2 G = base[(NP + j) * RUN2 + dd * TILE];
+                    const int2 G = gb[j * RUN2 + dd * TILE];
                     const int32_t g0 = G.x, g1 = G.y, gs = G.x + G.y;
 #pragma unroll
                     for (int q = 0; q < NP; q++) {
@@ -114,46 +120,53 @@ __device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const in
     }
 }
 
-// Persistent batched tensor kernel.  A CTA has TILE consumer threads (one
-// coefficient each) and one producer warp.  The producer's elected lane
-// claims units from the atomic counter one unit ahead (the claim and the
-// unit's table reads overlap the current unit's stages), and for each stage
-// writes a descriptor (dimensions, probes, blocks, limb, flags; on the last
-// stage the output pairs) into shared memory before the stage's copies, so
-// the consumers read no tables from global memory.  Each consumer keeps the
-// NP x NB x 3 sums of its coefficient in registers.
+// Persistent batched tensor kernel.  A CTA has G groups of TILE consumer
+// threads (one coefficient each) and one producer warp.  The producer's
+// elected lane claims units from the atomic counter one unit ahead (the claim
+// and the unit's table reads overlap the current unit's stages), and for each
+// stage writes a descriptor (dimensions, probes, blocks, limb, flags; on the
+// last stage the output pairs) into shared memory before the stage's copies,
+// so the consumers read no tables from global memory.  A stage holds the
+// chunk's G NP probe runs, then NB gallery runs; group g takes probes
+// g NP .. g NP + NP - 1 against every gallery run and keeps their NP x NB x 3
+// sums of its coefficient in registers.
 
-template <int NP, int NB, int STAGES, int DPS, int MINB>
-__global__ void __launch_bounds__(TILE + 32, MINB)
+template <int NP, int NB, int STAGES, int DPS, int MINB, int G>
+__global__ void __launch_bounds__(G * TILE + 32, MINB)
     k_tensor_batched(const BatchChunk* __restrict__ chunks, const BatchUnit* __restrict__ units,
                      uint32_t nunits, uint32_t* counter, uint32_t* __restrict__ X, int* err) {
+    constexpr int NPC = G * NP;  // probes of a chunk
     static_assert(BPFOLD_S % DPS == 0 && BPFOLD_02 % BPFOLD_S == 0, "stages must not straddle a partial fold");
-    static_assert(NP <= BATCH_NPMAX && NB <= 15 && DPS <= 255 && NUM_S <= 16, "descriptor fields");
+    static_assert(NPC <= BATCH_NPMAX && NPC < 32 && NB <= 15 && DPS <= 255 && NUM_S <= 16, "descriptor fields");
+    static_assert(G * TILE + 32 <= 1024, "threads per CTA");
     extern __shared__ __align__(128) int32_t smr[];
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
     __shared__ uint32_t hdr_info[STAGES], hdr_k0[STAGES];
-    __shared__ uint64_t hdr_pair[STAGES][NP];
+    __shared__ uint64_t hdr_pair[STAGES][NPC];
+    __shared__ const uint64_t* unit_probe[2][NPC];  // the producer's current and next unit
+    __shared__ uint64_t unit_pair[2][NPC];
     constexpr int RUN = DPS * 2 * TILE;
-    constexpr int STAGE_ELEMS = (NP + NB) * RUN;  // NP probe runs, then NB gallery runs
+    constexpr int STAGE_ELEMS = (NPC + NB) * RUN;  // NPC probe runs, then NB gallery runs
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], TILE);  // every consumer thread arrives
+            mbar_init(&empty[s], G * TILE);  // every consumer thread arrives
         }
         mbar_fence_init();
     }
     __syncthreads();
 
-    if (warp == TILE / 32) {  // producer warp
+    if (warp == G * TILE / 32) {  // producer warp
         if (lane == 0) {
             const uint64_t pol_g = policy_evict_first(), pol_p = policy_evict_last();
             uint32_t g = 0;  // stages issued by this CTA
             bool failed = false;
             uint32_t u = atomicAdd(counter, 1u);
-            UnitRegs<NP> cur = {}, nxt = {};
-            if (u < nunits) load_unit(cur, chunks, units, u);
+            UnitRegs cur = {}, nxt = {};
+            int cs = 0;  // shared-memory slot of the current unit's probes and pairs
+            if (u < nunits) load_unit<NPC>(cur, unit_probe[0], unit_pair[0], chunks, units, u);
             while (!failed) {
                 const bool stop = u >= nunits;
                 const uint32_t un = stop ? UNIT_STOP : atomicAdd(counter, 1u);  // next unit, claimed now
@@ -166,7 +179,7 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
                         break;
                     }
                     if (stop) {
-                        hdr_info[st] = F_STOP << 20;
+                        hdr_info[st] = F_STOP << HD_FLAGS;
                         mbar_arrive(&full[st]);
                         continue;
                     }
@@ -175,35 +188,35 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
                                            ((done % BPFOLD_S == 0 && done < cur.d) ? F_FOLD : 0u) |
                                            ((done % BPFOLD_02 == 0 && done < cur.d) ? F_FOLD02 : 0u) |
                                            (done == cur.d ? F_LAST : 0u);
-                    hdr_info[st] = nd | (cur.np << 8) | (cur.nb << 12) | (cur.limb << 16) | (flags << 20);
+                    hdr_info[st] = nd | (cur.np << HD_NP) | (cur.nb << HD_NB) | (cur.limb << HD_LIMB) |
+                                   (flags << HD_FLAGS);
                     if (flags & F_LAST) {
                         hdr_k0[st] = cur.tile * TILE;
-#pragma unroll
-                        for (int q = 0; q < NP; q++) hdr_pair[st][q] = cur.pair[q];
+                        for (uint32_t q = 0; q < cur.np; q++) hdr_pair[st][q] = unit_pair[cs][q];
                     }
                     const uint32_t bytes = nd * 2 * TILE * 4;
                     int32_t* dst = smr + (size_t)st * STAGE_ELEMS;
                     mbar_expect_tx(&full[st], bytes * (cur.np + cur.nb));
                     const uint64_t off = resident_offset(0, cur.limb, cur.tile * TILE, cur.d, 0, 0) +
                                          (uint64_t)si * RUN;
-#pragma unroll
-                    for (int q = 0; q < NP; q++)
-                        if ((uint32_t)q < cur.np)
-                            bulk_g2s(dst + q * RUN, (const int32_t*)cur.probe[q] + off, bytes, &full[st], pol_p);
+                    for (uint32_t q = 0; q < cur.np; q++)
+                        bulk_g2s(dst + q * RUN, (const int32_t*)unit_probe[cs][q] + off, bytes, &full[st], pol_p);
 #pragma unroll
                     for (int j = 0; j < NB; j++)
                         if ((uint32_t)j < cur.nb)
-                            bulk_g2s(dst + (NP + j) * RUN,
+                            bulk_g2s(dst + (NPC + j) * RUN,
                                      (const int32_t*)cur.gallery +
                                          resident_offset(cur.block + j, cur.limb, cur.tile * TILE, cur.d, 0, 0) +
                                          (uint64_t)si * RUN,
                                      bytes, &full[st], pol_g);
                     // the next unit's tables, once this unit's first stage is on its way
-                    if (si == 0 && un < nunits) load_unit(nxt, chunks, units, un);
+                    if (si == 0 && un < nunits)
+                        load_unit<NPC>(nxt, unit_probe[cs ^ 1], unit_pair[cs ^ 1], chunks, units, un);
                 }
                 if (stop) break;
                 u = un;
                 cur = nxt;
+                cs ^= 1;
             }
             // drain: the copies of the last stages issued land before this thread leaves
             for (uint32_t i = g > STAGES ? g - STAGES : 0; i < g; i++)
@@ -212,8 +225,9 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
         return;
     }
 
-    // consumers
-    const int t = threadIdx.x;
+    // consumers: group grp, coefficient t of the tile
+    const int grp = G == 1 ? 0 : threadIdx.x / TILE;
+    const int t = G == 1 ? threadIdx.x : threadIdx.x % TILE;
     int64_t s[NP][NB][3];
     for (uint32_t g = 0;; g++) {
         const int st = (int)(g % STAGES);
@@ -222,17 +236,19 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
             return;
         }
         const uint32_t info = hdr_info[st];
-        const uint32_t flags = info >> 20;
+        const uint32_t flags = info >> HD_FLAGS;
         if (flags & F_STOP) break;
-        const uint32_t nd = info & 0xFF, np = (info >> 8) & 15, nbu = (info >> 12) & 15;
-        const int l = (int)((info >> 16) & 15);
+        const uint32_t nd = info & 0xFF, npc = (info >> HD_NP) & 31, nbu = (info >> HD_NB) & 15;
+        const int l = (int)((info >> HD_LIMB) & 15);
+        // this group's probes of the chunk
+        const uint32_t np = npc > (uint32_t)(grp * NP) ? min((uint32_t)NP, npc - grp * NP) : 0u;
         // what the last stage stores, read before the stage is handed back
         uint64_t opair[NP];
         uint32_t k0 = 0;
         if (flags & F_LAST) {
             k0 = hdr_k0[st];
 #pragma unroll
-            for (int q = 0; q < NP; q++) opair[q] = hdr_pair[st][q];
+            for (int q = 0; q < NP; q++) opair[q] = (uint32_t)q < np ? hdr_pair[st][grp * NP + q] : 0;
         }
         if (flags & F_FIRST) {
 #pragma unroll
@@ -240,11 +256,13 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
 #pragma unroll
                 for (int j = 0; j < NB; j++) s[q][j][0] = s[q][j][1] = s[q][j][2] = 0;
         }
-        const int2* base = (const int2*)(smr + (size_t)st * STAGE_ELEMS) + t;  // (poly 0, poly 1) pairs
+        const int2* sbase = (const int2*)(smr + (size_t)st * STAGE_ELEMS) + t;  // (poly 0, poly 1) pairs
+        const int2* pb = sbase + grp * NP * (RUN / 2);
+        const int2* gb = sbase + NPC * (RUN / 2);
         if (nd == DPS && np == NP && nbu == NB)
-            stage_products<NP, NB, DPS, true>(s, base, nd, np, nbu);
-        else
-            stage_products<NP, NB, DPS, false>(s, base, nd, np, nbu);
+            stage_products<NP, NB, DPS, true>(s, pb, gb, nd, np, nbu);
+        else if (np > 0)
+            stage_products<NP, NB, DPS, false>(s, pb, gb, nd, np, nbu);
         mbar_arrive(&empty[st]);
         if (flags & F_FOLD) {
             const int32_t r32 = (int32_t)c_sr32[l];
@@ -284,23 +302,33 @@ using BatchFn = void (*)(const BatchChunk*, const BatchUnit*, uint32_t, uint32_t
 struct BatchVariant {
     const char* name;
     BatchFn fn;
-    int np, nb, stages, dps, minb;
+    int np, nb, stages, dps, minb, groups;
 };
-// name: np<probes>_nb<blocks>_s<stages>_d<dims per stage>_m<CTAs/SM>
+// name: np<probes per group>_nb<blocks>_s<stages>_d<dims per stage>_m<CTAs/SM>,
+// with a trailing _g<groups> when a CTA has more than one group of consumers
 #define HERS_BV(NP, NB, S, D, M) \
-    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M, k_tensor_batched<NP, NB, S, D, M>, NP, NB, S, D, M}
+    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M, k_tensor_batched<NP, NB, S, D, M, 1>, NP, NB, S, D, M, 1}
+#define HERS_BVG(NP, NB, S, D, M, G)                                                                         \
+    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M "_g" #G, k_tensor_batched<NP, NB, S, D, M, G>, NP, NB, S, D, M, \
+     G}
 static const BatchVariant kBatchVariants[] = {
     HERS_BV(1, 2, 4, 4, 2), HERS_BV(2, 2, 2, 4, 3), HERS_BV(2, 2, 3, 4, 2), HERS_BV(2, 2, 4, 2, 2),
     HERS_BV(4, 1, 2, 4, 2), HERS_BV(4, 2, 2, 4, 2), HERS_BV(4, 2, 3, 2, 2), HERS_BV(2, 1, 3, 4, 3),
     HERS_BV(1, 1, 4, 4, 3), HERS_BV(2, 1, 4, 4, 2), HERS_BV(4, 1, 4, 2, 2), HERS_BV(1, 2, 3, 4, 3),
+    HERS_BVG(2, 2, 2, 4, 2, 2), HERS_BVG(2, 2, 3, 2, 2, 2), HERS_BVG(2, 2, 4, 4, 1, 2),
+    HERS_BVG(4, 2, 2, 4, 1, 2), HERS_BVG(2, 1, 3, 4, 2, 2), HERS_BVG(4, 1, 2, 4, 2, 2),
 };
 #undef HERS_BV
+#undef HERS_BVG
 constexpr int NUM_BATCH_VARIANTS = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
-static int batch_smem(const BatchVariant& v) { return v.stages * (v.np + v.nb) * v.dps * 2 * TILE * 4; }
+static int batch_smem(const BatchVariant& v) {
+    return v.stages * (v.groups * v.np + v.nb) * v.dps * 2 * TILE * 4;
+}
+static int batch_threads(const BatchVariant& v) { return v.groups * TILE + 32; }
 
 int batch_variant_count() { return NUM_BATCH_VARIANTS; }
-int batch_variant_np(int v) { return kBatchVariants[v].np; }
+int batch_variant_np(int v) { return kBatchVariants[v].groups * kBatchVariants[v].np; }
 int batch_variant_nb(int v) { return kBatchVariants[v].nb; }
 
 // Direct launch of the persistent kernel of variant v over device tables.
@@ -313,14 +341,15 @@ cudaError_t launch_batched(int v, const BatchChunk* d_chunks, const BatchUnit* d
     const int smem = batch_smem(V);
     cudaError_t e = cudaFuncSetAttribute(V.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int per_sm = 0, sms = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, V.fn, TILE + 32, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, V.fn, batch_threads(V), smem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)per_sm * sms, nunits ? nunits : 1);
     e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    V.fn<<<grid, TILE + 32, smem, st>>>(d_chunks, d_units, nunits, d_counter, (uint32_t*)X, err);
+    V.fn<<<grid, batch_threads(V), smem, st>>>(d_chunks, d_units, nunits, d_counter, (uint32_t*)X, err);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -344,7 +373,7 @@ struct hers_batch {
     // launch parameters of the built variant (what the graph holds)
     BatchFn fn;
     unsigned grid;
-    int smem;
+    int smem, threads;
     BatchChunk* d_chunks;
     BatchUnit* d_units;
     uint32_t* d_counter;
@@ -458,11 +487,12 @@ cudaError_t batch_launch(hers_batch* B, cudaStream_t st, bool traced) {
     uint64_t* KS = C + B->npairs * 6 * N;
     cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(uint32_t), st);
     if (traced) cudaEventRecord(B->ev[0], st);
-    B->fn<<<B->grid, TILE + 32, B->smem, st>>>(B->d_chunks, B->d_units, B->nunits, B->d_counter,
+    B->fn<<<B->grid, B->threads, B->smem, st>>>(B->d_chunks, B->d_units, B->nunits, B->d_counter,
                                                 (uint32_t*)X, B->ctx->err);
     if (traced) cudaEventRecord(B->ev[1], st);
     if (e == cudaSuccess) e = cudaGetLastError();
-    cudaError_t el = launch_epilogue(B->ctx->tw, B->keys->k, B->npairs, X, C, KS, B->scores, st);
+    cudaError_t el = launch_epilogue(B->ctx->tw, B->keys->k, B->npairs, X, C, KS, B->scores, st, nullptr,
+                                     nullptr, B->ctx->epi_variant);
     if (traced) cudaEventRecord(B->ev[2], st);
     return e != cudaSuccess ? e : el;
 }
@@ -471,7 +501,7 @@ cudaError_t batch_launch(hers_batch* B, cudaStream_t st, bool traced) {
 int batch_build(hers_batch* B, const hers_batch_item* items, uint32_t nitems, int v) {
     hers_ctx* ctx = B->ctx;
     const BatchVariant& V = kBatchVariants[v];
-    Plan P = make_plan(items, nitems, V.np, V.nb);
+    Plan P = make_plan(items, nitems, V.groups * V.np, V.nb);
     if (P.units.size() >= UNIT_STOP) return fail(ctx, HERS_E_INVAL, "hers_batch_create: too many units");
     const size_t cbytes = P.chunks.size() * sizeof(BatchChunk);
     const size_t ubytes = P.units.size() * sizeof(BatchUnit);
@@ -486,7 +516,8 @@ int batch_build(hers_batch* B, const hers_batch_item* items, uint32_t nitems, in
     const int smem = batch_smem(V);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(V.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int per_sm = 0, sms = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, V.fn, TILE + 32, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, V.fn, batch_threads(V), smem);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_batch_create: setup");
     if (per_sm < 1) {
@@ -502,6 +533,7 @@ int batch_build(hers_batch* B, const hers_batch_item* items, uint32_t nitems, in
     B->fn = V.fn;
     B->grid = grid;
     B->smem = smem;
+    B->threads = batch_threads(V);
     B->d_chunks = d_chunks;
     B->d_units = d_units;
     B->d_counter = d_counter;

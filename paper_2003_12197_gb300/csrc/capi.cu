@@ -311,6 +311,7 @@ uint32_t hers_basew_digits(uint32_t logw) {
 
 int hers_keys_add_basew(hers_ctx* ctx, hers_keys* keys, uint64_t seed, uint32_t logw) {
     if (!ctx || !keys) return fail(ctx, HERS_E_INVAL, "hers_keys_add_basew: null argument");
+    if (!keys->k.sk) return fail(ctx, HERS_E_INVAL, "hers_keys_add_basew: the keys hold no secret key");
     if (logw < BASEW_MIN || logw > BASEW_MAX)
         return fail(ctx, HERS_E_INVAL, "hers_keys_add_basew: log2 w = %u not in [%u, %u]", logw, BASEW_MIN,
                     BASEW_MAX);
@@ -343,6 +344,7 @@ int hers_keys_export_basew(hers_ctx* ctx, const hers_keys* keys, uint64_t* evkw)
 
 int hers_keys_export(hers_ctx* ctx, const hers_keys* keys, int8_t* sk, uint64_t* pk, uint64_t* evk) {
     if (!ctx || !keys) return fail(ctx, HERS_E_INVAL, "hers_keys_export: null argument");
+    if (sk && !keys->k.sk) return fail(ctx, HERS_E_INVAL, "hers_keys_export: the keys hold no secret key");
     DeviceGuard g(ctx->device);
     cudaError_t e = cudaSuccess;
     if (sk) e = cudaMemcpy(sk, keys->k.sk, N, cudaMemcpyDeviceToHost);
@@ -438,7 +440,7 @@ int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
     const EpilogueStream ep = {ctx->ep, {ctx->ep_ev[0], ctx->ep_ev[1]}};
     cudaError_t e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, scores_ct,
                                   (uint64_t*)workspace, ctx->err, pick(ctx, stream), next_trace(ctx),
-                                  ctx->tensor_variant, nullptr, &ep);
+                                  ctx->tensor_variant, nullptr, &ep, ctx->epi_variant);
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search");
 }
 
@@ -469,7 +471,8 @@ int hers_search_basew(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gall
     DeviceGuard g(ctx->device);
     const KeySwitchW ksw = {keys->evkw_ntt, keys->logw, keys->ndig};
     cudaError_t e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, scores_ct, (uint64_t*)workspace,
-                                  ctx->err, pick(ctx, stream), next_trace(ctx), ctx->tensor_variant, &ksw);
+                                  ctx->err, pick(ctx, stream), next_trace(ctx), ctx->tensor_variant, &ksw, nullptr,
+                                  ctx->epi_variant);
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search_basew");
 }
 
@@ -512,7 +515,7 @@ int search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
     if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, probe_ct, d, 0, d, probe, st);
     if (e == cudaSuccess)
         e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, out_dev, ws, ctx->err, st,
-                          next_trace(ctx), ctx->tensor_variant, nullptr, &ep);
+                          next_trace(ctx), ctx->tensor_variant, nullptr, &ep, ctx->epi_variant);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(scores_ct_host, out_dev, nblocks * 4 * N * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && sync) e = cudaStreamSynchronize(st);
@@ -542,6 +545,7 @@ int hers_search_host_async(hers_ctx* ctx, const hers_keys* keys, const uint64_t*
 int hers_decrypt_scores(hers_ctx* ctx, const hers_keys* keys, const uint64_t* scores_ct,
                         uint64_t nblocks, int32_t* scores, uint64_t m, void* stream) {
     if (!ctx || !keys || !scores_ct || !scores) return fail(ctx, HERS_E_INVAL, "hers_decrypt_scores: null argument");
+    if (!keys->k.sk) return fail(ctx, HERS_E_INVAL, "hers_decrypt_scores: the keys hold no secret key");
     if (m > nblocks * N) return fail(ctx, HERS_E_INVAL, "hers_decrypt_scores: m > nblocks N");
     DeviceGuard g(ctx->device);
     cudaError_t e = launch_decrypt(ctx->tw, keys->k, scores_ct, nblocks, scores, m, pick(ctx, stream));
@@ -609,6 +613,76 @@ int hers_set_tensor_variant(hers_ctx* ctx, int v) {
         return fail(ctx, HERS_E_INVAL, "hers_set_tensor_variant: %d not in [0, %d)", v,
                     tensor_variant_count());
     ctx->tensor_variant = v;
+    return HERS_OK;
+}
+
+int hers_epilogue_variants(void) { return EPI_VARIANTS; }
+
+const char* hers_epilogue_variant_name(int v) {
+    const char* n = epilogue_variant_name(v);
+    return n ? n : "";
+}
+
+int hers_get_epilogue_variant(const hers_ctx* ctx) { return ctx ? ctx->epi_variant : -1; }
+
+int hers_set_epilogue_variant(hers_ctx* ctx, int v) {
+    if (!ctx) return HERS_E_INVAL;
+    if (v < 0 || v >= EPI_VARIANTS)
+        return fail(ctx, HERS_E_INVAL, "hers_set_epilogue_variant: %d not in [0, %d)", v, EPI_VARIANTS);
+    ctx->epi_variant = v;
+    return HERS_OK;
+}
+
+int hers_autotune_epilogue(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, uint64_t nblocks,
+                           uint32_t d, const uint64_t* probe, void* workspace, uint64_t workspace_bytes,
+                           void* stream, int* chosen, double* ms_per_variant) {
+    if (!ctx || !keys || !gallery || !probe || !workspace || nblocks == 0)
+        return fail(ctx, HERS_E_INVAL, "hers_autotune_epilogue: null argument or no blocks");
+    if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_autotune_epilogue: d = %u", d);
+    if (workspace_bytes < hers_search_workspace_bytes(nblocks))
+        return fail(ctx, HERS_E_NOMEM, "hers_autotune_epilogue: workspace too small");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick(ctx, stream);
+    uint64_t* ws = (uint64_t*)workspace;
+    uint64_t* X = ws;
+    uint64_t* C = X + nblocks * 15 * N;
+    uint64_t* KS = C + nblocks * 6 * N;
+    uint64_t* out = nullptr;
+    cudaError_t e = cudaMallocAsync(&out, nblocks * 4 * N * 8, st);
+    if (e != cudaSuccess) return fail(ctx, HERS_E_NOMEM, "hers_autotune_epilogue: %s", cudaGetErrorString(e));
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaFreeAsync(out, st);
+        return fail(ctx, HERS_E_CUDA, "hers_autotune_epilogue: event creation");
+    }
+    // each variant: the tensor kernel (untimed) to refill the accumulators,
+    // then the epilogue timed; 1 warm-up and 3 timed rounds, minimum kept
+    int best = -1;
+    float best_ms = 0;
+    for (int v = 0; v < EPI_VARIANTS && e == cudaSuccess; v++) {
+        float vbest = 0;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; rep++) {
+            e = launch_tensor(ctx->tensor_variant, gallery, nblocks, d, probe, (uint32_t*)X, ctx->err, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = launch_epilogue(ctx->tw, keys->k, nblocks, X, C, KS, out, st, nullptr, nullptr, v);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1 || (rep > 1 && ms < vbest)) vbest = ms;
+        }
+        if (ms_per_variant) ms_per_variant[v] = vbest;
+        if (e == cudaSuccess && (best < 0 || vbest < best_ms)) {
+            best = v;
+            best_ms = vbest;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(out, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_autotune_epilogue");
+    ctx->epi_variant = best;
+    if (chosen) *chosen = best;
     return HERS_OK;
 }
 

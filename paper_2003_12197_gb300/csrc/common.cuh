@@ -404,9 +404,10 @@ __device__ __forceinline__ void gs_phase(uint64_t v[16], int base, const ulonglo
     }
 }
 
+// t: the calling thread's index among the NTT_THREADS threads that run the
+// transform (as for the 32-bit transforms below).
 __device__ __forceinline__ void ntt_fwd_smem(uint64_t* sm, const ulonglong2* __restrict__ w, uint64_t p,
-                                             uint64_t one_s) {
-    const int t = threadIdx.x;
+                                             uint64_t one_s, int t = threadIdx.x) {
     uint64_t v[16];
     __syncthreads();
     {   // phase A
@@ -439,8 +440,7 @@ __device__ __forceinline__ void ntt_fwd_smem(uint64_t* sm, const ulonglong2* __r
 }
 
 __device__ __forceinline__ void ntt_inv_smem(uint64_t* sm, const ulonglong2* __restrict__ w, uint64_t p,
-                                             uint64_t ninv, uint64_t ninv_s) {
-    const int t = threadIdx.x;
+                                             uint64_t ninv, uint64_t ninv_s, int t = threadIdx.x) {
     uint64_t v[16];
     __syncthreads();
     {   // phase C pattern first (distances 1 .. 8)

@@ -19,6 +19,7 @@ struct hers_ctx {
     std::vector<cudaEvent_t> tev;
     uint32_t tcap = 0, tn = 0;
     int tensor_variant = 1;  // tensor-kernel shape used by searches on this context
+    int epi_variant = 0;     // epilogue form used by every search on this context (EPI_* flags)
     int pm = 0;              // plaintext modulus: 0 the default t, 1 the paper's t
     // the epilogue of a search runs on ep (the device's highest stream priority),
     // after ep_ev[0] (tensor done) and before ep_ev[1] (joined back to the caller)
@@ -78,6 +79,8 @@ struct DeviceGuard {
 
 // scheme.cu
 cudaError_t launch_keygen(const uint64_t* tw, uint64_t seed, DevKeys k, int* err, cudaStream_t st);
+// NTT forms (with Shoup companions) of the canonical pk and evk in k.
+cudaError_t launch_key_ntt(const uint64_t* tw, const DevKeys& k, cudaStream_t st);
 // Base-w gadget (w = 2^logw): digits and key generation / key switch pieces.
 constexpr uint32_t BASEW_MIN = 22, BASEW_MAX = 60;  // at most 5 digits: they fit the workspace
 uint32_t basew_digits(uint32_t logw);
@@ -97,11 +100,12 @@ cudaError_t launch_encrypt(const uint64_t* tw, const DevKeys& k, const int8_t* f
                            uint64_t* out_ct, int* err, cudaStream_t st);
 // out[c] += add[c] mod q for nct canonical ciphertexts.
 cudaError_t launch_ct_add(uint64_t* out, const uint64_t* add, uint64_t nct, cudaStream_t st);
-// Canonical ciphertexts of block b (d of them) recovered from the resident
-// form (inverse NTTs and the CRT of the search basis), plus add[i] mod q,
-// into out[i].
+// Canonical ciphertexts of blocks b .. b + nb - 1 (d each) recovered from the
+// resident form (inverse NTTs and the CRT of the search basis), plus add[c]
+// mod q when add is non-null, into out[c] (c counts from block b's first).
 cudaError_t launch_resident_to_canonical_add(const uint64_t* tw, const uint64_t* resident, uint64_t b,
-                                             uint32_t d, const uint64_t* add, uint64_t* out, cudaStream_t st);
+                                             uint32_t d, const uint64_t* add, uint64_t* out, cudaStream_t st,
+                                             uint32_t nb = 1);
 // Canonical cts ct[0 .. nct) (global indices ct_begin ..) of dimension d into
 // the resident form at `out` (the base of block 0; RES_WORDS_PER_DIM words per
 // (block, dimension)).
@@ -128,11 +132,17 @@ struct EpilogueStream {
     cudaStream_t stream;
     cudaEvent_t ev[2];
 };
+// Epilogue forms (every form computes the same bytes): EPI_INTT_SCALE_CLUSTER
+// fuses the inverse NTTs with scale-and-round (clusters of NUM_S CTAs);
+// EPI_KS_FUSED does the RNS key switch in one kernel per (pair, limb).
+// Variant v is the OR of the flags, 0 <= v < EPI_VARIANTS.
+constexpr int EPI_INTT_SCALE_CLUSTER = 1, EPI_KS_FUSED = 2, EPI_VARIANTS = 4;
+const char* epilogue_variant_name(int v);
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
                           uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev = nullptr,
                           int variant = DEFAULT_TENSOR_VARIANT, const KeySwitchW* ksw = nullptr,
-                          const EpilogueStream* ep = nullptr);
+                          const EpilogueStream* ep = nullptr, int epi = 0);
 // Epilogue over npairs accumulators X (uint32 [npairs][3][NUM_S][N] at the
 // start of the X area, 15 N words per pair); workspace C, KS as in
 // launch_search; `ev` (optional) receives the boundaries after the inverse
@@ -141,7 +151,7 @@ cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* 
 // [2][N] go after O in X (O [npairs][4][N] at X; 4 + 2 ndig <= 15 words per N).
 cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npairs, uint64_t* X,
                             uint64_t* C, uint64_t* KS, uint64_t* out, cudaStream_t st,
-                            cudaEvent_t* ev = nullptr, const KeySwitchW* ksw = nullptr);
+                            cudaEvent_t* ev = nullptr, const KeySwitchW* ksw = nullptr, int epi = 0);
 // The tensor kernel alone, into X [nblocks][3][NUM_S][N] (uint32).
 cudaError_t launch_tensor(int variant, const uint64_t* gallery, uint64_t nblocks, uint32_t d,
                           const uint64_t* probe, uint32_t* X, int* err, cudaStream_t st);
@@ -159,7 +169,7 @@ struct RangeItem {
 };
 
 // batch.cu: work tables of the persistent batched tensor kernel.
-constexpr int BATCH_NPMAX = 4;
+constexpr int BATCH_NPMAX = 16;
 struct BatchChunk {  // up to BATCH_NPMAX probes sharing one gallery segment
     const uint64_t* gallery;
     const uint64_t* probe[BATCH_NPMAX];

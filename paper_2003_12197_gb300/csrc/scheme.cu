@@ -97,9 +97,15 @@ cudaError_t launch_keygen(const uint64_t* tw, uint64_t seed, DevKeys k, int* err
     cudaError_t e = cudaFuncSetAttribute(k_keygen, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k_keygen<<<dim3(2, 3), NTT_THREADS, smem, st>>>(tw, seed, k, err);
+    count_launches(1);
+    e = cudaGetLastError();
+    return e != cudaSuccess ? e : launch_key_ntt(tw, k, st);
+}
+
+cudaError_t launch_key_ntt(const uint64_t* tw, const DevKeys& k, cudaStream_t st) {
     k_key_ntt<<<4, NTT_THREADS, N * 8, st>>>(tw, k.pk, k.pk_ntt);
     k_key_ntt<<<8, NTT_THREADS, N * 8, st>>>(tw, k.evk, k.evk_ntt);
-    count_launches(3);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -299,19 +305,21 @@ cudaError_t launch_ct_add(uint64_t* out, const uint64_t* add, uint64_t nct, cuda
     return cudaGetLastError();
 }
 
-// One CTA per polynomial P = 2 i + poly of block b: reads its eight limbs
-// from the resident form (centred values, NTT domain over the search basis),
-// undoes the NTTs (R2C_GROUPS groups of NTT_THREADS threads, each for
-// NUM_S / R2C_GROUPS limbs), recovers the canonical residues mod q1, q2 by the
-// CRT of the search basis (the resident value is the centred lift x,
+// One CTA per polynomial P = 2 i + poly of block b = b0 + blockIdx.y: reads
+// its eight limbs from the resident form (centred values, NTT domain over the
+// search basis), undoes the NTTs (R2C_GROUPS groups of NTT_THREADS threads,
+// each for NUM_S / R2C_GROUPS limbs), recovers the canonical residues mod q1,
+// q2 by the CRT of the search basis (the resident value is the centred lift x,
 // |x| < q/2, so x' = x + q 2^129 is in range and x' = x mod q), adds
-// add[i][poly][l] and writes out[i][poly][l].
+// add[i][poly][l] (when add is non-null) and writes out[i][poly][l]; add and
+// out advance by d ciphertexts per block.
 constexpr int R2C_GROUPS = 4;
 constexpr int R2C_SMEM = NUM_S * N * 4;
 __global__ void __launch_bounds__(NTT_THREADS * R2C_GROUPS, 1) k_resident_to_canonical_add(
-    const uint64_t* __restrict__ tw, const uint64_t* __restrict__ resident, uint64_t b, uint32_t d,
+    const uint64_t* __restrict__ tw, const uint64_t* __restrict__ resident, uint64_t b0, uint32_t d,
     const uint64_t* __restrict__ add, uint64_t* __restrict__ out) {
     extern __shared__ uint32_t sm32[];
+    const uint64_t b = b0 + blockIdx.y;
     const uint32_t i = blockIdx.x >> 1;
     const int poly = (int)(blockIdx.x & 1);
     const int32_t* res = (const int32_t*)resident;
@@ -323,7 +331,7 @@ __global__ void __launch_bounds__(NTT_THREADS * R2C_GROUPS, 1) k_resident_to_can
         for (int k = t; k < N; k += NTT_THREADS) s[swz32(k)] = uncentre32(res[resident_offset(b, l, k, d, i, poly)], r);
         ntt32_inv_mod(s, tw, l, t);
     }
-    const size_t row = (((size_t)i * 2 + poly) * 2) * N;
+    const size_t row = ((size_t)blockIdx.y * d * 4 + ((size_t)i * 2 + poly) * 2) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         uint32_t x[NUM_S], y[NUM_S];
 #pragma unroll
@@ -332,17 +340,19 @@ __global__ void __launch_bounds__(NTT_THREADS * R2C_GROUPS, 1) k_resident_to_can
 #pragma unroll
         for (int j = 0; j < 2; j++) {
             const uint64_t v = crt_combine_q(y, alpha, c_mi_q_cols, c_m_q_cols, j, 0);
-            out[row + j * N + k] = add_mod(v, add[row + j * N + k], c_mod[j]);
+            out[row + j * N + k] = add ? add_mod(v, add[row + j * N + k], c_mod[j]) : v;
         }
     }
 }
 
 cudaError_t launch_resident_to_canonical_add(const uint64_t* tw, const uint64_t* resident, uint64_t b,
-                                             uint32_t d, const uint64_t* add, uint64_t* out, cudaStream_t st) {
+                                             uint32_t d, const uint64_t* add, uint64_t* out, cudaStream_t st,
+                                             uint32_t nb) {
     cudaError_t e = cudaFuncSetAttribute(k_resident_to_canonical_add, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          R2C_SMEM);
     if (e != cudaSuccess) return e;
-    k_resident_to_canonical_add<<<2 * d, NTT_THREADS * R2C_GROUPS, R2C_SMEM, st>>>(tw, resident, b, d, add, out);
+    k_resident_to_canonical_add<<<dim3(2 * d, nb), NTT_THREADS * R2C_GROUPS, R2C_SMEM, st>>>(tw, resident, b, d,
+                                                                                            add, out);
     count_launches(1);
     return cudaGetLastError();
 }

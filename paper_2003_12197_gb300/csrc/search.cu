@@ -8,6 +8,8 @@
 //   scale    c_k = [round(t X_k / q)]_q, exact (CRT, no floating point);
 //   keyswitch (c0, c1, c2) -> (c0 + sum_j D_j evk_j0, c1 + sum_j D_j evk_j1),
 //            D_j = c2 mod q_j, once per gallery block.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -280,17 +282,9 @@ __global__ void __launch_bounds__(NTT_THREADS, 4) k_intt32_batch(const uint64_t*
 // PM: the context's plaintext modulus entry, a template argument so that the
 // digit tables are read as constant operands at fixed offsets.
 template <int PM>
-__global__ void __launch_bounds__(256) k_scale_round(const uint32_t* __restrict__ X,
-                                                     uint64_t* __restrict__ C,
-                                                     uint64_t* __restrict__ KS) {
+__device__ __forceinline__ void scale_round_coeff(const uint32_t xv[NUM_S], uint64_t out[2]) {
     const PlainMod& P = c_plain[PM];
-    const int k = blockIdx.x * 256 + threadIdx.x;
-    const int c = blockIdx.y;
-    const uint64_t b = blockIdx.z;
-    const uint32_t* x = X + ((b * 3 + c) * NUM_S) * N + k;
-    uint32_t xv[NUM_S], y[NUM_S];
-#pragma unroll
-    for (int l = 0; l < NUM_S; l++) xv[l] = x[(size_t)l * N];
+    uint32_t y[NUM_S];
     const uint32_t alpha = crt_y(xv, y);
 
     int64_t col[4];
@@ -311,13 +305,16 @@ __global__ void __launch_bounds__(256) k_scale_round(const uint32_t* __restrict_
     const __int128 rem = (__int128)(Rm - (u128)Q * qq);
     if (rem < 0) Q--;
     else if (rem >= (__int128)qq) Q++;
-
-    uint64_t out[2];
 #pragma unroll
-    for (int l = 0; l < 2; l++) {
-        out[l] = crt_combine_q(y, alpha, P.a_cols, P.am_cols, l, (int64_t)Q - (int64_t)P.dshift[l]);
-        C[((b * 3 + c) * 2 + l) * N + k] = out[l];
-    }
+    for (int l = 0; l < 2; l++) out[l] = crt_combine_q(y, alpha, P.a_cols, P.am_cols, l, (int64_t)Q - (int64_t)P.dshift[l]);
+}
+
+// Writes c's two limbs to C[b][c][l][N] at k and, for c = 2, the
+// relinearisation digits KS[b][0..3] (see k_scale_round).
+__device__ __forceinline__ void store_scaled(uint64_t* __restrict__ C, uint64_t* __restrict__ KS, uint64_t b, int c,
+                                             int k, const uint64_t out[2]) {
+#pragma unroll
+    for (int l = 0; l < 2; l++) C[((b * 3 + c) * 2 + l) * N + k] = out[l];
     if (c == 2) {
         uint64_t* ks = KS + b * 4 * N + k;
         ks[0] = out[0];
@@ -325,6 +322,72 @@ __global__ void __launch_bounds__(256) k_scale_round(const uint32_t* __restrict_
         ks[2 * N] = out[1];
         ks[3 * N] = out[1];
     }
+}
+
+template <int PM>
+__global__ void __launch_bounds__(256) k_scale_round(const uint32_t* __restrict__ X,
+                                                     uint64_t* __restrict__ C,
+                                                     uint64_t* __restrict__ KS) {
+    const int k = blockIdx.x * 256 + threadIdx.x;
+    const int c = blockIdx.y;
+    const uint64_t b = blockIdx.z;
+    const uint32_t* x = X + ((b * 3 + c) * NUM_S) * N + k;
+    uint32_t xv[NUM_S];
+#pragma unroll
+    for (int l = 0; l < NUM_S; l++) xv[l] = x[(size_t)l * N];
+    uint64_t out[2];
+    scale_round_coeff<PM>(xv, out);
+    store_scaled(C, KS, b, c, k, out);
+}
+
+// The inverse NTTs and the scale-and-round in one kernel.  A cluster of NUM_S
+// CTAs takes one accumulator polynomial (block b, component c): CTA rank l
+// undoes the NTT mod r_l (k_intt32_batch's schedule) and keeps the
+// coefficients in its shared memory; after a cluster barrier each CTA
+// rounds N / NUM_S coefficients, reading their eight residues from the eight
+// CTAs' shared memory (distributed shared memory).  The X accumulators are
+// read once and not written back.  A second cluster barrier keeps every CTA's
+// shared memory alive until its peers' reads are done.
+constexpr int ISC_SLICE = N / NUM_S;  // coefficients rounded per CTA
+static_assert(ISC_SLICE == 2 * NTT_THREADS, "two coefficients per thread");
+template <int PM>
+__global__ void __cluster_dims__(NUM_S, 1, 1) __launch_bounds__(NTT_THREADS, 4)
+    k_intt_scale_cluster(const uint64_t* __restrict__ tw, const uint32_t* __restrict__ X,
+                         uint64_t* __restrict__ C, uint64_t* __restrict__ KS) {
+    namespace cg = cooperative_groups;
+    __shared__ uint32_t sm32[N];
+    const cg::cluster_group cluster = cg::this_cluster();
+    const int l = (int)cluster.block_rank();
+    const int c = blockIdx.y;
+    const uint64_t b = blockIdx.z;
+    const int t = threadIdx.x;
+    const uint32_t* g = X + ((b * 3 + c) * NUM_S + l) * N;
+    uint32_t v[16];
+    const uint4* g4 = (const uint4*)(g + 16 * t);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const uint4 u = g4[i];
+        v[4 * i] = u.x;
+        v[4 * i + 1] = u.y;
+        v[4 * i + 2] = u.z;
+        v[4 * i + 3] = u.w;
+    }
+    ntt32_inv_regs(v, sm32, tw32_inv(tw, l), c_smod[l], c_sninv[l], c_sninv_s[l], t);
+    __syncthreads();  // the transform's last shared-memory reads are done
+#pragma unroll
+    for (int a = 0; a < 16; a++) sm32[t + 256 * a] = v[a];  // natural order, fully reduced
+    cluster.sync();
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int k = l * ISC_SLICE + h * NTT_THREADS + t;
+        uint32_t xv[NUM_S];
+#pragma unroll
+        for (int i = 0; i < NUM_S; i++) xv[i] = *cluster.map_shared_rank(sm32 + k, i);
+        uint64_t out[2];
+        scale_round_coeff<PM>(xv, out);
+        store_scaled(C, KS, b, c, k, out);
+    }
+    cluster.sync();
 }
 
 // ---------------------------------------------------------------- key switch
@@ -370,6 +433,42 @@ __global__ void __launch_bounds__(NTT_THREADS, 3) k_ks_inv_finish(const uint64_t
     ntt_inv_mod(sm, tw, l);
     const uint64_t* cc = C + ((b * 3 + c) * 2 + l) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) out[x * N + k] = add_mod(cc[k], sm[swz(k)], q);
+}
+
+// The key switch in one kernel: CTA per (b, l), two groups of NTT_THREADS
+// threads.  Group j takes D_j mod q_l (row (b, j, l) of KS) to the NTT
+// domain; then group c forms O_cl = D_0 evk_0[c][l] + D_1 evk_1[c][l] from
+// both transformed digits, undoes its NTT and adds C[b][c][l] into
+// out[b][c][l].  No intermediate leaves shared memory.
+__global__ void __launch_bounds__(2 * NTT_THREADS, 1) k_ks_fused(const uint64_t* __restrict__ tw,
+                                                             const uint64_t* __restrict__ KS,
+                                                             const uint64_t* __restrict__ evk_ntt,
+                                                             const uint64_t* __restrict__ C,
+                                                             uint64_t* __restrict__ out) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t b = blockIdx.x >> 1;
+    const int l = (int)(blockIdx.x & 1);
+    const int grp = threadIdx.x / NTT_THREADS, t = threadIdx.x % NTT_THREADS;
+    const uint64_t q = c_mod[l];
+    uint64_t* s = sm + grp * N;
+    const uint64_t* src = KS + ((b * 2 + grp) * 2 + l) * N;
+    for (int k = t; k < N; k += NTT_THREADS) s[swz(k)] = src[k];
+    ntt_fwd_smem(s, tw_fwd(tw, l), q, c_one_s[l], t);
+    const uint64_t* e0 = evk_ntt + (size_t)(((0 * 2 + grp) * 2 + l) * 2) * N;
+    const uint64_t* e1 = evk_ntt + (size_t)(((1 * 2 + grp) * 2 + l) * 2) * N;
+    uint64_t o[16];
+#pragma unroll
+    for (int a = 0; a < 16; a++) {
+        const int k = t + NTT_THREADS * a, x = swz(k);
+        o[a] = add_mod(shoup(sm[x], e0[k], e0[N + k], q), shoup(sm[N + x], e1[k], e1[N + k], q), q);
+    }
+    __syncthreads();  // both groups are done reading both digits
+#pragma unroll
+    for (int a = 0; a < 16; a++) s[swz(t + NTT_THREADS * a)] = o[a];
+    ntt_inv_smem(s, tw_inv(tw, l), q, c_ninv[l], c_ninv_s[l], t);
+    const uint64_t* cc = C + ((b * 3 + grp) * 2 + l) * N;
+    uint64_t* dst = out + ((b * 2 + grp) * 2 + l) * N;
+    for (int k = t; k < N; k += NTT_THREADS) dst[k] = add_mod(cc[k], s[swz(k)], q);
 }
 
 // out[b][c][l] = C[b][c][l] + O[b][c][l] mod q_l (O in the coefficient domain)
@@ -431,31 +530,56 @@ __global__ void __launch_bounds__(256) k_ks_mul_w(const uint64_t* __restrict__ W
 // (its intermediates reuse the X area: the partial products P [npairs][8][N],
 // or with the base-w gadget O [npairs][2][2][N] and the digits), canonical
 // score ciphertexts into out [npairs][2][2][N].
+const char* epilogue_variant_name(int v) {
+    static const char* names[EPI_VARIANTS] = {"split", "intt_scale_cluster", "ks_fused",
+                                              "intt_scale_cluster+ks_fused"};
+    return (v >= 0 && v < EPI_VARIANTS) ? names[v] : nullptr;
+}
+
 cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npairs, uint64_t* X,
                             uint64_t* C, uint64_t* KS, uint64_t* out, cudaStream_t st,
-                            cudaEvent_t* ev, const KeySwitchW* ksw) {
+                            cudaEvent_t* ev, const KeySwitchW* ksw, int epi) {
     uint64_t nl = 0;
     uint64_t* O = X;
     uint32_t* X32 = (uint32_t*)X;  // accumulators [npairs][3][NUM_S][N]
     const uint64_t max_z = 65535;
     const uint64_t chunk = 1u << 30;
-    const uint64_t npolys = npairs * 3 * NUM_S;  // chunks are multiples of NUM_S
-    for (uint64_t off = 0; off < npolys; off += chunk) {
-        const uint64_t n = npolys - off < chunk ? npolys - off : chunk;
-        k_intt32_batch<<<(unsigned)n, NTT_THREADS, 0, st>>>(tw, X32 + off * N);
-        nl++;
+    if (epi & EPI_INTT_SCALE_CLUSTER) {
+        // inverse NTTs and scale-and-round in one kernel (clusters of NUM_S CTAs)
+        for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
+            const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
+            const dim3 grid(NUM_S, 3, (unsigned)nb);
+            if (k.pm == 0)
+                k_intt_scale_cluster<0><<<grid, NTT_THREADS, 0, st>>>(tw, X32 + b0 * 3 * NUM_S * N, C + b0 * 6 * N,
+                                                                     KS + b0 * 4 * N);
+            else
+                k_intt_scale_cluster<1><<<grid, NTT_THREADS, 0, st>>>(tw, X32 + b0 * 3 * NUM_S * N, C + b0 * 6 * N,
+                                                                     KS + b0 * 4 * N);
+            nl++;
+        }
+        if (ev) {
+            cudaEventRecord(ev[0], st);
+            cudaEventRecord(ev[1], st);
+        }
+    } else {
+        const uint64_t npolys = npairs * 3 * NUM_S;  // chunks are multiples of NUM_S
+        for (uint64_t off = 0; off < npolys; off += chunk) {
+            const uint64_t n = npolys - off < chunk ? npolys - off : chunk;
+            k_intt32_batch<<<(unsigned)n, NTT_THREADS, 0, st>>>(tw, X32 + off * N);
+            nl++;
+        }
+        if (ev) cudaEventRecord(ev[0], st);
+        for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
+            const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
+            const dim3 grid(N / 256, 3, (unsigned)nb);
+            if (k.pm == 0)
+                k_scale_round<0><<<grid, 256, 0, st>>>(X32 + b0 * 3 * NUM_S * N, C + b0 * 6 * N, KS + b0 * 4 * N);
+            else
+                k_scale_round<1><<<grid, 256, 0, st>>>(X32 + b0 * 3 * NUM_S * N, C + b0 * 6 * N, KS + b0 * 4 * N);
+            nl++;
+        }
+        if (ev) cudaEventRecord(ev[1], st);
     }
-    if (ev) cudaEventRecord(ev[0], st);
-    for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
-        const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
-        const dim3 grid(N / 256, 3, (unsigned)nb);
-        if (k.pm == 0)
-            k_scale_round<0><<<grid, 256, 0, st>>>(X32 + b0 * 3 * NUM_S * N, C + b0 * 6 * N, KS + b0 * 4 * N);
-        else
-            k_scale_round<1><<<grid, 256, 0, st>>>(X32 + b0 * 3 * NUM_S * N, C + b0 * 6 * N, KS + b0 * 4 * N);
-        nl++;
-    }
-    if (ev) cudaEventRecord(ev[1], st);
     if (ksw) {
         // base-w gadget: digits after O in X, NTT, multiply-accumulate with evkw
         uint64_t* W = X + npairs * 4 * N;
@@ -488,6 +612,15 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
                                                                         out + b0 * 4 * N);
             nl++;
         }
+    } else if (epi & EPI_KS_FUSED) {
+        // RNS gadget, one kernel per (pair, limb)
+        cudaFuncSetAttribute(k_ks_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * N * 8);
+        for (uint64_t off = 0; off < npairs * 2; off += chunk) {  // chunk: an even number of rows
+            const uint64_t n = npairs * 2 - off < chunk ? npairs * 2 - off : chunk;
+            k_ks_fused<<<(unsigned)n, 2 * NTT_THREADS, 2 * N * 8, st>>>(tw, KS + off * 2 * N, k.evk_ntt,
+                                                                       C + off / 2 * 6 * N, out + off * 2 * N);
+            nl++;
+        }
     } else {
         // RNS gadget: partial products P [npairs][2 j][2 c][2 l][N] in the X area
         uint64_t* P = X;
@@ -513,7 +646,7 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
                           uint64_t* ws, int* err, cudaStream_t st, cudaEvent_t* ev, int variant,
-                          const KeySwitchW* ksw, const EpilogueStream* ep) {
+                          const KeySwitchW* ksw, const EpilogueStream* ep, int epi) {
     if (nblocks == 0) return cudaSuccess;
     uint64_t* X = ws;
     uint64_t* C = X + nblocks * 15 * N;
@@ -529,7 +662,7 @@ cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* 
         if (e != cudaSuccess) return e;
         es = ep->stream;
     }
-    e = launch_epilogue(tw, k, nblocks, X, C, KS, scores_ct, es, ev ? ev + 2 : nullptr, ksw);
+    e = launch_epilogue(tw, k, nblocks, X, C, KS, scores_ct, es, ev ? ev + 2 : nullptr, ksw, epi);
     if (ev) cudaEventRecord(ev[4], es);
     if (ep) {
         cudaError_t ej = cudaEventRecord(ep->ev[1], es);

@@ -103,6 +103,10 @@ struct hers_server {
     bool paused = false;  // admission held (requests queue up)
     uint64_t next_id = 1;
     uint64_t n_submitted = 0, n_completed = 0, n_batches = 0, n_entries = 0, max_batch_seen = 0;
+    // time spent, summed over retired batches: device time of the kernels
+    // (probe preparation, tensor, epilogue) and of the score copies to host
+    // memory (CUDA events), and host time planning and issuing batches
+    double t_kernels_ms = 0, t_copies_ms = 0, t_plan_ms = 0;
     int error = 0;
 };
 
@@ -119,6 +123,7 @@ struct Slot {
     BatchChunk* h_chunks = nullptr;  // pinned staging of the work tables
     BatchUnit* h_units = nullptr;
     size_t cap_chunks = 0, cap_units = 0;
+    cudaEvent_t ev[3] = {};  // batch start, kernels done, copies done
 };
 
 void CUDART_CB on_batch_done(void* arg) {
@@ -185,7 +190,7 @@ cudaError_t issue_batch(hers_server* srv, Slot* s, std::vector<BatchChunk>& chun
     BatchUnit* d_units = (BatchUnit*)(tb + (chunks.size() * sizeof(BatchChunk) + ALIGN - 1) / ALIGN * ALIGN);
     uint32_t* d_counter = (uint32_t*)((uint8_t*)d_units + (units.size() * sizeof(BatchUnit) + ALIGN - 1) / ALIGN * ALIGN);
 
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaEventRecord(s->ev[0], st);
     for (size_t i = 0; i < s->reqs.size() && e == cudaSuccess; i++) {
         const uint32_t d = items[i].d;
         e = cudaMemcpyAsync(pct[i], s->reqs[i]->probe_ct_host, (uint64_t)d * 4 * N * 8,
@@ -206,12 +211,15 @@ cudaError_t issue_batch(hers_server* srv, Slot* s, std::vector<BatchChunk>& chun
     if (e == cudaSuccess)
         e = launch_batched(srv->variant, d_chunks, d_units, (uint32_t)units.size(), d_counter, X, ctx->err,
                            ctx->device, st);
-    if (e == cudaSuccess) e = launch_epilogue(ctx->tw, srv->keys->k, npairs, X, C, KS, OUT, st);
+    if (e == cudaSuccess)
+        e = launch_epilogue(ctx->tw, srv->keys->k, npairs, X, C, KS, OUT, st, nullptr, nullptr, ctx->epi_variant);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev[1], st);
     for (size_t i = 0; i < s->reqs.size() && e == cudaSuccess; i++) {
         const Request* r = s->reqs[i];
         e = cudaMemcpyAsync(r->scores_host, OUT + items[i].pair_base * 4 * N,
                             (r->end - r->begin) * 4 * N * 8, cudaMemcpyDeviceToHost, st);
     }
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev[2], st);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(st, on_batch_done, s);
     return e;
 }
@@ -223,6 +231,12 @@ void scheduler(hers_server* srv) {
         // retire finished batches
         for (Slot* s : srv->slots)
             if (s->busy && s->done) {
+                float k_ms = 0, c_ms = 0;
+                if (cudaEventElapsedTime(&k_ms, s->ev[0], s->ev[1]) == cudaSuccess &&
+                    cudaEventElapsedTime(&c_ms, s->ev[1], s->ev[2]) == cudaSuccess) {
+                    srv->t_kernels_ms += k_ms;
+                    srv->t_copies_ms += c_ms;
+                }
                 srv->pool.release(s->off, s->bytes);
                 for (Request* r : s->reqs) {
                     r->status = 0;
@@ -247,6 +261,7 @@ void scheduler(hers_server* srv) {
         bool any_busy = false;
         for (Slot* s : srv->slots) any_busy = any_busy || s->busy;
         if (freeslot && !srv->pending.empty() && !srv->paused) {
+            const Clock::time_point t_plan0 = Clock::now();
             // admit from the head of the queue while the batch fits in the pool
             size_t take = std::min<size_t>(srv->pending.size(), srv->max_batch);
             std::vector<BatchChunk> chunks;
@@ -306,6 +321,7 @@ void scheduler(hers_server* srv) {
             cudaError_t e = ensure_staging(s, chunks.size(), units.size()) ? cudaSuccess : cudaErrorMemoryAllocation;
             if (e == cudaSuccess) e = issue_batch(srv, s, chunks, units, items, npairs);
             lk.lock();
+            srv->t_plan_ms += std::chrono::duration<double, std::milli>(Clock::now() - t_plan0).count();
             if (e != cudaSuccess) {
                 srv->error = HERS_E_CUDA;
                 for (Request* r : s->reqs) {
@@ -360,11 +376,15 @@ int hers_server_create(hers_ctx* ctx, const hers_keys* keys, const hers_server_g
             s->srv = srv;
             s->index = i;
             srv->slots[i] = s;
+            for (int k = 0; k < 3 && e == cudaSuccess; k++) e = cudaEventCreate(&s->ev[k]);
         }
     }
     if (e != cudaSuccess) {
         for (int i = 0; i < SRV_STREAMS; i++) {
             if (srv->streams[i]) cudaStreamDestroy(srv->streams[i]);
+            if (srv->slots[i])
+                for (int k = 0; k < 3; k++)
+                    if (srv->slots[i]->ev[k]) cudaEventDestroy(srv->slots[i]->ev[k]);
             delete srv->slots[i];
         }
         if (srv->pool_base) cudaFree(srv->pool_base);
@@ -442,6 +462,15 @@ int hers_server_stats(hers_server* srv, uint64_t* submitted, uint64_t* completed
     return srv->error;
 }
 
+int hers_server_timing(hers_server* srv, double* kernels_ms, double* copies_ms, double* plan_ms) {
+    if (!srv) return HERS_E_INVAL;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (kernels_ms) *kernels_ms = srv->t_kernels_ms;
+    if (copies_ms) *copies_ms = srv->t_copies_ms;
+    if (plan_ms) *plan_ms = srv->t_plan_ms;
+    return HERS_OK;
+}
+
 int hers_server_free(hers_server* srv) {
     if (!srv) return HERS_E_INVAL;
     {
@@ -457,6 +486,8 @@ int hers_server_free(hers_server* srv) {
         if (srv->slots[i]) {
             if (srv->slots[i]->h_chunks) cudaFreeHost(srv->slots[i]->h_chunks);
             if (srv->slots[i]->h_units) cudaFreeHost(srv->slots[i]->h_units);
+            for (int k = 0; k < 3; k++)
+                if (srv->slots[i]->ev[k]) cudaEventDestroy(srv->slots[i]->ev[k]);
             delete srv->slots[i];
         }
     }

@@ -170,7 +170,8 @@ int hers_search_stream(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gal
                                ctx->device, sm);
         cudaEventRecord(ev_free[s], sm);  // the resident chunk buffer may be refilled
         if (e == cudaSuccess)
-            e = launch_epilogue(ctx->tw, keys->k, npairs, base + L.X, base + L.C, base + L.KS, base + L.OUT, sm);
+            e = launch_epilogue(ctx->tw, keys->k, npairs, base + L.X, base + L.C, base + L.KS, base + L.OUT, sm,
+                                nullptr, nullptr, ctx->epi_variant);
         for (uint32_t p = 0; p < nprobes && e == cudaSuccess; p++)
             e = cudaMemcpyAsync(scores_ct + ((uint64_t)p * nblocks + b0) * 4 * N,
                                 base + L.OUT + (uint64_t)p * nb * 4 * N, (uint64_t)nb * 4 * N * 8,

@@ -89,3 +89,21 @@ def test_batched_autotune_scores_and_oracle(setup):
     osc, _ = O.search_block(oprb, ogal, oevk)
     assert np.array_equal(H.to_u64(b.item_scores(1, nb))[nb - 1], osc)
     b.close()
+
+
+@pytest.mark.parametrize("epi", [1, 2, 3])
+def test_batched_with_every_epilogue_form(setup, epi):
+    """A batch planned on a context with another epilogue form gives the same
+    bytes as the plain search (the form is captured in the batch's graph)."""
+    ctx = setup["ctx"]
+    keep = H.hers_get_epilogue_variant(ctx)
+    H.hers_set_epilogue_variant(ctx, epi)
+    try:
+        b = H.Batch(ctx, setup["keys"], setup["items"], flags=H.batch_variant_flag(1))
+        b.run()
+        torch.cuda.synchronize()
+        for i, (_, nb, _, _) in enumerate(setup["items"]):
+            assert torch.equal(b.item_scores(i, nb), setup["truth"][i][3]), f"item {i}"
+        b.close()
+    finally:
+        H.hers_set_epilogue_variant(ctx, keep)

@@ -29,6 +29,12 @@ def test_paper_t_search_bit_exact():
     nb = H.hers_blocks_for(m)
     sc = H.hers_search(ctx, keys, gal, nb, d, pr)
     scores = H.hers_decrypt_scores(ctx, keys, sc, m).cpu().numpy().astype(np.int64)
+    # every epilogue form at this t (the fused scale-and-round takes its own
+    # instantiation for the paper's t) gives the same bytes
+    for v in range(1, len(H.hers_epilogue_variants())):
+        H.hers_set_epilogue_variant(ctx, v)
+        assert torch.equal(H.hers_search(ctx, keys, gal, nb, d, pr), sc), H.hers_epilogue_variants()[v]
+    H.hers_set_epilogue_variant(ctx, 0)
     H.hers_check(ctx)
     O.set_plain_modulus(O.T_PAPER)
     try:

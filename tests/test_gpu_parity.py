@@ -177,7 +177,8 @@ def test_empty_inputs(ctx, keys):
 @pytest.mark.slow
 def test_config2_full_size(ctx, keys, oracle_keys):
     """1,048,576 entries (256 blocks), d = 64, one planted mate: every decrypted
-    score exact; sampled blocks' score ciphertexts bit-exact against the oracle."""
+    score exact; the score ciphertexts of the mate's block, the last block and
+    8 seeded random blocks bit-exact against the oracle."""
     m, d = 1 << 20, 64
     feats = W.gallery_features(m, d, FEAT_SEED)
     mate = int(W.mate_indices(m, 1, MATE_SEED)[0])
@@ -187,7 +188,11 @@ def test_config2_full_size(ctx, keys, oracle_keys):
     assert int(np.argmax(res["scores"])) == mate
     oprb = O.encrypt_probe(oracle_keys[1], q, PRB_SEED)
     sc = u64(res["sc"])
-    for b in sorted({mate // 4096, res["nb"] - 1}):
+    rng = np.random.default_rng(20032)
+    blocks = {mate // 4096, res["nb"] - 1}
+    while len(blocks) < 10:
+        blocks.add(int(rng.integers(0, res["nb"])))
+    for b in sorted(blocks):
         ogal = O.encrypt_gallery_block(oracle_keys[1], feats, b, GAL_SEED)
         osc, _ = O.search_block(oprb, ogal, oracle_keys[2])
         assert np.array_equal(sc[b], osc), f"block {b}"
@@ -334,3 +339,32 @@ def test_searches_on_several_streams_in_flight(ctx, keys, config1):
     for k in range(6):
         assert torch.equal(outs[k], res["sc"]), f"search {k}"
         assert torch.equal(copies[k], res["sc"]), f"copy after search {k}"
+
+
+def test_every_epilogue_form_gives_the_same_ciphertexts(ctx, keys, oracle_keys):
+    """The epilogue forms (split kernels, inverse NTTs fused with
+    scale-and-round in clusters, the fused key switch, both) compute the same
+    exact integers: every form gives the oracle's score ciphertexts, over 3
+    blocks with a ragged last block; and the epilogue autotuner keeps one."""
+    m, d = 2 * 4096 + 999, 19
+    feats = W.gallery_features(m, d, 4747)
+    q = W.probe_for_mate(77, d, 4747, 4848)
+    gal, _ = H.hers_encrypt_gallery(ctx, keys, torch.from_numpy(feats).cuda(), GAL_SEED)
+    pr = H.hers_probe_prepare(ctx, H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).cuda(), PRB_SEED))
+    names = H.hers_epilogue_variants()
+    assert len(names) == 4
+    keep = H.hers_get_epilogue_variant(ctx)
+    outs = []
+    for v in range(len(names)):
+        H.hers_set_epilogue_variant(ctx, v)
+        outs.append(u64(H.hers_search(ctx, keys, gal, 3, d, pr)))
+    oprb = O.encrypt_probe(oracle_keys[1], q, PRB_SEED)
+    for b in range(3):
+        ogal = O.encrypt_gallery_block(oracle_keys[1], feats, b, GAL_SEED)
+        osc, _ = O.search_block(oprb, ogal, oracle_keys[2])
+        for v, o in enumerate(outs):
+            assert np.array_equal(o[b], osc), (names[v], b)
+    chosen, ms = H.hers_autotune_epilogue(ctx, keys, gal, 3, d, pr)
+    assert 0 <= chosen < len(names) and set(ms) == set(names)
+    assert H.hers_get_epilogue_variant(ctx) == chosen
+    H.hers_set_epilogue_variant(ctx, keep)
