@@ -368,9 +368,8 @@ def run_gpu(args):
     else:
         variant, tune_ms = H.hers_autotune(ctx, keys, gal, nb, d, pr, workspace=ws)
     variant_name = H.hers_tensor_variants()[variant]
-    # and the epilogue form (inverse NTTs, scale-and-round, key switch) after it
-    epi, epi_ms = H.hers_autotune_epilogue(ctx, keys, gal, nb, d, pr, workspace=ws)
-    epi_name = H.hers_epilogue_variants()[epi]
+    # and the epilogue form (inverse NTTs, scale-and-round, key switch), timed alone after it
+    _, epi_ms = H.hers_autotune_epilogue(ctx, keys, gal, nb, d, pr, workspace=ws)
 
     # correctness of the benchmarked path: exact scores and the planted mate
     H.hers_search(ctx, keys, gal, nb, d, pr, out=sc, workspace=ws)
@@ -418,6 +417,33 @@ def run_gpu(args):
         torch.cuda.synchronize()
         dist.barrier()
         return dist.max(e0.elapsed_time(e1), dev)
+
+    # The configuration of the timed region: tensor shape, epilogue form and
+    # which of the two takes the high-priority stream, chosen by the step time
+    # with searches in flight.  There one search's epilogue shares the GPU with
+    # the next search's HBM-bound tensor kernel, so the epilogue's memory
+    # traffic and the SM resources the tensor shape leaves count, not only the
+    # times of the two alone.
+    tnames, enames = H.hers_tensor_variants(), H.hers_epilogue_variants()
+    t_cands = [variant] if args.variant else sorted(
+        {variant} | {i for i, n in enumerate(tnames) if n.endswith("_m1")})
+    combos = {}
+    for tv in t_cands:
+        H.hers_set_tensor_variant(ctx, tv)
+        for tf in (False, True):
+            H.hers_set_tensor_first(ctx, tf)
+            for ev_ in range(len(enames)):
+                H.hers_set_epilogue_variant(ctx, ev_)
+                for k in range(IN_FLIGHT):
+                    step_in_flight(k)
+                combos[(tv, tf, ev_)] = timed(step_in_flight, 10, trace=False) / 10
+    variant, tensor_first, epi = min(combos, key=combos.get)
+    variant_name, epi_name = tnames[variant], enames[epi]
+    H.hers_set_tensor_variant(ctx, variant)
+    H.hers_set_tensor_first(ctx, tensor_first)
+    H.hers_set_epilogue_variant(ctx, epi)
+    epi_inflight = {f"{tnames[a]}|{'tensor_first' if b else 'epilogue_first'}|{enames[c]}": round(v, 4)
+                    for (a, b, c), v in sorted(combos.items(), key=lambda kv: kv[1])}
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -585,8 +611,11 @@ def run_gpu(args):
                     "bit_exact_vs_device": e2e_ok},
             "autotune": {"chosen": variant_name,
                          "ms_per_variant": {k: round(v, 4) for k, v in tune_ms.items()},
-                         "epilogue_chosen": epi_name,
-                         "epilogue_ms_per_variant": {k: round(v, 4) for k, v in epi_ms.items()}},
+                         "epilogue_chosen": epi_name, "tensor_first": bool(tensor_first),
+                         "epilogue_ms_alone": {k: round(v, 4) for k, v in epi_ms.items()},
+                         "step_ms_in_flight": epi_inflight,
+                         "note": "tensor shape (timed alone above), epilogue form and stream priority "
+                                 "order are chosen together by the step time with searches in flight"},
             "roofline": {"kernel": f"k_tensor<{variant_name}> (tensor-product accumulate over d)",
                          "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -845,6 +874,20 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
     # pinned host arena for score ciphertexts, handed out as a ring
     arena_blocks = 4 * nblocks * 16
     arena = torch.empty((arena_blocks, 4 * N), dtype=torch.int64).pin_memory()
+    # the rate of a device -> arena copy (2 GiB), as the server's copy-outs see it
+    probe_n = min(arena.numel(), (2 << 30) // 8)
+    src = torch.empty(probe_n, dtype=torch.int64, device=dev)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    arena_ms = None
+    for _ in range(3):
+        c0.record()
+        arena.view(-1)[:probe_n].copy_(src, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        arena_ms = c0.elapsed_time(c1) if arena_ms is None else min(arena_ms, c0.elapsed_time(c1))
+    del src
+    host_diag = {"arena_d2h_gbs": probe_n * 8 / (arena_ms / 1e3) / 1e9,
+                 "host_mem_available_gb": host_mem_available() / 1e9}
     # sampled requests (up to SAMPLE per rate, at most SAMPLE_MAX_BLOCKS blocks
     # each) write to buffers of their own, kept for the mix-vs-alone check
     SAMPLE, SAMPLE_MAX_BLOCKS = 4, 600
@@ -856,6 +899,7 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
     clocks.start()
     clocks.mark_start()
     launches0 = H.hers_kernel_launches()
+    cpu0, wall0 = thread_cpu_seconds(), time.perf_counter()
     for ri, rate in enumerate(rates):
         tm0 = srv.timing()
         reqs = W.serving_requests(rate, window, max_requests, nblocks, dims, seed=int(rate))
@@ -920,6 +964,11 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
                         "achieved_req_s": len(reqs) / wall, "wall_s": wall})
     clocks.mark_stop()
     clk = clocks.stop()
+    cpu1, wall1 = thread_cpu_seconds(), time.perf_counter()
+    busy = sorted(((cpu1[k] - cpu0.get(k, 0.0), k[1]) for k in cpu1), reverse=True)[:6]
+    host_diag["threads_cpu_s"] = [[n, round(v, 2)] for v, n in busy]
+    host_diag["wall_s"] = round(wall1 - wall0, 2)
+    host_diag["nthreads"] = len(cpu1)
     launches = H.hers_kernel_launches() - launches0
     st = srv.stats()
     srv.close()
@@ -966,7 +1015,7 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
                        "resident_gallery_bytes": resident, "pool_bytes": st["pool_bytes"],
                        "max_batch": 16, "batch_variant": sv_name, "setup_s": setup_s,
                        "latency": "from the arrival time to the score ciphertexts in pinned host memory"},
-            "rates": results, "server": st, "gpu_launches": launches,
+            "rates": results, "server": st, "gpu_launches": launches, "host": host_diag,
             "correct": {"mix_equals_alone": f"{mix_ok}/{len(sampled)}",
                         "checked": "sampled requests of every rate, re-run alone through hers_search, "
                                    "score ciphertexts compared bit for bit"},
@@ -996,6 +1045,25 @@ def run_serving(args):
     keys.close()
     ctx.close()
     return 0
+
+
+def thread_cpu_seconds():
+    """{(tid, name): CPU seconds} of this process's threads (Linux /proc)."""
+    out = {}
+    tick = os.sysconf("SC_CLK_TCK") if hasattr(os, "sysconf") else 100
+    base = "/proc/self/task"
+    try:
+        tids = os.listdir(base)
+    except OSError:
+        return out
+    for tid in tids:
+        try:
+            name = open(f"{base}/{tid}/comm").read().strip()
+            f = open(f"{base}/{tid}/stat").read().rsplit(")", 1)[1].split()
+            out[(tid, name)] = (int(f[11]) + int(f[12])) / tick
+        except (OSError, IndexError, ValueError):
+            pass
+    return out
 
 
 def host_mem_available():
@@ -1045,10 +1113,31 @@ def run_scale(args):
     source = args.scale_source
     if source == "auto":
         source = "host" if host_mem_available() > gal_bytes + (24 << 30) else "device"
+    dev_copy, h2d_gbs = None, None
     if source == "host":
         g = torch.empty(gct.shape, dtype=torch.int64, pin_memory=True)
         g.copy_(gct)
-        del gct
+        # the rate of one large pinned-host -> device copy (up to 4 GiB of the gallery)
+        span = min(g.numel(), (4 << 30) // 8)
+        buf = torch.empty(span, dtype=torch.int64, device=dev)
+        flat = g.view(-1)[:span]
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = None
+        for _ in range(3):
+            h0.record()
+            buf.copy_(flat, non_blocking=True)
+            h1.record()
+            torch.cuda.synchronize()
+            best = h0.elapsed_time(h1) if best is None else min(best, h0.elapsed_time(h1))
+        h2d_gbs = span * 8 / (best / 1e3) / 1e9
+        del buf
+        # keep the device copy (when it and the search's buffers fit) to time
+        # the same search without host copies: the compute-only pass
+        need = nprobes * nb * 4 * N * 8 + H.hers_search_stream_workspace_bytes(d, nprobes, 32) + (8 << 30)
+        if torch.cuda.mem_get_info(dev)[0] > need:
+            dev_copy = gct
+        else:
+            del gct
         torch.cuda.empty_cache()
     else:
         g = gct
@@ -1066,6 +1155,17 @@ def run_scale(args):
     H.hers_search_stream(ctx, keys, g[: 4 * chunk], 4 * chunk, d, probes, chunk, bv,
                          out=sc[:, : 4 * chunk].contiguous(), workspace=ws)
     torch.cuda.synchronize()
+    dev_ms = None
+    if dev_copy is not None:
+        # the same chunked search with the gallery in device memory: no host copies
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        H.hers_search_stream(ctx, keys, dev_copy, nb, d, probes, chunk, bv, out=sc, workspace=ws)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        dev_ms = f0.elapsed_time(f1)
+        del dev_copy
+        torch.cuda.empty_cache()
     clocks = ClockSampler(local)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1118,6 +1218,17 @@ def run_scale(args):
                       "gallery_bytes": gal_bytes, "gallery_source": source, "chunk_blocks": chunk,
                       "batch_variant": bv_name, "setup_s": gen_s},
            "search_s_all_probes": ms / 1e3, "search_s_per_probe": ms / 1e3 / nprobes,
+           "streaming": None if source != "host" else {
+               "h2d_gbs_measured": h2d_gbs,
+               "h2d_gbs_during_search": gal_bytes / (ms / 1e3) / 1e9,
+               "device_source_s": None if dev_ms is None else dev_ms / 1e3,
+               "host_source_s": ms / 1e3,
+               "copies_hidden": None if dev_ms is None else dev_ms / ms,
+               "ceiling_entries_per_s": {
+                   "h2d": h2d_gbs * 1e9 / (32 * d) * nprobes,
+                   "compute": None if dev_ms is None else nprobes * m / (dev_ms / 1e3),
+                   "note": "min(H2D rate / 32 d bytes per entry x probes, the same search from device "
+                           "memory); copies_hidden = device-source time / host-source time"}},
            "paper_100M_d64_s": 1480.0,
            "correct": {"scores_exact_all": exact, "top1": f"{top1}/{nprobes}",
                        "oracle_blocks": checked, "oracle_bit_exact": oracle_ok},

@@ -562,7 +562,9 @@ int hers_autotune(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
  * "intt_scale_cluster" (inverse NTTs and scale-and-round in one kernel: a
  * cluster of eight CTAs per accumulator polynomial, residues exchanged in
  * distributed shared memory), 2 "ks_fused" (the key switch in one kernel per
- * block and limb), 3 both.  The context's form applies to every search on it
+ * block and limb), 3 both; adding 4 ("+shfl") makes the first data exchange
+ * of every inverse NTT of the accumulators a warp-shuffle transpose instead
+ * of a pass through shared memory.  The context's form applies to every search on it
  * (hers_search*, hers_batch_*, hers_server_*, hers_search_stream).
  * hers_autotune_epilogue times each form's epilogue after the tensor kernel
  * of the given search (1 warm-up, 3 timed, minimum kept), keeps the fastest
@@ -570,6 +572,22 @@ int hers_autotune(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
  * timings in ms.  It holds a temporary device buffer for nblocks score
  * ciphertexts during the call.  Synchronous.
  */
+/*
+ * Which half of a search takes the context's high-priority stream (no
+ * counterpart in the paper).  By default (0) hers_search and the host-buffer
+ * searches run the tensor kernel on the caller's stream and the epilogue on
+ * the high-priority stream, so that one search's epilogue is dispatched ahead
+ * of the next search's pending tensor CTAs.  With hers_set_tensor_first(ctx,
+ * 1) the tensor kernel runs on the high-priority stream and the epilogue on
+ * the caller's stream: a search's tensor kernel keeps its SMs and the
+ * previous search's epilogue runs in the registers and shared memory it
+ * leaves (useful with the one-CTA-per-SM tensor shapes).  Either way the call
+ * is ordered on the caller's stream as documented for hers_search, and the
+ * bytes are the same.  Setting it waits for the context's high-priority
+ * stream.
+ */
+int hers_set_tensor_first(hers_ctx* ctx, int on);
+int hers_get_tensor_first(const hers_ctx* ctx);
 int hers_epilogue_variants(void);
 const char* hers_epilogue_variant_name(int v);
 int hers_get_epilogue_variant(const hers_ctx* ctx);

@@ -133,6 +133,8 @@ def lib():
                 "hers_server_pause": ([vp, i32], i32),
                 "hers_server_free": ([vp], i32),
                 "hers_server_timing": ([vp, vp, vp, vp], i32),
+                "hers_set_tensor_first": ([vp, i32], i32),
+                "hers_get_tensor_first": ([vp], i32),
                 "hers_epilogue_variants": ([], i32),
                 "hers_epilogue_variant_name": ([i32], ctypes.c_char_p),
                 "hers_get_epilogue_variant": ([vp], i32),
@@ -551,6 +553,14 @@ def hers_get_tensor_variant(ctx: Context) -> int:
 
 def hers_set_tensor_variant(ctx: Context, v: int):
     ctx.check(lib().hers_set_tensor_variant(ctx.h, v), "hers_set_tensor_variant")
+
+
+def hers_set_tensor_first(ctx: Context, on: bool):
+    ctx.check(lib().hers_set_tensor_first(ctx.h, 1 if on else 0), "hers_set_tensor_first")
+
+
+def hers_get_tensor_first(ctx: Context) -> bool:
+    return bool(lib().hers_get_tensor_first(ctx.h))
 
 
 def hers_epilogue_variants():

@@ -54,6 +54,7 @@ __device__ __forceinline__ void madw_b(int64_t& acc, int32_t a, int32_t b) {
 struct UnitRegs {
     const uint64_t* gallery;
     uint32_t d, np, nb, block, limb, tile;
+    bool last;  // the last chunk to read these gallery rows
 };
 
 template <int NPC>
@@ -70,7 +71,8 @@ __device__ __forceinline__ void load_unit(UnitRegs& r, const uint64_t** probe_sl
         probe_slot[q] = C->probe[q];
         pair_slot[q] = C->pair[q] + U.block;
     }
-    r.nb = U.nb;
+    r.nb = U.nb & ~UNIT_LAST_CHUNK;
+    r.last = (U.nb & UNIT_LAST_CHUNK) != 0;
     r.block = U.block;
     r.limb = U.limb;
     r.tile = U.tile;
@@ -131,7 +133,12 @@ __device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const in
 // g NP .. g NP + NP - 1 against every gallery run and keeps their NP x NB x 3
 // sums of its coefficient in registers.
 
-template <int NP, int NB, int STAGES, int DPS, int MINB, int G>
+// POL selects the L2 policies of the copies: false, probe rows evict-last
+// and gallery rows evict-first; true, probe rows evict-normal and gallery rows
+// evict-normal except on the last chunk to read them (evict-first), so that
+// the chunks of one block that follow the first find its rows in L2 and
+// probe rows of finished (limb, tile) slices do not crowd them out.
+template <int NP, int NB, int STAGES, int DPS, int MINB, int G, bool POL>
 __global__ void __launch_bounds__(G * TILE + 32, MINB)
     k_tensor_batched(const BatchChunk* __restrict__ chunks, const BatchUnit* __restrict__ units,
                      uint32_t nunits, uint32_t* counter, uint32_t* __restrict__ X, int* err) {
@@ -160,7 +167,9 @@ __global__ void __launch_bounds__(G * TILE + 32, MINB)
 
     if (warp == G * TILE / 32) {  // producer warp
         if (lane == 0) {
-            const uint64_t pol_g = policy_evict_first(), pol_p = policy_evict_last();
+            const uint64_t pol_first = policy_evict_first();
+            const uint64_t pol_p = POL ? policy_evict_normal() : policy_evict_last();
+            const uint64_t pol_keep = POL ? policy_evict_normal() : pol_first;
             uint32_t g = 0;  // stages issued by this CTA
             bool failed = false;
             uint32_t u = atomicAdd(counter, 1u);
@@ -196,6 +205,7 @@ __global__ void __launch_bounds__(G * TILE + 32, MINB)
                     }
                     const uint32_t bytes = nd * 2 * TILE * 4;
                     int32_t* dst = smr + (size_t)st * STAGE_ELEMS;
+                    const uint64_t pol_g = cur.last ? pol_first : pol_keep;
                     mbar_expect_tx(&full[st], bytes * (cur.np + cur.nb));
                     const uint64_t off = resident_offset(0, cur.limb, cur.tile * TILE, cur.d, 0, 0) +
                                          (uint64_t)si * RUN;
@@ -307,19 +317,26 @@ struct BatchVariant {
 // name: np<probes per group>_nb<blocks>_s<stages>_d<dims per stage>_m<CTAs/SM>,
 // with a trailing _g<groups> when a CTA has more than one group of consumers
 #define HERS_BV(NP, NB, S, D, M) \
-    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M, k_tensor_batched<NP, NB, S, D, M, 1>, NP, NB, S, D, M, 1}
-#define HERS_BVG(NP, NB, S, D, M, G)                                                                         \
-    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M "_g" #G, k_tensor_batched<NP, NB, S, D, M, G>, NP, NB, S, D, M, \
-     G}
+    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M, k_tensor_batched<NP, NB, S, D, M, 1, false>, NP, NB, S, D, M, 1}
+#define HERS_BVG(NP, NB, S, D, M, G)                                                                             \
+    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M "_g" #G, k_tensor_batched<NP, NB, S, D, M, G, false>, NP, NB, S, D, \
+     M, G}
+// the same shapes with the L2 policies of POL = true ("_l2" names)
+#define HERS_BVP(NP, NB, S, D, M, G)                                                                             \
+    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M "_g" #G "_l2", k_tensor_batched<NP, NB, S, D, M, G, true>, NP, NB, \
+     S, D, M, G}
 static const BatchVariant kBatchVariants[] = {
     HERS_BV(1, 2, 4, 4, 2), HERS_BV(2, 2, 2, 4, 3), HERS_BV(2, 2, 3, 4, 2), HERS_BV(2, 2, 4, 2, 2),
     HERS_BV(4, 1, 2, 4, 2), HERS_BV(4, 2, 2, 4, 2), HERS_BV(4, 2, 3, 2, 2), HERS_BV(2, 1, 3, 4, 3),
     HERS_BV(1, 1, 4, 4, 3), HERS_BV(2, 1, 4, 4, 2), HERS_BV(4, 1, 4, 2, 2), HERS_BV(1, 2, 3, 4, 3),
     HERS_BVG(2, 2, 2, 4, 2, 2), HERS_BVG(2, 2, 3, 2, 2, 2), HERS_BVG(2, 2, 4, 4, 1, 2),
     HERS_BVG(4, 2, 2, 4, 1, 2), HERS_BVG(2, 1, 3, 4, 2, 2), HERS_BVG(4, 1, 2, 4, 2, 2),
+    HERS_BVP(2, 2, 2, 4, 3, 1), HERS_BVP(4, 2, 2, 4, 2, 1), HERS_BVP(2, 2, 3, 4, 2, 1),
+    HERS_BVP(2, 2, 2, 4, 2, 2),
 };
 #undef HERS_BV
 #undef HERS_BVG
+#undef HERS_BVP
 constexpr int NUM_BATCH_VARIANTS = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
 static int batch_smem(const BatchVariant& v) {
@@ -448,7 +465,8 @@ void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, int nb_max
                     for (uint64_t blk = s0; blk < s1; blk += nb_max) {
                         const uint32_t nbu = (uint32_t)std::min<uint64_t>(nb_max, s1 - blk);
                         for (uint32_t c2 = 0; c2 < nch; c2++)
-                            units.push_back({first + c2, (uint32_t)blk, l, tl, nbu});
+                            units.push_back({first + c2, (uint32_t)blk, l, tl,
+                                             nbu | (c2 + 1 == nch ? UNIT_LAST_CHUNK : 0u)});
                     }
         }
     }

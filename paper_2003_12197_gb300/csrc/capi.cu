@@ -437,7 +437,7 @@ int hers_search(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
                     (unsigned long long)workspace_bytes,
                     (unsigned long long)hers_search_workspace_bytes(nblocks));
     DeviceGuard g(ctx->device);
-    const EpilogueStream ep = {ctx->ep, {ctx->ep_ev[0], ctx->ep_ev[1]}};
+    const EpilogueStream ep = {ctx->ep, {ctx->ep_ev[0], ctx->ep_ev[1]}, ctx->tensor_first != 0};
     cudaError_t e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, scores_ct,
                                   (uint64_t*)workspace, ctx->err, pick(ctx, stream), next_trace(ctx),
                                   ctx->tensor_variant, nullptr, &ep, ctx->epi_variant);
@@ -503,7 +503,7 @@ int search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
         }
     }
     cudaStream_t st = pick(ctx, stream);
-    const EpilogueStream ep = {ctx->ep, {ctx->ep_ev[0], ctx->ep_ev[1]}};
+    const EpilogueStream ep = {ctx->ep, {ctx->ep_ev[0], ctx->ep_ev[1]}, ctx->tensor_first != 0};
     // workspace: [search scratch][probe cts d*4N][probe form d*RES_WORDS_PER_DIM][score cts nblocks*4N]
     // (hers_search_host_workspace_bytes sums the same parts)
     uint64_t* ws = (uint64_t*)workspace;
@@ -615,6 +615,17 @@ int hers_set_tensor_variant(hers_ctx* ctx, int v) {
     ctx->tensor_variant = v;
     return HERS_OK;
 }
+
+int hers_set_tensor_first(hers_ctx* ctx, int on) {
+    if (!ctx) return HERS_E_INVAL;
+    DeviceGuard g(ctx->device);
+    // searches already enqueued keep their order; wait for them before the roles change
+    cudaStreamSynchronize(ctx->ep);
+    ctx->tensor_first = on ? 1 : 0;
+    return HERS_OK;
+}
+
+int hers_get_tensor_first(const hers_ctx* ctx) { return ctx ? ctx->tensor_first : -1; }
 
 int hers_epilogue_variants(void) { return EPI_VARIANTS; }
 

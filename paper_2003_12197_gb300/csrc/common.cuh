@@ -623,22 +623,52 @@ __device__ __forceinline__ void ntt32_inv_smem(uint32_t* sm, const uint2* __rest
     __syncthreads();
 }
 
+// Transposes the 16 x 16 matrix held by the 16 lanes of each half-warp (lane
+// i of the half-warp holds row i in v) so that lane i holds column i: four
+// rounds of __shfl_xor_sync (distances 8, 4, 2, 1), each swapping the
+// off-diagonal halves of the blocks of that size.  Every lane of the warp
+// must call it.
+__device__ __forceinline__ void transpose16_shfl(uint32_t v[16], int i) {
+#pragma unroll
+    for (int m = 8; m >= 1; m >>= 1) {
+        const bool hi = (i & m) != 0;
+#pragma unroll
+        for (int a = 0; a < 16; a++) {
+            if (a & m) continue;
+            const uint32_t send = hi ? v[a] : v[a | m];
+            const uint32_t recv = __shfl_xor_sync(0xffffffffu, send, m);
+            if (hi) v[a] = recv;
+            else v[a | m] = recv;
+        }
+    }
+}
+
 // The inverse transform with its first and last phases on registers: v holds
 // the bit-reversed inputs at coefficients 16 t + a on entry and the outputs
 // (natural order, times N^-1, fully reduced) at coefficients t + 256 a on
 // exit, so the caller loads and stores them directly; sm (N words) carries
 // only the middle phase.  Ends with no barrier after its last shared-memory
 // read; a caller that reuses sm synchronises first.
+// SHFL: the first exchange (a transpose within each half-warp: coefficients
+// 16 t + a to 256 (t / 16) + (t % 16) + 16 a) goes through warp shuffles
+// instead of shared memory.
+template <bool SHFL = false>
 __device__ __forceinline__ void ntt32_inv_regs(uint32_t v[16], uint32_t* sm, const uint2* __restrict__ w,
                                                uint32_t r, uint32_t ninv, uint32_t ninv_s, int t) {
     gs_phase32<1, false>(v, 16 * t, w, r, ninv, ninv_s);
+    if (SHFL) {
+        transpose16_shfl(v, t & 15);
+    } else {
 #pragma unroll
-    for (int a = 0; a < 16; a++) sm[swz32(16 * t + a)] = v[a];
-    __syncwarp();
+        for (int a = 0; a < 16; a++) sm[swz32(16 * t + a)] = v[a];
+        __syncwarp();
+    }
     {
         const int base = 256 * (t >> 4) + (t & 15);
+        if (!SHFL) {
 #pragma unroll
-        for (int a = 0; a < 16; a++) v[a] = sm[swz32(base + 16 * a)];
+            for (int a = 0; a < 16; a++) v[a] = sm[swz32(base + 16 * a)];
+        }
         gs_phase32<16, false>(v, base, w, r, ninv, ninv_s);
 #pragma unroll
         for (int a = 0; a < 16; a++) sm[swz32(base + 16 * a)] = v[a];
@@ -742,6 +772,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
 __device__ __forceinline__ uint64_t policy_evict_last() {

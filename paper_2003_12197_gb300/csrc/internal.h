@@ -20,6 +20,7 @@ struct hers_ctx {
     uint32_t tcap = 0, tn = 0;
     int tensor_variant = 1;  // tensor-kernel shape used by searches on this context
     int epi_variant = 0;     // epilogue form used by every search on this context (EPI_* flags)
+    int tensor_first = 0;    // 1: the tensor kernel, not the epilogue, takes the high-priority stream
     int pm = 0;              // plaintext modulus: 0 the default t, 1 the paper's t
     // the epilogue of a search runs on ep (the device's highest stream priority),
     // after ep_ev[0] (tensor done) and before ep_ev[1] (joined back to the caller)
@@ -128,15 +129,21 @@ constexpr int DEFAULT_TENSOR_VARIANT = 1;
 // ep (optional): the epilogue runs on ep.stream (a high-priority stream), so
 // that its CTAs are dispatched ahead of pending CTAs of another search's
 // tensor kernel; ep.ev[0] and ep.ev[1] fork from and join back to st.
+// With tensor_first, the roles swap: the tensor kernel runs on ep.stream and
+// the epilogue on st, so a search's tensor kernel is dispatched ahead of the
+// previous search's epilogue and the epilogue fills what the SMs have left.
 struct EpilogueStream {
     cudaStream_t stream;
     cudaEvent_t ev[2];
+    bool tensor_first = false;
 };
 // Epilogue forms (every form computes the same bytes): EPI_INTT_SCALE_CLUSTER
 // fuses the inverse NTTs with scale-and-round (clusters of NUM_S CTAs);
-// EPI_KS_FUSED does the RNS key switch in one kernel per (pair, limb).
-// Variant v is the OR of the flags, 0 <= v < EPI_VARIANTS.
-constexpr int EPI_INTT_SCALE_CLUSTER = 1, EPI_KS_FUSED = 2, EPI_VARIANTS = 4;
+// EPI_KS_FUSED does the RNS key switch in one kernel per (pair, limb);
+// EPI_INTT_SHFL makes the inverse NTTs' first exchange a warp-shuffle
+// transpose instead of a pass through shared memory.  Variant v is the OR of
+// the flags, 0 <= v < EPI_VARIANTS.
+constexpr int EPI_INTT_SCALE_CLUSTER = 1, EPI_KS_FUSED = 2, EPI_INTT_SHFL = 4, EPI_VARIANTS = 8;
 const char* epilogue_variant_name(int v);
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,
@@ -179,8 +186,9 @@ struct BatchChunk {  // up to BATCH_NPMAX probes sharing one gallery segment
 struct BatchUnit {  // (chunk, first absolute block, limb, tile, blocks in the unit)
     uint32_t chunk, block;
     uint16_t limb, tile;
-    uint32_t nb;
+    uint32_t nb;  // blocks in the unit; bit 31 set on the last chunk to read these blocks' rows
 };
+constexpr uint32_t UNIT_LAST_CHUNK = 1u << 31;
 void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, int nb_max,
                  std::vector<BatchChunk>& chunks, std::vector<BatchUnit>& units, uint32_t* ngroups);
 constexpr int DEFAULT_BATCH_VARIANT = 1;

@@ -190,6 +190,9 @@ static const TensorVariant kTensorVariants[] = {
     HERS_TV(2, 4, 4, 2),  HERS_TV(2, 3, 4, 3),  HERS_TV(2, 2, 8, 2),  HERS_TV(1, 4, 4, 3),
     HERS_TV(4, 2, 4, 2),  HERS_TV(2, 4, 2, 3),  HERS_TV(2, 2, 4, 4),  HERS_TV(1, 2, 8, 3),
     HERS_TV(4, 2, 2, 3),  HERS_TVG(2, 3, 4, 3), HERS_TVG(2, 4, 4, 2), HERS_TVG(1, 4, 4, 3),
+    // one CTA per SM with a deep ring: an SM keeps registers and shared memory
+    // for CTAs of another search's epilogue running beside it
+    HERS_TV(2, 6, 4, 1),  HERS_TV(2, 8, 4, 1),  HERS_TV(4, 4, 4, 1),
 };
 #undef HERS_TV
 #undef HERS_TVG
@@ -242,6 +245,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 3) k_ntt_batch(const uint64_t* __
 // mod r_(P % NUM_S).  Each thread loads its 16 phase-one coefficients (16 t ..
 // 16 t + 15, four 16-byte loads) and stores its 16 outputs (t + 256 a,
 // coalesced) directly; shared memory carries only the middle phase.
+template <bool SHFL>
 __global__ void __launch_bounds__(NTT_THREADS, 4) k_intt32_batch(const uint64_t* __restrict__ tw,
                                                               uint32_t* __restrict__ data) {
     __shared__ uint32_t sm32[N];
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(NTT_THREADS, 4) k_intt32_batch(const uint64_t*
         v[4 * i + 2] = u.z;
         v[4 * i + 3] = u.w;
     }
-    ntt32_inv_regs(v, sm32, tw32_inv(tw, mi), c_smod[mi], c_sninv[mi], c_sninv_s[mi], t);
+    ntt32_inv_regs<SHFL>(v, sm32, tw32_inv(tw, mi), c_smod[mi], c_sninv[mi], c_sninv_s[mi], t);
 #pragma unroll
     for (int a = 0; a < 16; a++) g[t + 256 * a] = v[a];
 }
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(256) k_scale_round(const uint32_t* __restrict_
 // shared memory alive until its peers' reads are done.
 constexpr int ISC_SLICE = N / NUM_S;  // coefficients rounded per CTA
 static_assert(ISC_SLICE == 2 * NTT_THREADS, "two coefficients per thread");
-template <int PM>
+template <int PM, bool SHFL>
 __global__ void __cluster_dims__(NUM_S, 1, 1) __launch_bounds__(NTT_THREADS, 4)
     k_intt_scale_cluster(const uint64_t* __restrict__ tw, const uint32_t* __restrict__ X,
                          uint64_t* __restrict__ C, uint64_t* __restrict__ KS) {
@@ -372,7 +376,7 @@ __global__ void __cluster_dims__(NUM_S, 1, 1) __launch_bounds__(NTT_THREADS, 4)
         v[4 * i + 2] = u.z;
         v[4 * i + 3] = u.w;
     }
-    ntt32_inv_regs(v, sm32, tw32_inv(tw, l), c_smod[l], c_sninv[l], c_sninv_s[l], t);
+    ntt32_inv_regs<SHFL>(v, sm32, tw32_inv(tw, l), c_smod[l], c_sninv[l], c_sninv_s[l], t);
     __syncthreads();  // the transform's last shared-memory reads are done
 #pragma unroll
     for (int a = 0; a < 16; a++) sm32[t + 256 * a] = v[a];  // natural order, fully reduced
@@ -531,8 +535,14 @@ __global__ void __launch_bounds__(256) k_ks_mul_w(const uint64_t* __restrict__ W
 // or with the base-w gadget O [npairs][2][2][N] and the digits), canonical
 // score ciphertexts into out [npairs][2][2][N].
 const char* epilogue_variant_name(int v) {
-    static const char* names[EPI_VARIANTS] = {"split", "intt_scale_cluster", "ks_fused",
-                                              "intt_scale_cluster+ks_fused"};
+    static const char* names[EPI_VARIANTS] = {"split",
+                                              "intt_scale_cluster",
+                                              "ks_fused",
+                                              "intt_scale_cluster+ks_fused",
+                                              "split+shfl",
+                                              "intt_scale_cluster+shfl",
+                                              "ks_fused+shfl",
+                                              "intt_scale_cluster+ks_fused+shfl"};
     return (v >= 0 && v < EPI_VARIANTS) ? names[v] : nullptr;
 }
 
@@ -549,12 +559,14 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
         for (uint64_t b0 = 0; b0 < npairs; b0 += max_z) {
             const uint64_t nb = npairs - b0 < max_z ? npairs - b0 : max_z;
             const dim3 grid(NUM_S, 3, (unsigned)nb);
-            if (k.pm == 0)
-                k_intt_scale_cluster<0><<<grid, NTT_THREADS, 0, st>>>(tw, X32 + b0 * 3 * NUM_S * N, C + b0 * 6 * N,
-                                                                     KS + b0 * 4 * N);
-            else
-                k_intt_scale_cluster<1><<<grid, NTT_THREADS, 0, st>>>(tw, X32 + b0 * 3 * NUM_S * N, C + b0 * 6 * N,
-                                                                     KS + b0 * 4 * N);
+            const uint32_t* x = X32 + b0 * 3 * NUM_S * N;
+            uint64_t* c = C + b0 * 6 * N;
+            uint64_t* ks = KS + b0 * 4 * N;
+            const bool sh = (epi & EPI_INTT_SHFL) != 0;
+            if (k.pm == 0 && !sh) k_intt_scale_cluster<0, false><<<grid, NTT_THREADS, 0, st>>>(tw, x, c, ks);
+            else if (k.pm == 0) k_intt_scale_cluster<0, true><<<grid, NTT_THREADS, 0, st>>>(tw, x, c, ks);
+            else if (!sh) k_intt_scale_cluster<1, false><<<grid, NTT_THREADS, 0, st>>>(tw, x, c, ks);
+            else k_intt_scale_cluster<1, true><<<grid, NTT_THREADS, 0, st>>>(tw, x, c, ks);
             nl++;
         }
         if (ev) {
@@ -565,7 +577,8 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
         const uint64_t npolys = npairs * 3 * NUM_S;  // chunks are multiples of NUM_S
         for (uint64_t off = 0; off < npolys; off += chunk) {
             const uint64_t n = npolys - off < chunk ? npolys - off : chunk;
-            k_intt32_batch<<<(unsigned)n, NTT_THREADS, 0, st>>>(tw, X32 + off * N);
+            if (epi & EPI_INTT_SHFL) k_intt32_batch<true><<<(unsigned)n, NTT_THREADS, 0, st>>>(tw, X32 + off * N);
+            else k_intt32_batch<false><<<(unsigned)n, NTT_THREADS, 0, st>>>(tw, X32 + off * N);
             nl++;
         }
         if (ev) cudaEventRecord(ev[0], st);
@@ -652,6 +665,19 @@ cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* 
     uint64_t* C = X + nblocks * 15 * N;
     uint64_t* KS = C + nblocks * 6 * N;
     if (ev) cudaEventRecord(ev[0], st);
+    if (ep && ep->tensor_first) {
+        // the tensor kernel on the high-priority stream, the epilogue on st
+        cudaError_t e = cudaEventRecord(ep->ev[0], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ep->stream, ep->ev[0], 0);
+        if (e == cudaSuccess) e = launch_tensor(variant, gallery, nblocks, d, probe, (uint32_t*)X, err, ep->stream);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], ep->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ep->ev[1], ep->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ep->ev[1], 0);
+        if (e != cudaSuccess) return e;
+        e = launch_epilogue(tw, k, nblocks, X, C, KS, scores_ct, st, ev ? ev + 2 : nullptr, ksw, epi);
+        if (ev) cudaEventRecord(ev[4], st);
+        return e;
+    }
     cudaError_t e = launch_tensor(variant, gallery, nblocks, d, probe, (uint32_t*)X, err, st);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);

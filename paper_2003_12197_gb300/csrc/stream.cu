@@ -10,8 +10,10 @@
 //   3. one persistent batched tensor launch with every probe;
 //   4. the epilogue;
 //   5. the score ciphertexts are copied into their [probe][block] places.
-// Two chunk slots alternate: chunk c+1's copy and extension (a side stream)
-// overlap chunk c's search (the caller's stream).
+// Two chunk slots alternate.  Three streams: the copies (a stream of their
+// own, so the copy engine runs ahead as soon as a staging buffer is free),
+// the extensions (the context's stream) and the searches (the caller's
+// stream).  Chunk c+1's copy and extension overlap chunk c's search.
 #include <algorithm>
 #include <vector>
 
@@ -123,17 +125,25 @@ int hers_search_stream(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gal
         }
     }
 
-    cudaEvent_t ev_ext[2], ev_free[2], ev_join;
+    // ev_copied[s]: slot s's staging holds its chunk; ev_ext[s]: its resident
+    // buffer and tables are ready (and its staging may be refilled);
+    // ev_free[s]: its resident buffer may be refilled
+    cudaEvent_t ev_copied[2], ev_ext[2], ev_free[2], ev_join, ev_join2;
+    cudaStream_t scp = nullptr;  // the copies' stream (host galleries)
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < 2 && e == cudaSuccess; s++) {
         e = cudaEventCreateWithFlags(&ev_ext[s], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_free[s], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_copied[s], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join2, cudaEventDisableTiming);
+    if (e == cudaSuccess && gallery_on_host) e = cudaStreamCreateWithFlags(&scp, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_search_stream: events");
-    // the side stream starts after work already queued on the caller's stream
+    // the side streams start after work already queued on the caller's stream
     cudaEventRecord(ev_join, sm);
     cudaStreamWaitEvent(sc, ev_join, 0);
+    if (scp) cudaStreamWaitEvent(scp, ev_join, 0);
 
     int table_kind[2] = {-1, -1};
     for (uint64_t c = 0; c < nchunks && e == cudaSuccess; c++) {
@@ -142,14 +152,18 @@ int hers_search_stream(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gal
         const uint32_t nb = (uint32_t)std::min<uint64_t>(chunk_blocks, nblocks - b0);
         const int kind = (c == nchunks - 1 && nb != chunk_blocks) ? 1 : 0;
         uint64_t* base = slot[s];
-        // side stream: wait until the slot's previous chunk has been searched
-        if (c >= 2) cudaStreamWaitEvent(sc, ev_free[s], 0);
         const uint64_t* src = gallery_ct + b0 * d * 4 * N;
         const uint64_t* cts = src;
         if (gallery_on_host) {
-            e = cudaMemcpyAsync(base + L.staging, src, (uint64_t)nb * d * 4 * N * 8, cudaMemcpyHostToDevice, sc);
+            // copy stream: wait until the slot's staging has been extended from
+            if (c >= 2) cudaStreamWaitEvent(scp, ev_ext[s], 0);
+            e = cudaMemcpyAsync(base + L.staging, src, (uint64_t)nb * d * 4 * N * 8, cudaMemcpyHostToDevice, scp);
+            if (e == cudaSuccess) e = cudaEventRecord(ev_copied[s], scp);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, ev_copied[s], 0);
             cts = base + L.staging;
         }
+        // side stream: wait until the slot's previous chunk has been searched
+        if (c >= 2) cudaStreamWaitEvent(sc, ev_free[s], 0);
         if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, cts, (uint64_t)nb * d, 0, d, base + L.resident, sc);
         if (e == cudaSuccess && table_kind[s] != kind) {
             const Tables& t = T[s][kind];
@@ -177,14 +191,21 @@ int hers_search_stream(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gal
                                 base + L.OUT + (uint64_t)p * nb * 4 * N, (uint64_t)nb * 4 * N * 8,
                                 cudaMemcpyDeviceToDevice, sm);
     }
-    // join the side stream into the caller's
+    // join the side streams into the caller's
     cudaEventRecord(ev_join, sc);
     cudaStreamWaitEvent(sm, ev_join, 0);
+    if (scp) {
+        cudaEventRecord(ev_join2, scp);
+        cudaStreamWaitEvent(sm, ev_join2, 0);
+        cudaStreamDestroy(scp);  // destruction waits for its work to finish on the device
+    }
     for (int s = 0; s < 2; s++) {
         cudaEventDestroy(ev_ext[s]);
         cudaEventDestroy(ev_free[s]);
+        cudaEventDestroy(ev_copied[s]);
     }
     cudaEventDestroy(ev_join);
+    cudaEventDestroy(ev_join2);
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_search_stream");
 }
 

@@ -352,7 +352,7 @@ def test_every_epilogue_form_gives_the_same_ciphertexts(ctx, keys, oracle_keys):
     gal, _ = H.hers_encrypt_gallery(ctx, keys, torch.from_numpy(feats).cuda(), GAL_SEED)
     pr = H.hers_probe_prepare(ctx, H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).cuda(), PRB_SEED))
     names = H.hers_epilogue_variants()
-    assert len(names) == 4
+    assert len(names) == 8
     keep = H.hers_get_epilogue_variant(ctx)
     outs = []
     for v in range(len(names)):
@@ -368,3 +368,32 @@ def test_every_epilogue_form_gives_the_same_ciphertexts(ctx, keys, oracle_keys):
     assert 0 <= chosen < len(names) and set(ms) == set(names)
     assert H.hers_get_epilogue_variant(ctx) == chosen
     H.hers_set_epilogue_variant(ctx, keep)
+
+
+def test_tensor_first_ordering_in_flight(ctx, keys, config1):
+    """With the tensor kernel on the high-priority stream and the epilogue on
+    the caller's (hers_set_tensor_first), searches in flight on three streams
+    each equal the sequential search, and work enqueued after a search on its
+    stream sees the finished scores."""
+    res = config1["res"]
+    nb = res["nb"]
+    H.hers_set_tensor_first(ctx, True)
+    try:
+        assert H.hers_get_tensor_first(ctx)
+        streams = [torch.cuda.Stream() for _ in range(3)]
+        outs = [torch.empty_like(res["sc"]) for _ in range(6)]
+        wss = [torch.empty(H.hers_search_workspace_bytes(nb) // 8, dtype=torch.int64, device="cuda")
+               for _ in range(3)]
+        torch.cuda.synchronize()
+        copies = []
+        for k in range(6):
+            st = streams[k % 3]
+            H.hers_search(ctx, keys, res["gal"], nb, 64, res["pr"], out=outs[k], workspace=wss[k % 3], stream=st)
+            with torch.cuda.stream(st):
+                copies.append(outs[k].clone())
+        torch.cuda.synchronize()
+        for k in range(6):
+            assert torch.equal(outs[k], res["sc"]), f"search {k}"
+            assert torch.equal(copies[k], res["sc"]), f"copy after search {k}"
+    finally:
+        H.hers_set_tensor_first(ctx, False)
