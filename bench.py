@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--m", type=int, default=1 << 20, help="gallery entries per GPU")
     ap.add_argument("--d", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-select", action="store_true",
+                    help="plain workload: skip the in-flight choice of epilogue form (for profiling runs)")
     ap.add_argument("--plain-only", action="store_true",
                     help="plain workload: leave out the batched and serving objects of the line")
     ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "scale", "sweep", "topk", "enroll"],
@@ -92,6 +94,7 @@ def parse():
     ap.add_argument("--scale-m", type=int, default=100_000_000, help="scale: gallery entries")
     ap.add_argument("--scale-source", default="auto", choices=["auto", "host", "device"],
                     help="scale: where the canonical gallery lives (auto: host if it fits)")
+    ap.add_argument("--scale-chunk", type=int, default=32, help="scale: gallery blocks per streamed chunk")
     ap.add_argument("--oracle-blocks", type=int, default=4,
                     help="scale: random blocks checked against the oracle (plus the mate blocks "
                          "of the first probes)")
@@ -368,8 +371,10 @@ def run_gpu(args):
     else:
         variant, tune_ms = H.hers_autotune(ctx, keys, gal, nb, d, pr, workspace=ws)
     variant_name = H.hers_tensor_variants()[variant]
-    # and the epilogue form (inverse NTTs, scale-and-round, key switch), timed alone after it
+    # and the epilogue form (inverse NTTs, scale-and-round, key switch), timed alone after it,
+    # and the probe preparation form for this d
     _, epi_ms = H.hers_autotune_epilogue(ctx, keys, gal, nb, d, pr, workspace=ws)
+    ext_cluster, ext_ms = H.hers_autotune_extension(ctx, d)
 
     # correctness of the benchmarked path: exact scores and the planted mate
     H.hers_search(ctx, keys, gal, nb, d, pr, out=sc, workspace=ws)
@@ -424,20 +429,25 @@ def run_gpu(args):
     # the next search's HBM-bound tensor kernel, so the epilogue's memory
     # traffic and the SM resources the tensor shape leaves count, not only the
     # times of the two alone.
+    # (Measured and left out of the choice: the tensor kernel on the
+    # high-priority stream, hers_set_tensor_first, gained 2 us per step and
+    # cost a tenth of the host-buffer rate.)
     tnames, enames = H.hers_tensor_variants(), H.hers_epilogue_variants()
     t_cands = [variant] if args.variant else sorted(
         {variant} | {i for i, n in enumerate(tnames) if n.endswith("_m1")})
     combos = {}
-    for tv in t_cands:
+    for tv in ([] if args.no_select else t_cands):
         H.hers_set_tensor_variant(ctx, tv)
-        for tf in (False, True):
+        for tf in (False,):
             H.hers_set_tensor_first(ctx, tf)
             for ev_ in range(len(enames)):
                 H.hers_set_epilogue_variant(ctx, ev_)
                 for k in range(IN_FLIGHT):
                     step_in_flight(k)
                 combos[(tv, tf, ev_)] = timed(step_in_flight, 10, trace=False) / 10
-    variant, tensor_first, epi = min(combos, key=combos.get)
+    if not combos:
+        combos[(variant, False, 0)] = float("nan")
+    variant, tensor_first, epi = min(combos, key=lambda c: combos[c] if combos[c] == combos[c] else 0.0)
     variant_name, epi_name = tnames[variant], enames[epi]
     H.hers_set_tensor_variant(ctx, variant)
     H.hers_set_tensor_first(ctx, tensor_first)
@@ -612,6 +622,8 @@ def run_gpu(args):
             "autotune": {"chosen": variant_name,
                          "ms_per_variant": {k: round(v, 4) for k, v in tune_ms.items()},
                          "epilogue_chosen": epi_name, "tensor_first": bool(tensor_first),
+                         "probe_preparation": {"cluster_form": ext_cluster,
+                                               "ms": {k: round(v, 4) for k, v in ext_ms.items()}},
                          "epilogue_ms_alone": {k: round(v, 4) for k, v in epi_ms.items()},
                          "step_ms_in_flight": epi_inflight,
                          "note": "tensor shape (timed alone above), epilogue form and stream priority "
@@ -1113,7 +1125,7 @@ def run_scale(args):
     source = args.scale_source
     if source == "auto":
         source = "host" if host_mem_available() > gal_bytes + (24 << 30) else "device"
-    dev_copy, h2d_gbs = None, None
+    dev_copy, h2d_gbs, slice_gbs = None, None, [0.0]
     if source == "host":
         g = torch.empty(gct.shape, dtype=torch.int64, pin_memory=True)
         g.copy_(gct)
@@ -1130,10 +1142,21 @@ def run_scale(args):
             torch.cuda.synchronize()
             best = h0.elapsed_time(h1) if best is None else min(best, h0.elapsed_time(h1))
         h2d_gbs = span * 8 / (best / 1e3) / 1e9
+        # and every 4 GiB slice of the whole buffer once: a pinned buffer this
+        # large may not copy at one rate over its whole extent
+        slice_gbs = []
+        flat_all = g.view(-1)
+        for o in range(0, flat_all.numel(), span):
+            n_ = min(span, flat_all.numel() - o)
+            h0.record()
+            buf[:n_].copy_(flat_all[o:o + n_], non_blocking=True)
+            h1.record()
+            torch.cuda.synchronize()
+            slice_gbs.append(n_ * 8 / (h0.elapsed_time(h1) / 1e3) / 1e9)
         del buf
         # keep the device copy (when it and the search's buffers fit) to time
         # the same search without host copies: the compute-only pass
-        need = nprobes * nb * 4 * N * 8 + H.hers_search_stream_workspace_bytes(d, nprobes, 32) + (8 << 30)
+        need = nprobes * nb * 4 * N * 8 + H.hers_search_stream_workspace_bytes(d, nprobes, args.scale_chunk) + (8 << 30)
         if torch.cuda.mem_get_info(dev)[0] > need:
             dev_copy = gct
         else:
@@ -1145,7 +1168,7 @@ def run_scale(args):
                                                               PRB_SEED + 500 + i))
               for i, q in enumerate(qs)]
     sc = torch.empty((nprobes, nb, 2, 2, N), dtype=torch.int64, device=dev)
-    chunk = 32
+    chunk = args.scale_chunk
     bv_name = args.batch_variant or "np4_nb2_s2_d4_m2"
     bv = H.hers_batch_variants().index(bv_name)
     ws = torch.empty(H.hers_search_stream_workspace_bytes(d, nprobes, chunk) // 8,
@@ -1171,7 +1194,9 @@ def run_scale(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks.mark_start()
     e0.record(stream)
+    th0 = time.perf_counter()
     H.hers_search_stream(ctx, keys, g, nb, d, probes, chunk, bv, out=sc, workspace=ws)
+    enqueue_s = time.perf_counter() - th0
     e1.record(stream)
     torch.cuda.synchronize()
     clocks.mark_stop()
@@ -1220,7 +1245,10 @@ def run_scale(args):
            "search_s_all_probes": ms / 1e3, "search_s_per_probe": ms / 1e3 / nprobes,
            "streaming": None if source != "host" else {
                "h2d_gbs_measured": h2d_gbs,
+               "h2d_gbs_per_4gib_slice": {"min": min(slice_gbs), "max": max(slice_gbs),
+                                          "mean": sum(slice_gbs) / len(slice_gbs), "slices": len(slice_gbs)},
                "h2d_gbs_during_search": gal_bytes / (ms / 1e3) / 1e9,
+               "host_call_s": enqueue_s,
                "device_source_s": None if dev_ms is None else dev_ms / 1e3,
                "host_source_s": ms / 1e3,
                "copies_hidden": None if dev_ms is None else dev_ms / ms,

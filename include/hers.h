@@ -588,6 +588,21 @@ int hers_autotune(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
  */
 int hers_set_tensor_first(hers_ctx* ctx, int on);
 int hers_get_tensor_first(const hers_ctx* ctx);
+/*
+ * Probe preparation form (no counterpart in the paper).  hers_probe_prepare
+ * and the host-buffer searches extend a probe's 2 d polynomials to the
+ * resident form either with one CTA per polynomial or with a cluster of eight
+ * CTAs per polynomial (one per search prime, lifts shared through
+ * distributed shared memory); both give the same bytes.  The context takes
+ * the cluster form for calls of at most a threshold of polynomials (64 by
+ * default: probes of d <= 32).  hers_autotune_extension times both forms for
+ * a probe of dimension d (1 warm-up, 5 timed rounds of 8 preparations each,
+ * minimum kept; zero ciphertexts, a temporary device buffer of d (4 N + 16
+ * N) words), moves the threshold to this size's winner, and writes
+ * *cluster = 1 if the cluster form won and ms[0], ms[1] = ms per preparation
+ * (one CTA per polynomial, cluster).  Synchronous.
+ */
+int hers_autotune_extension(hers_ctx* ctx, uint32_t d, void* stream, int* cluster, double* ms);
 int hers_epilogue_variants(void);
 const char* hers_epilogue_variant_name(int v);
 int hers_get_epilogue_variant(const hers_ctx* ctx);

@@ -135,6 +135,7 @@ def lib():
                 "hers_server_timing": ([vp, vp, vp, vp], i32),
                 "hers_set_tensor_first": ([vp, i32], i32),
                 "hers_get_tensor_first": ([vp], i32),
+                "hers_autotune_extension": ([vp, u32, vp, vp, vp], i32),
                 "hers_epilogue_variants": ([], i32),
                 "hers_epilogue_variant_name": ([i32], ctypes.c_char_p),
                 "hers_get_epilogue_variant": ([vp], i32),
@@ -561,6 +562,15 @@ def hers_set_tensor_first(ctx: Context, on: bool):
 
 def hers_get_tensor_first(ctx: Context) -> bool:
     return bool(lib().hers_get_tensor_first(ctx.h))
+
+
+def hers_autotune_extension(ctx: Context, d: int, stream=None):
+    """(cluster form chosen, {"per_polynomial": ms, "cluster": ms}) for preparing a probe of dimension d."""
+    cl = ctypes.c_int()
+    ms = (ctypes.c_double * 2)()
+    ctx.check(lib().hers_autotune_extension(ctx.h, d, _stream(stream), ctypes.byref(cl), ms),
+              "hers_autotune_extension")
+    return bool(cl.value), {"per_polynomial": ms[0], "cluster": ms[1]}
 
 
 def hers_epilogue_variants():

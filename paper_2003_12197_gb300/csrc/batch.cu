@@ -48,6 +48,24 @@ __device__ __forceinline__ void madw_b(int64_t& acc, int32_t a, int32_t b) {
     asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
 }
 
+// The same signed 64-bit multiply-accumulate as a carry chain: the low words
+// of the product and the sum with carry out, then the signed high word of the
+// product plus the carry, so no separate 64-bit add follows the multiply.
+__device__ __forceinline__ void madc_b(int64_t& acc, int32_t a, int32_t b) {
+    uint32_t lo = (uint32_t)acc, hi = (uint32_t)((uint64_t)acc >> 32);
+    asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\t"
+        "madc.hi.s32 %1, %2, %3, %1;"
+        : "+r"(lo), "+r"(hi)
+        : "r"(a), "r"(b));
+    acc = (int64_t)(((uint64_t)hi << 32) | lo);
+}
+
+template <bool CC>
+__device__ __forceinline__ void mac_b(int64_t& acc, int32_t a, int32_t b) {
+    if (CC) madc_b(acc, a, b);
+    else madw_b(acc, a, b);
+}
+
 // A unit's table entries.  The scalars stay in the producer's registers; the
 // probe pointers and output pairs (NPC = G NP of each) go to a shared-memory
 // slot, so the producer's register count does not grow with the chunk size.
@@ -88,7 +106,7 @@ __device__ __forceinline__ void load_unit(UnitRegs& r, const uint64_t** probe_sl
 // no predicates.
 // pb: this group's first probe run; gb: the first gallery run (both already
 // offset to the thread's coefficient).
-template <int NP, int NB, int DPS, bool FULL>
+template <int NP, int NB, int DPS, bool FULL, bool CC>
 __device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const int2* pb, const int2* gb,
                                                uint32_t nd, uint32_t np, uint32_t nbu) {
     constexpr int RUN2 = DPS * TILE;  // (poly 0, poly 1) pairs of one run
@@ -111,9 +129,9 @@ __device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const in
 #pragma unroll
                     for (int q = 0; q < NP; q++) {
                         if (FULL || (uint32_t)q < np) {
-                            madw_b(s[q][j][0], a0[q], g0);
-                            madw_b(s[q][j][1], as[q], gs);
-                            madw_b(s[q][j][2], a1[q], g1);
+                            mac_b<CC>(s[q][j][0], a0[q], g0);
+                            mac_b<CC>(s[q][j][1], as[q], gs);
+                            mac_b<CC>(s[q][j][2], a1[q], g1);
                         }
                     }
                 }
@@ -138,7 +156,12 @@ __device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const in
 // evict-normal except on the last chunk to read them (evict-first), so that
 // the chunks of one block that follow the first find its rows in L2 and
 // probe rows of finished (limb, tile) slices do not crowd them out.
-template <int NP, int NB, int STAGES, int DPS, int MINB, int G, bool POL>
+// PF > 0: the producer also prefetches into L2 the gallery rows of the stage
+// PF stages ahead (in this unit, or the first stages of the next one), so a
+// stage's copy into shared memory finds them in L2 and the ring only has to
+// cover L2 latency.
+// CC: the multiply-accumulates as carry chains (madc_b) instead of mad.wide.
+template <int NP, int NB, int STAGES, int DPS, int MINB, int G, bool POL, int PF = 0, bool CC = false>
 __global__ void __launch_bounds__(G * TILE + 32, MINB)
     k_tensor_batched(const BatchChunk* __restrict__ chunks, const BatchUnit* __restrict__ units,
                      uint32_t nunits, uint32_t* counter, uint32_t* __restrict__ X, int* err) {
@@ -222,6 +245,23 @@ __global__ void __launch_bounds__(G * TILE + 32, MINB)
                     // the next unit's tables, once this unit's first stage is on its way
                     if (si == 0 && un < nunits)
                         load_unit<NPC>(nxt, unit_probe[cs ^ 1], unit_pair[cs ^ 1], chunks, units, un);
+                    if (PF > 0) {
+                        // gallery rows PF stages ahead into L2
+                        const uint32_t ahead = si + PF;
+                        const UnitRegs* pu = ahead < nst ? &cur : &nxt;
+                        const uint32_t pst = ahead < nst ? ahead : ahead - nst;
+                        if ((ahead < nst || un < nunits) && pst * DPS < pu->d) {
+                            const uint32_t pnd = min((uint32_t)DPS, pu->d - pst * DPS);
+#pragma unroll
+                            for (int j = 0; j < NB; j++)
+                                if ((uint32_t)j < pu->nb)
+                                    bulk_prefetch_l2((const int32_t*)pu->gallery +
+                                                         resident_offset(pu->block + j, pu->limb, pu->tile * TILE,
+                                                                         pu->d, 0, 0) +
+                                                         (uint64_t)pst * RUN,
+                                                     pnd * 2 * TILE * 4);
+                        }
+                    }
                 }
                 if (stop) break;
                 u = un;
@@ -270,9 +310,9 @@ __global__ void __launch_bounds__(G * TILE + 32, MINB)
         const int2* pb = sbase + grp * NP * (RUN / 2);
         const int2* gb = sbase + NPC * (RUN / 2);
         if (nd == DPS && np == NP && nbu == NB)
-            stage_products<NP, NB, DPS, true>(s, pb, gb, nd, np, nbu);
+            stage_products<NP, NB, DPS, true, CC>(s, pb, gb, nd, np, nbu);
         else if (np > 0)
-            stage_products<NP, NB, DPS, false>(s, pb, gb, nd, np, nbu);
+            stage_products<NP, NB, DPS, false, CC>(s, pb, gb, nd, np, nbu);
         mbar_arrive(&empty[st]);
         if (flags & F_FOLD) {
             const int32_t r32 = (int32_t)c_sr32[l];
@@ -325,6 +365,14 @@ struct BatchVariant {
 #define HERS_BVP(NP, NB, S, D, M, G)                                                                             \
     {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M "_g" #G "_l2", k_tensor_batched<NP, NB, S, D, M, G, true>, NP, NB, \
      S, D, M, G}
+// the L2-policy shapes with gallery rows prefetched into L2 PF stages ahead ("_pf<PF>")
+#define HERS_BVF(NP, NB, S, D, M, G, PF)                                                                 \
+    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M "_g" #G "_l2_pf" #PF,                                     \
+     k_tensor_batched<NP, NB, S, D, M, G, true, PF>, NP, NB, S, D, M, G}
+// the L2-policy shapes with carry-chain multiply-accumulates ("_cc")
+#define HERS_BVC(NP, NB, S, D, M, G)                                                                     \
+    {"np" #NP "_nb" #NB "_s" #S "_d" #D "_m" #M "_g" #G "_l2_cc",                                         \
+     k_tensor_batched<NP, NB, S, D, M, G, true, 0, true>, NP, NB, S, D, M, G}
 static const BatchVariant kBatchVariants[] = {
     HERS_BV(1, 2, 4, 4, 2), HERS_BV(2, 2, 2, 4, 3), HERS_BV(2, 2, 3, 4, 2), HERS_BV(2, 2, 4, 2, 2),
     HERS_BV(4, 1, 2, 4, 2), HERS_BV(4, 2, 2, 4, 2), HERS_BV(4, 2, 3, 2, 2), HERS_BV(2, 1, 3, 4, 3),
@@ -333,10 +381,16 @@ static const BatchVariant kBatchVariants[] = {
     HERS_BVG(4, 2, 2, 4, 1, 2), HERS_BVG(2, 1, 3, 4, 2, 2), HERS_BVG(4, 1, 2, 4, 2, 2),
     HERS_BVP(2, 2, 2, 4, 3, 1), HERS_BVP(4, 2, 2, 4, 2, 1), HERS_BVP(2, 2, 3, 4, 2, 1),
     HERS_BVP(2, 2, 2, 4, 2, 2),
+    HERS_BVF(2, 2, 2, 4, 3, 1, 4), HERS_BVF(2, 2, 2, 4, 3, 1, 8), HERS_BVF(4, 2, 2, 4, 2, 1, 4),
+    HERS_BVF(2, 2, 2, 2, 3, 1, 8),
+    HERS_BVC(2, 2, 2, 4, 3, 1), HERS_BVC(4, 2, 2, 4, 2, 1), HERS_BVC(2, 2, 3, 4, 2, 1),
+    HERS_BVC(2, 2, 2, 4, 2, 2),
 };
 #undef HERS_BV
 #undef HERS_BVG
 #undef HERS_BVP
+#undef HERS_BVF
+#undef HERS_BVC
 constexpr int NUM_BATCH_VARIANTS = sizeof(kBatchVariants) / sizeof(kBatchVariants[0]);
 
 static int batch_smem(const BatchVariant& v) {

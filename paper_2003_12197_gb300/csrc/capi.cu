@@ -422,7 +422,7 @@ int hers_probe_prepare(hers_ctx* ctx, const uint64_t* probe_ct, uint32_t d, uint
     if (!ctx || !probe_ct || !probe) return fail(ctx, HERS_E_INVAL, "hers_probe_prepare: null argument");
     if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_probe_prepare: d = %u", d);
     DeviceGuard g(ctx->device);
-    cudaError_t e = launch_extend_ntt(ctx->tw, probe_ct, d, 0, d, probe, pick(ctx, stream));
+    cudaError_t e = launch_extend_ntt(ctx->tw, probe_ct, d, 0, d, probe, pick(ctx, stream), ctx->ext_cluster_max);
     return e == cudaSuccess ? HERS_OK : cuda_fail(ctx, e, "hers_probe_prepare");
 }
 
@@ -512,7 +512,7 @@ int search_host(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery, u
     uint64_t* out_dev = probe + (uint64_t)d * RES_WORDS_PER_DIM;
     cudaError_t e = cudaMemcpyAsync(probe_ct, probe_ct_host, (uint64_t)d * 4 * N * 8,
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, probe_ct, d, 0, d, probe, st);
+    if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, probe_ct, d, 0, d, probe, st, ctx->ext_cluster_max);
     if (e == cudaSuccess)
         e = launch_search(ctx->tw, keys->k, gallery, nblocks, d, probe, out_dev, ws, ctx->err, st,
                           next_trace(ctx), ctx->tensor_variant, nullptr, &ep, ctx->epi_variant);
@@ -626,6 +626,53 @@ int hers_set_tensor_first(hers_ctx* ctx, int on) {
 }
 
 int hers_get_tensor_first(const hers_ctx* ctx) { return ctx ? ctx->tensor_first : -1; }
+
+int hers_autotune_extension(hers_ctx* ctx, uint32_t d, void* stream, int* cluster, double* ms) {
+    if (!ctx) return HERS_E_INVAL;
+    if (d == 0 || d > HERS_MAX_D) return fail(ctx, HERS_E_INVAL, "hers_autotune_extension: d = %u", d);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = pick(ctx, stream);
+    // d canonical ciphertexts (zero residues are canonical; the work does not
+    // depend on the values) and a prepared-probe buffer
+    void* buf = nullptr;
+    const uint64_t ct_bytes = (uint64_t)d * 4 * N * 8, pr_bytes = (uint64_t)d * RES_WORDS_PER_DIM * 8;
+    cudaError_t e = cudaMallocAsync(&buf, ct_bytes + pr_bytes, st);
+    if (e != cudaSuccess) return fail(ctx, HERS_E_NOMEM, "hers_autotune_extension: %s", cudaGetErrorString(e));
+    uint64_t* cts = (uint64_t*)buf;
+    uint64_t* pr = cts + (uint64_t)d * 4 * N;
+    e = cudaMemsetAsync(cts, 0, ct_bytes, st);
+    cudaEvent_t e0, e1;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best[2] = {0, 0};
+    // form 0: one CTA per polynomial; form 1: clusters (2 d polynomials <= the threshold)
+    for (int form = 0; form < 2 && e == cudaSuccess; form++) {
+        const uint64_t thr = form ? 2ull * d : 0;
+        for (int rep = 0; rep < 6 && e == cudaSuccess; rep++) {
+            e = cudaEventRecord(e0, st);
+            for (int k = 0; k < 8 && e == cudaSuccess; k++) e = launch_extend_ntt(ctx->tw, cts, d, 0, d, pr, st, thr);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (rep == 1 || (rep > 1 && t / 8 < best[form])) best[form] = t / 8;  // rep 0 warms up
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(buf, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hers_autotune_extension");
+    const bool use_cluster = best[1] < best[0];
+    // the threshold: this size (2 d polynomials) and smaller take the cluster form when it won
+    ctx->ext_cluster_max = use_cluster ? 2ull * d : (2ull * d > 2 ? 2ull * d - 2 : 0);
+    if (ctx->ext_cluster_max > EXT_CLUSTER_MAX_POLYS && !use_cluster) ctx->ext_cluster_max = EXT_CLUSTER_MAX_POLYS;
+    if (cluster) *cluster = use_cluster ? 1 : 0;
+    if (ms) {
+        ms[0] = best[0];
+        ms[1] = best[1];
+    }
+    return HERS_OK;
+}
 
 int hers_epilogue_variants(void) { return EPI_VARIANTS; }
 

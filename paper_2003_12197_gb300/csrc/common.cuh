@@ -795,6 +795,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// Prefetch of `bytes` (multiple of 16, 16-byte aligned) from global memory
+// into L2, with no destination in shared memory and no completion to wait for.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // ---------------------------------------------------------------- base extension Q -> r_i
 // x given by its residues (x1 mod q1, x2 mod q2), read as the centred integer
 // in (-q/2, q/2] (App. A's symmetric representative), and reduced mod each

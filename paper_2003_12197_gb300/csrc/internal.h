@@ -21,6 +21,7 @@ struct hers_ctx {
     int tensor_variant = 1;  // tensor-kernel shape used by searches on this context
     int epi_variant = 0;     // epilogue form used by every search on this context (EPI_* flags)
     int tensor_first = 0;    // 1: the tensor kernel, not the epilogue, takes the high-priority stream
+    uint64_t ext_cluster_max = 64;  // probe preparation: cluster form up to this many polynomials
     int pm = 0;              // plaintext modulus: 0 the default t, 1 the paper's t
     // the epilogue of a search runs on ep (the device's highest stream priority),
     // after ep_ev[0] (tensor done) and before ep_ev[1] (joined back to the caller)
@@ -110,8 +111,13 @@ cudaError_t launch_resident_to_canonical_add(const uint64_t* tw, const uint64_t*
 // Canonical cts ct[0 .. nct) (global indices ct_begin ..) of dimension d into
 // the resident form at `out` (the base of block 0; RES_WORDS_PER_DIM words per
 // (block, dimension)).
+// Calls of at most cluster_max_polys polynomials take the cluster form
+// (k_extend_ntt_cluster), larger ones one CTA per polynomial; both write the
+// same bytes.
+constexpr uint64_t EXT_CLUSTER_MAX_POLYS = 64;
 cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t ct_begin,
-                              uint32_t d, uint64_t* out, cudaStream_t st);
+                              uint32_t d, uint64_t* out, cudaStream_t st,
+                              uint64_t cluster_max_polys = EXT_CLUSTER_MAX_POLYS);
 cudaError_t launch_decrypt(const uint64_t* tw, const DevKeys& k, const uint64_t* scores_ct,
                            uint64_t nblocks, int32_t* scores, uint64_t m, cudaStream_t st);
 

@@ -466,16 +466,15 @@ __global__ void __cluster_dims__(NUM_S, 1, 1) __launch_bounds__(NTT_THREADS, 4)
     cluster.barrier_wait();
 }
 
-// Up to this many polynomials per call take the cluster form: probes of
-// d <= 32.  Measured (probe preparation in a CUDA graph, cluster form against
-// one CTA per polynomial): d = 16, 14.2 against 27.3 us; d = 32, 23.2 against
-// 27.6 us; d = 48, equal; d = 64, 38.9 against 28.3 us, as 8 CTAs per
-// polynomial no longer fit one wave.
-constexpr uint64_t EXT_CLUSTER_MAX_POLYS = 64;
-
+// By default up to EXT_CLUSTER_MAX_POLYS polynomials per call take the cluster
+// form: probes of d <= 32.  Measured (probe preparation in a CUDA graph,
+// cluster form against one CTA per polynomial): d = 16, 14.2 against 27.3 us;
+// d = 32, 23.2 against 27.6 us; d = 48, equal; d = 64, 38.9 against 28.3 us,
+// as 8 CTAs per polynomial no longer fit one wave.  A context's probe
+// preparation uses its own threshold (hers_autotune_extension).
 cudaError_t launch_extend_ntt(const uint64_t* tw, const uint64_t* ct, uint64_t nct, uint64_t ct_begin,
-                              uint32_t d, uint64_t* out, cudaStream_t st) {
-    if (2 * nct <= EXT_CLUSTER_MAX_POLYS) {
+                              uint32_t d, uint64_t* out, cudaStream_t st, uint64_t cluster_max_polys) {
+    if (2 * nct <= cluster_max_polys) {
         k_extend_ntt_cluster<<<(unsigned)(2 * nct * NUM_S), NTT_THREADS, 0, st>>>(tw, ct, ct_begin, d, out);
         count_launches(1);
         return cudaGetLastError();

@@ -48,7 +48,7 @@ def setup():
     ctx.close()
 
 
-@pytest.mark.parametrize("variant", range(24))
+@pytest.mark.parametrize("variant", range(32))
 def test_batched_variant_equals_plain_search(setup, variant):
     names = H.hers_batch_variants()
     if variant >= len(names):

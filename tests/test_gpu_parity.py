@@ -397,3 +397,18 @@ def test_tensor_first_ordering_in_flight(ctx, keys, config1):
             assert torch.equal(copies[k], res["sc"]), f"copy after search {k}"
     finally:
         H.hers_set_tensor_first(ctx, False)
+
+
+def test_extension_autotune_keeps_prepared_probes_identical(ctx, keys):
+    """hers_autotune_extension moves the context's cluster threshold; the
+    prepared probe is the same bytes in either form (d = 16 and 64, on both
+    sides of the default threshold)."""
+    for d in (16, 64):
+        q = W.probe_for_mate(3, d, FEAT_SEED, NOISE_SEED)
+        pct = H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).cuda(), PRB_SEED)
+        before = H.hers_probe_prepare(ctx, pct)
+        cluster, ms = H.hers_autotune_extension(ctx, d)
+        assert ms["per_polynomial"] > 0 and ms["cluster"] > 0
+        after = H.hers_probe_prepare(ctx, pct)
+        torch.cuda.synchronize()
+        assert torch.equal(before, after), (d, cluster)
