@@ -91,6 +91,10 @@ def parse():
                     help="serving: arrival rates (requests/s) to sweep")
     ap.add_argument("--window", type=float, default=2.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--max-requests", type=int, default=240, help="serving: cap per rate")
+    ap.add_argument("--max-batch", type=int, default=16, help="serving: requests per batch at most")
+    ap.add_argument("--host-alloc", default="register", choices=["torch", "register"],
+                    help="large page-locked host buffers (serving arena, scale gallery): torch's pinned "
+                         "allocator or huge-page mappings registered with cudaHostRegister")
     ap.add_argument("--scale-m", type=int, default=100_000_000, help="scale: gallery entries")
     ap.add_argument("--scale-source", default="auto", choices=["auto", "host", "device"],
                     help="scale: where the canonical gallery lives (auto: host if it fits)")
@@ -667,7 +671,8 @@ def run_gpu(args):
         out["batched"] = batched_section(ctx, keys, dev, local, args)
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        out["serving"] = serving_section(ctx, keys, dev, local, (50.0, 200.0, 2000.0), 1.5, 200)
+        out["serving"] = serving_section(ctx, keys, dev, local, (50.0, 200.0, 2000.0), 1.5, 200,
+                                         host_alloc=args.host_alloc)
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
     # the oracle on the host cores, last: its OpenMP threads share the host
@@ -841,7 +846,8 @@ def run_batched(args):
     return 0
 
 
-def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_variant=None):
+def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_variant=None, max_batch=16,
+                    host_alloc="register"):
     """Config 4: continuous-batching server over three resident 10M-entry
     galleries (2,442 blocks each) at d = 32, 64 and 128.  For each arrival rate,
     Poisson requests (size uniform in [10k, 10M] entries, start block uniform,
@@ -880,12 +886,12 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
     torch.cuda.synchronize()
     free_b, _ = torch.cuda.mem_get_info(dev)
     pool = max(1 << 30, free_b - (8 << 30))
-    sv_name = batch_variant or "np2_nb2_s2_d4_m3"
-    srv = H.Server(ctx, keys, gals, workspace_bytes=pool, max_batch=16,
+    sv_name = batch_variant or "np2_nb2_s2_d4_m3_g1_l2"
+    srv = H.Server(ctx, keys, gals, workspace_bytes=pool, max_batch=max_batch,
                    variant=H.hers_batch_variants().index(sv_name))
     # pinned host arena for score ciphertexts, handed out as a ring
     arena_blocks = 4 * nblocks * 16
-    arena = torch.empty((arena_blocks, 4 * N), dtype=torch.int64).pin_memory()
+    arena = host_buffer(arena_blocks * 4 * N, host_alloc).view(arena_blocks, 4 * N)
     # the rate of a device -> arena copy (2 GiB), as the server's copy-outs see it
     probe_n = min(arena.numel(), (2 << 30) // 8)
     src = torch.empty(probe_n, dtype=torch.int64, device=dev)
@@ -899,6 +905,8 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
         arena_ms = c0.elapsed_time(c1) if arena_ms is None else min(arena_ms, c0.elapsed_time(c1))
     del src
     host_diag = {"arena_d2h_gbs": probe_n * 8 / (arena_ms / 1e3) / 1e9,
+                 "arena_d2h_gbs_per_2gib_slice": copy_rate_slices(arena, dev, probe_n, h2d=False),
+                 "host_alloc": host_alloc,
                  "host_mem_available_gb": host_mem_available() / 1e9}
     # sampled requests (up to SAMPLE per rate, at most SAMPLE_MAX_BLOCKS blocks
     # each) write to buffers of their own, kept for the mix-vs-alone check
@@ -1025,7 +1033,7 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
                                    "entries (2,442 blocks) at d = 32, 64, 128; request size uniform in "
                                    "[10k, 10M] entries, start block uniform, d uniform",
                        "resident_gallery_bytes": resident, "pool_bytes": st["pool_bytes"],
-                       "max_batch": 16, "batch_variant": sv_name, "setup_s": setup_s,
+                       "max_batch": max_batch, "batch_variant": sv_name, "setup_s": setup_s,
                        "latency": "from the arrival time to the score ciphertexts in pinned host memory"},
             "rates": results, "server": st, "gpu_launches": launches, "host": host_diag,
             "correct": {"mix_equals_alone": f"{mix_ok}/{len(sampled)}",
@@ -1050,13 +1058,66 @@ def run_serving(args):
     ctx = H.Context(local)
     keys = H.hers_keygen(ctx, KEY_SEED)
     out = serving_section(ctx, keys, dev, local, [float(r) for r in args.rates.split(",")], args.window,
-                          args.max_requests, args.batch_variant)
+                          args.max_requests, args.batch_variant, args.max_batch, args.host_alloc)
     out = {"workload": "serving", "n_gpus": 1, "dtype": "u64", "higher_is_better": True,
            "data": "synthetic (seeded int8 features drawn on the device; Poisson arrivals)", **out}
     print(json.dumps(out))
     keys.close()
     ctx.close()
     return 0
+
+
+_HOST_BUFS = []  # host mappings kept alive (and registered with CUDA) until exit
+
+
+def host_buffer(nwords, mode):
+    """An int64 CPU tensor of nwords that CUDA copies treat as page-locked.
+    mode "torch": torch's pinned allocator (cudaHostAlloc).  mode "register":
+    an anonymous mapping advised to transparent huge pages, touched, then
+    registered with cudaHostRegister, so the pages are large and resident
+    before the GPU maps them."""
+    import torch
+    if mode == "torch":
+        return torch.empty(nwords, dtype=torch.int64, pin_memory=True)
+    import ctypes
+    import mmap
+
+    import numpy as np
+    nbytes = nwords * 8
+    mm = mmap.mmap(-1, nbytes, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+    if hasattr(mm, "madvise") and hasattr(mmap, "MADV_HUGEPAGE"):
+        mm.madvise(mmap.MADV_HUGEPAGE)
+    arr = np.frombuffer(mm, dtype=np.int64)
+    step = (1 << 30) // 8
+    for o in range(0, nwords, step):  # touch every page
+        arr[o:o + step] = 0
+    rt = ctypes.CDLL("libcudart.so.13")
+    rc = rt.cudaHostRegister(ctypes.c_void_p(arr.ctypes.data), ctypes.c_size_t(nbytes), ctypes.c_uint(1))
+    if rc != 0:
+        raise SystemExit(f"cudaHostRegister failed with {rc}")
+    _HOST_BUFS.append((mm, arr))
+    return torch.from_numpy(arr)
+
+
+def copy_rate_slices(host, dev, span_words, h2d=True):
+    """GB/s of copies between a host tensor and the device, slice by slice."""
+    import torch
+    buf = torch.empty(span_words, dtype=torch.int64, device=dev)
+    flat = host.view(-1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for o in range(0, flat.numel(), span_words):
+        n_ = min(span_words, flat.numel() - o)
+        e0.record()
+        if h2d:
+            buf[:n_].copy_(flat[o:o + n_], non_blocking=True)
+        else:
+            flat[o:o + n_].copy_(buf[:n_], non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        out.append(round(n_ * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9, 1))
+    del buf
+    return out
 
 
 def thread_cpu_seconds():
@@ -1127,7 +1188,7 @@ def run_scale(args):
         source = "host" if host_mem_available() > gal_bytes + (24 << 30) else "device"
     dev_copy, h2d_gbs, slice_gbs = None, None, [0.0]
     if source == "host":
-        g = torch.empty(gct.shape, dtype=torch.int64, pin_memory=True)
+        g = host_buffer(gct.numel(), args.host_alloc).view(gct.shape)
         g.copy_(gct)
         # the rate of one large pinned-host -> device copy (up to 4 GiB of the gallery)
         span = min(g.numel(), (4 << 30) // 8)
@@ -1142,18 +1203,10 @@ def run_scale(args):
             torch.cuda.synchronize()
             best = h0.elapsed_time(h1) if best is None else min(best, h0.elapsed_time(h1))
         h2d_gbs = span * 8 / (best / 1e3) / 1e9
-        # and every 4 GiB slice of the whole buffer once: a pinned buffer this
-        # large may not copy at one rate over its whole extent
-        slice_gbs = []
-        flat_all = g.view(-1)
-        for o in range(0, flat_all.numel(), span):
-            n_ = min(span, flat_all.numel() - o)
-            h0.record()
-            buf[:n_].copy_(flat_all[o:o + n_], non_blocking=True)
-            h1.record()
-            torch.cuda.synchronize()
-            slice_gbs.append(n_ * 8 / (h0.elapsed_time(h1) / 1e3) / 1e9)
         del buf
+        # and every 4 GiB slice of the whole buffer once: a page-locked buffer
+        # this large need not copy at one rate over its whole extent
+        slice_gbs = copy_rate_slices(g, dev, span)
         # keep the device copy (when it and the search's buffers fit) to time
         # the same search without host copies: the compute-only pass
         need = nprobes * nb * 4 * N * 8 + H.hers_search_stream_workspace_bytes(d, nprobes, args.scale_chunk) + (8 << 30)
@@ -1245,8 +1298,9 @@ def run_scale(args):
            "search_s_all_probes": ms / 1e3, "search_s_per_probe": ms / 1e3 / nprobes,
            "streaming": None if source != "host" else {
                "h2d_gbs_measured": h2d_gbs,
+               "host_alloc": args.host_alloc,
                "h2d_gbs_per_4gib_slice": {"min": min(slice_gbs), "max": max(slice_gbs),
-                                          "mean": sum(slice_gbs) / len(slice_gbs), "slices": len(slice_gbs)},
+                                          "mean": sum(slice_gbs) / len(slice_gbs), "all": slice_gbs},
                "h2d_gbs_during_search": gal_bytes / (ms / 1e3) / 1e9,
                "host_call_s": enqueue_s,
                "device_source_s": None if dev_ms is None else dev_ms / 1e3,
