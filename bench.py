@@ -22,7 +22,9 @@ between steps.  Multi-GPU: each rank searches its own 256-block gallery (the
 blocks are independent, Sec. 3.2 footnote), no data-path collective: weak
 scaling.  `--impl reference` times the CPU oracle on the host cores instead.
 
-On one GPU the same line also carries, each with its own clock record:
+On one GPU the same line also carries, each with its own clock record
+(and a `scale` object: config 5, a 50M-entry canonical gallery, 20M when
+the host lacks room, streamed from page-locked host memory with 16 probes):
   batched  64 probes against uneven subsets of 256 blocks at mixed d, one
            CUDA graph per step, against 64 sequential plain searches;
   serving  the continuous-batching server over three resident 10M-entry
@@ -450,14 +452,15 @@ def run_gpu(args):
                     step_in_flight(k)
                 combos[(tv, tf, ev_)] = timed(step_in_flight, 10, trace=False) / 10
     if not combos:
-        combos[(variant, False, 0)] = float("nan")
-    variant, tensor_first, epi = min(combos, key=lambda c: combos[c] if combos[c] == combos[c] else 0.0)
+        combos[(variant, False, 0)] = None  # not timed (--no-select)
+    variant, tensor_first, epi = min(combos, key=lambda c: combos[c] if combos[c] is not None else 0.0)
     variant_name, epi_name = tnames[variant], enames[epi]
     H.hers_set_tensor_variant(ctx, variant)
     H.hers_set_tensor_first(ctx, tensor_first)
     H.hers_set_epilogue_variant(ctx, epi)
-    epi_inflight = {f"{tnames[a]}|{'tensor_first' if b else 'epilogue_first'}|{enames[c]}": round(v, 4)
-                    for (a, b, c), v in sorted(combos.items(), key=lambda kv: kv[1])}
+    epi_inflight = {f"{tnames[a]}|{'tensor_first' if b else 'epilogue_first'}|{enames[c]}":
+                    (round(v, 4) if v is not None else None)
+                    for (a, b, c), v in sorted(combos.items(), key=lambda kv: kv[1] or 0.0)}
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -673,6 +676,13 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         out["serving"] = serving_section(ctx, keys, dev, local, (50.0, 200.0, 2000.0), 1.5, 200,
                                          host_alloc=args.host_alloc)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        # config 5 streamed from page-locked host memory: 50M entries (102 GB)
+        # when the host has room for them, else 20M
+        m5 = 50_000_000 if host_mem_available() > 150e9 else 20_000_000
+        out["scale"] = scale_section(ctx, keys, dev, local, m5, "host", args.host_alloc, 32,
+                                     "np4_nb2_s2_d4_m2", 2)
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
     # the oracle on the host cores, last: its OpenMP threads share the host
@@ -891,7 +901,7 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
                    variant=H.hers_batch_variants().index(sv_name))
     # pinned host arena for score ciphertexts, handed out as a ring
     arena_blocks = 4 * nblocks * 16
-    arena = host_buffer(arena_blocks * 4 * N, host_alloc).view(arena_blocks, 4 * N)
+    arena = host_buffer(arena_blocks * 4 * N, host_alloc, dev).view(arena_blocks, 4 * N)
     # the rate of a device -> arena copy (2 GiB), as the server's copy-outs see it
     probe_n = min(arena.numel(), (2 << 30) // 8)
     src = torch.empty(probe_n, dtype=torch.int64, device=dev)
@@ -904,7 +914,8 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
         torch.cuda.synchronize()
         arena_ms = c0.elapsed_time(c1) if arena_ms is None else min(arena_ms, c0.elapsed_time(c1))
     del src
-    host_diag = {"arena_d2h_gbs": probe_n * 8 / (arena_ms / 1e3) / 1e9,
+    host_diag = {"host_memcpy_gbs_before": host_memcpy_gbs(),
+                 "arena_d2h_gbs": probe_n * 8 / (arena_ms / 1e3) / 1e9,
                  "arena_d2h_gbs_per_2gib_slice": copy_rate_slices(arena, dev, probe_n, h2d=False),
                  "host_alloc": host_alloc,
                  "host_mem_available_gb": host_mem_available() / 1e9}
@@ -915,6 +926,16 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
                    for _ in range(SAMPLE * len(rates))]
     sampled = []   # (gallery, b0, b1, probe index, buffer)
     results = []
+    # warm-up, not measured: one full batch of requests through every stage
+    # (kernels, copies into the arena, host callbacks)
+    warm = W.serving_requests(10000.0, 1.0, 16, nblocks, dims, seed=7)
+    wids = []
+    for wi, (_, gi, b0, b1) in enumerate(warm):
+        o = (wi * nblocks) % max(1, arena_blocks - nblocks)
+        wids.append(srv.submit(gi, b0, b1, probes[gi][wi % 8], arena[o: o + (b1 - b0)]))
+    for rid in wids:
+        if srv.wait(rid, 600000)[0] != 0:
+            raise SystemExit("serving warm-up request failed")
     clocks = ClockSampler(local)
     clocks.start()
     clocks.mark_start()
@@ -987,6 +1008,7 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
     cpu1, wall1 = thread_cpu_seconds(), time.perf_counter()
     busy = sorted(((cpu1[k] - cpu0.get(k, 0.0), k[1]) for k in cpu1), reverse=True)[:6]
     host_diag["threads_cpu_s"] = [[n, round(v, 2)] for v, n in busy]
+    host_diag["host_memcpy_gbs_after"] = host_memcpy_gbs()
     host_diag["wall_s"] = round(wall1 - wall0, 2)
     host_diag["nthreads"] = len(cpu1)
     launches = H.hers_kernel_launches() - launches0
@@ -1025,6 +1047,8 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
     torch.cuda.synchronize()
     plain_s = e0.elapsed_time(e1) / 1e3
     best = max(results, key=lambda r: r["entries_per_s"])
+    del arena
+    host_buffers_release()
     return {"metric": "encrypted gallery entries scored/sec and p50/p99 latency (serving)",
             "unit": "entries/s", "value": best["entries_per_s"],
             "p50_ms": results[0]["p50_ms"], "p99_ms": results[0]["p99_ms"],
@@ -1070,12 +1094,18 @@ def run_serving(args):
 _HOST_BUFS = []  # host mappings kept alive (and registered with CUDA) until exit
 
 
-def host_buffer(nwords, mode):
+HOST_BUF_LOG = []  # what host_buffer() did, for the JSON line
+
+
+def host_buffer(nwords, mode, dev=None):
     """An int64 CPU tensor of nwords that CUDA copies treat as page-locked.
     mode "torch": torch's pinned allocator (cudaHostAlloc).  mode "register":
     an anonymous mapping advised to transparent huge pages, touched, then
     registered with cudaHostRegister, so the pages are large and resident
-    before the GPU maps them."""
+    before the GPU maps them.  With dev, every 4 GiB slice is then copied to
+    the device once; a slice at under half the median rate has its pages
+    dropped and faulted in afresh (at most 3 rounds), since some regions of
+    very large page-locked buffers copied 8-40x slower than the rest."""
     import torch
     if mode == "torch":
         return torch.empty(nwords, dtype=torch.int64, pin_memory=True)
@@ -1092,11 +1122,47 @@ def host_buffer(nwords, mode):
     for o in range(0, nwords, step):  # touch every page
         arr[o:o + step] = 0
     rt = ctypes.CDLL("libcudart.so.13")
-    rc = rt.cudaHostRegister(ctypes.c_void_p(arr.ctypes.data), ctypes.c_size_t(nbytes), ctypes.c_uint(1))
-    if rc != 0:
-        raise SystemExit(f"cudaHostRegister failed with {rc}")
+    ptr, size = ctypes.c_void_p(arr.ctypes.data), ctypes.c_size_t(nbytes)
+    if rt.cudaHostRegister(ptr, size, ctypes.c_uint(1)) != 0:
+        raise SystemExit("cudaHostRegister failed")
+    t = torch.from_numpy(arr)
+    log = {"gb": round(nbytes / 1e9, 1), "repaired_slices": []}
+    try:
+        log["thp"] = open("/sys/kernel/mm/transparent_hugepage/enabled").read().strip()
+    except OSError:
+        pass
+    if dev is not None:
+        span = (4 << 30) // 8
+        for _ in range(3):
+            rates = copy_rate_slices(t, dev, span)
+            med = sorted(rates)[len(rates) // 2]
+            slow = [i for i, r in enumerate(rates) if r < 0.5 * med]
+            log.setdefault("slice_gbs_first", rates)
+            if not slow:
+                break
+            rt.cudaHostUnregister(ptr)
+            for i in slow:
+                o, n_ = i * span * 8, min(span * 8, nbytes - i * span * 8)
+                mm.madvise(mmap.MADV_DONTNEED, o, n_)
+                arr[i * span: i * span + n_ // 8] = 0
+            if rt.cudaHostRegister(ptr, size, ctypes.c_uint(1)) != 0:
+                raise SystemExit("cudaHostRegister failed")
+            log["repaired_slices"].append(slow)
+    HOST_BUF_LOG.append(log)
     _HOST_BUFS.append((mm, arr))
-    return torch.from_numpy(arr)
+    return t
+
+
+def host_buffers_release():
+    """Unregisters the host mappings host_buffer() made; their memory goes back
+    when the last tensor over it is gone."""
+    import ctypes
+    if not _HOST_BUFS:
+        return
+    rt = ctypes.CDLL("libcudart.so.13")
+    for mm, arr in _HOST_BUFS:
+        rt.cudaHostUnregister(ctypes.c_void_p(arr.ctypes.data))
+    _HOST_BUFS.clear()
 
 
 def copy_rate_slices(host, dev, span_words, h2d=True):
@@ -1118,6 +1184,19 @@ def copy_rate_slices(host, dev, span_words, h2d=True):
         out.append(round(n_ * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9, 1))
     del buf
     return out
+
+
+def host_memcpy_gbs(nbytes=1 << 30):
+    """The host's own memory copy rate (one numpy copy of nbytes, after a
+    warm-up copy): shows when host memory is slow for everyone, e.g. when
+    other jobs on the machine load it."""
+    import numpy as np
+    a = np.ones(nbytes // 8, dtype=np.int64)
+    b = np.empty_like(a)
+    np.copyto(b, a)
+    t0 = time.perf_counter()
+    np.copyto(b, a)
+    return round(nbytes / (time.perf_counter() - t0) / 1e9, 2)
 
 
 def thread_cpu_seconds():
@@ -1149,26 +1228,21 @@ def host_mem_available():
     return 0
 
 
-def run_scale(args):
-    """Config 5: 100,000,000 entries (24,415 blocks), d = 64, 16 probes, 100
-    planted mates (probes 0..15 target mates 0..15).  The gallery is held in
-    canonical form (204.8 GB): in pinned host memory and streamed in chunks
-    when the host has room, else in device memory.  Every decrypted score is
-    checked against the plaintext inner products, top-1 for every probe, and
-    sampled blocks against the oracle."""
+def scale_section(ctx, keys, dev, local, m, source, host_alloc, chunk, bv_name, oracle_blocks):
+    """Config 5: m entries (100,000,000: 24,415 blocks), d = 64, 16 probes,
+    100 planted mates (probes 0..15 target mates 0..15).  The gallery is held
+    in canonical form (204.8 GB at 100M): in page-locked host memory and
+    streamed in chunks when the host has room, else in device memory.  Every
+    decrypted score is checked against the plaintext inner products, top-1
+    for every probe, and sampled blocks against the oracle.  Returns the
+    result object; the host gallery is released on return."""
     import numpy as np
     import torch
 
     import paper_2003_12197_gb300 as H
     import workloads as W
 
-    _, _, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    H.build_library()
-    ctx = H.Context(local)
-    keys = H.hers_keygen(ctx, KEY_SEED)
-    m, d, nprobes = args.scale_m, 64, 16
+    d, nprobes = 64, 16
     nb = H.hers_blocks_for(m)
     t0 = time.perf_counter()
     feats = W.gallery_features_device(m, d, FEAT_SEED + 500, dev)
@@ -1183,12 +1257,11 @@ def run_scale(args):
     H.hers_check(ctx)
     gen_s = time.perf_counter() - t0
     gal_bytes = gct.numel() * 8
-    source = args.scale_source
     if source == "auto":
         source = "host" if host_mem_available() > gal_bytes + (24 << 30) else "device"
     dev_copy, h2d_gbs, slice_gbs = None, None, [0.0]
     if source == "host":
-        g = host_buffer(gct.numel(), args.host_alloc).view(gct.shape)
+        g = host_buffer(gct.numel(), host_alloc, dev).view(gct.shape)
         g.copy_(gct)
         # the rate of one large pinned-host -> device copy (up to 4 GiB of the gallery)
         span = min(g.numel(), (4 << 30) // 8)
@@ -1209,7 +1282,7 @@ def run_scale(args):
         slice_gbs = copy_rate_slices(g, dev, span)
         # keep the device copy (when it and the search's buffers fit) to time
         # the same search without host copies: the compute-only pass
-        need = nprobes * nb * 4 * N * 8 + H.hers_search_stream_workspace_bytes(d, nprobes, args.scale_chunk) + (8 << 30)
+        need = nprobes * nb * 4 * N * 8 + H.hers_search_stream_workspace_bytes(d, nprobes, chunk) + (8 << 30)
         if torch.cuda.mem_get_info(dev)[0] > need:
             dev_copy = gct
         else:
@@ -1221,8 +1294,6 @@ def run_scale(args):
                                                               PRB_SEED + 500 + i))
               for i, q in enumerate(qs)]
     sc = torch.empty((nprobes, nb, 2, 2, N), dtype=torch.int64, device=dev)
-    chunk = args.scale_chunk
-    bv_name = args.batch_variant or "np4_nb2_s2_d4_m2"
     bv = H.hers_batch_variants().index(bv_name)
     ws = torch.empty(H.hers_search_stream_workspace_bytes(d, nprobes, chunk) // 8,
                      dtype=torch.int64, device=dev)
@@ -1271,12 +1342,12 @@ def run_scale(args):
         top1 += int(torch.argmax(scores).item()) == int(mates[i])
     # sampled blocks against the oracle
     oracle_ok, checked = True, []
-    if args.oracle_blocks >= 0:
+    if oracle_blocks >= 0:
         import oracle as O
         _, opk, oevk = O.keygen(KEY_SEED)
         pick = [(0, int(mates[0]) // N), (1, int(mates[1]) // N)]
         brng = np.random.default_rng(7)
-        pick += [(int(brng.integers(0, nprobes)), int(brng.integers(0, nb))) for _ in range(args.oracle_blocks)]
+        pick += [(int(brng.integers(0, nprobes)), int(brng.integers(0, nb))) for _ in range(oracle_blocks)]
         oprb = {}
         for pi, b in pick:
             if pi not in oprb:
@@ -1298,7 +1369,8 @@ def run_scale(args):
            "search_s_all_probes": ms / 1e3, "search_s_per_probe": ms / 1e3 / nprobes,
            "streaming": None if source != "host" else {
                "h2d_gbs_measured": h2d_gbs,
-               "host_alloc": args.host_alloc,
+               "host_alloc": host_alloc,
+               "host_buffer": HOST_BUF_LOG[-1] if host_alloc != "torch" and HOST_BUF_LOG else None,
                "h2d_gbs_per_4gib_slice": {"min": min(slice_gbs), "max": max(slice_gbs),
                                           "mean": sum(slice_gbs) / len(slice_gbs), "all": slice_gbs},
                "h2d_gbs_during_search": gal_bytes / (ms / 1e3) / 1e9,
@@ -1315,6 +1387,26 @@ def run_scale(args):
            "correct": {"scores_exact_all": exact, "top1": f"{top1}/{nprobes}",
                        "oracle_blocks": checked, "oracle_bit_exact": oracle_ok},
            "clocks": clk}
+    del g
+    host_buffers_release()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_scale(args):
+    """Config 5 on its own (see scale_section)."""
+    import torch
+
+    import paper_2003_12197_gb300 as H
+
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    H.build_library()
+    ctx = H.Context(local)
+    keys = H.hers_keygen(ctx, KEY_SEED)
+    out = scale_section(ctx, keys, dev, local, args.scale_m, args.scale_source, args.host_alloc, args.scale_chunk,
+                        args.batch_variant or "np4_nb2_s2_d4_m2", args.oracle_blocks)
     print(json.dumps(out))
     keys.close()
     ctx.close()

@@ -400,8 +400,8 @@ const char* hers_batch_variant_name(int v);
  * memory.  Each id is waited for once.
  * variant: the batched tensor-kernel shape (hers_batch_variant_name).
  * A request of dimension d over n blocks holds 8 (14 d N + 29 N n) bytes of
- * the pool while it runs, plus its share of the batch's work tables
- * (16 bytes per (block, limb, tile) and probe chunk).
+ * the pool while it runs, plus its share of the batch's work tables (a few
+ * hundred bytes per segment of a gallery that one set of requests covers).
  */
 typedef struct hers_server_gallery {
     const uint64_t* gallery;  /* device: resident gallery (block 0) */

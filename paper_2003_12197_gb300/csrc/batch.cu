@@ -75,25 +75,38 @@ struct UnitRegs {
     bool last;  // the last chunk to read these gallery rows
 };
 
-template <int NPC>
+// Unit u's table entries: the segment holding u (binary search over the
+// segments' first units), then u's chunk, block group, limb and tile within it.
+template <int NPC, int NB>
 __device__ __forceinline__ void load_unit(UnitRegs& r, const uint64_t** probe_slot, uint64_t* pair_slot,
                                           const BatchChunk* __restrict__ chunks,
-                                          const BatchUnit* __restrict__ units, uint32_t u) {
-    const BatchUnit U = units[u];
-    const BatchChunk* C = chunks + U.chunk;
+                                          const BatchSeg* __restrict__ segs, uint32_t nsegs, uint32_t u) {
+    uint32_t lo = 0, hi = nsegs - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (segs[mid].first_unit <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchSeg S = segs[lo];
+    uint32_t x = u - S.first_unit;
+    const uint32_t c = x % S.nch;
+    x /= S.nch;
+    const uint32_t bg = x % S.nbg;
+    x /= S.nbg;
+    const BatchChunk* C = chunks + S.first_chunk + c;
     r.gallery = C->gallery;
     r.d = C->d;
     r.np = C->np;
+    r.block = S.s0 + bg * NB;
+    r.nb = min((uint32_t)NB, S.s1 - r.block);
+    r.last = c + 1 == S.nch;
+    r.tile = x % NTILES;
+    r.limb = x / NTILES;
 #pragma unroll
     for (int q = 0; q < NPC; q++) {  // entries past np are zero in the table
         probe_slot[q] = C->probe[q];
-        pair_slot[q] = C->pair[q] + U.block;
+        pair_slot[q] = C->pair[q] + r.block;
     }
-    r.nb = U.nb & ~UNIT_LAST_CHUNK;
-    r.last = (U.nb & UNIT_LAST_CHUNK) != 0;
-    r.block = U.block;
-    r.limb = U.limb;
-    r.tile = U.tile;
 }
 
 // One stage's products into the 64-bit sums: for dd < nd, probe q < np,
@@ -163,7 +176,7 @@ __device__ __forceinline__ void stage_products(int64_t (&s)[NP][NB][3], const in
 // CC: the multiply-accumulates as carry chains (madc_b) instead of mad.wide.
 template <int NP, int NB, int STAGES, int DPS, int MINB, int G, bool POL, int PF = 0, bool CC = false>
 __global__ void __launch_bounds__(G * TILE + 32, MINB)
-    k_tensor_batched(const BatchChunk* __restrict__ chunks, const BatchUnit* __restrict__ units,
+    k_tensor_batched(const BatchChunk* __restrict__ chunks, const BatchSeg* __restrict__ segs, uint32_t nsegs,
                      uint32_t nunits, uint32_t* counter, uint32_t* __restrict__ X, int* err) {
     constexpr int NPC = G * NP;  // probes of a chunk
     static_assert(BPFOLD_S % DPS == 0 && BPFOLD_02 % BPFOLD_S == 0, "stages must not straddle a partial fold");
@@ -198,7 +211,7 @@ __global__ void __launch_bounds__(G * TILE + 32, MINB)
             uint32_t u = atomicAdd(counter, 1u);
             UnitRegs cur = {}, nxt = {};
             int cs = 0;  // shared-memory slot of the current unit's probes and pairs
-            if (u < nunits) load_unit<NPC>(cur, unit_probe[0], unit_pair[0], chunks, units, u);
+            if (u < nunits) load_unit<NPC, NB>(cur, unit_probe[0], unit_pair[0], chunks, segs, nsegs, u);
             while (!failed) {
                 const bool stop = u >= nunits;
                 const uint32_t un = stop ? UNIT_STOP : atomicAdd(counter, 1u);  // next unit, claimed now
@@ -244,7 +257,7 @@ __global__ void __launch_bounds__(G * TILE + 32, MINB)
                                      bytes, &full[st], pol_g);
                     // the next unit's tables, once this unit's first stage is on its way
                     if (si == 0 && un < nunits)
-                        load_unit<NPC>(nxt, unit_probe[cs ^ 1], unit_pair[cs ^ 1], chunks, units, un);
+                        load_unit<NPC, NB>(nxt, unit_probe[cs ^ 1], unit_pair[cs ^ 1], chunks, segs, nsegs, un);
                     if (PF > 0) {
                         // gallery rows PF stages ahead into L2
                         const uint32_t ahead = si + PF;
@@ -348,7 +361,7 @@ __global__ void __launch_bounds__(G * TILE + 32, MINB)
     }
 }
 
-using BatchFn = void (*)(const BatchChunk*, const BatchUnit*, uint32_t, uint32_t*, uint32_t*, int*);
+using BatchFn = void (*)(const BatchChunk*, const BatchSeg*, uint32_t, uint32_t, uint32_t*, uint32_t*, int*);
 struct BatchVariant {
     const char* name;
     BatchFn fn;
@@ -403,8 +416,8 @@ int batch_variant_np(int v) { return kBatchVariants[v].groups * kBatchVariants[v
 int batch_variant_nb(int v) { return kBatchVariants[v].nb; }
 
 // Direct launch of the persistent kernel of variant v over device tables.
-cudaError_t launch_batched(int v, const BatchChunk* d_chunks, const BatchUnit* d_units, uint32_t nunits,
-                           uint32_t* d_counter, uint64_t* X, int* err, int device, cudaStream_t st) {
+cudaError_t launch_batched(int v, const BatchChunk* d_chunks, const BatchSeg* d_segs, uint32_t nsegs,
+                           uint32_t nunits, uint32_t* d_counter, uint64_t* X, int* err, int device, cudaStream_t st) {
     // X: the X area of the pairs' workspace; the kernel writes uint32 accumulators
     // [pair][3][NUM_S][N] at its start
     if (v < 0 || v >= NUM_BATCH_VARIANTS) return cudaErrorInvalidValue;
@@ -420,7 +433,7 @@ cudaError_t launch_batched(int v, const BatchChunk* d_chunks, const BatchUnit* d
     const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)per_sm * sms, nunits ? nunits : 1);
     e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-    V.fn<<<grid, batch_threads(V), smem, st>>>(d_chunks, d_units, nunits, d_counter, (uint32_t*)X, err);
+    V.fn<<<grid, batch_threads(V), smem, st>>>(d_chunks, d_segs, nsegs, nunits, d_counter, (uint32_t*)X, err);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -446,7 +459,8 @@ struct hers_batch {
     unsigned grid;
     int smem, threads;
     BatchChunk* d_chunks;
-    BatchUnit* d_units;
+    BatchSeg* d_segs;
+    uint32_t nsegs;
     uint32_t* d_counter;
     double tune_ms[NUM_BATCH_VARIANTS];
 };
@@ -455,9 +469,9 @@ namespace {
 
 struct Plan {
     std::vector<BatchChunk> chunks;
-    std::vector<BatchUnit> units;
+    std::vector<BatchSeg> segs;
     uint32_t ngroups = 0;
-    uint64_t npairs = 0;
+    uint64_t npairs = 0, nunits = 0;
 };
 
 }  // namespace
@@ -475,7 +489,9 @@ namespace hers {
 // blocks, and the chunks of one block run back to back, so a gallery run is
 // read from HBM once and from L2 by the other chunks.
 void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, int nb_max,
-                 std::vector<BatchChunk>& chunks, std::vector<BatchUnit>& units, uint32_t* ngroups) {
+                 std::vector<BatchChunk>& chunks, std::vector<BatchSeg>& segs, uint32_t* ngroups,
+                 uint64_t* nunits) {
+    uint64_t unit = 0;
     std::map<std::pair<const uint64_t*, uint32_t>, std::vector<uint32_t>> by_gallery;
     std::vector<std::pair<const uint64_t*, uint32_t>> order;
     for (uint32_t i = 0; i < nitems; i++) {
@@ -514,17 +530,14 @@ void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, int nb_max
                 chunks.push_back(ch);
             }
             const uint32_t nch = (uint32_t)chunks.size() - first;
-            for (uint16_t l = 0; l < NUM_S; l++)
-                for (uint16_t tl = 0; tl < NTILES; tl++)
-                    for (uint64_t blk = s0; blk < s1; blk += nb_max) {
-                        const uint32_t nbu = (uint32_t)std::min<uint64_t>(nb_max, s1 - blk);
-                        for (uint32_t c2 = 0; c2 < nch; c2++)
-                            units.push_back({first + c2, (uint32_t)blk, l, tl,
-                                             nbu | (c2 + 1 == nch ? UNIT_LAST_CHUNK : 0u)});
-                    }
+            const uint32_t nbg = (uint32_t)((s1 - s0 + nb_max - 1) / nb_max);
+            segs.push_back({(uint32_t)std::min<uint64_t>(unit, 0xFFFFFFFFull), first, nch, nbg, (uint32_t)s0,
+                            (uint32_t)s1});
+            unit += (uint64_t)NUM_S * NTILES * nbg * nch;
         }
     }
     if (ngroups) *ngroups = groups;
+    if (nunits) *nunits = unit;
 }
 
 }  // namespace hers
@@ -538,7 +551,7 @@ Plan make_plan(const hers_batch_item* items, uint32_t nitems, int np_max, int nb
         r[i] = {items[i].gallery, 0, items[i].nblocks, items[i].d, items[i].probe, P.npairs};
         P.npairs += items[i].nblocks;
     }
-    plan_ranges(r.data(), nitems, np_max, nb_max, P.chunks, P.units, &P.ngroups);
+    plan_ranges(r.data(), nitems, np_max, nb_max, P.chunks, P.segs, &P.ngroups, &P.nunits);
     return P;
 }
 
@@ -559,7 +572,7 @@ cudaError_t batch_launch(hers_batch* B, cudaStream_t st, bool traced) {
     uint64_t* KS = C + B->npairs * 6 * N;
     cudaError_t e = cudaMemsetAsync(B->d_counter, 0, sizeof(uint32_t), st);
     if (traced) cudaEventRecord(B->ev[0], st);
-    B->fn<<<B->grid, B->threads, B->smem, st>>>(B->d_chunks, B->d_units, B->nunits, B->d_counter,
+    B->fn<<<B->grid, B->threads, B->smem, st>>>(B->d_chunks, B->d_segs, B->nsegs, B->nunits, B->d_counter,
                                                 (uint32_t*)X, B->ctx->err);
     if (traced) cudaEventRecord(B->ev[1], st);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -574,17 +587,17 @@ int batch_build(hers_batch* B, const hers_batch_item* items, uint32_t nitems, in
     hers_ctx* ctx = B->ctx;
     const BatchVariant& V = kBatchVariants[v];
     Plan P = make_plan(items, nitems, V.groups * V.np, V.nb);
-    if (P.units.size() >= UNIT_STOP) return fail(ctx, HERS_E_INVAL, "hers_batch_create: too many units");
+    if (P.nunits >= UNIT_STOP) return fail(ctx, HERS_E_INVAL, "hers_batch_create: too many units");
     const size_t cbytes = P.chunks.size() * sizeof(BatchChunk);
-    const size_t ubytes = P.units.size() * sizeof(BatchUnit);
+    const size_t ubytes = P.segs.size() * sizeof(BatchSeg);
     const size_t total = ((cbytes + 255) / 256) * 256 + ((ubytes + 255) / 256) * 256 + 256;
     cudaError_t e = cudaMalloc(&B->dev, total);
     if (e != cudaSuccess) return fail(ctx, HERS_E_NOMEM, "hers_batch_create: %s", cudaGetErrorString(e));
     BatchChunk* d_chunks = (BatchChunk*)B->dev;
-    BatchUnit* d_units = (BatchUnit*)((char*)B->dev + ((cbytes + 255) / 256) * 256);
-    uint32_t* d_counter = (uint32_t*)((char*)d_units + ((ubytes + 255) / 256) * 256);
+    BatchSeg* d_segs = (BatchSeg*)((char*)B->dev + ((cbytes + 255) / 256) * 256);
+    uint32_t* d_counter = (uint32_t*)((char*)d_segs + ((ubytes + 255) / 256) * 256);
     e = cudaMemcpy(d_chunks, P.chunks.data(), cbytes, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_units, P.units.data(), ubytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_segs, P.segs.data(), ubytes, cudaMemcpyHostToDevice);
     const int smem = batch_smem(V);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(V.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int per_sm = 0, sms = 0;
@@ -600,18 +613,19 @@ int batch_build(hers_batch* B, const hers_batch_item* items, uint32_t nitems, in
                     "%d + %d bytes shared)",
                     V.name, fa.numRegs, fa.maxThreadsPerBlock, (int)fa.sharedSizeBytes, smem);
     }
-    const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)per_sm * sms, P.units.size());
+    const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)per_sm * sms, P.nunits);
 
     B->fn = V.fn;
     B->grid = grid;
     B->smem = smem;
     B->threads = batch_threads(V);
     B->d_chunks = d_chunks;
-    B->d_units = d_units;
+    B->d_segs = d_segs;
+    B->nsegs = (uint32_t)P.segs.size();
     B->d_counter = d_counter;
     B->variant = v;
     B->ngroups = P.ngroups;
-    B->nunits = (uint32_t)P.units.size();
+    B->nunits = (uint32_t)P.nunits;
     B->npairs = P.npairs;
     cudaStream_t cs = ctx->stream;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);

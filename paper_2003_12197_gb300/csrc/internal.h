@@ -189,20 +189,27 @@ struct BatchChunk {  // up to BATCH_NPMAX probes sharing one gallery segment
     uint64_t pair[BATCH_NPMAX];  // pair of probe q at absolute block b: pair[q] + b (mod 2^64)
     uint32_t d, np;
 };
-struct BatchUnit {  // (chunk, first absolute block, limb, tile, blocks in the unit)
-    uint32_t chunk, block;
-    uint16_t limb, tile;
-    uint32_t nb;  // blocks in the unit; bit 31 set on the last chunk to read these blocks' rows
+// A segment: blocks [s0, s1) of one gallery, all searched by the same probes,
+// cut into nch probe chunks.  Its work units are (limb, tile, block group of
+// the kernel's NB blocks, chunk), numbered in that order from first_unit; the
+// kernel decodes a unit index into them, so no per-unit table is built.
+struct BatchSeg {
+    uint32_t first_unit;
+    uint32_t first_chunk, nch;
+    uint32_t nbg;  // block groups: ceil((s1 - s0) / NB)
+    uint32_t s0, s1;
 };
-constexpr uint32_t UNIT_LAST_CHUNK = 1u << 31;
+// Plans range items into chunks and segments; *nunits receives the number of
+// work units (HERS_E_INVAL-worthy when it reaches 2^32 - 1: the caller checks).
 void plan_ranges(const RangeItem* items, uint32_t nitems, int np_max, int nb_max,
-                 std::vector<BatchChunk>& chunks, std::vector<BatchUnit>& units, uint32_t* ngroups);
+                 std::vector<BatchChunk>& chunks, std::vector<BatchSeg>& segs, uint32_t* ngroups,
+                 uint64_t* nunits);
 constexpr int DEFAULT_BATCH_VARIANT = 1;
 int batch_variant_count();
 int batch_variant_np(int v);
 int batch_variant_nb(int v);
-cudaError_t launch_batched(int v, const BatchChunk* d_chunks, const BatchUnit* d_units, uint32_t nunits,
-                           uint32_t* d_counter, uint64_t* X, int* err, int device, cudaStream_t st);
+cudaError_t launch_batched(int v, const BatchChunk* d_chunks, const BatchSeg* d_segs, uint32_t nsegs,
+                           uint32_t nunits, uint32_t* d_counter, uint64_t* X, int* err, int device, cudaStream_t st);
 
 // Kernel launches issued by this library in this process (all contexts).
 void count_launches(uint64_t n);

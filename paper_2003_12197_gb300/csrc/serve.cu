@@ -121,8 +121,8 @@ struct Slot {
     uint64_t off = 0, bytes = 0;
     std::vector<Request*> reqs;
     BatchChunk* h_chunks = nullptr;  // pinned staging of the work tables
-    BatchUnit* h_units = nullptr;
-    size_t cap_chunks = 0, cap_units = 0;
+    BatchSeg* h_segs = nullptr;
+    size_t cap_chunks = 0, cap_segs = 0;
     cudaEvent_t ev[3] = {};  // batch start, kernels done, copies done
 };
 
@@ -143,7 +143,7 @@ uint64_t request_words(uint32_t d, uint64_t nblocks) {
     return (uint64_t)d * (4 * N + RES_WORDS_PER_DIM) + nblocks * (SEARCH_WS_WORDS_PER_BLOCK + 4 * N);
 }
 
-bool ensure_staging(Slot* s, size_t nchunks, size_t nunits) {
+bool ensure_staging(Slot* s, size_t nchunks, size_t nsegs) {
     if (nchunks > s->cap_chunks) {
         if (s->h_chunks) cudaFreeHost(s->h_chunks);
         s->cap_chunks = std::max(nchunks, 2 * s->cap_chunks);
@@ -153,12 +153,12 @@ bool ensure_staging(Slot* s, size_t nchunks, size_t nunits) {
             return false;
         }
     }
-    if (nunits > s->cap_units) {
-        if (s->h_units) cudaFreeHost(s->h_units);
-        s->cap_units = std::max(nunits, 2 * s->cap_units);
-        if (cudaMallocHost(&s->h_units, s->cap_units * sizeof(BatchUnit)) != cudaSuccess) {
-            s->h_units = nullptr;
-            s->cap_units = 0;
+    if (nsegs > s->cap_segs) {
+        if (s->h_segs) cudaFreeHost(s->h_segs);
+        s->cap_segs = std::max(nsegs, 2 * s->cap_segs);
+        if (cudaMallocHost(&s->h_segs, s->cap_segs * sizeof(BatchSeg)) != cudaSuccess) {
+            s->h_segs = nullptr;
+            s->cap_segs = 0;
             return false;
         }
     }
@@ -168,7 +168,7 @@ bool ensure_staging(Slot* s, size_t nchunks, size_t nunits) {
 // Plans and issues one batch on slot s (called by the scheduler thread with
 // the requests already removed from the queue; the lock is not held).
 cudaError_t issue_batch(hers_server* srv, Slot* s, std::vector<BatchChunk>& chunks,
-                        std::vector<BatchUnit>& units, const std::vector<RangeItem>& items,
+                        std::vector<BatchSeg>& segs, uint64_t nunits, const std::vector<RangeItem>& items,
                         uint64_t npairs) {
     hers_ctx* ctx = srv->ctx;
     cudaStream_t st = srv->streams[s->index];
@@ -187,8 +187,8 @@ cudaError_t issue_batch(hers_server* srv, Slot* s, std::vector<BatchChunk>& chun
     uint64_t* OUT = KS + npairs * 4 * N;
     uint8_t* tb = (uint8_t*)(OUT + npairs * 4 * N);
     BatchChunk* d_chunks = (BatchChunk*)tb;
-    BatchUnit* d_units = (BatchUnit*)(tb + (chunks.size() * sizeof(BatchChunk) + ALIGN - 1) / ALIGN * ALIGN);
-    uint32_t* d_counter = (uint32_t*)((uint8_t*)d_units + (units.size() * sizeof(BatchUnit) + ALIGN - 1) / ALIGN * ALIGN);
+    BatchSeg* d_segs = (BatchSeg*)(tb + (chunks.size() * sizeof(BatchChunk) + ALIGN - 1) / ALIGN * ALIGN);
+    uint32_t* d_counter = (uint32_t*)((uint8_t*)d_segs + (segs.size() * sizeof(BatchSeg) + ALIGN - 1) / ALIGN * ALIGN);
 
     cudaError_t e = cudaEventRecord(s->ev[0], st);
     for (size_t i = 0; i < s->reqs.size() && e == cudaSuccess; i++) {
@@ -203,13 +203,13 @@ cudaError_t issue_batch(hers_server* srv, Slot* s, std::vector<BatchChunk>& chun
             for (size_t i = 0; i < items.size(); i++)
                 if (ch.probe[q] == items[i].probe) ch.probe[q] = pct[i] + (uint64_t)items[i].d * 4 * N;
     std::copy(chunks.begin(), chunks.end(), s->h_chunks);
-    std::copy(units.begin(), units.end(), s->h_units);
+    std::copy(segs.begin(), segs.end(), s->h_segs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_chunks, s->h_chunks, chunks.size() * sizeof(BatchChunk), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_units, s->h_units, units.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(d_segs, s->h_segs, segs.size() * sizeof(BatchSeg), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = launch_batched(srv->variant, d_chunks, d_units, (uint32_t)units.size(), d_counter, X, ctx->err,
+        e = launch_batched(srv->variant, d_chunks, d_segs, (uint32_t)segs.size(), (uint32_t)nunits, d_counter, X, ctx->err,
                            ctx->device, st);
     if (e == cudaSuccess)
         e = launch_epilogue(ctx->tw, srv->keys->k, npairs, X, C, KS, OUT, st, nullptr, nullptr, ctx->epi_variant);
@@ -265,14 +265,15 @@ void scheduler(hers_server* srv) {
             // admit from the head of the queue while the batch fits in the pool
             size_t take = std::min<size_t>(srv->pending.size(), srv->max_batch);
             std::vector<BatchChunk> chunks;
-            std::vector<BatchUnit> units;
+            std::vector<BatchSeg> segs;
+            uint64_t nunits = 0;
             std::vector<RangeItem> items;
             uint64_t npairs = 0, off = 0, bytes = 0;
             bool got = false;
             while (take > 0) {
                 items.clear();
                 chunks.clear();
-                units.clear();
+                segs.clear();
                 npairs = 0;
                 uint64_t words = 0;
                 for (size_t i = 0; i < take; i++) {
@@ -285,9 +286,9 @@ void scheduler(hers_server* srv) {
                 }
                 uint32_t ng = 0;
                 plan_ranges(items.data(), (uint32_t)items.size(), batch_variant_np(srv->variant),
-                            batch_variant_nb(srv->variant), chunks, units, &ng);
+                            batch_variant_nb(srv->variant), chunks, segs, &ng, &nunits);
                 bytes = words * 8 + (chunks.size() * sizeof(BatchChunk) + ALIGN) +
-                        (units.size() * sizeof(BatchUnit) + ALIGN) + ALIGN;
+                        (segs.size() * sizeof(BatchSeg) + ALIGN) + ALIGN;
                 if (srv->pool.alloc(bytes, &off)) {
                     got = true;
                     break;
@@ -318,8 +319,9 @@ void scheduler(hers_server* srv) {
             lk.unlock();
             // probe placeholders (i + 1) -> item order; issue_batch maps them to prepared probes
             for (size_t i = 0; i < items.size(); i++) items[i].probe = (const uint64_t*)(uintptr_t)(i + 1);
-            cudaError_t e = ensure_staging(s, chunks.size(), units.size()) ? cudaSuccess : cudaErrorMemoryAllocation;
-            if (e == cudaSuccess) e = issue_batch(srv, s, chunks, units, items, npairs);
+            cudaError_t e = ensure_staging(s, chunks.size(), segs.size()) ? cudaSuccess : cudaErrorMemoryAllocation;
+            if (e == cudaSuccess && nunits >= 0xFFFFFFFFull) e = cudaErrorInvalidValue;
+            if (e == cudaSuccess) e = issue_batch(srv, s, chunks, segs, nunits, items, npairs);
             lk.lock();
             srv->t_plan_ms += std::chrono::duration<double, std::milli>(Clock::now() - t_plan0).count();
             if (e != cudaSuccess) {
@@ -485,7 +487,7 @@ int hers_server_free(hers_server* srv) {
         cudaStreamDestroy(srv->streams[i]);
         if (srv->slots[i]) {
             if (srv->slots[i]->h_chunks) cudaFreeHost(srv->slots[i]->h_chunks);
-            if (srv->slots[i]->h_units) cudaFreeHost(srv->slots[i]->h_units);
+            if (srv->slots[i]->h_segs) cudaFreeHost(srv->slots[i]->h_segs);
             for (int k = 0; k < 3; k++)
                 if (srv->slots[i]->ev[k]) cudaEventDestroy(srv->slots[i]->ev[k]);
             delete srv->slots[i];

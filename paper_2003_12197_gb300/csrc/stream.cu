@@ -10,10 +10,11 @@
 //   3. one persistent batched tensor launch with every probe;
 //   4. the epilogue;
 //   5. the score ciphertexts are copied into their [probe][block] places.
-// Two chunk slots alternate.  Three streams: the copies (a stream of their
-// own, so the copy engine runs ahead as soon as a staging buffer is free),
-// the extensions (the context's stream) and the searches (the caller's
-// stream).  Chunk c+1's copy and extension overlap chunk c's search.
+// Two chunk slots alternate, fed from a ring of NSTAGE staging buffers.
+// Three streams: the copies (a stream of their own, so the copy engine runs
+// up to NSTAGE chunks ahead as soon as a staging buffer is free), the
+// extensions (the context's stream) and the searches (the caller's stream).
+// Chunk c+1's copy and extension overlap chunk c's search.
 #include <algorithm>
 #include <vector>
 
@@ -25,16 +26,20 @@ using namespace hers;
 
 namespace {
 
+// Staging buffers for host chunks: the copy stream may run this many chunks
+// ahead of the extensions.
+constexpr int NSTAGE = 4;
+
 struct SlotLayout {
-    uint64_t staging, resident, X, C, KS, OUT, tables;  // word offsets in the slot
+    uint64_t resident, X, C, KS, OUT, tables;  // word offsets in the slot
     uint64_t words;
+    uint64_t staging_words;  // one staging buffer (after the two slots)
 };
 
 SlotLayout slot_layout(uint32_t d, uint32_t nprobes, uint32_t chunk, uint64_t table_bytes) {
     SlotLayout L;
     uint64_t w = 0;
-    L.staging = w;
-    w += (uint64_t)chunk * d * 4 * N;
+    L.staging_words = ((uint64_t)chunk * d * 4 * N + 31) / 32 * 32;
     L.resident = w;
     w += (uint64_t)chunk * d * RES_WORDS_PER_DIM;
     const uint64_t pairs = (uint64_t)nprobes * chunk;
@@ -53,9 +58,10 @@ SlotLayout slot_layout(uint32_t d, uint32_t nprobes, uint32_t chunk, uint64_t ta
 }
 
 uint64_t table_bytes_for(uint32_t nprobes, uint32_t chunk) {
-    // at most one chunk record per probe and one unit per (block, limb, tile, probe)
-    return (uint64_t)nprobes * sizeof(BatchChunk) + 256 +
-           (uint64_t)chunk * NUM_S * NTILES * nprobes * sizeof(BatchUnit) + 256 + 64;
+    // at most one chunk record per probe and one segment per chunk (every probe
+    // searches the whole chunk: one segment)
+    (void)chunk;
+    return (uint64_t)nprobes * sizeof(BatchChunk) + 256 + (uint64_t)nprobes * sizeof(BatchSeg) + 256 + 64;
 }
 
 }  // namespace
@@ -63,7 +69,8 @@ uint64_t table_bytes_for(uint32_t nprobes, uint32_t chunk) {
 extern "C" {
 
 uint64_t hers_search_stream_workspace_bytes(uint32_t d, uint32_t nprobes, uint32_t chunk_blocks) {
-    return 2 * slot_layout(d, nprobes, chunk_blocks, table_bytes_for(nprobes, chunk_blocks)).words * 8;
+    const SlotLayout L = slot_layout(d, nprobes, chunk_blocks, table_bytes_for(nprobes, chunk_blocks));
+    return (2 * L.words + NSTAGE * L.staging_words) * 8;
 }
 
 int hers_search_stream(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery_ct,
@@ -81,28 +88,32 @@ int hers_search_stream(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gal
         if (!probes[p]) return fail(ctx, HERS_E_INVAL, "hers_search_stream: probe %u is null", p);
     const uint64_t tbytes = table_bytes_for(nprobes, chunk_blocks);
     const SlotLayout L = slot_layout(d, nprobes, chunk_blocks, tbytes);
-    if (workspace_bytes < 2 * L.words * 8)
+    const uint64_t need = (2 * L.words + NSTAGE * L.staging_words) * 8;
+    if (workspace_bytes < need)
         return fail(ctx, HERS_E_NOMEM, "hers_search_stream: workspace %llu < %llu bytes",
-                    (unsigned long long)workspace_bytes, (unsigned long long)(2 * L.words * 8));
+                    (unsigned long long)workspace_bytes, (unsigned long long)need);
     DeviceGuard g(ctx->device);
     cudaStream_t sm = (cudaStream_t)stream, sc = ctx->stream;
     uint64_t* slot[2] = {(uint64_t*)workspace, (uint64_t*)workspace + L.words};
+    uint64_t* staging[NSTAGE];
+    for (int k = 0; k < NSTAGE; k++) staging[k] = (uint64_t*)workspace + 2 * L.words + k * L.staging_words;
     const int np_var = batch_variant_np(variant);
 
     // Work tables: the same plan for every full chunk, one copy per slot (the
     // tables point at the slot's resident buffer); the last chunk may be shorter.
-    auto plan = [&](int s, uint32_t nb, std::vector<BatchChunk>& ch, std::vector<BatchUnit>& un) {
+    auto plan = [&](int s, uint32_t nb, std::vector<BatchChunk>& ch, std::vector<BatchSeg>& un, uint64_t* nu) {
         std::vector<RangeItem> items(nprobes);
         for (uint32_t p = 0; p < nprobes; p++)
             items[p] = {slot[s] + L.resident, 0, nb, d, probes[p], (uint64_t)p * nb};
         uint32_t ng = 0;
-        plan_ranges(items.data(), nprobes, np_var, batch_variant_nb(variant), ch, un, &ng);
+        plan_ranges(items.data(), nprobes, np_var, batch_variant_nb(variant), ch, un, &ng, nu);
     };
     const uint64_t nchunks = (nblocks + chunk_blocks - 1) / chunk_blocks;
     const uint32_t last_nb = (uint32_t)(nblocks - (nchunks - 1) * chunk_blocks);
     struct Tables {
         BatchChunk* chunks;
-        BatchUnit* units;
+        BatchSeg* units;
+        uint32_t nsegs;
         uint32_t* counter;
         uint32_t nunits;
     };
@@ -111,30 +122,35 @@ int hers_search_stream(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gal
     // for the chunk it currently runs (re-uploaded when the size changes)
     Tables T[2][2];
     std::vector<BatchChunk> hc[2][2];
-    std::vector<BatchUnit> hu[2][2];
+    std::vector<BatchSeg> hu[2][2];
+    uint64_t nu[2][2] = {{0, 0}, {0, 0}};
     for (int s = 0; s < 2; s++) {
-        plan(s, chunk_blocks, hc[s][0], hu[s][0]);
-        plan(s, last_nb, hc[s][1], hu[s][1]);
+        plan(s, chunk_blocks, hc[s][0], hu[s][0], &nu[s][0]);
+        plan(s, last_nb, hc[s][1], hu[s][1], &nu[s][1]);
         for (int k = 0; k < 2; k++) {
             uint8_t* tb = (uint8_t*)(slot[s] + L.tables);
             T[s][k].chunks = (BatchChunk*)tb;
-            T[s][k].units = (BatchUnit*)(tb + (hc[s][k].size() * sizeof(BatchChunk) + 255) / 256 * 256);
+            T[s][k].units = (BatchSeg*)(tb + (hc[s][k].size() * sizeof(BatchChunk) + 255) / 256 * 256);
+            T[s][k].nsegs = (uint32_t)hu[s][k].size();
             T[s][k].counter = (uint32_t*)((uint8_t*)T[s][k].units +
-                                          (hu[s][k].size() * sizeof(BatchUnit) + 255) / 256 * 256);
-            T[s][k].nunits = (uint32_t)hu[s][k].size();
+                                          (hu[s][k].size() * sizeof(BatchSeg) + 255) / 256 * 256);
+            T[s][k].nunits = (uint32_t)nu[s][k];
         }
     }
 
-    // ev_copied[s]: slot s's staging holds its chunk; ev_ext[s]: its resident
-    // buffer and tables are ready (and its staging may be refilled);
-    // ev_free[s]: its resident buffer may be refilled
-    cudaEvent_t ev_copied[2], ev_ext[2], ev_free[2], ev_join, ev_join2;
+    // ev_copied[k]: staging k holds its chunk; ev_staged[k]: staging k has
+    // been extended from and may be refilled; ev_ext[s]: slot s's resident
+    // buffer and tables are ready; ev_free[s]: its resident buffer may be refilled
+    cudaEvent_t ev_copied[NSTAGE], ev_staged[NSTAGE], ev_ext[2], ev_free[2], ev_join, ev_join2;
     cudaStream_t scp = nullptr;  // the copies' stream (host galleries)
     cudaError_t e = cudaSuccess;
     for (int s = 0; s < 2 && e == cudaSuccess; s++) {
         e = cudaEventCreateWithFlags(&ev_ext[s], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_free[s], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_copied[s], cudaEventDisableTiming);
+    }
+    for (int k = 0; k < NSTAGE && e == cudaSuccess; k++) {
+        e = cudaEventCreateWithFlags(&ev_copied[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_staged[k], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_join2, cudaEventDisableTiming);
@@ -154,23 +170,25 @@ int hers_search_stream(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gal
         uint64_t* base = slot[s];
         const uint64_t* src = gallery_ct + b0 * d * 4 * N;
         const uint64_t* cts = src;
+        const int k = (int)(c % NSTAGE);
         if (gallery_on_host) {
-            // copy stream: wait until the slot's staging has been extended from
-            if (c >= 2) cudaStreamWaitEvent(scp, ev_ext[s], 0);
-            e = cudaMemcpyAsync(base + L.staging, src, (uint64_t)nb * d * 4 * N * 8, cudaMemcpyHostToDevice, scp);
-            if (e == cudaSuccess) e = cudaEventRecord(ev_copied[s], scp);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, ev_copied[s], 0);
-            cts = base + L.staging;
+            // copy stream: wait until staging k has been extended from
+            if (c >= NSTAGE) cudaStreamWaitEvent(scp, ev_staged[k], 0);
+            e = cudaMemcpyAsync(staging[k], src, (uint64_t)nb * d * 4 * N * 8, cudaMemcpyHostToDevice, scp);
+            if (e == cudaSuccess) e = cudaEventRecord(ev_copied[k], scp);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, ev_copied[k], 0);
+            cts = staging[k];
         }
         // side stream: wait until the slot's previous chunk has been searched
         if (c >= 2) cudaStreamWaitEvent(sc, ev_free[s], 0);
         if (e == cudaSuccess) e = launch_extend_ntt(ctx->tw, cts, (uint64_t)nb * d, 0, d, base + L.resident, sc);
+        if (e == cudaSuccess && gallery_on_host) e = cudaEventRecord(ev_staged[k], sc);
         if (e == cudaSuccess && table_kind[s] != kind) {
             const Tables& t = T[s][kind];
             e = cudaMemcpyAsync(t.chunks, hc[s][kind].data(), hc[s][kind].size() * sizeof(BatchChunk),
                                 cudaMemcpyHostToDevice, sc);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(t.units, hu[s][kind].data(), hu[s][kind].size() * sizeof(BatchUnit),
+                e = cudaMemcpyAsync(t.units, hu[s][kind].data(), hu[s][kind].size() * sizeof(BatchSeg),
                                     cudaMemcpyHostToDevice, sc);
             table_kind[s] = kind;  // a pageable source is staged before cudaMemcpyAsync returns
         }
@@ -180,7 +198,7 @@ int hers_search_stream(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gal
         const Tables& t = T[s][kind];
         const uint64_t npairs = (uint64_t)nprobes * nb;
         if (e == cudaSuccess)
-            e = launch_batched(variant, t.chunks, t.units, t.nunits, t.counter, base + L.X, ctx->err,
+            e = launch_batched(variant, t.chunks, t.units, t.nsegs, t.nunits, t.counter, base + L.X, ctx->err,
                                ctx->device, sm);
         cudaEventRecord(ev_free[s], sm);  // the resident chunk buffer may be refilled
         if (e == cudaSuccess)
@@ -202,7 +220,10 @@ int hers_search_stream(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gal
     for (int s = 0; s < 2; s++) {
         cudaEventDestroy(ev_ext[s]);
         cudaEventDestroy(ev_free[s]);
-        cudaEventDestroy(ev_copied[s]);
+    }
+    for (int k = 0; k < NSTAGE; k++) {
+        cudaEventDestroy(ev_copied[k]);
+        cudaEventDestroy(ev_staged[k]);
     }
     cudaEventDestroy(ev_join);
     cudaEventDestroy(ev_join2);
