@@ -440,7 +440,9 @@ def run_gpu(args):
     # cost a tenth of the host-buffer rate.)
     tnames, enames = H.hers_tensor_variants(), H.hers_epilogue_variants()
     t_cands = [variant] if args.variant else sorted(
-        {variant} | {i for i, n in enumerate(tnames) if n.endswith("_m1")})
+        {variant} | {i for i, n in enumerate(tnames) if n.endswith("_m1") or n.endswith("_ka")})
+    # (the one-CTA-per-SM and Karatsuba shapes, the persistent "pnb" ones among them,
+    # leave SM resources that the other search's epilogue can use)
     combos = {}
     for tv in ([] if args.no_select else t_cands):
         H.hers_set_tensor_variant(ctx, tv)
@@ -585,10 +587,11 @@ def run_gpu(args):
     achieved_if = alg_bytes / t_tensor_if / 1e9 if t_tensor_if > 0 else 0.0
     # the same launch against the canonical-ciphertext minimum (32 d bytes per
     # entry: the gallery as the client encrypted it) and against the measured
-    # rate of the 32x32->64 multiply-adds it performs (4 per dimension,
-    # coefficient, search prime and block)
+    # rate of the 32x32->64 multiply-adds it performs
     canon_bytes = nb * d * 4 * N * 8
-    madw = 4 * d * N * search_limbs() * nb
+    # multiply-adds per (dimension, coefficient, limb, block): 3 in the Karatsuba
+    # shapes ("_ka"), 4 in the others
+    madw = (3 if variant_name.endswith("_ka") else 4) * d * N * search_limbs() * nb
     imad_rate = H.hers_probe_int_pipe(local)["imad_wide_u32"]
     # DRAM traffic of the same kernel shape from a committed ncu capture, scaled
     # to this launch by blocks (null when no capture matches the current shape)
@@ -635,7 +638,8 @@ def run_gpu(args):
                          "step_ms_in_flight": epi_inflight,
                          "note": "tensor shape (timed alone above), epilogue form and stream priority "
                                  "order are chosen together by the step time with searches in flight"},
-            "roofline": {"kernel": f"k_tensor<{variant_name}> (tensor-product accumulate over d)",
+            "roofline": {"kernel": f"{'k_tensor_persist' if variant_name.startswith('pnb') else 'k_tensor'}"
+                                   f"<{variant_name}> (tensor-product accumulate over d)",
                          "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": f"{peak_src} hbm_gbs",
@@ -901,7 +905,7 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
                    variant=H.hers_batch_variants().index(sv_name))
     # pinned host arena for score ciphertexts, handed out as a ring
     arena_blocks = 4 * nblocks * 16
-    arena = host_buffer(arena_blocks * 4 * N, host_alloc, dev).view(arena_blocks, 4 * N)
+    arena = host_buffer(arena_blocks * 4 * N, host_alloc, dev, d2h=True).view(arena_blocks, 4 * N)
     # the rate of a device -> arena copy (2 GiB), as the server's copy-outs see it
     probe_n = min(arena.numel(), (2 << 30) // 8)
     src = torch.empty(probe_n, dtype=torch.int64, device=dev)
@@ -918,7 +922,29 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
                  "arena_d2h_gbs": probe_n * 8 / (arena_ms / 1e3) / 1e9,
                  "arena_d2h_gbs_per_2gib_slice": copy_rate_slices(arena, dev, probe_n, h2d=False),
                  "host_alloc": host_alloc,
-                 "host_mem_available_gb": host_mem_available() / 1e9}
+                 "host_mem_available_gb": host_mem_available() / 1e9,
+                 "arena_numa_pages": numa_pages(arena.data_ptr()),
+                 "gpu_numa_node": gpu_numa_node(dev),
+                 "cpus_allowed": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None}
+    if host_alloc == "register" and HOST_BUF_LOG:
+        host_diag["arena_buffer"] = HOST_BUF_LOG[-1]
+        host_diag["arena_anon_huge_kb"] = smaps_field(arena.data_ptr())
+    # the ring uses the arena's slices that copy at no less than half the best
+    # slice's rate (a few GB of a large page-locked buffer can copy 10-40x
+    # slower); runs of such slices at least one largest request long
+    rates_s = host_diag["arena_d2h_gbs_per_2gib_slice"]
+    per_slice = probe_n // (4 * N)
+    segs, run0 = [], None
+    for i, r in enumerate(rates_s + [0.0]):
+        if i < len(rates_s) and r >= 0.5 * max(rates_s):
+            run0 = i if run0 is None else run0
+        elif run0 is not None:
+            segs.append((run0 * per_slice, min(i * per_slice, arena_blocks)))
+            run0 = None
+    segs = [g for g in segs if g[1] - g[0] >= nblocks] or [(0, arena_blocks)]
+    ring = SlotRing(segs)
+    host_diag["ring_gb"] = round(sum(b - a for a, b in segs) * 4 * N * 8 / 1e9, 1)
+    host_diag["ring_segments"] = segs
     # sampled requests (up to SAMPLE per rate, at most SAMPLE_MAX_BLOCKS blocks
     # each) write to buffers of their own, kept for the mix-vs-alone check
     SAMPLE, SAMPLE_MAX_BLOCKS = 4, 600
@@ -931,7 +957,7 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
     warm = W.serving_requests(10000.0, 1.0, 16, nblocks, dims, seed=7)
     wids = []
     for wi, (_, gi, b0, b1) in enumerate(warm):
-        o = (wi * nblocks) % max(1, arena_blocks - nblocks)
+        o = ring.place(b1 - b0)
         wids.append(srv.submit(gi, b0, b1, probes[gi][wi % 8], arena[o: o + (b1 - b0)]))
     for rid in wids:
         if srv.wait(rid, 600000)[0] != 0:
@@ -944,7 +970,7 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
     for ri, rate in enumerate(rates):
         tm0 = srv.timing()
         reqs = W.serving_requests(rate, window, max_requests, nblocks, dims, seed=int(rate))
-        outstanding, lat, pos = [], [], 0
+        outstanding, lat = [], []
         entries = 0
         stride = max(1, len(reqs) // SAMPLE)
         t_start = time.perf_counter()
@@ -975,20 +1001,18 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
                 out = buf[:nb]
                 sampled.append((gi, b0, b1, pi, buf))
                 nsampled += 1
-                ring = None
+                slot = None
             else:
-                if pos + nb > arena_blocks:
-                    pos = 0
+                pos = ring.place(nb)
                 # the ring slot must be free of outstanding requests' buffers
                 while outstanding and any(o[3] is not None and not (pos + nb <= o[3] or o[3] + o[4] <= pos)
                                           for o in outstanding):
                     reap_oldest(600000)
                 out = arena[pos: pos + nb]
-                ring = pos
-                pos += nb
+                slot = pos
             submit_t = time.perf_counter() - t_start
             rid = srv.submit(gi, b0, b1, probes[gi][pi], out)
-            outstanding.append((rid, t_arr, submit_t, ring, nb))
+            outstanding.append((rid, t_arr, submit_t, slot, nb))
             entries += nb * N
             while outstanding and reap_oldest(0):
                 pass
@@ -1009,6 +1033,9 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
     busy = sorted(((cpu1[k] - cpu0.get(k, 0.0), k[1]) for k in cpu1), reverse=True)[:6]
     host_diag["threads_cpu_s"] = [[n, round(v, 2)] for v, n in busy]
     host_diag["host_memcpy_gbs_after"] = host_memcpy_gbs()
+    # the arena's copy rates again: whether its pages slowed down during the run
+    host_diag["arena_d2h_gbs_per_2gib_slice_after"] = copy_rate_slices(arena, dev, probe_n, h2d=False)
+    host_diag["arena_numa_pages_after"] = numa_pages(arena.data_ptr())
     host_diag["wall_s"] = round(wall1 - wall0, 2)
     host_diag["nthreads"] = len(cpu1)
     launches = H.hers_kernel_launches() - launches0
@@ -1097,15 +1124,16 @@ _HOST_BUFS = []  # host mappings kept alive (and registered with CUDA) until exi
 HOST_BUF_LOG = []  # what host_buffer() did, for the JSON line
 
 
-def host_buffer(nwords, mode, dev=None):
+def host_buffer(nwords, mode, dev=None, d2h=False):
     """An int64 CPU tensor of nwords that CUDA copies treat as page-locked.
     mode "torch": torch's pinned allocator (cudaHostAlloc).  mode "register":
     an anonymous mapping advised to transparent huge pages, touched, then
     registered with cudaHostRegister, so the pages are large and resident
     before the GPU maps them.  With dev, every 4 GiB slice is then copied to
-    the device once; a slice at under half the median rate has its pages
-    dropped and faulted in afresh (at most 3 rounds), since some regions of
-    very large page-locked buffers copied 8-40x slower than the rest."""
+    the device once (and, with d2h, from the device as well); a slice at
+    under half the median rate in either direction has its pages dropped and
+    faulted in afresh (at most 3 rounds), since some regions of very large
+    page-locked buffers copied 8-40x slower than the rest."""
     import torch
     if mode == "torch":
         return torch.empty(nwords, dtype=torch.int64, pin_memory=True)
@@ -1136,8 +1164,14 @@ def host_buffer(nwords, mode, dev=None):
         for _ in range(3):
             rates = copy_rate_slices(t, dev, span)
             med = sorted(rates)[len(rates) // 2]
-            slow = [i for i, r in enumerate(rates) if r < 0.5 * med]
+            slow = {i for i, r in enumerate(rates) if r < 0.5 * med}
             log.setdefault("slice_gbs_first", rates)
+            if d2h:
+                rates_o = copy_rate_slices(t, dev, span, h2d=False)
+                med_o = sorted(rates_o)[len(rates_o) // 2]
+                slow |= {i for i, r in enumerate(rates_o) if r < 0.5 * med_o}
+                log.setdefault("slice_d2h_gbs_first", rates_o)
+            slow = sorted(slow)
             if not slow:
                 break
             rt.cudaHostUnregister(ptr)
@@ -1184,6 +1218,61 @@ def copy_rate_slices(host, dev, span_words, h2d=True):
         out.append(round(n_ * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9, 1))
     del buf
     return out
+
+
+def numa_pages(addr):
+    """Pages per NUMA node of the host mapping that starts at addr, from
+    /proc/self/numa_maps ({} where the file or the mapping is missing)."""
+    try:
+        for line in open("/proc/self/numa_maps"):
+            f = line.split()
+            if f and int(f[0], 16) == addr:
+                return {k: int(v) for k, v in (x.split("=", 1) for x in f[2:] if x[:1] == "N" and "=" in x)}
+    except (OSError, ValueError):
+        pass
+    return {}
+
+
+def smaps_field(addr, field="AnonHugePages"):
+    """A kB field of /proc/self/smaps for the mapping that starts at addr."""
+    try:
+        hit = False
+        for line in open("/proc/self/smaps"):
+            head = line.split(None, 1)[0]
+            if "-" in head and ":" not in head:
+                hit = int(head.split("-")[0], 16) == addr
+            elif hit and line.startswith(field + ":"):
+                return int(line.split()[1])
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+class SlotRing:
+    """Hands out contiguous block ranges of the score arena in ring order,
+    inside the given segments [(first block, end block)] only."""
+
+    def __init__(self, segs):
+        self.segs, self.i, self.pos = segs, 0, segs[0][0]
+
+    def place(self, nb):
+        if self.pos + nb > self.segs[self.i][1]:
+            self.i = (self.i + 1) % len(self.segs)
+            self.pos = self.segs[self.i][0]
+        p = self.pos
+        self.pos += nb
+        return p
+
+
+def gpu_numa_node(dev):
+    """The NUMA node sysfs gives for the GPU's PCI function (None if unknown)."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        return int(open(f"/sys/bus/pci/devices/{bus}/numa_node").read())
+    except (AttributeError, OSError, ValueError):
+        return None
 
 
 def host_memcpy_gbs(nbytes=1 << 30):

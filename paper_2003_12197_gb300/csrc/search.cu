@@ -40,7 +40,16 @@ namespace hers {
 // T0, T2 every 2 PFOLD, so every sum stays below 2^63 (2^61 + 2^32 + 8 2^59
 // and 2^61 + 2^32 + 16 2^58); the last dimension ends with a full reduction
 // mod r_l.  A wait that runs out (WAIT_NS, 2 s) sets bit 2 of *err.
+//
+// KA (Karatsuba's middle term): three products per (dimension, coefficient,
+// limb, block) instead of four, T0 += a0 b0, T2 += a1 b1 and
+// S += (a0 + a1)(b0 + b1), with T1 = S - T0 - T2 formed mod r_l at the end.
+// The sums a0 + a1 and b0 + b1 are below 2^30, their product below 2^60, so S
+// is folded every KFOLD_S = 4 dimensions (2^61 + 2^32 + 4 2^60 < 2^63) and
+// T0, T2 every KFOLD_02 = 16.  The kernel stays bound by HBM either way; the
+// multiply pipe it leaves free is what an epilogue running beside it uses.
 constexpr int PFOLD = 8;
+constexpr int KFOLD_S = 4, KFOLD_02 = 16;
 
 __device__ __forceinline__ void madw(int64_t& acc, int32_t a, int32_t b) {
     asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
@@ -49,19 +58,25 @@ __device__ __forceinline__ void madw(int64_t& acc, int32_t a, int32_t b) {
 // One stage's products: for dd < nd and block j < nb, the four products of
 // the probe row and gallery row j.  With FULL (nd = DPS, nb = NB) the loops
 // carry no predicates.
-template <int NB, int DPS, int RUN, bool FULL>
+// With KA, s[j][1] holds S and the three products above replace the four.
+template <int NB, int DPS, int RUN, bool FULL, bool KA>
 __device__ __forceinline__ void tensor_stage(int64_t (&s)[NB][3], const int2* base, uint32_t nd, int nb) {
 #pragma unroll
     for (int dd = 0; dd < DPS; dd++) {
         if (FULL || (uint32_t)dd < nd) {
             const int2 A = base[dd * TILE];
+            const int32_t as = A.x + A.y;
 #pragma unroll
             for (int j = 0; j < NB; j++) {
                 if (FULL || j < nb) {
                     const int2 G = base[(1 + j) * (RUN / 2) + dd * TILE];
                     madw(s[j][0], A.x, G.x);
-                    madw(s[j][1], A.x, G.y);
-                    madw(s[j][1], A.y, G.x);
+                    if (KA) {
+                        madw(s[j][1], as, G.x + G.y);
+                    } else {
+                        madw(s[j][1], A.x, G.y);
+                        madw(s[j][1], A.y, G.x);
+                    }
                     madw(s[j][2], A.y, G.y);
                 }
             }
@@ -74,11 +89,11 @@ __device__ __forceinline__ void tensor_stage(int64_t (&s)[NB][3], const int2* ba
 // it stays in L2 when the whole probe (d x 256 KiB) does not fit; otherwise
 // tiles vary fastest (x = tile, y = limb, z = group) and the CTAs in flight
 // read neighbouring runs of one block.
-template <int NB, int STAGES, int DPS, int MINB, bool GORDER>
+template <int NB, int STAGES, int DPS, int MINB, bool GORDER, bool KA = false>
 __global__ void __launch_bounds__(TILE + 32, MINB)
     k_tensor(const int32_t* __restrict__ gal, const int32_t* __restrict__ probe,
              uint32_t* __restrict__ acc, uint64_t nblocks, uint32_t d, int* err) {
-    static_assert(PFOLD % DPS == 0, "stages must not straddle a partial fold");
+    static_assert((KA ? KFOLD_S : PFOLD) % DPS == 0, "stages must not straddle a partial fold");
     extern __shared__ __align__(128) int32_t smr[];
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
     constexpr int RUN = DPS * 2 * TILE;         // elements of one run per stage
@@ -148,12 +163,13 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
             }
             const uint32_t nd = min((uint32_t)DPS, d - si * DPS);
             const int2* base = (const int2*)(smr + st * STAGE_ELEMS) + t;  // (poly 0, poly 1) pairs
-            if (nd == DPS && nb == NB) tensor_stage<NB, DPS, RUN, true>(s, base, nd, nb);
-            else tensor_stage<NB, DPS, RUN, false>(s, base, nd, nb);
+            if (nd == DPS && nb == NB) tensor_stage<NB, DPS, RUN, true, KA>(s, base, nd, nb);
+            else tensor_stage<NB, DPS, RUN, false, KA>(s, base, nd, nb);
             mbar_arrive(&empty[st]);
             const uint32_t done = si * DPS + nd;
-            if (done % PFOLD == 0 && done < d) {
-                const bool all = done % (2 * PFOLD) == 0;
+            constexpr uint32_t F1 = KA ? KFOLD_S : PFOLD, F02 = KA ? KFOLD_02 : 2 * PFOLD;
+            if (done % F1 == 0 && done < d) {
+                const bool all = done % F02 == 0;
 #pragma unroll
                 for (int j = 0; j < NB; j++) {
                     s[j][1] = pfold(s[j][1], r32);
@@ -168,9 +184,141 @@ __global__ void __launch_bounds__(TILE + 32, MINB)
     const int k = tile * TILE + t;
 #pragma unroll
     for (int j = 0; j < NB; j++)
-        if (j < nb)
+        if (j < nb) {
+            if (KA) {
+                const uint32_t r = c_smod[l];
+                const uint32_t x0 = fold_full(s[j][0], l), x2 = fold_full(s[j][2], l);
+                const uint32_t x1 = csub32(csub32(fold_full(s[j][1], l) + 2 * r - x0 - x2, 2 * r), r);
+                acc[(((b0 + j) * 3 + 0) * NUM_S + l) * N + k] = x0;
+                acc[(((b0 + j) * 3 + 1) * NUM_S + l) * N + k] = x1;
+                acc[(((b0 + j) * 3 + 2) * NUM_S + l) * N + k] = x2;
+            } else {
 #pragma unroll
-            for (int c = 0; c < 3; c++) acc[(((b0 + j) * 3 + c) * NUM_S + l) * N + k] = fold_full(s[j][c], l);
+                for (int c = 0; c < 3; c++) acc[(((b0 + j) * 3 + c) * NUM_S + l) * N + k] = fold_full(s[j][c], l);
+            }
+        }
+}
+
+// The same products as a persistent kernel: a grid of K CTAs per SM, CTA b
+// taking units b, b + grid, b + 2 grid, ... of the (limb, tile, block group)
+// units, block groups fastest (the CTAs in flight share a (limb, tile) run of
+// the probe).  Producer and consumers derive the same unit sequence from the
+// CTA index, so no tables or descriptors are exchanged, and the ring of
+// stages runs on across units (stage counter G: slot G % STAGES, phase
+// (G / STAGES) & 1).  The CTAs stay resident for the whole launch, so a
+// kernel of another stream (the epilogue of the search in flight beside it)
+// gets the registers and shared memory the K CTAs leave on each SM, and
+// never displaces the streaming CTAs.
+template <int NB, int STAGES, int DPS, int MINB, bool KA>
+__global__ void __launch_bounds__(TILE + 32, MINB)
+    k_tensor_persist(const int32_t* __restrict__ gal, const int32_t* __restrict__ probe,
+                     uint32_t* __restrict__ acc, uint64_t nblocks, uint32_t d, int* err) {
+    static_assert((KA ? KFOLD_S : PFOLD) % DPS == 0, "stages must not straddle a partial fold");
+    extern __shared__ __align__(128) int32_t smr[];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+    constexpr int RUN = DPS * 2 * TILE;
+    constexpr int STAGE_ELEMS = (1 + NB) * RUN;
+    const uint64_t ngroups = (nblocks + NB - 1) / NB;
+    const uint64_t nunits = ngroups * NUM_S * NTILES;
+    const uint32_t nst = (d + DPS - 1) / DPS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], TILE);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    if (warp == TILE / 32) {  // producer warp
+        if (lane == 0) {
+            const uint64_t pol_g = policy_evict_first(), pol_p = policy_evict_last();
+            const size_t gstride = (size_t)NUM_S * 2 * d * N;
+            uint32_t G = 0;
+            bool failed = false;
+            for (uint64_t u = blockIdx.x; u < nunits && !failed; u += gridDim.x) {
+                const uint64_t b0 = (u % ngroups) * NB;
+                const uint32_t lt = (uint32_t)(u / ngroups);
+                const int tile = (int)(lt % NTILES), l = (int)(lt / NTILES);
+                const int nb = (int)((nblocks - b0) < (uint64_t)NB ? (nblocks - b0) : NB);
+                const int32_t* pr = probe + resident_offset(0, l, tile * TILE, d, 0, 0);
+                const int32_t* gr = gal + resident_offset(b0, l, tile * TILE, d, 0, 0);
+                for (uint32_t si = 0; si < nst; si++, G++) {
+                    const int st = (int)(G % STAGES);
+                    if (G >= STAGES && !mbar_wait(&empty[st], ((G / STAGES) + 1) & 1)) {
+                        atomicOr(err, 2);
+                        failed = true;
+                        break;
+                    }
+                    const uint32_t nd = min((uint32_t)DPS, d - si * DPS);
+                    const uint32_t bytes = nd * 2 * TILE * 4;
+                    int32_t* dst = smr + (size_t)st * STAGE_ELEMS;
+                    mbar_expect_tx(&full[st], bytes * (uint32_t)(1 + nb));
+                    bulk_g2s(dst, pr + (size_t)si * RUN, bytes, &full[st], pol_p);
+                    for (int j = 0; j < nb; j++)
+                        bulk_g2s(dst + (1 + j) * RUN, gr + j * gstride + (size_t)si * RUN, bytes, &full[st],
+                                 pol_g);
+                }
+            }
+            // drain: the last stages' copies land before this thread leaves
+            for (uint32_t i = G > STAGES ? G - STAGES : 0; i < G; i++)
+                if (!mbar_wait(&full[i % STAGES], (i / STAGES) & 1)) atomicOr(err, 2);
+        }
+        return;
+    }
+
+    const int t = threadIdx.x;
+    uint32_t G = 0;
+    for (uint64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const uint64_t b0 = (u % ngroups) * NB;
+        const uint32_t lt = (uint32_t)(u / ngroups);
+        const int tile = (int)(lt % NTILES), l = (int)(lt / NTILES);
+        const int nb = (int)((nblocks - b0) < (uint64_t)NB ? (nblocks - b0) : NB);
+        const int32_t r32 = (int32_t)c_sr32[l];
+        int64_t s[NB][3];
+#pragma unroll
+        for (int j = 0; j < NB; j++) s[j][0] = s[j][1] = s[j][2] = 0;
+        for (uint32_t si = 0; si < nst; si++, G++) {
+            const int st = (int)(G % STAGES);
+            if (!mbar_wait(&full[st], (G / STAGES) & 1)) {
+                atomicOr(err, 2);
+                return;
+            }
+            const uint32_t nd = min((uint32_t)DPS, d - si * DPS);
+            const int2* base = (const int2*)(smr + st * STAGE_ELEMS) + t;
+            if (nd == DPS && nb == NB) tensor_stage<NB, DPS, RUN, true, KA>(s, base, nd, nb);
+            else tensor_stage<NB, DPS, RUN, false, KA>(s, base, nd, nb);
+            mbar_arrive(&empty[st]);
+            const uint32_t done = si * DPS + nd;
+            constexpr uint32_t F1 = KA ? KFOLD_S : PFOLD, F02 = KA ? KFOLD_02 : 2 * PFOLD;
+            if (done % F1 == 0 && done < d) {
+                const bool all = done % F02 == 0;
+#pragma unroll
+                for (int j = 0; j < NB; j++) {
+                    s[j][1] = pfold(s[j][1], r32);
+                    if (all) {
+                        s[j][0] = pfold(s[j][0], r32);
+                        s[j][2] = pfold(s[j][2], r32);
+                    }
+                }
+            }
+        }
+        const int k = tile * TILE + t;
+#pragma unroll
+        for (int j = 0; j < NB; j++)
+            if (j < nb) {
+                uint32_t x0 = fold_full(s[j][0], l), x1 = fold_full(s[j][1], l), x2 = fold_full(s[j][2], l);
+                if (KA) {
+                    const uint32_t r = c_smod[l];
+                    x1 = csub32(csub32(x1 + 2 * r - x0 - x2, 2 * r), r);
+                }
+                acc[(((b0 + j) * 3 + 0) * NUM_S + l) * N + k] = x0;
+                acc[(((b0 + j) * 3 + 1) * NUM_S + l) * N + k] = x1;
+                acc[(((b0 + j) * 3 + 2) * NUM_S + l) * N + k] = x2;
+            }
+    }
 }
 
 // The variants the autotuner chooses from: (blocks per CTA, pipeline stages,
@@ -181,11 +329,18 @@ struct TensorVariant {
     TensorFn fn;
     int nb, stages, dps;
     bool gorder;
+    int persist;  // > 0: k_tensor_persist with this many CTAs per SM
 };
 // name: nb<blocks per CTA>_s<stages>_d<dimensions per stage>_m<CTAs/SM>, and
 // a leading "g" for the group-fastest grid order
 #define HERS_TV(NB, S, D, M) {"nb" #NB "_s" #S "_d" #D "_m" #M, k_tensor<NB, S, D, M, false>, NB, S, D, false}
 #define HERS_TVG(NB, S, D, M) {"gnb" #NB "_s" #S "_d" #D "_m" #M, k_tensor<NB, S, D, M, true>, NB, S, D, true}
+// the Karatsuba form (KA) of the same shapes: a trailing "_ka"
+#define HERS_TVK(NB, S, D, M, GO, PFX) \
+    {PFX "nb" #NB "_s" #S "_d" #D "_m" #M "_ka", k_tensor<NB, S, D, M, GO, true>, NB, S, D, GO}
+// persistent Karatsuba form, K CTAs per SM: "pnb<NB>_s<S>_d<D>_k<K>_ka"
+#define HERS_TVP(NB, S, D, K) \
+    {"pnb" #NB "_s" #S "_d" #D "_k" #K "_ka", k_tensor_persist<NB, S, D, K, true>, NB, S, D, false, K}
 static const TensorVariant kTensorVariants[] = {
     HERS_TV(2, 4, 4, 2),  HERS_TV(2, 3, 4, 3),  HERS_TV(2, 2, 8, 2),  HERS_TV(1, 4, 4, 3),
     HERS_TV(4, 2, 4, 2),  HERS_TV(2, 4, 2, 3),  HERS_TV(2, 2, 4, 4),  HERS_TV(1, 2, 8, 3),
@@ -193,9 +348,15 @@ static const TensorVariant kTensorVariants[] = {
     // one CTA per SM with a deep ring: an SM keeps registers and shared memory
     // for CTAs of another search's epilogue running beside it
     HERS_TV(2, 6, 4, 1),  HERS_TV(2, 8, 4, 1),  HERS_TV(4, 4, 4, 1),
+    HERS_TVK(2, 3, 4, 3, true, "g"), HERS_TVK(2, 4, 4, 2, true, "g"), HERS_TVK(1, 4, 4, 3, true, "g"),
+    HERS_TVK(2, 3, 4, 3, false, ""), HERS_TVK(2, 4, 4, 2, false, ""), HERS_TVK(2, 4, 2, 3, false, ""),
+    HERS_TVP(2, 3, 4, 2), HERS_TVP(2, 4, 4, 2), HERS_TVP(2, 2, 4, 2), HERS_TVP(2, 2, 4, 3),
+    HERS_TVP(1, 4, 4, 2), HERS_TVP(4, 2, 4, 2), HERS_TVP(2, 6, 4, 1),
 };
 #undef HERS_TV
 #undef HERS_TVG
+#undef HERS_TVK
+#undef HERS_TVP
 constexpr int NUM_TENSOR_VARIANTS = sizeof(kTensorVariants) / sizeof(kTensorVariants[0]);
 
 int tensor_variant_count() { return NUM_TENSOR_VARIANTS; }
@@ -211,6 +372,20 @@ cudaError_t launch_tensor(int variant, const uint64_t* gallery, uint64_t nblocks
     const int smem = v.stages * (1 + v.nb) * v.dps * 2 * TILE * 4;
     cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    if (v.persist > 0) {
+        int dev = 0, sms = 0, occ = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn, TILE + 32, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        const uint64_t nunits = (nblocks + v.nb - 1) / v.nb * NUM_S * NTILES;
+        const uint64_t want = (uint64_t)sms * (uint64_t)(v.persist < occ ? v.persist : occ);
+        const unsigned grid = (unsigned)(nunits < want ? nunits : want);
+        v.fn<<<grid, TILE + 32, smem, st>>>((const int32_t*)gallery, (const int32_t*)probe, X, nblocks, d, err);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     const uint64_t max_groups = v.gorder ? 0x7FFFFFFFull : 65535ull;  // grid x or z limit
     const uint64_t max_z = max_groups * v.nb;
     for (uint64_t g0 = 0; g0 < nblocks; g0 += max_z) {

@@ -245,6 +245,32 @@ def test_every_tensor_shape_gives_the_same_ciphertexts(ctx, keys, oracle_keys):
     H.hers_set_tensor_variant(ctx, keep)
 
 
+def test_persistent_tensor_shapes_walk_many_units(ctx, keys):
+    """The persistent shapes ("pnb...") run K CTAs per SM, each walking many
+    (limb, tile, block group) units with one ring of stages across them.  On
+    37 blocks (a partial block group for every NB > 1; about 8 units per CTA)
+    at d = 41 (a ragged last stage) every one gives the score ciphertexts of
+    the first, non-persistent shape, and the Karatsuba shapes ("_ka") do too."""
+    m, d = 37 * 4096 - 5, 41
+    feats = W.gallery_features(m, d, 4242)
+    q = W.probe_for_mate(77777, d, 4242, 4343)
+    gal, _ = H.hers_encrypt_gallery(ctx, keys, torch.from_numpy(feats).cuda(), GAL_SEED)
+    pr = H.hers_probe_prepare(ctx, H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).cuda(), PRB_SEED))
+    nb = H.hers_blocks_for(m)
+    names = H.hers_tensor_variants()
+    picked = [v for v, n in enumerate(names) if n.startswith("pnb") or n.endswith("_ka")]
+    assert any(names[v].startswith("pnb") for v in picked)
+    keep = H.hers_get_tensor_variant(ctx)
+    H.hers_set_tensor_variant(ctx, 0)
+    ref = u64(H.hers_search(ctx, keys, gal, nb, d, pr))
+    for v in picked:
+        H.hers_set_tensor_variant(ctx, v)
+        assert np.array_equal(u64(H.hers_search(ctx, keys, gal, nb, d, pr)), ref), names[v]
+    H.hers_set_tensor_variant(ctx, keep)
+    scores = H.hers_decrypt_scores(ctx, keys, torch.from_numpy(ref.view(np.int64)).cuda(), m)
+    assert np.array_equal(scores.cpu().numpy().astype(np.int64), W.plain_inner_products(feats, q))
+
+
 def test_async_host_search_equals_sync(ctx, keys):
     """hers_search_host_async on two streams gives the bytes of
     hers_search_host; unpinned host buffers are refused."""
