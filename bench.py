@@ -440,9 +440,9 @@ def run_gpu(args):
     # cost a tenth of the host-buffer rate.)
     tnames, enames = H.hers_tensor_variants(), H.hers_epilogue_variants()
     t_cands = [variant] if args.variant else sorted(
-        {variant} | {i for i, n in enumerate(tnames) if n.endswith("_m1") or n.endswith("_ka")})
-    # (the one-CTA-per-SM and Karatsuba shapes, the persistent "pnb" ones among them,
-    # leave SM resources that the other search's epilogue can use)
+        {variant} | {i for i, n in enumerate(tnames) if n.endswith("_ka") or n.startswith("pnb")})
+    # (the Karatsuba shapes leave multiply-pipe time, and the persistent "pnb"
+    # shapes registers and shared memory on every SM, to the other search's epilogue)
     combos = {}
     for tv in ([] if args.no_select else t_cands):
         H.hers_set_tensor_variant(ctx, tv)

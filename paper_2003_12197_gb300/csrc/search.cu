@@ -341,6 +341,13 @@ struct TensorVariant {
 // persistent Karatsuba form, K CTAs per SM: "pnb<NB>_s<S>_d<D>_k<K>_ka"
 #define HERS_TVP(NB, S, D, K) \
     {"pnb" #NB "_s" #S "_d" #D "_k" #K "_ka", k_tensor_persist<NB, S, D, K, true>, NB, S, D, false, K}
+// and with the four products: "pnb<NB>_s<S>_d<D>_k<K>"
+#define HERS_TVQ(NB, S, D, K) \
+    {"pnb" #NB "_s" #S "_d" #D "_k" #K, k_tensor_persist<NB, S, D, K, false>, NB, S, D, false, K}
+// persistent Karatsuba form, K CTAs per SM, registers budgeted for M CTAs per
+// SM (M > K: fewer registers, more left to another kernel beside it)
+#define HERS_TVR(NB, S, D, K, M) \
+    {"pnb" #NB "_s" #S "_d" #D "_k" #K "_m" #M "_ka", k_tensor_persist<NB, S, D, M, true>, NB, S, D, false, K}
 static const TensorVariant kTensorVariants[] = {
     HERS_TV(2, 4, 4, 2),  HERS_TV(2, 3, 4, 3),  HERS_TV(2, 2, 8, 2),  HERS_TV(1, 4, 4, 3),
     HERS_TV(4, 2, 4, 2),  HERS_TV(2, 4, 2, 3),  HERS_TV(2, 2, 4, 4),  HERS_TV(1, 2, 8, 3),
@@ -352,11 +359,15 @@ static const TensorVariant kTensorVariants[] = {
     HERS_TVK(2, 3, 4, 3, false, ""), HERS_TVK(2, 4, 4, 2, false, ""), HERS_TVK(2, 4, 2, 3, false, ""),
     HERS_TVP(2, 3, 4, 2), HERS_TVP(2, 4, 4, 2), HERS_TVP(2, 2, 4, 2), HERS_TVP(2, 2, 4, 3),
     HERS_TVP(1, 4, 4, 2), HERS_TVP(4, 2, 4, 2), HERS_TVP(2, 6, 4, 1),
+    HERS_TVP(2, 3, 2, 2), HERS_TVP(2, 4, 2, 2), HERS_TVP(2, 5, 2, 2), HERS_TVP(1, 3, 4, 3),
+    HERS_TVQ(2, 3, 4, 2), HERS_TVR(2, 3, 4, 2, 4), HERS_TVR(2, 3, 4, 2, 3),
 };
 #undef HERS_TV
 #undef HERS_TVG
 #undef HERS_TVK
 #undef HERS_TVP
+#undef HERS_TVQ
+#undef HERS_TVR
 constexpr int NUM_TENSOR_VARIANTS = sizeof(kTensorVariants) / sizeof(kTensorVariants[0]);
 
 int tensor_variant_count() { return NUM_TENSOR_VARIANTS; }
@@ -420,8 +431,10 @@ __global__ void __launch_bounds__(NTT_THREADS, 3) k_ntt_batch(const uint64_t* __
 // mod r_(P % NUM_S).  Each thread loads its 16 phase-one coefficients (16 t ..
 // 16 t + 15, four 16-byte loads) and stores its 16 outputs (t + 256 a,
 // coalesced) directly; shared memory carries only the middle phase.
-template <bool SHFL>
-__global__ void __launch_bounds__(NTT_THREADS, 4) k_intt32_batch(const uint64_t* __restrict__ tw,
+// LEAN: a register budget for 5 CTAs per SM (48 registers) instead of 4, so
+// that more CTAs fit beside the persistent tensor kernel of a search in flight.
+template <bool SHFL, bool LEAN = false>
+__global__ void __launch_bounds__(NTT_THREADS, LEAN ? 5 : 4) k_intt32_batch(const uint64_t* __restrict__ tw,
                                                               uint32_t* __restrict__ data) {
     __shared__ uint32_t sm32[N];
     const uint64_t P = blockIdx.x;
@@ -576,8 +589,10 @@ __global__ void __cluster_dims__(NUM_S, 1, 1) __launch_bounds__(NTT_THREADS, 4)
 // times evk_j[c][l] (NTT values with Shoup companions) for both c, into
 // P[b][j][c][l] (reduced).  k_ks_inv_finish: CTA per (b, c, l):
 // P[b][0][c][l] + P[b][1][c][l] back to coefficients, plus C[b][c][l], into
-// out[b][c][l].
-__global__ void __launch_bounds__(NTT_THREADS, 3) k_ks_fwd_mul(const uint64_t* __restrict__ tw,
+// out[b][c][l].  LEAN: a register budget for 4 CTAs per SM instead of 3 (as
+// for k_intt32_batch).
+template <bool LEAN>
+__global__ void __launch_bounds__(NTT_THREADS, LEAN ? 4 : 3) k_ks_fwd_mul(const uint64_t* __restrict__ tw,
                                                             const uint64_t* __restrict__ KS,
                                                             const uint64_t* __restrict__ evk_ntt,
                                                             uint64_t* __restrict__ P) {
@@ -597,7 +612,8 @@ __global__ void __launch_bounds__(NTT_THREADS, 3) k_ks_fwd_mul(const uint64_t* _
     }
 }
 
-__global__ void __launch_bounds__(NTT_THREADS, 3) k_ks_inv_finish(const uint64_t* __restrict__ tw,
+template <bool LEAN>
+__global__ void __launch_bounds__(NTT_THREADS, LEAN ? 4 : 3) k_ks_inv_finish(const uint64_t* __restrict__ tw,
                                                                const uint64_t* __restrict__ P,
                                                                const uint64_t* __restrict__ C,
                                                                uint64_t* __restrict__ out) {
@@ -717,7 +733,15 @@ const char* epilogue_variant_name(int v) {
                                               "split+shfl",
                                               "intt_scale_cluster+shfl",
                                               "ks_fused+shfl",
-                                              "intt_scale_cluster+ks_fused+shfl"};
+                                              "intt_scale_cluster+ks_fused+shfl",
+                                              "split+lean",
+                                              "intt_scale_cluster+lean",
+                                              "ks_fused+lean",
+                                              "intt_scale_cluster+ks_fused+lean",
+                                              "split+shfl+lean",
+                                              "intt_scale_cluster+shfl+lean",
+                                              "ks_fused+shfl+lean",
+                                              "intt_scale_cluster+ks_fused+shfl+lean"};
     return (v >= 0 && v < EPI_VARIANTS) ? names[v] : nullptr;
 }
 
@@ -752,7 +776,10 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
         const uint64_t npolys = npairs * 3 * NUM_S;  // chunks are multiples of NUM_S
         for (uint64_t off = 0; off < npolys; off += chunk) {
             const uint64_t n = npolys - off < chunk ? npolys - off : chunk;
-            if (epi & EPI_INTT_SHFL) k_intt32_batch<true><<<(unsigned)n, NTT_THREADS, 0, st>>>(tw, X32 + off * N);
+            const bool sh = (epi & EPI_INTT_SHFL) != 0, lean = (epi & EPI_LEAN) != 0;
+            if (sh && lean) k_intt32_batch<true, true><<<(unsigned)n, NTT_THREADS, 0, st>>>(tw, X32 + off * N);
+            else if (sh) k_intt32_batch<true><<<(unsigned)n, NTT_THREADS, 0, st>>>(tw, X32 + off * N);
+            else if (lean) k_intt32_batch<false, true><<<(unsigned)n, NTT_THREADS, 0, st>>>(tw, X32 + off * N);
             else k_intt32_batch<false><<<(unsigned)n, NTT_THREADS, 0, st>>>(tw, X32 + off * N);
             nl++;
         }
@@ -814,13 +841,20 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
         uint64_t* P = X;
         for (uint64_t off = 0; off < npairs * 4; off += chunk) {  // chunk: a multiple of 4 rows
             const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
-            k_ks_fwd_mul<<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, KS + off * N, k.evk_ntt, P + off * 2 * N);
+            if (epi & EPI_LEAN)
+                k_ks_fwd_mul<true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, KS + off * N, k.evk_ntt, P + off * 2 * N);
+            else
+                k_ks_fwd_mul<false><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, KS + off * N, k.evk_ntt, P + off * 2 * N);
             nl++;
         }
         for (uint64_t off = 0; off < npairs * 4; off += chunk) {
             const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
-            k_ks_inv_finish<<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, P + off * 2 * N, C + off / 4 * 6 * N,
-                                                                     out + off * N);
+            if (epi & EPI_LEAN)
+                k_ks_inv_finish<true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, P + off * 2 * N, C + off / 4 * 6 * N,
+                                                                         out + off * N);
+            else
+                k_ks_inv_finish<false><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, P + off * 2 * N, C + off / 4 * 6 * N,
+                                                                          out + off * N);
             nl++;
         }
     }

@@ -369,7 +369,8 @@ def test_searches_on_several_streams_in_flight(ctx, keys, config1):
 
 def test_every_epilogue_form_gives_the_same_ciphertexts(ctx, keys, oracle_keys):
     """The epilogue forms (split kernels, inverse NTTs fused with
-    scale-and-round in clusters, the fused key switch, both) compute the same
+    scale-and-round in clusters, the fused key switch, both; each with the
+    shuffle exchange and with the lean register budget) compute the same
     exact integers: every form gives the oracle's score ciphertexts, over 3
     blocks with a ragged last block; and the epilogue autotuner keeps one."""
     m, d = 2 * 4096 + 999, 19
@@ -378,7 +379,7 @@ def test_every_epilogue_form_gives_the_same_ciphertexts(ctx, keys, oracle_keys):
     gal, _ = H.hers_encrypt_gallery(ctx, keys, torch.from_numpy(feats).cuda(), GAL_SEED)
     pr = H.hers_probe_prepare(ctx, H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).cuda(), PRB_SEED))
     names = H.hers_epilogue_variants()
-    assert len(names) == 8
+    assert len(names) == 16 and names[8].endswith("+lean")
     keep = H.hers_get_epilogue_variant(ctx)
     outs = []
     for v in range(len(names)):
