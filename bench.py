@@ -111,6 +111,9 @@ def parse():
     ap.add_argument("--batched-blocks", type=int, default=256,
                     help="batched: gallery blocks split into uneven subsets (256 = the config)")
     ap.add_argument("--batched-probes", type=int, default=64, help="batched: probes (64 = the config)")
+    ap.add_argument("--epilogue", default=None,
+                    help="plain: epilogue form by name (hers_epilogue_variants()); the in-flight choice "
+                         "then takes only this form")
     ap.add_argument("--variant", default=None,
                     help="tensor-kernel shape by name (skips the autotuner), e.g. nb2_s3_d4_m3")
     return ap.parse_args()
@@ -448,13 +451,13 @@ def run_gpu(args):
         H.hers_set_tensor_variant(ctx, tv)
         for tf in (False,):
             H.hers_set_tensor_first(ctx, tf)
-            for ev_ in range(len(enames)):
+            for ev_ in ([enames.index(args.epilogue)] if args.epilogue else range(len(enames))):
                 H.hers_set_epilogue_variant(ctx, ev_)
                 for k in range(IN_FLIGHT):
                     step_in_flight(k)
                 combos[(tv, tf, ev_)] = timed(step_in_flight, 10, trace=False) / 10
     if not combos:
-        combos[(variant, False, 0)] = None  # not timed (--no-select)
+        combos[(variant, False, enames.index(args.epilogue) if args.epilogue else 0)] = None  # not timed
     variant, tensor_first, epi = min(combos, key=lambda c: combos[c] if combos[c] is not None else 0.0)
     variant_name, epi_name = tnames[variant], enames[epi]
     H.hers_set_tensor_variant(ctx, variant)
