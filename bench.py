@@ -814,7 +814,8 @@ def batched_section(ctx, keys, dev, local, args):
     # the batched kernel forms the tensor by Karatsuba: 3 multiply-adds per
     # (probe, block, dimension, coefficient, limb)
     imad = sum(nb * d for _, nb, d, _ in items) * N * search_limbs() * 3
-    pipe = H.hers_probe_int_pipe(local)["imad_wide_u32"]
+    rates = H.hers_probe_int_pipe(local)
+    pipe, pipe_reg = rates["imad_wide_u32"], rates["mad_wide_s32_outer"]
     t_tensor = min(tensor_ms) / 1e3
     gal_bytes = sum(H.hers_gallery_bytes(nb, d) for _, _, nb, d in gals)
     probe_bytes = sum(H.hers_probe_bytes(d) for _, _, d, _ in items)
@@ -837,7 +838,13 @@ def batched_section(ctx, keys, dev, local, args):
         "roofline": {"kernel": f"k_tensor_batched<{info['variant']}>", "bound": "alu",
                      "achieved": imad / t_tensor / 1e12, "peak": pipe / 1e12, "unit": "T IMAD.WIDE/s",
                      "frac": imad / t_tensor / pipe, "mad_wide_per_element": 3,
-                     "peak_source": "measured in this run (hers_probe_int_pipe)",
+                     "peak_source": "measured in this run (hers_probe_int_pipe): IMAD.WIDE.U32 with a "
+                                    "constant factor, the accumulate fused",
+                     "register_form": {"peak": pipe_reg / 1e12, "frac": imad / t_tensor / pipe_reg,
+                                       "note": "against the rate of the kernel's own form (hers_probe_int_pipe "
+                                               "op 3: both factors in registers from shared memory, 64-bit "
+                                               "register sums, 4 x 4 outer products), in which the compiler "
+                                               "fuses about half of the accumulates"},
                      "gallery_bytes": gal_bytes, "probe_bytes": probe_bytes,
                      "hbm_gbs_if_read_once": (gal_bytes + probe_bytes) / t_tensor / 1e9},
         "correct": {"bit_exact_vs_plain": exact, "scores_exact": scores_exact, "top1": f"{top1}/{nprobes}"},
@@ -911,11 +918,17 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
     sv_name = batch_variant or "np2_nb2_s2_d4_m3_g1_l2"
     srv = H.Server(ctx, keys, gals, workspace_bytes=pool, max_batch=max_batch,
                    variant=H.hers_batch_variants().index(sv_name))
+    # the host's own copy rate, measured before the arena exists (its fresh
+    # arrays must not disturb the arena's pages)
+    memcpy_before = host_memcpy_gbs()
     # pinned host arena for score ciphertexts, handed out as a ring
     arena_blocks = 4 * nblocks * 16
     arena = host_buffer(arena_blocks * 4 * N, host_alloc, dev, d2h=True).view(arena_blocks, 4 * N)
     # the rate of a device -> arena copy (2 GiB), as the server's copy-outs see it
     probe_n = min(arena.numel(), (2 << 30) // 8)
+    # (and of every 2 GiB slice, now and after each of the next two steps: some
+    # slices of large page-locked buffers have turned slow after registration)
+    slices_at_alloc = copy_rate_slices(arena, dev, probe_n, h2d=False)
     src = torch.empty(probe_n, dtype=torch.int64, device=dev)
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     arena_ms = None
@@ -926,7 +939,10 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
         torch.cuda.synchronize()
         arena_ms = c0.elapsed_time(c1) if arena_ms is None else min(arena_ms, c0.elapsed_time(c1))
     del src
-    host_diag = {"host_memcpy_gbs_before": host_memcpy_gbs(),
+    slices_after_probe = copy_rate_slices(arena, dev, probe_n, h2d=False)
+    host_diag = {"arena_d2h_gbs_per_2gib_slice_at_alloc": slices_at_alloc,
+                 "arena_d2h_gbs_per_2gib_slice_after_probe_copies": slices_after_probe,
+                 "host_memcpy_gbs_before": memcpy_before,
                  "arena_d2h_gbs": probe_n * 8 / (arena_ms / 1e3) / 1e9,
                  "arena_d2h_gbs_per_2gib_slice": copy_rate_slices(arena, dev, probe_n, h2d=False),
                  "host_alloc": host_alloc,
@@ -1040,7 +1056,6 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
     cpu1, wall1 = thread_cpu_seconds(), time.perf_counter()
     busy = sorted(((cpu1[k] - cpu0.get(k, 0.0), k[1]) for k in cpu1), reverse=True)[:6]
     host_diag["threads_cpu_s"] = [[n, round(v, 2)] for v, n in busy]
-    host_diag["host_memcpy_gbs_after"] = host_memcpy_gbs()
     # the arena's copy rates again: whether its pages slowed down during the run
     host_diag["arena_d2h_gbs_per_2gib_slice_after"] = copy_rate_slices(arena, dev, probe_n, h2d=False)
     host_diag["arena_numa_pages_after"] = numa_pages(arena.data_ptr())
@@ -1132,10 +1147,19 @@ _HOST_BUFS = []  # host mappings kept alive (and registered with CUDA) until exi
 HOST_BUF_LOG = []  # what host_buffer() did, for the JSON line
 
 
+def numa_balancing():
+    """The kernel's automatic NUMA balancing switch (read only), or None."""
+    try:
+        return int(open("/proc/sys/kernel/numa_balancing").read().split()[0])
+    except (OSError, ValueError, IndexError):
+        return None
+
+
 def host_buffer(nwords, mode, dev=None, d2h=False):
     """An int64 CPU tensor of nwords that CUDA copies treat as page-locked.
     mode "torch": torch's pinned allocator (cudaHostAlloc).  mode "register":
-    an anonymous mapping advised to transparent huge pages, touched, then
+    an anonymous mapping advised to transparent huge pages, touched with a
+    non-zero pattern (its contents are undefined to the caller), then
     registered with cudaHostRegister, so the pages are large and resident
     before the GPU maps them.  With dev, every 4 GiB slice is then copied to
     the device once (and, with d2h, from the device as well); a slice at
@@ -1154,15 +1178,18 @@ def host_buffer(nwords, mode, dev=None, d2h=False):
     if hasattr(mm, "madvise") and hasattr(mmap, "MADV_HUGEPAGE"):
         mm.madvise(mmap.MADV_HUGEPAGE)
     arr = np.frombuffer(mm, dtype=np.int64)
+    # touch every page with a non-zero pattern: the kernel may split huge
+    # pages that are mostly zero-filled when memory runs short, and a region
+    # split into small pages copied 10-40x slower than the rest
     step = (1 << 30) // 8
-    for o in range(0, nwords, step):  # touch every page
-        arr[o:o + step] = 0
+    for o in range(0, nwords, step):
+        arr[o:o + step] = -1
     rt = ctypes.CDLL("libcudart.so.13")
     ptr, size = ctypes.c_void_p(arr.ctypes.data), ctypes.c_size_t(nbytes)
     if rt.cudaHostRegister(ptr, size, ctypes.c_uint(1)) != 0:
         raise SystemExit("cudaHostRegister failed")
     t = torch.from_numpy(arr)
-    log = {"gb": round(nbytes / 1e9, 1), "repaired_slices": []}
+    log = {"gb": round(nbytes / 1e9, 1), "repaired_slices": [], "numa_balancing": numa_balancing()}
     try:
         log["thp"] = open("/sys/kernel/mm/transparent_hugepage/enabled").read().strip()
     except OSError:
@@ -1186,7 +1213,7 @@ def host_buffer(nwords, mode, dev=None, d2h=False):
             for i in slow:
                 o, n_ = i * span * 8, min(span * 8, nbytes - i * span * 8)
                 mm.madvise(mmap.MADV_DONTNEED, o, n_)
-                arr[i * span: i * span + n_ // 8] = 0
+                arr[i * span: i * span + n_ // 8] = -1
             if rt.cudaHostRegister(ptr, size, ctypes.c_uint(1)) != 0:
                 raise SystemExit("cudaHostRegister failed")
             log["repaired_slices"].append(slow)
@@ -1733,8 +1760,24 @@ def run_enroll(args):
     return 0
 
 
+def numpy_hugepages_off():
+    """Stops numpy from advising its large arrays to transparent huge pages.
+    Building huge pages for fresh numpy arrays (2 x 1 GiB) was seen to turn
+    the first 6 GiB of an already registered 20.5 GB page-locked buffer from
+    193 GB/s device copies to 2-9 GB/s; the bench's large host buffers take
+    their huge pages explicitly instead (host_buffer)."""
+    import numpy as np
+    for mod in ("_core", "core"):
+        f = getattr(getattr(getattr(np, mod, None), "multiarray", None), "_set_madvise_hugepage", None)
+        if f is not None:
+            f(False)
+            return True
+    return False
+
+
 def main():
     args = parse()
+    numpy_hugepages_off()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":

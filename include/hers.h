@@ -639,7 +639,10 @@ int hers_topk(hers_ctx* ctx, const int32_t* scores, uint64_t m, uint32_t k, int6
  * `device`, in operations per second over all SMs, for op 0 = 32x32 -> 64-bit
  * multiply-add (IMAD.WIDE.U32, the tensor kernel's inner operation), 1 =
  * 32-bit multiply-add, 2 = high half of a 64x64-bit product (__umul64hi, the
- * Shoup/Barrett step).  Runs one kernel of `iters` iterations per thread;
+ * Shoup/Barrett step), 3 = signed 32x32 -> 64-bit multiply-add with both
+ * factors in registers from shared memory into a 64-bit register sum (the
+ * batched tensor kernel's form; 4 x 4 outer products, 16 per iteration).
+ * Runs one kernel of `iters` iterations per thread;
  * allocates an 8-byte buffer for the duration of the call.
  */
 int hers_probe_int_pipe(int device, uint32_t op, uint64_t iters, double* ops_per_s);

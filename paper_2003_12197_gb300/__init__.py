@@ -772,7 +772,7 @@ class Server:
             pass
 
 
-INT_PIPE_OPS = ("imad_wide_u32", "imad_u32", "umul64hi")
+INT_PIPE_OPS = ("imad_wide_u32", "imad_u32", "umul64hi", "mad_wide_s32_outer")
 
 
 def hers_probe_int_pipe(device: int = 0, iters: int = 1 << 16):

@@ -35,6 +35,46 @@ __global__ void __launch_bounds__(256) k_intpipe(uint64_t iters, uint32_t c, uin
     if (r == 0x123456789ull) sink[0] = r;  // keeps the chains live
 }
 
+// Op 3: the batched tensor kernel's instruction form, a signed 32x32->64
+// multiply-add with both factors in registers (read from shared memory) into
+// a 64-bit register sum, as the 4 x 4 outer product of 4 values of each side
+// per iteration (16 sums per thread).  The compiler fuses only about half of
+// these accumulates into the IMAD.WIDE (the rest take a separate 64-bit add),
+// so this rate, not op 0's, is what such a loop can reach.
+__global__ void __launch_bounds__(256) k_intpipe_outer(uint64_t iters, uint32_t c, uint64_t* sink) {
+    __shared__ int32_t sa[1024], sb[1024];
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+        sa[i] = (int32_t)((uint32_t)i * c) >> 3;
+        sb[i] = (int32_t)((uint32_t)(i + 7) * (c ^ 0x5bd1e995u)) >> 3;
+    }
+    __syncthreads();
+    int64_t acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0;
+    const int t = threadIdx.x & 31;
+    for (uint64_t it = 0; it < iters; it++) {
+        const int base = (int)((it * 8) & 1023) & ~31;
+        int32_t a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            a[i] = sa[(base + t + 32 * i) & 1023];
+            b[i] = sb[(base + t + 32 * i + 7) & 1023];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc[i][j]) : "r"(a[i]), "r"(b[j]));
+    }
+    int64_t r = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) r ^= acc[i][j];
+    if (r == 0x123456789ll) sink[0] = (uint64_t)r;  // keeps the sums live
+}
+
 // One thread waits on an mbarrier that nothing arrives on, with the same
 // bounded wait the streaming kernels use; the give-up path is theirs too.
 __global__ void k_wait_timeout(uint64_t limit_ns, int* err) {
@@ -79,7 +119,7 @@ extern "C" int hers_selftest_wait_timeout(hers_ctx* ctx, uint64_t limit_ns, doub
 
 extern "C" int hers_probe_int_pipe(int device, uint32_t op, uint64_t iters, double* ops_per_s) {
     using namespace hers;
-    if (!ops_per_s || op > 2 || iters == 0) return HERS_E_INVAL;
+    if (!ops_per_s || op > 3 || iters == 0) return HERS_E_INVAL;
     if (cudaSetDevice(device) != cudaSuccess) return HERS_E_CUDA;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
@@ -93,8 +133,11 @@ extern "C" int hers_probe_int_pipe(int device, uint32_t op, uint64_t iters, doub
     auto launch = [&](uint64_t it) {
         if (op == 0) k_intpipe<0><<<blocks, threads>>>(it, 0x9E3779B1u, sink);
         else if (op == 1) k_intpipe<1><<<blocks, threads>>>(it, 0x9E3779B1u, sink);
-        else k_intpipe<2><<<blocks, threads>>>(it, 0x9E3779B1u, sink);
+        else if (op == 2) k_intpipe<2><<<blocks, threads>>>(it, 0x9E3779B1u, sink);
+        else k_intpipe_outer<<<blocks, threads>>>(it, 0x9E3779B1u, sink);
     };
+    // op 3 does 16 multiply-adds per thread and iteration, the others 8
+    const double per_iter = op == 3 ? 16.0 : 8.0;
     launch(iters / 8 + 1);  // warm-up
     cudaEventRecord(e0);
     launch(iters);
@@ -107,6 +150,6 @@ extern "C" int hers_probe_int_pipe(int device, uint32_t op, uint64_t iters, doub
     cudaEventDestroy(e1);
     cudaFree(sink);
     if (e != cudaSuccess || ms <= 0) return HERS_E_CUDA;
-    *ops_per_s = (double)blocks * threads * (double)iters * 8.0 / (ms * 1e-3);
+    *ops_per_s = (double)blocks * threads * (double)iters * per_iter / (ms * 1e-3);
     return HERS_OK;
 }
