@@ -567,7 +567,10 @@ int hers_autotune(hers_ctx* ctx, const hers_keys* keys, const uint64_t* gallery,
  * of a pass through shared memory, and adding 8 ("+lean") builds the split
  * inverse NTTs and the two-kernel key switch for one more CTA per SM (fewer
  * registers), so that more of them fit beside a persistent tensor kernel of
- * another search in flight.  The context's form applies to every search on it
+ * another search in flight, and adding 16 ("+ksshfl") makes the in-warp
+ * exchange of the split key switch's 64-bit NTTs (a 16 x 16 transpose inside
+ * each half-warp) a warp-shuffle transpose instead of a pass through shared
+ * memory.  The context's form applies to every search on it
  * (hers_search*, hers_batch_*, hers_server_*, hers_search_stream).
  * hers_autotune_epilogue times each form's epilogue after the tensor kernel
  * of the given search (1 warm-up, 3 timed, minimum kept), keeps the fastest

@@ -404,8 +404,32 @@ __device__ __forceinline__ void gs_phase(uint64_t v[16], int base, const ulonglo
     }
 }
 
+// Transposes the 16 x 16 matrix of 64-bit words held by the 16 lanes of each
+// half-warp (lane i holds row i in v; afterwards it holds column i): four
+// rounds of 64-bit __shfl_xor_sync (distances 8, 4, 2, 1), each swapping the
+// off-diagonal halves of the blocks of that size.  Every lane of the warp
+// must call it.
+__device__ __forceinline__ void transpose16_shfl64(uint64_t v[16], int i) {
+#pragma unroll
+    for (int m = 8; m >= 1; m >>= 1) {
+        const bool hi = (i & m) != 0;
+#pragma unroll
+        for (int a = 0; a < 16; a++) {
+            if (a & m) continue;
+            const uint64_t send = hi ? v[a] : v[a | m];
+            const uint64_t recv = __shfl_xor_sync(0xffffffffu, send, m);
+            if (hi) v[a] = recv;
+            else v[a | m] = recv;
+        }
+    }
+}
+
 // t: the calling thread's index among the NTT_THREADS threads that run the
-// transform (as for the 32-bit transforms below).
+// transform (as for the 32-bit transforms below).  SHFL: the exchange
+// between the two phases that stay inside a half-warp (coefficients
+// 256 (t / 16) + (t % 16) + 16 a and 16 t + a, a 16 x 16 transpose) goes
+// through warp shuffles instead of shared memory.
+template <bool SHFL = false>
 __device__ __forceinline__ void ntt_fwd_smem(uint64_t* sm, const ulonglong2* __restrict__ w, uint64_t p,
                                              uint64_t one_s, int t = threadIdx.x) {
     uint64_t v[16];
@@ -424,14 +448,20 @@ __device__ __forceinline__ void ntt_fwd_smem(uint64_t* sm, const ulonglong2* __r
 #pragma unroll
         for (int a = 0; a < 16; a++) v[a] = sm[swz(base + 16 * a)];
         ct_phase<16>(v, base, w, p);
+        if (SHFL) {
+            transpose16_shfl64(v, t & 15);
+        } else {
 #pragma unroll
-        for (int a = 0; a < 16; a++) sm[swz(base + 16 * a)] = v[a];
+            for (int a = 0; a < 16; a++) sm[swz(base + 16 * a)] = v[a];
+        }
     }
-    __syncwarp();
+    if (!SHFL) __syncwarp();
     {   // phase C, then full reduction (values < 50p)
         const int base = 16 * t;
+        if (!SHFL) {
 #pragma unroll
-        for (int a = 0; a < 16; a++) v[a] = sm[swz(base + a)];
+            for (int a = 0; a < 16; a++) v[a] = sm[swz(base + a)];
+        }
         ct_phase<1>(v, base, w, p);
 #pragma unroll
         for (int a = 0; a < 16; a++) sm[swz(base + a)] = csub(shoup_lazy(v[a], 1, one_s, p), p);
@@ -439,6 +469,7 @@ __device__ __forceinline__ void ntt_fwd_smem(uint64_t* sm, const ulonglong2* __r
     __syncthreads();
 }
 
+template <bool SHFL = false>
 __device__ __forceinline__ void ntt_inv_smem(uint64_t* sm, const ulonglong2* __restrict__ w, uint64_t p,
                                              uint64_t ninv, uint64_t ninv_s, int t = threadIdx.x) {
     uint64_t v[16];
@@ -448,14 +479,20 @@ __device__ __forceinline__ void ntt_inv_smem(uint64_t* sm, const ulonglong2* __r
 #pragma unroll
         for (int a = 0; a < 16; a++) v[a] = sm[swz(base + a)];
         gs_phase<1, false>(v, base, w, p, ninv, ninv_s);
+        if (SHFL) {
+            transpose16_shfl64(v, t & 15);
+        } else {
 #pragma unroll
-        for (int a = 0; a < 16; a++) sm[swz(base + a)] = v[a];
+            for (int a = 0; a < 16; a++) sm[swz(base + a)] = v[a];
+        }
     }
-    __syncwarp();
+    if (!SHFL) __syncwarp();
     {   // distances 16 .. 128
         const int base = 256 * (t >> 4) + (t & 15);
+        if (!SHFL) {
 #pragma unroll
-        for (int a = 0; a < 16; a++) v[a] = sm[swz(base + 16 * a)];
+            for (int a = 0; a < 16; a++) v[a] = sm[swz(base + 16 * a)];
+        }
         gs_phase<16, false>(v, base, w, p, ninv, ninv_s);
 #pragma unroll
         for (int a = 0; a < 16; a++) sm[swz(base + 16 * a)] = v[a];
@@ -472,11 +509,13 @@ __device__ __forceinline__ void ntt_inv_smem(uint64_t* sm, const ulonglong2* __r
     __syncthreads();
 }
 
+template <bool SHFL = false>
 __device__ __forceinline__ void ntt_fwd_mod(uint64_t* a, const uint64_t* tw, int i) {
-    ntt_fwd_smem(a, tw_fwd(tw, i), c_mod[i], c_one_s[i]);
+    ntt_fwd_smem<SHFL>(a, tw_fwd(tw, i), c_mod[i], c_one_s[i]);
 }
+template <bool SHFL = false>
 __device__ __forceinline__ void ntt_inv_mod(uint64_t* a, const uint64_t* tw, int i) {
-    ntt_inv_smem(a, tw_inv(tw, i), c_mod[i], c_ninv[i], c_ninv_s[i]);
+    ntt_inv_smem<SHFL>(a, tw_inv(tw, i), c_mod[i], c_ninv[i], c_ninv_s[i]);
 }
 // Out-of-line versions for kernels that run several NTTs among other work:
 // each call then gets its own register allocation.

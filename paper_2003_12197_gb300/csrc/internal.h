@@ -149,9 +149,12 @@ struct EpilogueStream {
 // EPI_INTT_SHFL makes the inverse NTTs' first exchange a warp-shuffle
 // transpose instead of a pass through shared memory; EPI_LEAN compiles the
 // split inverse NTTs and key-switch kernels for one more CTA per SM (fewer
-// registers), so more of them run beside a persistent tensor kernel.  Variant
-// v is the OR of the flags, 0 <= v < EPI_VARIANTS.
-constexpr int EPI_INTT_SCALE_CLUSTER = 1, EPI_KS_FUSED = 2, EPI_INTT_SHFL = 4, EPI_LEAN = 8, EPI_VARIANTS = 16;
+// registers), so more of them run beside a persistent tensor kernel;
+// EPI_KS_SHFL makes the in-warp exchange of the split key switch's 64-bit
+// NTTs a warp-shuffle transpose.  Variant v is the OR of the flags,
+// 0 <= v < EPI_VARIANTS.
+constexpr int EPI_INTT_SCALE_CLUSTER = 1, EPI_KS_FUSED = 2, EPI_INTT_SHFL = 4, EPI_LEAN = 8, EPI_KS_SHFL = 16,
+              EPI_VARIANTS = 32;
 const char* epilogue_variant_name(int v);
 cudaError_t launch_search(const uint64_t* tw, const DevKeys& k, const uint64_t* gallery,
                           uint64_t nblocks, uint32_t d, const uint64_t* probe, uint64_t* scores_ct,

@@ -10,6 +10,9 @@
 //            D_j = c2 mod q_j, once per gallery block.
 #include <cooperative_groups.h>
 
+#include <string>
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -590,8 +593,8 @@ __global__ void __cluster_dims__(NUM_S, 1, 1) __launch_bounds__(NTT_THREADS, 4)
 // P[b][j][c][l] (reduced).  k_ks_inv_finish: CTA per (b, c, l):
 // P[b][0][c][l] + P[b][1][c][l] back to coefficients, plus C[b][c][l], into
 // out[b][c][l].  LEAN: a register budget for 4 CTAs per SM instead of 3 (as
-// for k_intt32_batch).
-template <bool LEAN>
+// for k_intt32_batch).  SHFL: the NTTs' in-warp exchange by shuffles.
+template <bool LEAN, bool SHFL = false>
 __global__ void __launch_bounds__(NTT_THREADS, LEAN ? 4 : 3) k_ks_fwd_mul(const uint64_t* __restrict__ tw,
                                                             const uint64_t* __restrict__ KS,
                                                             const uint64_t* __restrict__ evk_ntt,
@@ -603,7 +606,7 @@ __global__ void __launch_bounds__(NTT_THREADS, LEAN ? 4 : 3) k_ks_fwd_mul(const 
     const uint64_t q = c_mod[l];
     const uint64_t* src = KS + x * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) sm[swz(k)] = src[k];
-    ntt_fwd_mod(sm, tw, l);
+    ntt_fwd_mod<SHFL>(sm, tw, l);
 #pragma unroll
     for (int c = 0; c < 2; c++) {
         const uint64_t* e = evk_ntt + (size_t)(((j * 2 + c) * 2 + l) * 2) * N;
@@ -612,7 +615,7 @@ __global__ void __launch_bounds__(NTT_THREADS, LEAN ? 4 : 3) k_ks_fwd_mul(const 
     }
 }
 
-template <bool LEAN>
+template <bool LEAN, bool SHFL = false>
 __global__ void __launch_bounds__(NTT_THREADS, LEAN ? 4 : 3) k_ks_inv_finish(const uint64_t* __restrict__ tw,
                                                                const uint64_t* __restrict__ P,
                                                                const uint64_t* __restrict__ C,
@@ -625,7 +628,7 @@ __global__ void __launch_bounds__(NTT_THREADS, LEAN ? 4 : 3) k_ks_inv_finish(con
     const uint64_t* p0 = P + (((b * 2 + 0) * 2 + c) * 2 + l) * N;
     const uint64_t* p1 = P + (((b * 2 + 1) * 2 + c) * 2 + l) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) sm[swz(k)] = add_mod(p0[k], p1[k], q);
-    ntt_inv_mod(sm, tw, l);
+    ntt_inv_mod<SHFL>(sm, tw, l);
     const uint64_t* cc = C + ((b * 3 + c) * 2 + l) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) out[x * N + k] = add_mod(cc[k], sm[swz(k)], q);
 }
@@ -726,23 +729,16 @@ __global__ void __launch_bounds__(256) k_ks_mul_w(const uint64_t* __restrict__ W
 // or with the base-w gadget O [npairs][2][2][N] and the digits), canonical
 // score ciphertexts into out [npairs][2][2][N].
 const char* epilogue_variant_name(int v) {
-    static const char* names[EPI_VARIANTS] = {"split",
-                                              "intt_scale_cluster",
-                                              "ks_fused",
-                                              "intt_scale_cluster+ks_fused",
-                                              "split+shfl",
-                                              "intt_scale_cluster+shfl",
-                                              "ks_fused+shfl",
-                                              "intt_scale_cluster+ks_fused+shfl",
-                                              "split+lean",
-                                              "intt_scale_cluster+lean",
-                                              "ks_fused+lean",
-                                              "intt_scale_cluster+ks_fused+lean",
-                                              "split+shfl+lean",
-                                              "intt_scale_cluster+shfl+lean",
-                                              "ks_fused+shfl+lean",
-                                              "intt_scale_cluster+ks_fused+shfl+lean"};
-    return (v >= 0 && v < EPI_VARIANTS) ? names[v] : nullptr;
+    // the base form (flags 1, 2), then "+shfl", "+lean", "+ksshfl" for flags 4, 8, 16
+    static const std::vector<std::string> names = [] {
+        static const char* base[4] = {"split", "intt_scale_cluster", "ks_fused", "intt_scale_cluster+ks_fused"};
+        std::vector<std::string> n;
+        for (int f = 0; f < EPI_VARIANTS; f++)
+            n.push_back(std::string(base[f & 3]) + ((f & EPI_INTT_SHFL) ? "+shfl" : "") +
+                        ((f & EPI_LEAN) ? "+lean" : "") + ((f & EPI_KS_SHFL) ? "+ksshfl" : ""));
+        return n;
+    }();
+    return (v >= 0 && v < EPI_VARIANTS) ? names[v].c_str() : nullptr;
 }
 
 cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npairs, uint64_t* X,
@@ -841,20 +837,25 @@ cudaError_t launch_epilogue(const uint64_t* tw, const DevKeys& k, uint64_t npair
         uint64_t* P = X;
         for (uint64_t off = 0; off < npairs * 4; off += chunk) {  // chunk: a multiple of 4 rows
             const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
-            if (epi & EPI_LEAN)
-                k_ks_fwd_mul<true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, KS + off * N, k.evk_ntt, P + off * 2 * N);
-            else
-                k_ks_fwd_mul<false><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, KS + off * N, k.evk_ntt, P + off * 2 * N);
+            const uint64_t* ks = KS + off * N;
+            uint64_t* pp = P + off * 2 * N;
+            const bool lean = (epi & EPI_LEAN) != 0, sh = (epi & EPI_KS_SHFL) != 0;
+            if (lean && sh) k_ks_fwd_mul<true, true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, ks, k.evk_ntt, pp);
+            else if (lean) k_ks_fwd_mul<true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, ks, k.evk_ntt, pp);
+            else if (sh) k_ks_fwd_mul<false, true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, ks, k.evk_ntt, pp);
+            else k_ks_fwd_mul<false><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, ks, k.evk_ntt, pp);
             nl++;
         }
         for (uint64_t off = 0; off < npairs * 4; off += chunk) {
             const uint64_t n = npairs * 4 - off < chunk ? npairs * 4 - off : chunk;
-            if (epi & EPI_LEAN)
-                k_ks_inv_finish<true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, P + off * 2 * N, C + off / 4 * 6 * N,
-                                                                         out + off * N);
-            else
-                k_ks_inv_finish<false><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, P + off * 2 * N, C + off / 4 * 6 * N,
-                                                                          out + off * N);
+            const uint64_t* pp = P + off * 2 * N;
+            const uint64_t* cc = C + off / 4 * 6 * N;
+            uint64_t* o = out + off * N;
+            const bool lean = (epi & EPI_LEAN) != 0, sh = (epi & EPI_KS_SHFL) != 0;
+            if (lean && sh) k_ks_inv_finish<true, true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, pp, cc, o);
+            else if (lean) k_ks_inv_finish<true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, pp, cc, o);
+            else if (sh) k_ks_inv_finish<false, true><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, pp, cc, o);
+            else k_ks_inv_finish<false><<<(unsigned)n, NTT_THREADS, N * 8, st>>>(tw, pp, cc, o);
             nl++;
         }
     }

@@ -91,7 +91,7 @@ def test_batched_autotune_scores_and_oracle(setup):
     b.close()
 
 
-@pytest.mark.parametrize("epi", [1, 2, 3, 7, 8, 12])
+@pytest.mark.parametrize("epi", [1, 2, 3, 7, 8, 12, 16, 28])
 def test_batched_with_every_epilogue_form(setup, epi):
     """A batch planned on a context with another epilogue form gives the same
     bytes as the plain search (the form is captured in the batch's graph)."""

@@ -379,7 +379,7 @@ def test_every_epilogue_form_gives_the_same_ciphertexts(ctx, keys, oracle_keys):
     gal, _ = H.hers_encrypt_gallery(ctx, keys, torch.from_numpy(feats).cuda(), GAL_SEED)
     pr = H.hers_probe_prepare(ctx, H.hers_encrypt_probe(ctx, keys, torch.from_numpy(q).cuda(), PRB_SEED))
     names = H.hers_epilogue_variants()
-    assert len(names) == 16 and names[8].endswith("+lean")
+    assert len(names) == 32 and names[8].endswith("+lean") and names[16].endswith("+ksshfl")
     keep = H.hers_get_epilogue_variant(ctx)
     outs = []
     for v in range(len(names)):
