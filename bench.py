@@ -81,7 +81,7 @@ def parse():
                     help="plain workload: skip the in-flight choice of epilogue form (for profiling runs)")
     ap.add_argument("--plain-only", action="store_true",
                     help="plain workload: leave out the batched and serving objects of the line")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "scale", "sweep", "topk", "enroll"],
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving", "scale", "sweep", "topk", "enroll", "hostmem"],
                     help="plain: 1,048,576 entries, d = 64, one probe (the headline line); "
                          "batched: 64 probes x uneven subsets of 256 blocks, mixed d; "
                          "serving: Poisson requests against 10M-entry galleries at d 32/64/128; "
@@ -101,6 +101,7 @@ def parse():
     ap.add_argument("--scale-source", default="auto", choices=["auto", "host", "device"],
                     help="scale: where the canonical gallery lives (auto: host if it fits)")
     ap.add_argument("--scale-chunk", type=int, default=32, help="scale: gallery blocks per streamed chunk")
+    ap.add_argument("--hostmem-gib", type=int, default=96, help="hostmem: size of each page-locked buffer")
     ap.add_argument("--oracle-blocks", type=int, default=4,
                     help="scale: random blocks checked against the oracle (plus the mate blocks "
                          "of the first probes)")
@@ -354,6 +355,7 @@ def run_gpu(args):
     if rank == 0:
         H.build_library()
     dist.barrier()
+    sections = rank == 0 and world == 1 and not args.plain_only
 
     m, d = args.m, args.d
     nb = H.hers_blocks_for(m)
@@ -682,7 +684,7 @@ def run_gpu(args):
     del gal, pct, pr, ws, sc, lanes, wsh, pct_host, sc_host, streams, sc_plain
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
-    if rank == 0 and world == 1 and not args.plain_only:
+    if sections:
         out["batched"] = batched_section(ctx, keys, dev, local, args)
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
@@ -956,8 +958,8 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
                  "arena_numa_pages": numa_pages(arena.data_ptr()),
                  "gpu_numa_node": gpu_numa_node(dev),
                  "cpus_allowed": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None}
-    if host_alloc == "register" and HOST_BUF_LOG:
-        host_diag["arena_buffer"] = HOST_BUF_LOG[-1]
+    if host_alloc == "register":
+        host_diag["arena_buffer"] = HOST_BUF_LOG.get(arena.data_ptr())
         host_diag["arena_anon_huge_kb"] = smaps_field(arena.data_ptr())
     # the ring uses the arena's slices that copy at no less than half the best
     # slice's rate (a few GB of a large page-locked buffer can copy 10-40x
@@ -1121,8 +1123,8 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
     torch.cuda.synchronize()
     plain_s = e0.elapsed_time(e1) / 1e3
     best = max(results, key=lambda r: r["entries_per_s"])
+    host_buffers_release(arena)
     del arena
-    host_buffers_release()
     return {"metric": "encrypted gallery entries scored/sec and p50/p99 latency (serving)",
             "unit": "entries/s", "value": best["entries_per_s"],
             "p50_ms": results[0]["p50_ms"], "p99_ms": results[0]["p99_ms"],
@@ -1168,7 +1170,7 @@ def run_serving(args):
 _HOST_BUFS = []  # host mappings kept alive (and registered with CUDA) until exit
 
 
-HOST_BUF_LOG = []  # what host_buffer() did, for the JSON line
+HOST_BUF_LOG = {}  # what host_buffer() did, by the buffer's address, for the JSON line
 
 
 def numa_balancing():
@@ -1241,21 +1243,26 @@ def host_buffer(nwords, mode, dev=None, d2h=False):
             if rt.cudaHostRegister(ptr, size, ctypes.c_uint(1)) != 0:
                 raise SystemExit("cudaHostRegister failed")
             log["repaired_slices"].append(slow)
-    HOST_BUF_LOG.append(log)
+    HOST_BUF_LOG[t.data_ptr()] = log
     _HOST_BUFS.append((mm, arr))
     return t
 
 
-def host_buffers_release():
-    """Unregisters the host mappings host_buffer() made; their memory goes back
-    when the last tensor over it is gone."""
+def host_buffers_release(t=None):
+    """Unregisters the host mappings host_buffer() made (only the one under
+    tensor t, when given); their memory goes back when the last tensor over
+    it is gone."""
     import ctypes
     if not _HOST_BUFS:
         return
     rt = ctypes.CDLL("libcudart.so.13")
+    keep = []
     for mm, arr in _HOST_BUFS:
-        rt.cudaHostUnregister(ctypes.c_void_p(arr.ctypes.data))
-    _HOST_BUFS.clear()
+        if t is None or arr.ctypes.data == t.data_ptr():
+            rt.cudaHostUnregister(ctypes.c_void_p(arr.ctypes.data))
+        else:
+            keep.append((mm, arr))
+    _HOST_BUFS[:] = keep
 
 
 def copy_rate_slices(host, dev, span_words, h2d=True):
@@ -1529,7 +1536,7 @@ def scale_section(ctx, keys, dev, local, m, source, host_alloc, chunk, bv_name, 
            "streaming": None if source != "host" else {
                "h2d_gbs_measured": h2d_gbs,
                "host_alloc": host_alloc,
-               "host_buffer": HOST_BUF_LOG[-1] if host_alloc != "torch" and HOST_BUF_LOG else None,
+               "host_buffer": HOST_BUF_LOG.get(g.data_ptr()) if host_alloc != "torch" else None,
                "h2d_gbs_per_4gib_slice": {"min": min(slice_gbs), "max": max(slice_gbs),
                                           "mean": sum(slice_gbs) / len(slice_gbs), "all": slice_gbs},
                "h2d_gbs_per_4gib_slice_before_timed": slices_before_timed,
@@ -1739,6 +1746,68 @@ def run_topk(args):
     return 0
 
 
+def run_hostmem(args):
+    """Host-to-device copy rate of every 4 GiB slice of a large page-locked
+    host buffer (--hostmem-gib GiB), made four ways: the huge-page mapping of
+    host_buffer() registered whole, the same registered in 4 GiB pieces, a
+    mapping of base pages registered whole, and torch's pinned allocator.
+    Each is measured right after it is made, after 12 more small page-locked
+    buffers, and 2 s later; no kernel runs.  One JSON line."""
+    import ctypes
+    import gc
+    import mmap
+
+    import numpy as np
+    import torch
+    dev = torch.device("cuda", 0)
+    nbytes, span = args.hostmem_gib << 30, 4 << 30
+    rt = ctypes.CDLL("libcudart.so.13")
+
+    def mapped(huge, pieces):
+        mm = mmap.mmap(-1, nbytes, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+        if huge and hasattr(mmap, "MADV_HUGEPAGE"):
+            mm.madvise(mmap.MADV_HUGEPAGE)
+        arr = np.frombuffer(mm, dtype=np.int64)
+        step = (1 << 30) // 8
+        for o in range(0, arr.size, step):
+            arr[o:o + step] = -1
+        ptr = arr.ctypes.data
+        regs = [ptr + o for o in range(0, nbytes, span)] if pieces else [ptr]
+        for r in regs:
+            if rt.cudaHostRegister(ctypes.c_void_p(r), ctypes.c_size_t(span if pieces else nbytes),
+                                   ctypes.c_uint(1)) != 0:
+                raise SystemExit("cudaHostRegister failed")
+        return torch.from_numpy(arr), (mm, arr, regs)
+
+    def release(keep):
+        if keep is not None:
+            for r in keep[2]:
+                rt.cudaHostUnregister(ctypes.c_void_p(r))
+
+    forms = {"huge_pages_registered_whole": lambda: mapped(True, False),
+             "huge_pages_registered_in_4gib_pieces": lambda: mapped(True, True),
+             "base_pages_registered_whole": lambda: mapped(False, False),
+             "torch_pinned_allocator": lambda: (torch.empty(nbytes // 8, dtype=torch.int64, pin_memory=True),
+                                                None)}
+    out = {}
+    for name, make in forms.items():
+        t, keep = make()
+        r = {"at_allocation": copy_rate_slices(t, dev, span // 8)}
+        extra = [torch.empty((600, 4 * N), dtype=torch.int64).pin_memory() for _ in range(12)]
+        r["after_12_more_pinned_buffers"] = copy_rate_slices(t, dev, span // 8)
+        time.sleep(2)
+        r["2_s_later"] = copy_rate_slices(t, dev, span // 8)
+        out[name] = r
+        del extra
+        release(keep)
+        del t, keep
+        gc.collect()
+        torch.cuda.synchronize()
+    print(json.dumps({"workload": "hostmem", "gib": args.hostmem_gib, "slice_gib": 4,
+                      "unit": "GB/s host to device per slice", "forms": out}))
+    return 0
+
+
 def run_enroll(args):
     """Online enrollment (Alg 6): a resident gallery of 1,048,576 - 1,000
     entries at d = 64; the last block's 1,000 empty slots are filled one entry
@@ -1828,6 +1897,8 @@ def main():
         return run_topk(args)
     if args.workload == "enroll":
         return run_enroll(args)
+    if args.workload == "hostmem":
+        return run_hostmem(args)
     return run_gpu(args)
 
 
