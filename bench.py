@@ -969,19 +969,7 @@ def serving_section(ctx, keys, dev, local, rates, window, max_requests, batch_va
     slow_seen = set()   # slices measured slow at any point of this run
 
     def fast_ring(rates_s):
-        """A ring over the runs of slices at no less than half the best
-        slice's rate, now and at every earlier measurement (slow slices have
-        turned fast again and then slow within one run), that hold at least
-        one largest request."""
-        slow_seen.update(i for i, r in enumerate(rates_s) if r < 0.5 * max(rates_s))
-        segs, run0 = [], None
-        for i, r in enumerate(rates_s + [0.0]):
-            if i < len(rates_s) and i not in slow_seen:
-                run0 = i if run0 is None else run0
-            elif run0 is not None:
-                segs.append((run0 * per_slice, min(i * per_slice, arena_blocks)))
-                run0 = None
-        segs = [g for g in segs if g[1] - g[0] >= nblocks] or [(0, arena_blocks)]
+        segs = fast_segments(rates_s, slow_seen, per_slice, arena_blocks, nblocks)
         return SlotRing(segs), segs
 
     ring, segs = fast_ring(host_diag["arena_d2h_gbs_per_2gib_slice"])
@@ -1312,6 +1300,24 @@ def smaps_field(addr, field="AnonHugePages"):
     except (OSError, ValueError):
         pass
     return None
+
+
+def fast_segments(rates, slow_seen, per_slice, total, min_len):
+    """Runs of slices, as (first block, end block), whose copy rate is at no
+    less than half the best slice's rate in `rates` and that were never slow
+    before (slow_seen, updated here with the slices slow now: slow slices have
+    turned fast again and then slow within one run); only runs of at least
+    min_len blocks.  Slice i holds blocks [i per_slice, (i + 1) per_slice),
+    the last one cut at total.  With no such run, the whole buffer."""
+    slow_seen.update(i for i, r in enumerate(rates) if r < 0.5 * max(rates))
+    segs, run0 = [], None
+    for i in range(len(rates) + 1):
+        if i < len(rates) and i not in slow_seen:
+            run0 = i if run0 is None else run0
+        elif run0 is not None:
+            segs.append((run0 * per_slice, min(i * per_slice, total)))
+            run0 = None
+    return [g for g in segs if g[1] - g[0] >= min_len] or [(0, total)]
 
 
 class SlotRing:
