@@ -379,13 +379,13 @@ const char* hers_batch_variant_name(int v);
  * A scheduler thread admits queued requests in arrival order while their
  * device memory fits a pool carved out of free HBM at creation.  The pool is
  * workspace_bytes, or all free HBM minus 1 GiB when that is 0.  Each admitted
- * set of up to max_batch requests runs as one batch on one of two streams:
+ * set of up to max_batch requests runs as one batch on one of three streams:
  *  - probe copy-in and preparation;
  *  - the persistent batched tensor kernel, where overlapping block ranges of
  *    one gallery share each gallery read;
  *  - the epilogue;
  *  - copy-out of each request's score ciphertexts.
- * Batches on the two streams overlap on the device.  Requests arriving
+ * Batches on the three streams overlap on the device.  Requests arriving
  * meanwhile form the next batch as soon as a stream and memory free up.  Every
  * result equals hers_search's on the same range.
  *
@@ -424,7 +424,7 @@ int hers_server_stats(hers_server* srv, uint64_t* submitted, uint64_t* completed
 /* Where the server's time went, summed over its finished batches: device
  * time of each batch's kernels (probe preparation, tensor kernel, epilogue)
  * and of its score copies to host memory (CUDA events on the batch's stream;
- * batches on the two streams overlap, so the sums can exceed wall time), and
+ * batches on the three streams overlap, so the sums can exceed wall time), and
  * host time the scheduler spent planning and issuing batches.  Any pointer
  * may be NULL. */
 int hers_server_timing(hers_server* srv, double* kernels_ms, double* copies_ms, double* plan_ms);
