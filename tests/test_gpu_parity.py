@@ -178,7 +178,10 @@ def test_empty_inputs(ctx, keys):
 def test_config2_full_size(ctx, keys, oracle_keys):
     """1,048,576 entries (256 blocks), d = 64, one planted mate: every decrypted
     score exact; the score ciphertexts of the mate's block, the last block and
-    8 seeded random blocks bit-exact against the oracle."""
+    8 seeded random blocks bit-exact against the oracle.  Then the launch
+    configuration the bench times (the persistent Karatsuba tensor shape, the
+    lean epilogue, three searches in flight on three streams) gives the same
+    score ciphertexts for all 256 blocks."""
     m, d = 1 << 20, 64
     feats = W.gallery_features(m, d, FEAT_SEED)
     mate = int(W.mate_indices(m, 1, MATE_SEED)[0])
@@ -196,6 +199,28 @@ def test_config2_full_size(ctx, keys, oracle_keys):
         ogal = O.encrypt_gallery_block(oracle_keys[1], feats, b, GAL_SEED)
         osc, _ = O.search_block(oprb, ogal, oracle_keys[2])
         assert np.array_equal(sc[b], osc), f"block {b}"
+    # the bench's launch configuration
+    keep_t, keep_e = H.hers_get_tensor_variant(ctx), H.hers_get_epilogue_variant(ctx)
+    H.hers_set_tensor_variant(ctx, H.hers_tensor_variants().index("pnb2_s3_d4_k2_m4_ka"))
+    H.hers_set_epilogue_variant(ctx, H.hers_epilogue_variants().index("split+lean"))
+    try:
+        nb = res["nb"]
+        lanes = [(H.hers_probe_prepare(ctx, res["pct"]),
+                  torch.empty(H.hers_search_workspace_bytes(nb) // 8, dtype=torch.int64, device="cuda"),
+                  torch.empty((nb, 2, 2, H.N), dtype=torch.int64, device="cuda"), torch.cuda.Stream())
+                 for _ in range(3)]
+        torch.cuda.synchronize()
+        for k in range(6):
+            p_, w_, o_, st_ = lanes[k % 3]
+            H.hers_probe_prepare(ctx, res["pct"], out=p_, stream=st_)
+            H.hers_search(ctx, keys, res["gal"], nb, d, p_, out=o_, workspace=w_, stream=st_)
+        torch.cuda.synchronize()
+        H.hers_check(ctx)
+        for i, (_, _, o_, _) in enumerate(lanes):
+            assert np.array_equal(u64(o_), sc), f"lane {i}"
+    finally:
+        H.hers_set_tensor_variant(ctx, keep_t)
+        H.hers_set_epilogue_variant(ctx, keep_e)
 
 
 def test_inline_temporaries_on_default_stream(ctx, keys):
