@@ -1664,9 +1664,7 @@ def run_sweep(args):
         gbs = alg / (phases["tensor"] / 1e3) / 1e9
         out_points.append({"m": m, "d": d, "blocks": nb, "ms_per_step": ms, "entries_per_s": m / (ms / 1e3),
                            "phases_ms": {k: round(v, 4) for k, v in phases.items()},
-            "phases_note": "per-phase CUDA-event times of the timed searches, each on its own stream; "
-                           "with two searches in flight a phase's time includes the other search's "
-                           "kernels running beside it",
+                           "phases_note": "per-phase CUDA-event times of the timed searches, run one at a time",
                            "variant": H.hers_tensor_variants()[variant],
                            "tensor_gbs": gbs, "tensor_frac": gbs / peak,
                            "exact": exact, "top1": top1})
